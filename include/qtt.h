@@ -1,0 +1,189 @@
+/*
+ * qtt.h -- C ABI of the GB300 QTT denoising-convolution library (libqtt.so).
+ *
+ * The library computes, on one GPU, the hot path of "Denoising Convolution
+ * Algorithms and Applications to SAR Signal Processing" (arXiv 2301.13339):
+ *
+ *   noisy samples on a 2^d (1D) or 2^dy x 2^dx (2D) grid
+ *     -> QTT reshape (Sec. 4)
+ *     -> TT-SVD with the max-rank modification (Alg. 1, Sec. 5 (1)):
+ *        the rank truncation is the denoiser (Sec. 6)
+ *     -> convolution with the sinc imaging kernel (Eq. GAF, Eq. sinc_kern1/2)
+ *        as a QTT Toeplitz operator applied core by core, then TT-rounding
+ *     -> Full (Alg. 3) back to the dense array.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Dense arrays are caller-owned DEVICE memory, contiguous; a 2D image is
+ *   row-major F[y][x] (x fast).  Sizes are powers of two given as log2.
+ * - QTT tensors (qtt_tensor) and operators (qtt_op) are library-owned handles
+ *   living in device memory; free them with qtt_free / qtt_op_free.
+ * - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on that stream unless stated otherwise; TT ranks
+ *   stay on the device, so the decompose -> convolve -> full chain never
+ *   waits for the host.  qtt_get_ranks / qtt_get_cores / qtt_op_create
+ *   synchronise the stream.
+ * - Element types: QTT_F64 (real double, FP64 arithmetic throughout) and
+ *   QTT_C64 (complex float = interleaved re,im float pairs, FP32
+ *   arithmetic with FP64 only in the reductions that feed rank decisions).
+ * - Errors: every call returns a qtt_status; qtt_last_error() gives a
+ *   thread-local message.  Errors detected on the device (an iteration limit
+ *   reached, a rank above its capacity) are recorded in a device status word
+ *   of the handle and returned by the next qtt_get_ranks.  No call aborts the
+ *   process or traps the device.
+ * - The library allocates its own device workspace (grow-only, reused); it is
+ *   released by qtt_release_workspace().
+ */
+#ifndef QTT_H_
+#define QTT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QTT_OK = 0,
+  QTT_EINVAL = -1,        /* bad argument (sizes not powers of two, NULL ...) */
+  QTT_ENOMEM = -2,        /* device allocation failed                          */
+  QTT_ECUDA = -3,         /* a CUDA runtime call failed                        */
+  QTT_ETIMEOUT = -4,      /* a device iteration limit was reached              */
+  QTT_ERANK = -5,         /* a rank exceeded its capacity                      */
+  QTT_EUNSUPPORTED = -6   /* valid request this build does not implement       */
+} qtt_status;
+
+typedef enum { QTT_F64 = 0, QTT_C64 = 2 } qtt_dtype;
+
+/* Truncation parameters of one TT-SVD or rounding sweep.
+ *   eps    relative accuracy; per-cut threshold tau = eps/sqrt(d-1)*||A||_F,
+ *          rank = smallest r with sqrt(sum_{i>r} sigma_i^2) <= tau
+ *          (Sec. 4 eps-rank, Alg. 1).  eps = 0: cap only.
+ *   rmax   rank cap R_max (Sec. 5 modification (1)); <= 0: no cap beyond the
+ *          library's capacity QTT_RANK_CAP.
+ *   refine 1: second Gram pass on the projected unfolding before the rank
+ *          decision (relative accuracy of small singular values); 0: single
+ *          pass.  FP64 calls always refine. */
+typedef struct {
+  double eps;
+  int rmax;
+  int refine;
+} qtt_trunc;
+
+/* Largest TT rank any handle can hold (capacity of the per-cut Jacobi). */
+#define QTT_RANK_CAP 64
+
+typedef struct qtt_tensor qtt_tensor;
+typedef struct qtt_op qtt_op;
+
+/* qtt_decompose -- Alg. 2 steps 1-2: QTT reshape + TT-SVD (Alg. 1) with the
+ * max-rank modification (Sec. 5 (1)).
+ *   x           device array, 2^d elements of dt (1D) or 2^dy x 2^dx (2D,
+ *               row-major).  Not modified.
+ *   ndim        1 or 2;  log2_shape = {d} or {dy, dx}.
+ *   interleave  2D only: 1 = bit-interleaved QTT modes x1,y1,x2,y2,...
+ *               0 = x bits then y bits.
+ *   tr          truncation (eps, rmax, refine).
+ *   out         receives a new handle (caller frees with qtt_free).
+ * Asynchronous; ranks stay on the device.  QTT_EINVAL on bad sizes or
+ * d < 2 or d > 30. */
+qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_shape,
+                         int interleave, const qtt_trunc* tr, void* stream,
+                         qtt_tensor** out);
+
+/* qtt_conv_sinc -- Alg. 2 step 3 with the convolution done by the QTT
+ * Toeplitz operator of the sinc kernel (Sec. 1 [KKT13]; kernel Eq. GAF with
+ * Delta_x = 1/B on the midpoint grid of [0,1]^D, h = 2^-d per axis), then
+ * TT-rounding.  2D: the x operator then the y operator, each followed by a
+ * rounding.
+ *   B          ndim bandwidths (B_x, B_y order for 2D).
+ *   normalize  1: kernel divided by its midpoint-rule integral (Eq.
+ *              sinc_kern1/2), 0: A = 1.
+ *   eps_op     accuracy of the operator's generating vector QTT.
+ *   round_tr   truncation of the rounding (eps_round, R_round cap, refine).
+ *   sketch     rank of the random sketch used by the rounding (>= the
+ *              rounded rank + oversampling; <= QTT_RANK_CAP).  <= 0: default.
+ *   seed       seed of the sketch's counter-based generator.
+ * Operators are built on first use and cached per (n, B, normalize, eps_op,
+ * dtype); building synchronises the stream once.  out: new handle. */
+qtt_status qtt_conv_sinc(const qtt_tensor* f, const double* B, int normalize, double eps_op,
+                         const qtt_trunc* round_tr, int sketch, unsigned long long seed,
+                         void* stream, qtt_tensor** out);
+
+/* qtt_round -- TT-rounding of t in place (randomized sketch of rank
+ * `sketch`, right orthogonalisation, left-to-right truncated SVD sweep with
+ * the thresholds of tr). */
+qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned long long seed,
+                     void* stream);
+
+/* qtt_to_full -- Alg. 2 step 4 / Alg. 3 (Full): expand t into the caller's
+ * device array y (same element type and shape as the decomposed input, 2D
+ * written back in row-major array order).  Asynchronous. */
+qtt_status qtt_to_full(const qtt_tensor* t, void* y, void* stream);
+
+/* qtt_conv_adjoint -- adjoint of qtt_conv_sinc's operator applied to r in
+ * QTT (for the real even sinc kernel T^H = T: correlation with the flipped
+ * kernel), rounded with round_tr.  If grad_cores is not NULL it must hold
+ * d device pointers; core k receives dL/dconj(F_k) of
+ * L(F) = ||full(T F) - g||^2 where r = full(T F) - g is given in QTT:
+ * the contraction of w = 2 T^H r with the left/right partial products of
+ * f's cores (environment sweeps).  adj_out (may be NULL) receives T^H r. */
+qtt_status qtt_conv_adjoint(const qtt_tensor* f, const qtt_tensor* r, const double* B,
+                            int normalize, double eps_op, const qtt_trunc* round_tr,
+                            int sketch, unsigned long long seed, void* const* grad_cores,
+                            qtt_tensor** adj_out, void* stream);
+
+/* Handle inspection and construction (tests, checkpoints). */
+/* ranks_host: d+1 ints r_0..r_d.  Synchronises; returns the device status. */
+qtt_status qtt_get_ranks(const qtt_tensor* t, int* ranks_host, void* stream);
+/* d, element type, ndim and log2 shape of a handle (host-side, no sync). */
+qtt_status qtt_get_info(const qtt_tensor* t, int* d, qtt_dtype* dt, int* ndim,
+                        int* log2_shape, int* interleave);
+/* Copy the cores to host memory, packed core after core, each core
+ * r_{k-1} x 2 x r_k column-major (alpha fastest, then i_k, then beta).
+ * host_buf must hold sum_k 2 r_{k-1} r_k elements.  Synchronises. */
+qtt_status qtt_get_cores(const qtt_tensor* t, void* host_buf, void* stream);
+/* Build a handle from host cores in the packed layout above (ranks given
+ * as d+1 ints with r_0 = r_d = 1, each <= QTT_RANK_CAP). */
+qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_dtype dt,
+                          int ndim, const int* log2_shape, int interleave, void* stream,
+                          qtt_tensor** out);
+/* Release a handle.  qtt_free synchronises the device; qtt_free_async
+ * releases the storage in stream order (the stream must be the one the
+ * handle was last used on). */
+void qtt_free(qtt_tensor* t);
+void qtt_free_async(qtt_tensor* t, void* stream);
+
+/* Operator plan of the 1D sinc Toeplitz operator on 2^d points (Sec. 1
+ * [KKT13], Eq. GAF / sinc_kern1): generating vector chat[t] = c(t - 2^d)
+ * (chat[0] = 0), its QTT by TT-SVD at eps_op, and operator cores
+ * O_k[(b,alpha), j, i, (b',beta)] from the borrow chain of j - i.
+ * Synchronises the stream (plan-time). */
+qtt_status qtt_op_create(int d, double B, int normalize, double eps_op, qtt_dtype dt,
+                         void* stream, qtt_op** out);
+/* Operator ranks P_0..P_d (d+1 ints) on the host. */
+qtt_status qtt_op_get_ranks(const qtt_op* op, int* ranks_host);
+/* Operator cores to host, packed, each P_{k-1} x 2 (j) x 2 (i) x P_k
+ * column-major (p fastest, then j, then i, then q), element type real
+ * double for QTT_F64 operators and real float for QTT_C64 operators. */
+qtt_status qtt_op_get_cores(const qtt_op* op, void* host_buf);
+void qtt_op_free(qtt_op* op);
+
+/* Operator x vector without rounding (tests): out has ranks P_k r_k, each
+ * at most QTT_PRODUCT_CAP; QTT_EINVAL otherwise. */
+#define QTT_PRODUCT_CAP 4096
+qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_tensor** out);
+
+/* Release the library's cached workspace and operator plans. */
+void qtt_release_workspace(void);
+
+/* Thread-local description of the last error ("" if none). */
+const char* qtt_last_error(void);
+
+/* Version string. */
+const char* qtt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTT_H_ */

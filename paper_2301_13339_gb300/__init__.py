@@ -1,0 +1,327 @@
+"""GB300 QTT denoising convolution (arXiv 2301.13339) -- Python binding.
+
+Thin ctypes marshalling over ``libqtt.so`` (the C ABI in ``include/qtt.h``):
+every step of the computation runs in the library's CUDA kernels.  PyTorch
+provides device memory and streams only.  If the compiled library is missing
+the import fails; there is no CPU fallback.
+
+The functions carry the names of the C entry points:
+``qtt_decompose``, ``qtt_conv_sinc``, ``qtt_round``, ``qtt_to_full``,
+``qtt_conv_adjoint``, ``qtt_matvec``, ``qtt_op_create`` ...
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "QTTError", "QTTTensor", "QTTOperator", "lib", "load", "qtt_decompose", "qtt_conv_sinc",
+    "qtt_round", "qtt_to_full", "qtt_conv_adjoint", "qtt_matvec", "qtt_op_create",
+    "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
+]
+
+QTT_F64 = 0
+QTT_C64 = 2
+QTT_RANK_CAP = 64
+
+_STATUS = {0: "QTT_OK", -1: "QTT_EINVAL", -2: "QTT_ENOMEM", -3: "QTT_ECUDA",
+           -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED"}
+
+EXPORTED_SYMBOLS = [
+    "qtt_decompose", "qtt_conv_sinc", "qtt_round", "qtt_to_full", "qtt_conv_adjoint",
+    "qtt_get_ranks", "qtt_get_info", "qtt_get_cores", "qtt_from_cores", "qtt_free",
+    "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
+    "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version",
+]
+
+
+class QTTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Trunc(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libqtt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libqtt.so not found at {path}: run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    L = ctypes.CDLL(path)
+    vp, i, d, ull = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong
+    ip = ctypes.POINTER(ctypes.c_int)
+    dp = ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    tp = ctypes.POINTER(_Trunc)
+    sig = {
+        "qtt_decompose": (i, [vp, i, i, ip, i, tp, vp, pp]),
+        "qtt_conv_sinc": (i, [vp, dp, i, d, tp, i, ull, vp, pp]),
+        "qtt_round": (i, [vp, tp, i, ull, vp]),
+        "qtt_to_full": (i, [vp, vp, vp]),
+        "qtt_conv_adjoint": (i, [vp, vp, dp, i, d, tp, i, ull, pp, pp, vp]),
+        "qtt_get_ranks": (i, [vp, ip, vp]),
+        "qtt_get_info": (i, [vp, ip, ip, ip, ip, ip]),
+        "qtt_get_cores": (i, [vp, vp, vp]),
+        "qtt_from_cores": (i, [vp, ip, i, i, i, ip, i, vp, pp]),
+        "qtt_free": (None, [vp]),
+        "qtt_free_async": (None, [vp, vp]),
+        "qtt_op_create": (i, [i, d, i, d, i, vp, pp]),
+        "qtt_op_get_ranks": (i, [vp, ip]),
+        "qtt_op_get_cores": (i, [vp, vp]),
+        "qtt_op_free": (None, [vp]),
+        "qtt_matvec": (i, [vp, vp, vp, pp]),
+        "qtt_release_workspace": (None, []),
+        "qtt_last_error": (ctypes.c_char_p, []),
+        "qtt_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def lib():
+    return load()
+
+
+def _check(st):
+    if st != 0:
+        raise QTTError(st, _lib.qtt_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return QTT_F64
+    if t.dtype == torch.complex64:
+        return QTT_C64
+    raise TypeError(f"unsupported dtype {t.dtype}: use torch.float64 or torch.complex64")
+
+
+def _np_dtype(code):
+    return np.float64 if code == QTT_F64 else np.complex64
+
+
+class QTTTensor:
+    """Library-owned QTT tensor (device cores, device ranks)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle) if not isinstance(handle, ctypes.c_void_p) else handle
+        d = ctypes.c_int()
+        dt = ctypes.c_int()
+        nd = ctypes.c_int()
+        sh = (ctypes.c_int * 2)()
+        il = ctypes.c_int()
+        _check(_lib.qtt_get_info(self._h, ctypes.byref(d), ctypes.byref(dt), ctypes.byref(nd), sh,
+                                 ctypes.byref(il)))
+        self.d = d.value
+        self.dtype_code = dt.value
+        self.ndim = nd.value
+        self.log2_shape = tuple(sh[k] for k in range(self.ndim))
+        self.interleave = il.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def shape(self):
+        return tuple(1 << s for s in self.log2_shape)
+
+    def ranks(self, stream=None):
+        r = (ctypes.c_int * (self.d + 1))()
+        _check(_lib.qtt_get_ranks(self._h, r, _stream(stream)))
+        return [r[k] for k in range(self.d + 1)]
+
+    def cores(self, stream=None):
+        """Cores as numpy arrays of shape (r_{k-1}, 2, r_k) (host copies)."""
+        r = self.ranks(stream)
+        n = sum(r[k] * 2 * r[k + 1] for k in range(self.d))
+        buf = np.empty(n, dtype=_np_dtype(self.dtype_code))
+        _check(_lib.qtt_get_cores(self._h, buf.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        out, o = [], 0
+        for k in range(self.d):
+            c = r[k] * 2 * r[k + 1]
+            out.append(buf[o:o + c].reshape((r[k], 2, r[k + 1]), order="F").copy())
+            o += c
+        return out
+
+    def free(self, stream=None):
+        if self._h is not None and self._h.value:
+            if stream is None:
+                _lib.qtt_free(self._h)
+            else:
+                _lib.qtt_free_async(self._h, _stream(stream))
+        self._h = None
+
+    def __del__(self):
+        try:
+            if _lib is not None and self._h is not None and self._h.value:
+                _lib.qtt_free(self._h)
+        except Exception:
+            pass
+
+
+class QTTOperator:
+    def __init__(self, handle, d, dtype_code):
+        self._h = handle
+        self.d = d
+        self.dtype_code = dtype_code
+
+    def ranks(self):
+        r = (ctypes.c_int * (self.d + 1))()
+        _check(_lib.qtt_op_get_ranks(self._h, r))
+        return [r[k] for k in range(self.d + 1)]
+
+    def cores(self):
+        """Cores as numpy arrays O[p, j, i, q] of shape (P_{k-1}, 2, 2, P_k)."""
+        P = self.ranks()
+        n = sum(P[k] * 4 * P[k + 1] for k in range(self.d))
+        buf = np.empty(n, dtype=np.float64 if self.dtype_code == QTT_F64 else np.float32)
+        _check(_lib.qtt_op_get_cores(self._h, buf.ctypes.data_as(ctypes.c_void_p)))
+        out, o = [], 0
+        for k in range(self.d):
+            c = P[k] * 4 * P[k + 1]
+            out.append(buf[o:o + c].reshape((P[k], 2, 2, P[k + 1]), order="F").copy())
+            o += c
+        return out
+
+    def __del__(self):
+        try:
+            if _lib is not None and self._h is not None and self._h.value:
+                _lib.qtt_op_free(self._h)
+        except Exception:
+            pass
+
+
+def _trunc(eps, rmax, refine):
+    return _Trunc(float(eps), int(rmax or 0), int(bool(refine)))
+
+
+def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None):
+    """QTT reshape + TT-SVD (Alg. 1 with the max-rank cap of Sec. 5) of a
+    contiguous CUDA tensor (1D length 2^d, or 2D 2^dy x 2^dx row-major)."""
+    load()
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    code = _dtype_code(x)
+    shape = []
+    for n in x.shape:
+        ln = int(n).bit_length() - 1
+        if n < 2 or (1 << ln) != n:
+            raise ValueError(f"sizes must be powers of two >= 2, got {tuple(x.shape)}")
+        shape.append(ln)
+    sh = (ctypes.c_int * 2)(*(shape + [0] * (2 - len(shape))))
+    tr = _trunc(eps, rmax, refine)
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_decompose(ctypes.c_void_p(x.data_ptr()), code, x.dim(), sh, int(interleave),
+                              ctypes.byref(tr), _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_conv_sinc(f, B, normalize=True, eps_op=1e-7, eps_round=1e-7, rround=0, refine=True,
+                  sketch=0, seed=20230131, stream=None):
+    """QTT Toeplitz convolution with the sinc kernel + TT-rounding."""
+    load()
+    Bs = [float(B)] * f.ndim if np.isscalar(B) else [float(b) for b in B]
+    Barr = (ctypes.c_double * 2)(*(Bs + [0.0] * (2 - len(Bs))))
+    tr = _trunc(eps_round, rround, refine)
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_conv_sinc(f.handle, Barr, int(bool(normalize)), float(eps_op),
+                              ctypes.byref(tr), int(sketch), int(seed), _stream(stream),
+                              ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_round(t, eps, rmax=0, refine=True, sketch=0, seed=20230131, stream=None):
+    load()
+    tr = _trunc(eps, rmax, refine)
+    _check(_lib.qtt_round(t.handle, ctypes.byref(tr), int(sketch), int(seed), _stream(stream)))
+    return t
+
+
+def qtt_to_full(t, out=None, stream=None):
+    """Full (Alg. 3) into a new (or the given) CUDA tensor of the input's shape."""
+    import torch
+    load()
+    dt = torch.float64 if t.dtype_code == QTT_F64 else torch.complex64
+    if out is None:
+        out = torch.empty(t.shape, dtype=dt, device="cuda")
+    if out.dtype != dt or tuple(out.shape) != t.shape or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype/shape or is not contiguous")
+    _check(_lib.qtt_to_full(t.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def qtt_conv_adjoint(f, r, B, normalize=True, eps_op=1e-7, eps_round=1e-7, rround=0,
+                     refine=True, sketch=0, seed=20230131, grad_cores=None, stream=None):
+    load()
+    Bs = [float(B)] * f.ndim if np.isscalar(B) else [float(b) for b in B]
+    Barr = (ctypes.c_double * 2)(*(Bs + [0.0] * (2 - len(Bs))))
+    tr = _trunc(eps_round, rround, refine)
+    adj = ctypes.c_void_p()
+    gp = None
+    if grad_cores is not None:
+        gp = (ctypes.c_void_p * len(grad_cores))(*[g.data_ptr() for g in grad_cores])
+    _check(_lib.qtt_conv_adjoint(f.handle, r.handle, Barr, int(bool(normalize)), float(eps_op),
+                                 ctypes.byref(tr), int(sketch), int(seed), gp, ctypes.byref(adj),
+                                 _stream(stream)))
+    return QTTTensor(adj) if adj.value else None
+
+
+def qtt_op_create(d, B, normalize=True, eps_op=1e-7, dtype_code=QTT_C64, stream=None):
+    load()
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_op_create(int(d), float(B), int(bool(normalize)), float(eps_op),
+                              int(dtype_code), _stream(stream), ctypes.byref(out)))
+    return QTTOperator(out, int(d), int(dtype_code))
+
+
+def qtt_matvec(op, t, stream=None):
+    load()
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_matvec(op._h, t.handle, _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):
+    """Handle from host cores (numpy arrays (r_{k-1}, 2, r_k))."""
+    load()
+    d = len(cores)
+    code = QTT_F64 if cores[0].dtype == np.float64 else QTT_C64
+    nd = _np_dtype(code)
+    ranks = [1] + [int(c.shape[2]) for c in cores]
+    buf = np.concatenate([np.asarray(c, dtype=nd).reshape(-1, order="F") for c in cores])
+    buf = np.ascontiguousarray(buf)
+    r = (ctypes.c_int * (d + 1))(*ranks)
+    sh = (ctypes.c_int * 2)(*(list(shape_log2) + [0] * (2 - len(shape_log2))))
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_from_cores(buf.ctypes.data_as(ctypes.c_void_p), r, d, code, len(shape_log2),
+                               sh, int(interleave), _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def version():
+    load()
+    return _lib.qtt_version().decode()

@@ -1,0 +1,482 @@
+// TT-rounding of the operator x vector product Y = O X (the convolution step
+// of Alg. 2 done with the QTT Toeplitz operator), without forming Y.
+//
+// Y_k[(a + r_{k-1} p), j, (b + r_k q)] = sum_i O_k[p, j, i, q] X_k[a, i, b]
+// has ranks R_k = P_k r_k (about 16 x 64).  Textbook rounding (QR sweep, then
+// truncated-SVD sweep) would factor R_k x 2 R_k matrices.  Instead:
+//   1. left sketch   WL_k = Omega_{<=k}^T Y_{<=k}  (l_k x R_k) for a Gaussian
+//                    TT Omega of ranks l_k (counter-based Philox4x32-10
+//                    generator, Salmon et al. 2011), computed core by core
+//                    through the factors O_k and X_k;
+//   2. right-to-left Z = Y_k C_k (R_{k-1} x 2 l'_k); an orthonormal basis
+//                    V of the row space of the sketch WL_{k-1} Z becomes the
+//                    right-orthonormal core Q_k = V^H, C_{k-1} = Z V
+//                    (randomised range finder per cut: the TT is now right-
+//                    orthonormal with ranks l' <= sketch);
+//   3. left-to-right truncated SVD sweep on that TT with the threshold rule
+//                    of Alg. 1 (tau = eps/sqrt(d-1) ||Y||) and the rank cap:
+//                    the deterministic rounding step.
+// All factorisations are Gram + Jacobi (+ refinement) on <= 128 x 128.
+#include "qtt_internal.cuh"
+#include <algorithm>
+
+namespace qtt {
+
+// launch helpers implemented in k_svd.cu
+template <typename T>
+void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, int mg_const,
+                      int mg_cap, int mode, double eps, int dmodes, int rmax,
+                      const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
+                      T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
+                      int write_norm2, int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- Philox
+__host__ __device__ inline void philox_round(uint32_t c[4], const uint32_t k[2]) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  uint32_t n1 = lo1;
+  uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  uint32_t n3 = lo0;
+  c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  uint32_t k[2] = {k0, k1};
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c, k);
+    k[0] += 0x9E3779B9u;
+    k[1] += 0xBB67AE85u;
+  }
+}
+
+// out[e] ~ N(0, 1), e < n; counter = (e, core, 0, 0), key = seed.
+template <typename R>
+__global__ void gauss_fill_kernel(R* out, long long n, unsigned long long seed, uint32_t core) {
+  const long long e2 = ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (2 * e2 >= n) return;
+  uint32_t c[4] = {(uint32_t)e2, (uint32_t)(e2 >> 32), core, 0x51ca7u};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = ((double)c[0] + 0.5) * 2.3283064365386963e-10;
+  const double u2 = ((double)c[1] + 0.5) * 2.3283064365386963e-10;
+  const double rad = sqrt(-2.0 * log(u1));
+  out[2 * e2] = (R)(rad * cospi(2.0 * u2));
+  if (2 * e2 + 1 < n) out[2 * e2 + 1] = (R)(rad * sinpi(2.0 * u2));
+}
+
+#define GRID1(n) (unsigned)(((n) + 255) / 256), 256, 0, s
+
+// ---------------------------------------------------------------- step 1
+// A1[s + lk (j + 2 c)] = sum_{s'} Om[s' + l0 (j + 2 s)] WL0[s' + l0 c],  c < R0
+template <typename T, typename R>
+__global__ void k_a1(const R* Om, int l0, int lk, const T* WL0, const int* xr, int k, int Pin,
+                     int Rc0, T* A1) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int R0 = Pin * xr[k - 1];
+  if (e >= (long long)lk * 2 * Rc0) return;
+  const int s = (int)(e % lk), j = (int)((e / lk) % 2), c = (int)(e / (2LL * lk));
+  if (c >= R0) return;
+  typename KAccOf<T>::type acc;
+  for (int sp = 0; sp < l0; ++sp) acc.add_rmul(Om[sp + l0 * (j + 2 * s)], WL0[sp + (size_t)l0 * c]);
+  A1[s + (size_t)lk * (j + 2 * c)] = acc.get();
+}
+// A2[s + lk (j + 2 (p + Pin (i + 2 b)))] = sum_a A1[s + lk (j + 2 (a + r0 p))] X[a + r0 (i + 2 b)]
+template <typename T>
+__global__ void k_a2(const T* A1, int lk, const T* X, const int* xr, int k, int Pin, int rcap1,
+                     T* A2) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = xr[k - 1], r1 = xr[k];
+  if (e >= (long long)lk * 2 * Pin * 2 * rcap1) return;
+  const int s = (int)(e % lk);
+  long long t = e / lk;
+  const int j = (int)(t % 2); t /= 2;
+  const int p = (int)(t % Pin); t /= Pin;
+  const int i = (int)(t % 2); t /= 2;
+  const int b = (int)t;
+  if (b >= r1) return;
+  typename KAccOf<T>::type acc;
+  for (int a = 0; a < r0; ++a)
+    acc.add_mul(A1[s + (size_t)lk * (j + 2 * (a + r0 * p))], X[a + (size_t)r0 * (i + 2 * b)]);
+  A2[s + (size_t)lk * (j + 2 * (p + Pin * (i + 2 * b)))] = acc.get();
+}
+// WL1[s + lk (b + r1 q)] = sum_{j,p,i} O[p + Pin (j + 2 (i + 2 q))] A2[s + lk (j + 2 (p + Pin (i + 2 b)))]
+template <typename T, typename R>
+__global__ void k_wl(const R* O, int Pin, int Pout, const T* A2, int lk, const int* xr, int k,
+                     int Rc1, T* WL1) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r1 = xr[k];
+  if (e >= (long long)lk * Rc1) return;
+  const int s = (int)(e % lk), c = (int)(e / lk);
+  if (c >= Pout * r1) return;
+  const int b = c % r1, q = c / r1;
+  typename KAccOf<T>::type acc;
+  for (int i = 0; i < 2; ++i)
+    for (int p = 0; p < Pin; ++p)
+      for (int j = 0; j < 2; ++j) {
+        const R o = O[p + Pin * (j + 2 * (i + 2 * q))];
+        if (o != (R)0) acc.add_rmul(o, A2[s + (size_t)lk * (j + 2 * (p + Pin * (i + 2 * b)))]);
+      }
+  WL1[s + (size_t)lk * c] = acc.get();
+}
+
+// In-place scaling of a sketch block to unit max-abs entry (one CTA).  The
+// sketch of Y_{<=k} grows like (sqrt(l) ||Y_k||)^k; any scaling of a sketch
+// leaves its row space unchanged, so each WL_k is rescaled as it is formed.
+template <typename T>
+__global__ void k_normalize(T* A, long long n) {
+  __shared__ float red[32];
+  float mx = 0.f;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) mx = fmaxf(mx, sqrtf((float)sabs2(A[e])));
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float m = red[0];
+  if (!(m > 0.f) || !(m < 3.0e38f)) return;
+  const typename Sc<T>::R sc = (typename Sc<T>::R)(1.0 / (double)m);
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) A[e] = rscale(A[e], sc);
+}
+
+// ---------------------------------------------------------------- step 2
+// B1[a + r0 (i + 2 (q + Pout t))] = sum_b X[a + r0 (i + 2 b)] C[(b + r1 q) + ldc t]
+template <typename T>
+__global__ void k_b1(const T* X, const int* xr, int k, int rcap0, int Pout, const T* C, int ldc,
+                     int lq, int d, T* B1) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = xr[k - 1], r1 = xr[k];
+  if (e >= (long long)rcap0 * 2 * Pout * lq) return;
+  const int a = (int)(e % rcap0);
+  long long t = e / rcap0;
+  const int i = (int)(t % 2); t /= 2;
+  const int q = (int)(t % Pout); t /= Pout;
+  const int tt = (int)t;
+  if (a >= r0) return;
+  typename KAccOf<T>::type acc;
+  for (int b = 0; b < r1; ++b)
+    acc.add_mul(X[a + (size_t)r0 * (i + 2 * b)], C[(b + r1 * q) + (size_t)ldc * tt]);
+  B1[a + (size_t)r0 * (i + 2 * (q + Pout * tt))] = acc.get();
+}
+// Z[(a + r0 p) + ldz (j + 2 t)] = sum_{q,i} O[p + Pin (j + 2 (i + 2 q))] B1[a + r0 (i + 2 (q + Pout t))]
+template <typename T, typename R>
+__global__ void k_z(const R* O, int Pin, int Pout, const T* B1, const int* xr, int k, int rcap0,
+                    int lq, int ldz, T* Z) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = xr[k - 1];
+  if (e >= (long long)rcap0 * Pin * 2 * lq) return;
+  const int a = (int)(e % rcap0);
+  long long t = e / rcap0;
+  const int p = (int)(t % Pin); t /= Pin;
+  const int j = (int)(t % 2); t /= 2;
+  const int tt = (int)t;
+  if (a >= r0) return;
+  typename KAccOf<T>::type acc;
+  for (int q = 0; q < Pout; ++q)
+    for (int i = 0; i < 2; ++i) {
+      const R o = O[p + Pin * (j + 2 * (i + 2 * q))];
+      if (o != (R)0) acc.add_rmul(o, B1[a + (size_t)r0 * (i + 2 * (q + Pout * tt))]);
+    }
+  Z[(a + r0 * p) + (size_t)ldz * (j + 2 * tt)] = acc.get();
+}
+// S[s + l0 u] = sum_{c < R0} WL[s + l0 c] Z[c + ldz u]
+template <typename T>
+__global__ void k_s(const T* WL, int l0, const T* Z, int ldz, const int* xr, int k, int Pin,
+                    int ncolu, T* S) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)l0 * ncolu) return;
+  const int R0 = Pin * xr[k - 1];
+  const int s = (int)(e % l0), u = (int)(e / l0);
+  typename KAccOf<T>::type acc;
+  for (int c = 0; c < R0; ++c) acc.add_mul(WL[s + (size_t)l0 * c], Z[c + (size_t)ldz * u]);
+  S[e] = acc.get();
+}
+// column Gram  G[u + ldg v] = sum_s conj(S[s + ls u]) S[s + ls v],  u, v < n (rows ls)
+template <typename T>
+__global__ void k_gram_cols(const T* S, int ls, int n, double2* G, int ldg) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int u = e % n, v = e / n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s2 = 0; s2 < ls; ++s2) {
+    const double2 a = to_d2(S[s2 + (size_t)ls * u]), b = to_d2(S[s2 + (size_t)ls * v]);
+    acc.x += a.x * b.x + a.y * b.y;     // conj(a) b
+    acc.y += a.x * b.y - a.y * b.x;
+  }
+  G[u + (size_t)ldg * v] = acc;
+}
+// SV[s + ls w] = sum_u S[s + ls u] V[u + n w]
+template <typename T>
+__global__ void k_sv(const T* S, int ls, int n, const T* V, T* SV) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ls * n) return;
+  const int s2 = e % ls, w = e / ls;
+  typename KAccOf<T>::type acc;
+  for (int u = 0; u < n; ++u) acc.add_mul(S[s2 + (size_t)ls * u], V[u + (size_t)n * w]);
+  SV[e] = acc.get();
+}
+// Q[s + lq0 (j + 2 t)] = conj(V[(j + 2 t) + n s]),  n = 2 lq
+template <typename T>
+__global__ void k_qcore(const T* V, int n, int lq0, T* Q) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= lq0 * n) return;
+  const int s2 = e % lq0, u = e / lq0;
+  Q[e] = conjg(V[u + (size_t)n * s2]);
+}
+// Cn[c + ldc s] = sum_u Z[c + ldz u] V[u + n s],  c < R0
+template <typename T>
+__global__ void k_c(const T* Z, int ldz, const T* V, int n, int lq0, const int* xr, int k, int Pin,
+                    int ldc, T* Cn) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)ldc * lq0) return;
+  const int c = (int)(e % ldc), s2 = (int)(e / ldc);
+  if (c >= Pin * xr[k - 1]) return;
+  typename KAccOf<T>::type acc;
+  for (int u = 0; u < n; ++u) acc.add_mul(Z[c + (size_t)ldz * u], V[u + (size_t)n * s2]);
+  Cn[c + (size_t)ldc * s2] = acc.get();
+}
+
+// ---------------------------------------------------------------- step 3
+// Zt[(s + t0 j) + m u] = sum_{s' < lq0} Lc[s + t0 s'] Tp[s' + lq0 (j + 2 u)],  m = 2 t0
+template <typename T>
+__global__ void k_zt(const T* Lc, const int* tr, int k, int tcap0, const T* Tp, int lq0, int lq,
+                     T* Zt) {
+  const int t0 = tr[k - 1];
+  const int m = 2 * t0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * tcap0 * lq) return;
+  const int row = e % (2 * tcap0), u = e / (2 * tcap0);
+  if (row >= m) return;
+  const int s2 = row % t0, j = row / t0;
+  typename KAccOf<T>::type acc;
+  for (int sp = 0; sp < lq0; ++sp) acc.add_mul(Lc[s2 + (size_t)t0 * sp], Tp[sp + (size_t)lq0 * (j + 2 * u)]);
+  Zt[row + (size_t)m * u] = acc.get();
+}
+// row Gram  G[a + ldg b] = sum_u Z[a + m u] conj(Z[b + m u]),  m = mul * *mptr
+template <typename T>
+__global__ void k_gram_rows(const T* Zt, const int* mptr, int mul, int mcap, int ncol, double2* G,
+                            int ldg) {
+  const int m = mul * (*mptr);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mcap * mcap) return;
+  const int a = e % mcap, b = e / mcap;
+  if (a >= m || b >= m) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int u = 0; u < ncol; ++u) {
+    const double2 x = to_d2(Zt[a + (size_t)m * u]), y = to_d2(Zt[b + (size_t)m * u]);
+    acc.x += x.x * y.x + x.y * y.y;     // x conj(y)
+    acc.y += x.y * y.x - x.x * y.y;
+  }
+  G[a + (size_t)ldg * b] = acc;
+}
+// W[c + m u] = sum_a conj(U[a + m c]) Z[a + m u],  c < rows (= rmul * *rptr or m)
+template <typename T>
+__global__ void k_proj_rows(const T* U, const T* Zt, const int* mptr, int mul, const int* rptr,
+                            int mcap, int ncol, T* W) {
+  const int m = mul * (*mptr);
+  const int rr = rptr ? *rptr : m;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mcap * ncol) return;
+  const int c = e % mcap, u = e / mcap;
+  if (c >= rr) return;
+  typename KAccOf<T>::type acc;
+  for (int a = 0; a < m; ++a) acc.add_cmul(U[a + (size_t)m * c], Zt[a + (size_t)m * u]);
+  W[c + (size_t)rr * u] = acc.get();
+}
+__global__ void k_one(void* p, int is_f64) {
+  if (threadIdx.x == 0) {
+    if (is_f64) *(double*)p = 1.0;
+    else *(float2*)p = make_float2(1.f, 0.f);
+  }
+}
+__global__ void k_set_ranks_one(int* r, int d) {
+  if (threadIdx.x == 0) { r[0] = 1; r[d] = 1; }
+}
+
+template <typename T>
+static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr,
+                                  int sketch, unsigned long long seed, cudaStream_t s,
+                                  qtt_tensor** out) {
+  using R = typename Sc<T>::R;
+  const int d = x->desc.d;
+  const bool refine = tr.refine || !Sc<T>::cplx;
+  if (sketch <= 0) sketch = QTT_RANK_CAP;
+  sketch = std::min(sketch, QTT_RANK_CAP);
+  const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
+  const std::vector<int>& P = op->P;
+  const std::vector<int>& xcap = x->rcap;
+  std::vector<int> Rc(d + 1), l(d + 1), lq(d + 1), ocap(d + 1);
+  for (int k = 0; k <= d; ++k) Rc[k] = P[k] * xcap[k];
+  for (int k = 0; k <= d; ++k) {
+    long long lim = std::min<long long>(1LL << std::min(k, 40), 1LL << std::min(d - k, 40));
+    l[k] = (int)std::min<long long>({(long long)sketch, lim, (long long)Rc[k]});
+  }
+  l[0] = l[d] = 1;
+  lq[d] = 1;
+  for (int k = d; k >= 2; --k) lq[k - 1] = std::min(l[k - 1], 2 * lq[k]);
+  lq[0] = 1;
+  ocap[0] = 1;
+  for (int k = 1; k < d; ++k) ocap[k] = std::min({2 * ocap[k - 1], lq[k], rmax_eff});
+  ocap[d] = 1;
+
+  const R* Oc = (const R*)op->cores;
+  const T* Xc = (const T*)x->cores;
+  // --- buffers
+  int Rmax = 1, lmax = 1;
+  for (int k = 0; k <= d; ++k) { Rmax = std::max(Rmax, Rc[k]); lmax = std::max(lmax, l[k]); }
+  int Pmax = 1, xmax = 1;
+  for (int k = 0; k <= d; ++k) { Pmax = std::max(Pmax, P[k]); xmax = std::max(xmax, xcap[k]); }
+  std::vector<size_t> wloff(d);
+  size_t wltot = 0;
+  for (int k = 0; k < d; ++k) { wloff[k] = wltot; wltot += (size_t)l[k] * Rc[k]; }
+  std::vector<size_t> omoff(d);
+  size_t omtot = 0;
+  for (int k = 1; k < d; ++k) { omoff[k] = omtot; omtot += (size_t)l[k - 1] * 2 * l[k]; }
+  T* WL = (T*)scratch_alloc(sizeof(T) * std::max<size_t>(wltot, 1), s);
+  R* Om = (R*)scratch_alloc(sizeof(R) * std::max<size_t>(omtot, 1), s);
+  const size_t a1sz = (size_t)lmax * 2 * Rmax;
+  const size_t a2sz = (size_t)lmax * 2 * Pmax * 2 * xmax;
+  T* A1 = (T*)scratch_alloc(sizeof(T) * a1sz, s);
+  T* A2 = (T*)scratch_alloc(sizeof(T) * std::max(a2sz, (size_t)xmax * 2 * Pmax * 64), s);
+  T* Z = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * 2 * 64, s);
+  T* C0 = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * 64, s);
+  T* C1 = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * 64, s);
+  T* S = (T*)scratch_alloc(sizeof(T) * 64 * 128, s);
+  T* SV = (T*)scratch_alloc(sizeof(T) * 128 * 128, s);
+  T* SV2 = (T*)scratch_alloc(sizeof(T) * 128 * 128, s);
+  T* V1 = (T*)scratch_alloc(sizeof(T) * 128 * 128, s);
+  T* V = (T*)scratch_alloc(sizeof(T) * 128 * 128, s);
+  double2* G = (double2*)scratch_alloc(sizeof(double2) * 128 * 128, s);
+  T* Zt = (T*)scratch_alloc(sizeof(T) * 128 * 64, s);
+  T* W1 = (T*)scratch_alloc(sizeof(T) * 128 * 64, s);
+  T* Lc = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
+  T* one = (T*)scratch_alloc(sizeof(T), s);
+  if (!WL || !Om || !A1 || !A2 || !Z || !C0 || !C1 || !S || !SV || !SV2 || !V1 || !V || !G || !Zt ||
+      !W1 || !Lc || !one) {
+    set_error("round: scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  const int is64 = Sc<T>::cplx ? 0 : 1;
+  k_one<<<1, 32, 0, s>>>(one, is64);
+  // intermediate right-orthonormal TT (host-known ranks lq)
+  TensorDesc pd = x->desc;
+  qtt_tensor* Tp = nullptr;
+  qtt_status st = tensor_alloc(pd, lq, s, &Tp);
+  if (st != QTT_OK) return st;
+  T* Tpc = (T*)Tp->cores;
+  // output
+  qtt_tensor* y = nullptr;
+  st = tensor_alloc(x->desc, ocap, s, &y);
+  if (st != QTT_OK) { qtt_free(Tp); return st; }
+  k_set_ranks_one<<<1, 32, 0, s>>>(y->ranks, d);
+
+  // --- 1. Gaussian sketch cores and left sketches
+  for (int k = 1; k < d; ++k) {
+    const long long n = (long long)l[k - 1] * 2 * l[k];
+    gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
+                                                                              (uint32_t)k);
+  }
+  cudaMemcpyAsync(WL + wloff[0], one, sizeof(T), cudaMemcpyDeviceToDevice, s);
+  for (int k = 1; k < d; ++k) {
+    const int l0 = l[k - 1], lk = l[k];
+    const R* Ok = Oc + op->off[k - 1];
+    const T* Xk = Xc + x->off[k - 1];
+    k_a1<T, R><<<GRID1((long long)lk * 2 * Rc[k - 1])>>>(Om + omoff[k], l0, lk, WL + wloff[k - 1],
+                                                         x->ranks, k, P[k - 1], Rc[k - 1], A1);
+    k_a2<T><<<GRID1((long long)lk * 2 * P[k - 1] * 2 * xcap[k])>>>(A1, lk, Xk, x->ranks, k, P[k - 1],
+                                                                   xcap[k], A2);
+    k_wl<T, R><<<GRID1((long long)lk * Rc[k])>>>(Ok, P[k - 1], P[k], A2, lk, x->ranks, k, Rc[k],
+                                                 WL + wloff[k]);
+    k_normalize<T><<<1, 1024, 0, s>>>(WL + wloff[k], (long long)lk * Rc[k]);
+  }
+  // --- 2. right-to-left orthogonalising pass
+  T* Ccur = C0;
+  T* Cnext = C1;
+  cudaMemcpyAsync(Ccur, one, sizeof(T), cudaMemcpyDeviceToDevice, s);
+  int ldc = 1;  // = Rc[d]
+  for (int k = d; k >= 1; --k) {
+    const R* Ok = Oc + op->off[k - 1];
+    const T* Xk = Xc + x->off[k - 1];
+    const int n2 = 2 * lq[k];
+    k_b1<T><<<GRID1((long long)xcap[k - 1] * 2 * P[k] * lq[k])>>>(Xk, x->ranks, k, xcap[k - 1], P[k],
+                                                                   Ccur, ldc, lq[k], d, A2);
+    const int ldz = Rc[k - 1];
+    T* Zdst = (k == 1) ? Tpc + Tp->off[0] : Z;
+    k_z<T, R><<<GRID1((long long)xcap[k - 1] * P[k - 1] * 2 * lq[k])>>>(Ok, P[k - 1], P[k], A2, x->ranks,
+                                                                        k, xcap[k - 1], lq[k], ldz, Zdst);
+    if (k == 1) break;
+    const int l0 = l[k - 1];
+    k_s<T><<<GRID1((long long)l0 * n2)>>>(WL + wloff[k - 1], l0, Z, ldz, x->ranks, k, P[k - 1], n2, S);
+    k_gram_cols<T><<<GRID1(n2 * n2)>>>(S, l0, n2, G, 128);
+    launch_eig_dense<T>(G, 128, nullptr, 0, n2, n2, 0 /*ALL*/, 0.0, d, 0, nullptr, 0, n2, nullptr,
+                        V1, nullptr, nullptr, nullptr, nullptr, 0, y->status, s);
+    const T* Vuse = V1;
+    if (refine) {
+      k_sv<T><<<GRID1(l0 * n2)>>>(S, l0, n2, V1, SV);
+      k_gram_cols<T><<<GRID1(n2 * n2)>>>(SV, l0, n2, G, 128);
+      launch_eig_dense<T>(G, 128, nullptr, 0, n2, n2, 0, 0.0, d, 0, nullptr, 0, n2, V1, SV2, V,
+                          nullptr, nullptr, nullptr, 0, y->status, s);
+      Vuse = V;
+    }
+    const int lq0 = lq[k - 1];
+    k_qcore<T><<<GRID1(lq0 * n2)>>>(Vuse, n2, lq0, Tpc + Tp->off[k - 1]);
+    k_c<T><<<GRID1((long long)ldz * lq0)>>>(Z, ldz, Vuse, n2, lq0, x->ranks, k, P[k - 1], ldz, Cnext);
+    std::swap(Ccur, Cnext);
+    ldc = ldz;
+  }
+  // Tp ranks (host-known)
+  set_ranks_from_host(Tp->ranks, lq, s);
+  // --- 3. left-to-right truncation
+  cudaMemcpyAsync(Lc, one, sizeof(T), cudaMemcpyDeviceToDevice, s);
+  T* yc = (T*)y->cores;
+  for (int k = 1; k <= d; ++k) {
+    const int lq0 = lq[k - 1], lqk = lq[k];
+    const int tcap0 = ocap[k - 1];
+    T* Ztd = (k == d) ? yc + y->off[d - 1] : Zt;
+    k_zt<T><<<GRID1(2 * tcap0 * lqk)>>>(Lc, y->ranks, k, tcap0, Tpc + Tp->off[k - 1], lq0, lqk, Ztd);
+    if (k == d) break;
+    const int mcap = 2 * tcap0;
+    k_gram_rows<T><<<GRID1(mcap * mcap)>>>(Zt, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
+    T* corek = yc + y->off[k - 1];
+    if (refine) {
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 0 /*ALL*/, tr.eps, d, rmax_eff,
+                          nullptr, 0, lqk, nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1,
+                          y->status, s);
+      k_proj_rows<T><<<GRID1(mcap * lqk)>>>(V1, Zt, y->ranks + (k - 1), 2, nullptr, mcap, lqk, W1);
+      k_gram_rows<T><<<GRID1(mcap * mcap)>>>(W1, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, tr.eps, d, rmax_eff,
+                          nullptr, 0, lqk, V1, V, corek, y->ranks + k, nullptr, y->norm2, 0,
+                          y->status, s);
+    } else {
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1, tr.eps, d, rmax_eff, nullptr, 0,
+                          lqk, nullptr, corek, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,
+                          y->status, s);
+    }
+    // Lc = core_k^H Zt  (t_k x lq_k)
+    k_proj_rows<T><<<GRID1(mcap * lqk)>>>(corek, Zt, y->ranks + (k - 1), 2, y->ranks + k, mcap, lqk,
+                                          Lc);
+  }
+  st = cuda_check(cudaGetLastError(), "round launch");
+  scratch_free(WL, s); scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
+  scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
+  scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s); scratch_free(G, s);
+  scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s); scratch_free(one, s);
+  tensor_free_async(Tp, s);
+  if (st != QTT_OK) { qtt_free(y); return st; }
+  *out = y;
+  return QTT_OK;
+}
+
+qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,
+                         unsigned long long seed, cudaStream_t s, qtt_tensor** out) {
+  if (op->d != x->desc.d) { set_error("round: operator/tensor mode count mismatch"); return QTT_EINVAL; }
+  if (op->dt != x->desc.dt) { set_error("round: operator/tensor dtype mismatch"); return QTT_EINVAL; }
+  if (x->desc.dt == QTT_F64) return round_product_t<double>(op, x, tr, sketch, seed, s, out);
+  return round_product_t<float2>(op, x, tr, sketch, seed, s, out);
+}
+
+}  // namespace qtt

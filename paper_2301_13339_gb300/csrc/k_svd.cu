@@ -1,0 +1,650 @@
+// TT-SVD on the GPU (Alg. 1 with the max-rank modification of Sec. 5 (1)).
+//
+// Each step of Alg. 1 factors the unfolding M_k (m_k x n_k, m_k = 2 r_{k-1},
+// n_k = 2^{d-k}, Lemma 5.1) and carries Sigma V^* to the next step.  The
+// factorisation is done through the Gram matrix M M^H (m_k <= 128):
+//   pass 1  G = M M^H, Jacobi eigen-decomposition G = U1 L U1^H;
+//   pass 2  (refinement) W1 = U1^H M, G2 = W1 W1^H, Jacobi again: G2 is
+//           diagonally dominant up to scaling, so Jacobi resolves its small
+//           eigenvalues to relative accuracy (this is what makes the
+//           Gram route as accurate as an SVD of M);
+//   rank    r = min(rank_tau, R_max, m, n) from the eigenvalues sigma_i^2,
+//           tau = eps/sqrt(d-1) ||A||_F (Sec. 4 eps-rank);
+//   next    W = U_r^H M = Sigma_r V_r^*, whose reshape to (2 r) x (n/2) is the
+//           next unfolding; its Gram is accumulated by the same kernel.
+// Ranks live on the device: every kernel reads the ranks it needs, grids are
+// sized for the host-side capacities.
+#include "qtt_internal.cuh"
+#include <cstdio>
+#include <algorithm>
+
+namespace qtt {
+
+// --------------------------------------------------------------------------
+// Fused projection + Gram kernel.
+//   W = U^H M          (r x n, or W = M when U == nullptr)
+//   fold = 0:  gram += W W^H                        (r x r)
+//   fold = 1:  gram += W' W'^H, W' = reshape(W, [2r, n/2]) column-major:
+//              W'[a + r i, c] = W[a, 2c + i]          (2r x 2r)
+//   fold < 0:  no Gram.
+// Per-CTA partial Grams go to gram_part[blockIdx.x] (ldp x ldp, zero padded).
+// m = m_mul * *m_ptr, r = r_ptr ? *r_ptr : m.
+// --------------------------------------------------------------------------
+constexpr int PG_THREADS = 256;
+constexpr int PG_CC = 32;  // columns per chunk (even)
+
+template <typename T, int TM>
+__global__ void __launch_bounds__(PG_THREADS)
+proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_mul, long long n,
+                 const T* __restrict__ U, const int* __restrict__ r_ptr, T* __restrict__ W,
+                 int fold, T* __restrict__ gram_part, int ldp, int mcap, int rcap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sUt = reinterpret_cast<T*>(smem_raw);                  // rcap x mcap : sUt[c + rcap*i] = conj(U[i,c])
+  T* sM = sUt + (U ? (size_t)rcap * mcap : 0);              // mcap x CC
+  T* sW = U ? sM + (size_t)mcap * PG_CC : sM;               // rcap x CC (alias when U == null)
+  const int tid = threadIdx.x;
+  const int m = m_mul * (*m_ptr);
+  const int r = U ? (r_ptr ? *r_ptr : m) : m;
+  const int ldw = U ? rcap : mcap;
+  const int mg = (fold == 1) ? 2 * r : r;
+
+  if (U) {
+    for (int e = tid; e < r * m; e += PG_THREADS) {
+      int i = e % m, c = e / m;
+      sUt[c + rcap * i] = conjg(U[i + (size_t)m * c]);
+    }
+  }
+  // Gram accumulators: thread (ti, tj) of a 16 x 16 grid owns rows ti*TM.., cols tj*TM..
+  const int ti = tid % 16, tj = tid / 16;
+  T acc[TM][TM];
+#pragma unroll
+  for (int x = 0; x < TM; ++x)
+#pragma unroll
+    for (int y = 0; y < TM; ++y) acc[x][y] = szero<T>();
+
+  const long long nchunks = (n + PG_CC - 1) / PG_CC;
+  for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const long long c0 = ch * PG_CC;
+    const int ncol = (int)((n - c0) < PG_CC ? (n - c0) : PG_CC);
+    __syncthreads();
+    // load M chunk: contiguous m*ncol elements
+    const T* Mc = M + (size_t)c0 * m;
+    for (int e = tid; e < m * ncol; e += PG_THREADS) {
+      int i = e % m, j = e / m;
+      sM[i + mcap * j] = Mc[e];
+    }
+    __syncthreads();
+    if (U) {
+      // W chunk = U^H Mchunk, 4 x 4 register tiles
+      const int rb = (r + 3) / 4, jb = (ncol + 3) / 4;
+      for (int tb = tid; tb < rb * jb; tb += PG_THREADS) {
+        const int cb = (tb % rb) * 4, jb0 = (tb / rb) * 4;
+        T o[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) o[x][y] = szero<T>();
+        for (int i = 0; i < m; ++i) {
+          T u[4], v[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) u[x] = (cb + x < r) ? sUt[(cb + x) + rcap * i] : szero<T>();
+#pragma unroll
+          for (int y = 0; y < 4; ++y) v[y] = (jb0 + y < ncol) ? sM[i + mcap * (jb0 + y)] : szero<T>();
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) mac(o[x][y], u[x], v[y]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            if (cb + x < r && jb0 + y < ncol) sW[(cb + x) + rcap * (jb0 + y)] = o[x][y];
+      }
+      __syncthreads();
+      if (W) {
+        T* Wc = W + (size_t)c0 * r;
+        for (int e = tid; e < r * ncol; e += PG_THREADS) {
+          int c = e % r, j = e / r;
+          Wc[e] = sW[c + rcap * j];
+        }
+      }
+    }
+    if (fold >= 0) {
+      // Gram of this chunk
+      const int ncg = (fold == 1) ? ncol / 2 : ncol;
+      for (int j = 0; j < ncg; ++j) {
+        T a[TM], b[TM];
+#pragma unroll
+        for (int x = 0; x < TM; ++x) {
+          const int ra = ti * TM + x, rb2 = tj * TM + x;
+          if (fold == 1) {
+            a[x] = (ra < mg) ? sW[(ra % r) + ldw * (2 * j + ra / r)] : szero<T>();
+            b[x] = (rb2 < mg) ? sW[(rb2 % r) + ldw * (2 * j + rb2 / r)] : szero<T>();
+          } else {
+            a[x] = (ra < mg) ? sW[ra + ldw * j] : szero<T>();
+            b[x] = (rb2 < mg) ? sW[rb2 + ldw * j] : szero<T>();
+          }
+        }
+#pragma unroll
+        for (int x = 0; x < TM; ++x)
+#pragma unroll
+          for (int y = 0; y < TM; ++y) macb(acc[x][y], a[x], b[y]);
+      }
+    }
+  }
+  if (fold >= 0) {
+    T* gp = gram_part + (size_t)blockIdx.x * ldp * ldp;
+#pragma unroll
+    for (int x = 0; x < TM; ++x)
+#pragma unroll
+      for (int y = 0; y < TM; ++y) {
+        const int ra = ti * TM + x, rb2 = tj * TM + y;
+        if (ra < ldp && rb2 < ldp) gp[ra + (size_t)ldp * rb2] = acc[x][y];
+      }
+  }
+}
+
+// Sum of the per-CTA partial Grams in double: out[e] = sum_p part[p][e].
+template <typename T>
+__global__ void gram_reduce_kernel(const T* __restrict__ part, int nparts, int ldp,
+                                   double2* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tot = ldp * ldp;
+  if (e >= tot) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int p = 0; p < nparts; ++p) {
+    double2 v = to_d2(part[(size_t)p * tot + e]);
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[e] = s;
+}
+
+// --------------------------------------------------------------------------
+// One-CTA Jacobi eigen-decomposition of a Hermitian mg x mg matrix (mg <= 128)
+// given as a dense double2 array (ld = ldp).  Cyclic parallel ordering
+// (round robin: n/2 disjoint rotations per step, n-1 steps per sweep).  The
+// matrix is kept packed (upper triangle) in shared memory; the rotations of
+// one step are applied as 2 x 2 block updates B' = J_P^H B J_Q, which need no
+// ordering between them.  A rotation is skipped when
+// |a_pq| <= tol sqrt(|a_pp a_qq|) (relative criterion: keeps small
+// eigenvalues of scaled-diagonally-dominant matrices accurate).
+// --------------------------------------------------------------------------
+constexpr int EIG_THREADS = 1024;
+constexpr int EIG_MAXN = 128;
+
+enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
+
+template <typename T>
+struct EigArgs {
+  const double2* G;     // dense, ld = ldp
+  int ldp;
+  const int* mg_ptr;    // mg = mg_mul * *mg_ptr, or mg_const when mg_ptr is null
+  int mg_mul;
+  int mg_const;
+  int mode;
+  double eps;           // relative accuracy for the rank decision
+  int dmodes;           // d (number of modes) for tau = eps / sqrt(d-1) * ||A||
+  int rmax;             // cap (> 0)
+  const int* ncols_ptr; // ncols = ncols_mul * *ncols_ptr, or ncols_const if null
+  int ncols_mul;
+  long long ncols_const;
+  const T* U1;          // optional: core = U1 * U[:, :r] (U1 is mg x mg, ld mg)
+  T* Uout;              // sorted eigenvectors (ld = mg): all (MODE_ALL) or first r
+  T* core_out;          // optional: core (ld = mg, r columns)
+  int* rank_out;        // MODE_DECIDE: receives r
+  double* sig_out;      // optional: sorted eigenvalues
+  double* norm2;        // squared norm (read for tau; written when write_norm2)
+  int write_norm2;
+  int* status;
+};
+
+__device__ __forceinline__ int pk_idx(int i, int j) { return (j * (j + 1)) / 2 + i; }  // i <= j
+
+template <typename T>
+__device__ __forceinline__ T pk_get(const T* A, int i, int j) {
+  return (i <= j) ? A[pk_idx(i, j)] : conjg(A[pk_idx(j, i)]);
+}
+template <typename T>
+__device__ __forceinline__ void pk_set(T* A, int i, int j, T v) {
+  if (i <= j) A[pk_idx(i, j)] = v;
+  else A[pk_idx(j, i)] = conjg(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
+  using R = typename Sc<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_pp[EIG_MAXN / 2], s_pq[EIG_MAXN / 2];
+  __shared__ R s_c[EIG_MAXN / 2], s_s[EIG_MAXN / 2];
+  __shared__ T s_u[EIG_MAXN / 2];
+  __shared__ double s_d[EIG_MAXN / 2][2];
+  __shared__ int s_rot[EIG_MAXN / 2];
+  __shared__ int s_nrot;
+  __shared__ double s_lam[EIG_MAXN];
+  __shared__ int s_perm[EIG_MAXN];
+  __shared__ double s_red[32];
+  __shared__ int s_r;
+  __shared__ unsigned short s_blk[(EIG_MAXN / 2) * (EIG_MAXN / 2 + 1) / 2][2];
+
+  const int tid = threadIdx.x;
+  const int mg = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+  const int n = (mg + 1) & ~1;            // even
+  const int np = n / 2;
+  T* A = reinterpret_cast<T*>(smem_raw);  // packed, n(n+1)/2
+  T* V = A + (n * (n + 1)) / 2;           // n x n, column-major
+
+  // load + identity
+  double tr_local = 0.0;
+  for (int e = tid; e < (n * (n + 1)) / 2; e += EIG_THREADS) {
+    // invert pk_idx: find j with j(j+1)/2 <= e
+    int j = (int)floor((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= e) ++j;
+    while (j * (j + 1) / 2 > e) --j;
+    const int i = e - j * (j + 1) / 2;
+    T v = szero<T>();
+    if (i < mg && j < mg) {
+      double2 g = a.G[i + (size_t)a.ldp * j];
+      if (i == j) { g.y = 0.0; tr_local += g.x; }
+      from_d2(g, v);
+    }
+    A[e] = v;
+  }
+  for (int e = tid; e < n * n; e += EIG_THREADS) {
+    const int i = e % n, j = e / n;
+    V[e] = (i == j) ? sone(T()) : szero<T>();
+  }
+  // block table (P <= Q)
+  {
+    int nb = np * (np + 1) / 2;
+    for (int b = tid; b < nb; b += EIG_THREADS) {
+      int Q = (int)floor((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+      while ((Q + 1) * (Q + 2) / 2 <= b) ++Q;
+      while (Q * (Q + 1) / 2 > b) --Q;
+      int P = b - Q * (Q + 1) / 2;
+      s_blk[b][0] = (unsigned short)P;
+      s_blk[b][1] = (unsigned short)Q;
+    }
+  }
+  // trace reduction (norm^2 at the first level)
+  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
+  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
+    if (a.write_norm2) *a.norm2 = t;
+  }
+
+  const double tol = Sc<T>::eps;
+  const int maxsweep = Sc<T>::cplx ? 30 : 40;
+  const int nb = np * (np + 1) / 2;
+  bool converged = (n <= 1);
+  for (int sweep = 0; sweep < maxsweep && !converged; ++sweep) {
+    if (tid == 0) s_nrot = 0;
+    __syncthreads();
+    for (int step = 0; step < n - 1; ++step) {
+      if (tid < np) {
+        int p, q;
+        if (tid == 0) { p = n - 1; q = step; }
+        else { p = (step + tid) % (n - 1); q = (step - tid + (n - 1)) % (n - 1); }
+        if (p > q) { int t = p; p = q; q = t; }
+        s_pp[tid] = p;
+        s_pq[tid] = q;
+        const double app = (double)sreal(A[pk_idx(p, p)]);
+        const double aqq = (double)sreal(A[pk_idx(q, q)]);
+        const T apq = A[pk_idx(p, q)];
+        const double b = sqrt((double)sabs2(apq));
+        int rot = 0;
+        double c = 1.0, s = 0.0, t = 0.0;
+        T u = sone(T());
+        if (b > 0.0 && b > tol * sqrt(fabs(app) * fabs(aqq))) {
+          const double zeta = (aqq - app) / (2.0 * b);
+          t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+          u = rscale(apq, (R)(1.0 / b));
+          rot = 1;
+          atomicAdd(&s_nrot, 1);
+        }
+        s_rot[tid] = rot;
+        s_c[tid] = (R)c;
+        s_s[tid] = (R)s;
+        s_u[tid] = u;
+        s_d[tid][0] = app - t * b;
+        s_d[tid][1] = aqq + t * b;
+      }
+      __syncthreads();
+      for (int bi = tid; bi < nb; bi += EIG_THREADS) {
+        const int P = s_blk[bi][0], Q = s_blk[bi][1];
+        const int rP = s_rot[P], rQ = s_rot[Q];
+        if (!rP && !rQ) continue;
+        const int i0 = s_pp[P], i1 = s_pq[P];
+        if (P == Q) {
+          A[pk_idx(i0, i0)] = rscale(sone(T()), (R)s_d[P][0]);
+          A[pk_idx(i1, i1)] = rscale(sone(T()), (R)s_d[P][1]);
+          A[pk_idx(i0, i1)] = szero<T>();
+          continue;
+        }
+        const int j0 = s_pp[Q], j1 = s_pq[Q];
+        T b00 = pk_get(A, i0, j0), b01 = pk_get(A, i0, j1);
+        T b10 = pk_get(A, i1, j0), b11 = pk_get(A, i1, j1);
+        // left: J_P^H B  with J^H = [[c, -s u], [s conj(u), c]]
+        if (rP) {
+          const R c = s_c[P], s = s_s[P];
+          const T u = s_u[P];
+          const T su = rscale(u, s), scu = rscale(conjg(u), s);
+          T n00 = ssub(rscale(b00, c), smul(su, b10));
+          T n01 = ssub(rscale(b01, c), smul(su, b11));
+          T n10 = sadd(smul(scu, b00), rscale(b10, c));
+          T n11 = sadd(smul(scu, b01), rscale(b11, c));
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        // right: B J_Q with J = [[c, s u], [-s conj(u), c]]
+        if (rQ) {
+          const R c = s_c[Q], s = s_s[Q];
+          const T u = s_u[Q];
+          const T su = rscale(u, s), scu = rscale(conjg(u), s);
+          T n00 = ssub(rscale(b00, c), smul(b01, scu));
+          T n01 = sadd(smul(b00, su), rscale(b01, c));
+          T n10 = ssub(rscale(b10, c), smul(b11, scu));
+          T n11 = sadd(smul(b10, su), rscale(b11, c));
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        pk_set(A, i0, j0, b00);
+        pk_set(A, i0, j1, b01);
+        pk_set(A, i1, j0, b10);
+        pk_set(A, i1, j1, b11);
+      }
+      for (int e = tid; e < n * np; e += EIG_THREADS) {
+        const int P = e / n, row = e % n;
+        if (!s_rot[P]) continue;
+        const int p = s_pp[P], q = s_pq[P];
+        const R c = s_c[P], s = s_s[P];
+        const T u = s_u[P];
+        const T vp = V[row + n * p], vq = V[row + n * q];
+        // [vp, vq] J = [c vp - s conj(u) vq, s u vp + c vq]
+        V[row + n * p] = ssub(rscale(vp, c), smul(rscale(conjg(u), s), vq));
+        V[row + n * q] = sadd(smul(rscale(u, s), vp), rscale(vq, c));
+      }
+      __syncthreads();
+    }
+    converged = (s_nrot == 0);
+    __syncthreads();
+  }
+  if (!converged && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
+
+  // eigenvalues and descending order (ties by index)
+  for (int i = tid; i < mg; i += EIG_THREADS) s_lam[i] = (double)sreal(A[pk_idx(i, i)]);
+  __syncthreads();
+  for (int i = tid; i < mg; i += EIG_THREADS) {
+    const double li = s_lam[i];
+    int rk = 0;
+    for (int j = 0; j < mg; ++j) {
+      const double lj = s_lam[j];
+      rk += (lj > li) || (lj == li && j < i);
+    }
+    s_perm[rk] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r = mg;
+    if (a.mode == EIG_MODE_DECIDE) {
+      const long long ncols = a.ncols_ptr ? (long long)a.ncols_mul * (*a.ncols_ptr) : a.ncols_const;
+      int kmax = mg < ncols ? mg : (int)ncols;
+      if (kmax < 1) kmax = 1;
+      const double nrm2 = *a.norm2;
+      const double tau2 = (a.dmodes > 1) ? a.eps * a.eps / (double)(a.dmodes - 1) * nrm2 : 0.0;
+      double tail = 0.0;
+      r = kmax;
+      for (int c = kmax - 1; c >= 1; --c) {
+        const double l = s_lam[s_perm[c]];
+        tail += (l > 0.0 ? l : 0.0);
+        if (tail <= tau2) r = c;
+        else break;
+      }
+      if (a.rmax > 0 && r > a.rmax) r = a.rmax;
+      if (r < 1) r = 1;
+      if (a.rank_out) *a.rank_out = r;
+    }
+    s_r = r;
+  }
+  __syncthreads();
+  const int r = s_r;
+  if (a.sig_out)
+    for (int c = tid; c < mg; c += EIG_THREADS) a.sig_out[c] = s_lam[s_perm[c]];
+  const int ncopy = (a.mode == EIG_MODE_ALL) ? mg : r;
+  if (Sc<T>::cplx) {
+    // FP32: the accumulated rotations leave V orthonormal only to
+    // ~sqrt(#rotations) eps; one Newton-Schulz step V (3 I - V^H V) / 2
+    // squares that error.  G = V^H V goes into the (no longer needed) packed A.
+    const int ng = n * (n + 1) / 2;
+    for (int e = tid; e < ng; e += EIG_THREADS) {
+      int j = (int)floor((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((j + 1) * (j + 2) / 2 <= e) ++j;
+      while (j * (j + 1) / 2 > e) --j;
+      const int i = e - j * (j + 1) / 2;
+      T acc = szero<T>();
+      for (int l = 0; l < n; ++l) macc(acc, V[l + n * i], V[l + n * j]);
+      A[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
+      const int i = e % mg, c = e / mg;
+      const int pc = s_perm[c];
+      T acc = rscale(V[i + n * pc], (typename Sc<T>::R)1.5);
+      T corr = szero<T>();
+      for (int l = 0; l < n; ++l) mac(corr, V[i + n * l], pk_get(A, l, pc));
+      a.Uout[e] = ssub(acc, rscale(corr, (typename Sc<T>::R)0.5));
+    }
+  } else {
+    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
+      const int i = e % mg, c = e / mg;
+      a.Uout[e] = V[i + n * s_perm[c]];
+    }
+  }
+  __syncthreads();
+  if (a.core_out) {
+    if (a.U1) {
+      for (int e = tid; e < mg * r; e += EIG_THREADS) {
+        const int i = e % mg, c = e / mg;
+        typename KAccOf<T>::type acc;
+        for (int l = 0; l < mg; ++l) acc.add_mul(a.U1[i + (size_t)mg * l], a.Uout[l + (size_t)mg * c]);
+        a.core_out[e] = acc.get();
+      }
+    } else if (a.core_out != a.Uout) {
+      for (int e = tid; e < mg * r; e += EIG_THREADS) a.core_out[e] = a.Uout[e];
+    }
+  }
+}
+
+template <typename T>
+static size_t eig_smem_bytes(int mg_cap) {
+  const int n = (mg_cap + 1) & ~1;
+  return sizeof(T) * ((size_t)n * (n + 1) / 2 + (size_t)n * n);
+}
+
+template <typename T>
+static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
+  const size_t sm = eig_smem_bytes<T>(mg_cap);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(gram_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)eig_smem_bytes<T>(EIG_MAXN));
+    configured = true;
+  }
+  gram_eig_kernel<T><<<1, EIG_THREADS, sm, s>>>(a);
+}
+
+template <typename T>
+static size_t pg_smem_bytes(bool has_u, int mcap, int rcap) {
+  size_t e = (size_t)mcap * PG_CC;
+  if (has_u) e += (size_t)rcap * mcap + (size_t)rcap * PG_CC;
+  return e * sizeof(T);
+}
+
+template <typename T, int TM>
+static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
+                         int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
+                         T* gp, int ldp, int mcap, int rcap) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(proj_gram_kernel<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pg_smem_bytes<T>(true, 128, 128));
+    configured = true;
+  }
+  proj_gram_kernel<T, TM><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp,
+                                                       ldp, mcap, rcap);
+}
+
+// Launch the fused projection/Gram kernel.  Returns the number of partials.
+template <typename T>
+static int launch_proj_gram(const T* M, const int* m_ptr, int m_mul, int mcap, long long n,
+                            const T* U, const int* r_ptr, int rcap, T* W, int fold, T* gp,
+                            int ldp, int max_parts, cudaStream_t s) {
+  const long long nchunks = (n + PG_CC - 1) / PG_CC;
+  int grid = (int)std::min<long long>(nchunks, (long long)max_parts);
+  if (grid < 1) grid = 1;
+  const bool has_u = (U != nullptr);
+  const int rc = has_u ? rcap : mcap;
+  const int mgcap = (fold == 1) ? 2 * rc : rc;
+  const size_t sm = pg_smem_bytes<T>(has_u, mcap, rcap);
+  if (fold < 0 || mgcap <= 16)
+    launch_pg_tm<T, 1>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+  else if (mgcap <= 32)
+    launch_pg_tm<T, 2>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+  else if (mgcap <= 64)
+    launch_pg_tm<T, 4>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+  else
+    launch_pg_tm<T, 8>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+  return grid;
+}
+
+template <typename T>
+static void launch_reduce(const T* gp, int nparts, int ldp, double2* out, cudaStream_t s) {
+  const int tot = ldp * ldp;
+  gram_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(gp, nparts, ldp, out);
+}
+
+__global__ void set_boundary_ranks_kernel(int* ranks, int d) {
+  if (threadIdx.x == 0) {
+    ranks[0] = 1;
+    ranks[d] = 1;
+  }
+}
+
+// Eigen-decomposition of a dense double2 Gram (ld = ldp): see EigArgs.
+template <typename T>
+void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, int mg_const,
+                      int mg_cap, int mode, double eps, int dmodes, int rmax,
+                      const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
+                      T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
+                      int write_norm2, int* status, cudaStream_t s) {
+  EigArgs<T> a;
+  a.G = G; a.ldp = ldp; a.mg_ptr = mg_ptr; a.mg_mul = mg_mul; a.mg_const = mg_const;
+  a.mode = mode; a.eps = eps; a.dmodes = dmodes; a.rmax = rmax; a.ncols_ptr = ncols_ptr;
+  a.ncols_mul = ncols_mul; a.ncols_const = ncols_const; a.U1 = U1; a.Uout = Uout;
+  a.core_out = core_out; a.rank_out = rank_out; a.sig_out = sig_out; a.norm2 = norm2;
+  a.write_norm2 = write_norm2; a.status = status;
+  launch_eig<T>(a, mg_cap, s);
+}
+
+// Reduce per-CTA partial Grams, then eigen-decompose.
+template <typename T>
+void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr, int mg_mul,
+                     int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
+                     int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
+                     int* rank_out, double* sig_out, double* norm2, int write_norm2,
+                     int* status, cudaStream_t s) {
+  double2* gfin = (double2*)scratch_alloc(sizeof(double2) * ldp * ldp, s);
+  launch_reduce<T>(gram_part, nparts, ldp, gfin, s);
+  launch_eig_dense<T>(gfin, ldp, mg_ptr, mg_mul, 0, mg_cap, mode, eps, dmodes, rmax, ncols_ptr,
+                      ncols_mul, ncols_const, U1, Uout, core_out, rank_out, sig_out, norm2,
+                      write_norm2, status, s);
+  scratch_free(gfin, s);
+}
+
+template <typename T>
+qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s) {
+  const long long N = 1LL << d;
+  const bool refine = tr.refine || !Sc<T>::cplx;
+  const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
+  const int max_parts = 2 * 152;
+  const int LDP = 128;
+  T* bufA = (T*)scratch_alloc(sizeof(T) * N, s);
+  T* bufB = (T*)scratch_alloc(sizeof(T) * N, s);
+  T* gp = (T*)scratch_alloc(sizeof(T) * (size_t)max_parts * LDP * LDP, s);
+  T* U1 = (T*)scratch_alloc(sizeof(T) * LDP * LDP, s);
+  T* U2 = (T*)scratch_alloc(sizeof(T) * LDP * LDP, s);
+  if (!bufA || !bufB || !gp || !U1 || !U2) {
+    set_error("tt_svd: scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  set_boundary_ranks_kernel<<<1, 32, 0, s>>>(t->ranks, d);
+  T* cores = (T*)t->cores;
+  int* rk = t->ranks;
+  // Gram of the first unfolding (2 x 2^{d-1})
+  int nparts = launch_proj_gram<T>(v, rk + 0, 2, 2, N / 2, nullptr, nullptr, 0, nullptr, 0, gp,
+                                   2, max_parts, s);
+  int ldp = 2;
+  const T* M = v;
+  for (int k = 1; k <= d - 1; ++k) {
+    const long long n = N >> k;
+    const int mcap = 2 * t->rcap[k - 1];
+    const int rcapk = t->rcap[k];
+    T* core_k = cores + t->off[k - 1];
+    T* Wout = (k == d - 1) ? cores + t->off[d - 1] : (refine ? bufB : (M == bufA ? bufB : bufA));
+    const int fold_next = (k < d - 1) ? 1 : -1;
+    const int ldp_next = 2 * rcapk;
+    if (refine) {
+      // pass 1: all eigenvectors of M M^H
+      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
+                         nullptr, 0, n, nullptr, U1, nullptr, nullptr, nullptr, t->norm2,
+                         k == 1, t->status, s);
+      // W1 = U1^H M, Gram of W1
+      nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
+                                   mcap, max_parts, s);
+      // pass 2: decide the rank; core = U1 * U2[:, :r]
+      launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
+                         rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
+                         t->status, s);
+      // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
+      nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
+                                   fold_next, gp, ldp_next, max_parts, s);
+    } else {
+      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
+                         rmax_eff, nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
+                         t->norm2, k == 1, t->status, s);
+      nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, core_k, rk + k, rcapk, Wout,
+                                   fold_next, gp, ldp_next, max_parts, s);
+    }
+    ldp = ldp_next;
+    M = Wout;
+  }
+  scratch_free(bufA, s);
+  scratch_free(bufB, s);
+  scratch_free(gp, s);
+  scratch_free(U1, s);
+  scratch_free(U2, s);
+  return cuda_check(cudaGetLastError(), "tt_svd launch");
+}
+
+template qtt_status tt_svd<double>(const double*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t);
+template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t);
+template void launch_eig_dense<double>(const double2*, int, const int*, int, int, int, int, double,
+                                       int, int, const int*, int, long long, const double*,
+                                       double*, double*, int*, double*, double*, int, int*,
+                                       cudaStream_t);
+template void launch_eig_dense<float2>(const double2*, int, const int*, int, int, int, int, double,
+                                       int, int, const int*, int, long long, const float2*,
+                                       float2*, float2*, int*, double*, double*, int, int*,
+                                       cudaStream_t);
+template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
+                                      int, int, const int*, int, long long, const double*, double*,
+                                      double*, int*, double*, double*, int, int*, cudaStream_t);
+template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, int, int, double,
+                                      int, int, const int*, int, long long, const float2*, float2*,
+                                      float2*, int*, double*, double*, int, int*, cudaStream_t);
+
+}  // namespace qtt

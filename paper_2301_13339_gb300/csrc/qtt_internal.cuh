@@ -1,0 +1,219 @@
+// Internal declarations of libqtt (not part of the C ABI).
+//
+// Element types: T = double (real, FP64 path) or float2 (complex float, FP32
+// path).  R is the matching real type.  Reductions that feed rank decisions
+// (traces, partial-Gram sums) are carried in double.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <string>
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+// ---------------------------------------------------------------- scalars
+template <typename T> struct Sc;
+template <> struct Sc<double> {
+  using R = double;
+  static constexpr bool cplx = false;
+  static constexpr double eps = 2.220446049250313e-16;
+};
+template <> struct Sc<float2> {
+  using R = float;
+  static constexpr bool cplx = true;
+  static constexpr double eps = 1.1920928955078125e-07;
+};
+
+__host__ __device__ __forceinline__ double zero_of(double) { return 0.0; }
+__host__ __device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f); }
+template <typename T> __host__ __device__ __forceinline__ T szero() { return zero_of(T()); }
+__host__ __device__ __forceinline__ double sone(double) { return 1.0; }
+__host__ __device__ __forceinline__ float2 sone(float2) { return make_float2(1.f, 0.f); }
+
+__host__ __device__ __forceinline__ double conjg(double a) { return a; }
+__host__ __device__ __forceinline__ float2 conjg(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double sadd(double a, double b) { return a + b; }
+__host__ __device__ __forceinline__ float2 sadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double ssub(double a, double b) { return a - b; }
+__host__ __device__ __forceinline__ float2 ssub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double smul(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ float2 smul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// real scaling
+__host__ __device__ __forceinline__ double rscale(double a, double s) { return a * s; }
+__host__ __device__ __forceinline__ float2 rscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double sreal(double a) { return a; }
+__host__ __device__ __forceinline__ float sreal(float2 a) { return a.x; }
+__host__ __device__ __forceinline__ double sabs2(double a) { return a * a; }
+__host__ __device__ __forceinline__ float sabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// acc += a * b
+__device__ __forceinline__ void mac(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void mac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void macc(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void macc(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+__device__ __forceinline__ void macb(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void macb(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+}
+// acc += r * b  (r real)
+__device__ __forceinline__ void rmac(double& acc, double r, double b) { acc = fma(r, b, acc); }
+__device__ __forceinline__ void rmac(float2& acc, float r, float2 b) {
+  acc.x = fmaf(r, b.x, acc.x);
+  acc.y = fmaf(r, b.y, acc.y);
+}
+
+// Compensated (Kahan) accumulation for the FP32 path: acc + comp carries the
+// sum of rounded products to ~1 ulp instead of ~sqrt(K) ulp.  FP64 sums are
+// plain.
+struct KAcc64 {
+  double s = 0.0;
+  __device__ __forceinline__ void add_mul(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add_cmul(double a, double b) { s = fma(a, b, s); }   // conj(a) b
+  __device__ __forceinline__ void add_rmul(double r, double b) { s = fma(r, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+struct KAcc32 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 p) {
+    float y = p.x - c.x, t = s.x + y;
+    c.x = (t - s.x) - y;
+    s.x = t;
+    y = p.y - c.y;
+    t = s.y + y;
+    c.y = (t - s.y) - y;
+    s.y = t;
+  }
+  __device__ __forceinline__ void add_mul(float2 a, float2 b) {
+    add(make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)));
+  }
+  __device__ __forceinline__ void add_cmul(float2 a, float2 b) {   // conj(a) b
+    add(make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x)));
+  }
+  __device__ __forceinline__ void add_rmul(float r, float2 b) { add(make_float2(r * b.x, r * b.y)); }
+  __device__ __forceinline__ float2 get() const { return make_float2(s.x - c.x, s.y - c.y); }
+};
+template <typename T> struct KAccOf;
+template <> struct KAccOf<double> { using type = KAcc64; };
+template <> struct KAccOf<float2> { using type = KAcc32; };
+
+// double-precision accumulator of a T value (for reductions)
+__host__ __device__ __forceinline__ double2 to_d2(double a) { return make_double2(a, 0.0); }
+__host__ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ void from_d2(double2 v, double& o) { o = v.x; }
+__host__ __device__ __forceinline__ void from_d2(double2 v, float2& o) { o = make_float2((float)v.x, (float)v.y); }
+
+// ---------------------------------------------------------------- status
+// Device status word bits (OR-ed by kernels; read by qtt_get_ranks).
+enum : int {
+  DEV_ST_JACOBI_LIMIT = 1,   // Jacobi sweep limit reached before convergence
+  DEV_ST_RANK_OVERFLOW = 2,  // a rank larger than its capacity was requested
+};
+
+// ---------------------------------------------------------------- handles
+struct TensorDesc {
+  int d = 0;
+  qtt_dtype dt = QTT_C64;
+  int ndim = 1;
+  int log2_shape[2] = {0, 0};   // {d} or {dy, dx}
+  int interleave = 1;
+};
+
+}  // namespace qtt
+
+struct qtt_tensor {
+  qtt::TensorDesc desc;
+  std::vector<int> rcap;          // host capacity per cut, d+1 entries
+  std::vector<size_t> off;        // element offset of core k (0-based), d entries
+  size_t total = 0;               // elements allocated for cores
+  void* cores = nullptr;          // device, element type of desc.dt
+  int* ranks = nullptr;           // device, d+1 ints
+  int* status = nullptr;          // device, 1 int
+  double* norm2 = nullptr;        // device, 1 double (squared norm at creation)
+};
+
+struct qtt_op {
+  int d = 0;                      // number of modes the operator acts on
+  qtt_dtype dt = QTT_C64;         // data type it is applied to (cores are real R)
+  std::vector<int> P;             // ranks P_0..P_d (host)
+  std::vector<size_t> off;        // offsets of the cores (elements of R)
+  size_t total = 0;
+  void* cores = nullptr;          // device, real (double for F64, float for C64)
+};
+
+namespace qtt {
+
+size_t elem_size(qtt_dtype dt);
+void set_error(const char* fmt, ...);
+qtt_status cuda_check(cudaError_t e, const char* what);
+
+// capacities: r_k <= min(2^k, 2^(d-k), rmax, cap)
+std::vector<int> rank_caps(int d, int rmax, int cap);
+
+// allocate a tensor handle with the given capacity profile (no data)
+qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap,
+                        cudaStream_t s, qtt_tensor** out);
+
+// ------------------------------------------------------------- TT-SVD
+// Decompose the vector v (2^d elements, QTT order, device) into t (allocated
+// by the caller with caps from rank_caps).  eps/rmax/refine as qtt_trunc.
+template <typename T>
+qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s);
+
+// ------------------------------------------------------------- small SVD
+// One-CTA SVD helper used by the rounding sweeps: see k_svd.cu.
+template <typename T>
+void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr, int mg_mul,
+                     int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
+                     int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
+                     int* rank_out, double* sig_out, double* norm2, int write_norm2,
+                     int* status, cudaStream_t s);
+
+// ------------------------------------------------------------- full
+template <typename T>
+qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s);
+
+// ------------------------------------------------------------- permutations
+template <typename T>
+void launch_morton_gather(const T* img, T* v, int dx, int dy, int interleave, cudaStream_t s);
+
+// ------------------------------------------------------------- operator
+qtt_status op_sinc_create(int d, double B, int normalize, double eps_op, qtt_dtype dt,
+                          cudaStream_t s, qtt_op** out);
+qtt_status op_embed_axis(const qtt_op* op1d, const TensorDesc& desc, int axis, cudaStream_t s,
+                         qtt_op** out);
+void op_free(qtt_op* op);
+
+// ------------------------------------------------------------- conv / rounding
+qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_tensor** out);
+qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,
+                         unsigned long long seed, cudaStream_t s, qtt_tensor** out);
+
+// write host-known ranks (<= 32 modes) to a device rank array, stream-ordered
+void set_ranks_from_host(int* dev_ranks, const std::vector<int>& r, cudaStream_t s);
+// stream-ordered release of a handle
+void tensor_free_async(qtt_tensor* t, cudaStream_t s);
+
+// stream-ordered scratch allocation
+void* scratch_alloc(size_t bytes, cudaStream_t s);
+void scratch_free(void* p, cudaStream_t s);
+
+}  // namespace qtt
