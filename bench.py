@@ -1,0 +1,349 @@
+"""Benchmark: QTT decompose + convolve + reconstruct, Msamples/s.
+
+Workload (default): one 1D complex64 line of N = 2^20 samples, 50 point
+scatterers over 3 complex Gaussian bumps (width 0.05), complex white noise at
+SNR 20 dB; sinc kernel B = 1024 (normalised); TT-SVD with ranks capped at 64
+(eps = 0); operator eps_op = 1e-7; rounding eps_round = 1e-7.
+
+A step = qtt_decompose + qtt_conv_sinc (matvec + rounding) + qtt_to_full on
+one line whose input is already resident in device memory.  The input (8 MiB)
+is smaller than L2, so L2 is flushed (a 512 MiB write) before every timed
+step, outside the timed region; each step is timed with CUDA events on the
+library's stream and the per-step times are summed.
+
+Also reported: e2e (same metric through the C ABI with host buffers: pinned
+H2D copy of the input and D2H copy of the output inside the timed region),
+parity E2 against the FP64 oracle on the same input, per-kernel CUDA-event
+times from a second (profiled) pass, the roofline of the dominant kernel,
+the oracle's own throughput on the host cores (cpu_baseline) and the SM
+clocks sampled with nvidia-smi during the timed region.
+
+Multi-GPU (torchrun): each rank processes its own line (replicas only, weak
+scaling); the time is the max over ranks.
+
+--impl reference: the FP64 oracle (numpy, host cores) on the same workload,
+one line per step.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "line_2p20_c64": dict(d=20, B=1024.0, rmax=64, eps=0.0, eps_op=1e-7, eps_round=1e-7,
+                          nscat=50, nbumps=3, snr_db=20.0, tol=1e-5),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_input(wl, rank=0):
+    import synth
+    rng = synth.config_rng(1, sub=rank if rank else None)
+    x, clean = synth.line_1d_scatterers(rng, 2 ** wl["d"], nscat=wl["nscat"],
+                                        nbumps=wl["nbumps"], snr_db=wl["snr_db"])
+    return x.astype(np.complex64), clean
+
+
+def run_oracle(x, wl):
+    from oracle import pipeline as P
+    t0 = time.perf_counter()
+    out = P.conv_sinc_qtt(x.astype(np.complex128), wl["B"], wl["eps"], wl["rmax"],
+                          eps_op=wl["eps_op"], eps_round=wl["eps_round"])
+    return out, time.perf_counter() - t0
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.fh = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_arm(args, wl):
+    import torch
+    import torch.distributed as dist
+    import paper_2301_13339_gb300 as q
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    q.load()
+    L = q.lib()
+    stream = torch.cuda.Stream(device=dev)
+    N = 2 ** wl["d"]
+    x, _ = make_input(wl, rank)
+    xd = torch.from_numpy(x).to(dev)
+    out = torch.empty(N, dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    refine = args.refine
+
+    def step(s, xin=xd, dst=out):
+        f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s)
+        y = q.qtt_conv_sinc(f, wl["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"],
+                            refine=True, sketch=0, stream=s)
+        q.qtt_to_full(y, out=dst, stream=s)
+        f.free(stream=s)
+        y.free(stream=s)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region (device-resident input)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dev.index)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step(stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # ---- e2e through the C ABI with host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    xdev2 = torch.empty_like(xd)
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            eve[i][0].record(stream)
+            xdev2.copy_(xh, non_blocking=True)
+            step(stream, xin=xdev2, dst=out)
+            oh.copy_(out, non_blocking=True)
+            eve[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eve)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- profiled pass: per-kernel CUDA-event times on the same workload
+    import ctypes
+    L.qtt_profile_enable.argtypes = [ctypes.c_int]
+    L.qtt_profile_read.restype = ctypes.c_int
+    L.qtt_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.qtt_profile_reset()
+    L.qtt_profile_enable(1)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            step(stream)
+    torch.cuda.synchronize(dev)
+    L.qtt_profile_enable(0)
+    cap, stride = 64, 64
+    names = ctypes.create_string_buffer(cap * stride)
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int * cap)()
+    nk = L.qtt_profile_read(names, stride, ms, cnt, cap)
+    kern = {}
+    for i in range(nk):
+        nm = names.raw[i * stride:(i + 1) * stride].split(b"\0")[0].decode()
+        kern[nm] = {"ms_per_step": ms[i] / args.steps, "launches_per_step": cnt[i] / args.steps}
+    L.qtt_profile_reset()
+    out_host = out.cpu().numpy()
+    return dict(world=world, rank=rank, total_ms=total_ms, e2e_ms=e2e_ms, wall_s=t_wall,
+                clocks=clk, kernels=kern, out=out_host, x=x, dev=dev)
+
+
+def roofline(kernels, wl, peaks, peak_kind):
+    """Dominant kernel's achieved rate against its bound."""
+    if not kernels:
+        return None
+    name = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    if name.startswith("jacobi_eig"):
+        name_eig = name
+    kinfo = kernels[name]
+    avg_ms = kinfo["ms_per_step"] / max(kinfo["launches_per_step"], 1e-9)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # FP32 CUDA-core peak of the whole GPU: 152 SMs x 128 FMA/clk x 2 flop
+    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    N = 2 ** wl["d"]
+    if name.startswith("jacobi_eig"):
+        # one complex Hermitian eigen-decomposition of a 128 x 128 Gram per
+        # launch at the capped levels; algorithmic work counted as the
+        # LAPACK-style 9 n^3 real flops x 4 (complex)
+        n = 2 * wl["rmax"]
+        flops = 9 * n ** 3 * 4
+        ach = flops / (avg_ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "traffic": None,
+                "avg_launch_ms": avg_ms, "peak_source": f"152 SM x 128 FP32 FMA/clk at {sm_mhz:.0f} MHz"}
+    if name in ("proj_gram", "full_expand", "morton_gather"):
+        # algorithmic bytes: every launch streams its input unfolding once
+        bytes_per_launch = 8.0 * N * 2 / max(kinfo["launches_per_step"], 1)
+        ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+        pk = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                "frac": ach / pk, "traffic": None, "avg_launch_ms": avg_ms,
+                "peak_source": peak_kind}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": fp32_peak_tflops,
+            "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_ms,
+            "peak_source": "fp32 cuda cores"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="line_2p20_c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--refine", type=int, default=0, help="second Gram pass in the TT-SVD")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    wl = WORKLOADS[args.workload]
+    N = 2 ** wl["d"]
+    metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"
+    config = {"workload": args.workload, "samples_per_line": N, "dtype_in": "complex64",
+              "B": wl["B"], "rmax": wl["rmax"], "eps": wl["eps"], "eps_op": wl["eps_op"],
+              "eps_round": wl["eps_round"], "snr_db": wl["snr_db"],
+              "l2": "flushed (512 MiB write) before every timed step, outside the timed region"}
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+        x, _ = make_input(wl)
+        for _ in range(args.warmup):
+            run_oracle(x, wl)
+        ts = []
+        for _ in range(args.steps):
+            _, t = run_oracle(x, wl)
+            ts.append(t)
+        tot = sum(ts)
+        v = N * args.steps / tot / 1e6
+        cores = len(os.sched_getaffinity(0))
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "Msamples/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cores,
+                                 "kind": "oracle",
+                                 "sample": f"one full line (2^{wl['d']} samples) per step"},
+                "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    res = gpu_arm(args, wl)
+    world, rank = res["world"], res["rank"]
+    if rank != 0:
+        return
+    peaks, peak_kind = _peaks()
+    value = world * N * args.steps / (res["total_ms"] * 1e-3) / 1e6
+    e2e = world * N * args.steps / (res["e2e_ms"] * 1e-3) / 1e6
+    kern = res["kernels"]
+    launches = sum(k["launches_per_step"] for k in kern.values()) * args.steps
+    line = {"metric": metric, "value": value, "unit": "Msamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)",
+            "data": "synthetic", "config": config,
+            "e2e": {"value": e2e, "unit": "Msamples/s", "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": int(round(launches)),
+            "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in kern.items()},
+            "roofline": roofline(kern, wl, peaks, peak_kind),
+            "clocks": res["clocks"], "refine": args.refine}
+    if not args.no_cpu_baseline:
+        ref, t = run_oracle(res["x"], wl)
+        from oracle import conv as C
+        e2 = C.rel_l2(res["out"].astype(np.complex128), ref)
+        line["parity"] = {"e2_vs_oracle": e2, "tol": wl["tol"], "ok": bool(e2 <= wl["tol"])}
+        line["cpu_baseline"] = {"value": N / t / 1e6, "unit": "Msamples/s",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"one full line (2^{wl['d']} samples), numpy FP64"}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,16 @@ void qtt_op_free(qtt_op* op);
 #define QTT_PRODUCT_CAP 4096
 qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_tensor** out);
 
+/* Per-kernel timing.  When enabled, each kernel launch of the library is
+ * bracketed by CUDA events on its stream (adds ~2 event records per launch).
+ * qtt_profile_read synchronises the device and writes, for up to cap kernel
+ * names, the name (names + i*name_stride, NUL-terminated), the summed
+ * milliseconds and the launch count; it returns the number of names.
+ * qtt_profile_reset drops the records. */
+void qtt_profile_enable(int on);
+int qtt_profile_read(char* names, int name_stride, double* ms, int* counts, int cap);
+void qtt_profile_reset(void);
+
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);
 

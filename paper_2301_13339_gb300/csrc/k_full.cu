@@ -86,6 +86,7 @@ void launch_morton_gather(const T* img, T* v, int dx, int dy, int interleave, cu
   offset_table_kernel<<<(int)(((1LL << a) + 255) / 256), 256, 0, s>>>(mm, 0, a, tlo);
   offset_table_kernel<<<(int)(((1LL << (d - a)) + 255) / 256), 256, 0, s>>>(mm, a, d - a, thi);
   const long long N = 1LL << d;
+  QTT_PROF("morton_gather", s);
   morton_gather_kernel<T><<<(int)((N + 255) / 256), 256, 0, s>>>(img, v, tlo, thi, a, N);
   scratch_free(tlo, s);
   scratch_free(thi, s);
@@ -240,6 +241,7 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
   for (int k = 1; k <= a; ++k) {
     T* Lnext = (k & 1) ? Lb0 : Lb1;
     const long long tot = (1LL << (k - 1)) * 2 * t->rcap[k];
+    QTT_PROF("full_partials", s);
     left_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(Lcur, cores + t->off[k - 1],
                                                                      t->ranks, k, t->rcap[k], Lnext);
     Lcur = Lnext;
@@ -251,6 +253,7 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
     T* Rnext = ((d - k) & 1) ? Rb1 : Rb0;
     const int ldo = t->rcap[k - 1];
     const long long tot = (long long)ldo << (d - k + 1);
+    QTT_PROF("full_partials", s);
     right_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(
         Rcur, ldcur, cores + t->off[k - 1], t->ranks, k, d, ldo, Rnext);
     Rcur = Rnext;
@@ -260,6 +263,7 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
   offset_table_kernel<<<(int)((nhi + 255) / 256), 256, 0, s>>>(mm, a, d - a, thi);
   order64_kernel<<<1, 64, 0, s>>>(tlo, a, order);
   dim3 grid((unsigned)((nlo + FX_TL - 1) / FX_TL), (unsigned)((nhi + FX_TH - 1) / FX_TH));
+  QTT_PROF("full_expand", s);
   expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, tlo, thi, order,
                                         y);
   scratch_free(Lb0, s);

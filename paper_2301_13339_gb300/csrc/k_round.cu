@@ -143,6 +143,100 @@ __global__ void k_normalize(T* A, long long n) {
   for (long long e = threadIdx.x; e < n; e += blockDim.x) A[e] = rscale(A[e], sc);
 }
 
+// ---------------------------------------------------------------- QR
+// One-CTA Householder QR of A = S^H (m x nc, m = rows of the basis, nc <= 64)
+// read from S (nc x m, ld ls); writes the first nq columns of Q (m x nq, ld m)
+// with orthonormal columns spanning the row space of S (Householder QR is
+// backward stable and keeps Q orthonormal also when S is rank deficient).
+// H_k = I - tau_k v_k v_k^H (LAPACK's convention), Q = H_1 ... H_kmax.
+constexpr int QR_THREADS = 256;
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS)
+k_house_q(const T* __restrict__ S, int ls, int m, int nc, int nq, T* __restrict__ Q) {
+  using R = typename Sc<T>::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);      // m x nc, ld m
+  T* E = A + (size_t)m * nc;                  // m x nq, ld m
+  __shared__ T s_tau[128];
+  __shared__ R s_red[QR_THREADS / 32];
+  __shared__ T s_scal;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_THREADS / 32;
+  for (int e = tid; e < m * nc; e += QR_THREADS) {
+    const int i = e % m, j = e / m;
+    A[e] = conjg(S[j + (size_t)ls * i]);
+  }
+  __syncthreads();
+  const int kmax = min(m, nc);
+  for (int k = 0; k < kmax; ++k) {
+    R part = (R)0;
+    for (int i = k + 1 + tid; i < m; i += QR_THREADS) part += sabs2(A[i + (size_t)m * k]);
+    part = warp_sum(part);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double xn2 = 0.0;
+      for (int w = 0; w < nw; ++w) xn2 += (double)s_red[w];
+      const double2 al = to_d2(A[k + (size_t)m * k]);
+      T tau = szero<T>(), scal = szero<T>();
+      if (xn2 > 0.0 || al.y != 0.0) {
+        const double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
+        const double beta = (al.x >= 0.0) ? -nrm : nrm;
+        from_d2(make_double2((beta - al.x) / beta, -al.y / beta), tau);
+        // scal = 1 / (alpha - beta)
+        const double dr = al.x - beta, di = al.y, den = dr * dr + di * di;
+        from_d2(make_double2(dr / den, -di / den), scal);
+        from_d2(make_double2(beta, 0.0), A[k + (size_t)m * k]);
+      }
+      s_tau[k] = tau;
+      s_scal = scal;
+    }
+    __syncthreads();
+    const T scal = s_scal, tau = s_tau[k];
+    for (int i = k + 1 + tid; i < m; i += QR_THREADS) A[i + (size_t)m * k] = smul(A[i + (size_t)m * k], scal);
+    __syncthreads();
+    // trailing columns: A <- (I - conj(tau) v v^H) A, v = [1; A[k+1:, k]]
+    const T ctau = conjg(tau);
+    for (int j = k + 1 + warp; j < nc; j += nw) {
+      T w = szero<T>();
+      for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
+        macc(w, vi, A[i + (size_t)m * j]);
+      }
+      w = warp_sum(w);
+      const T f = smul(ctau, w);
+      for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
+        A[i + (size_t)m * j] = ssub(A[i + (size_t)m * j], smul(vi, f));
+      }
+    }
+    __syncthreads();
+  }
+  // Q = H_1 ... H_kmax applied to the first nq columns of I
+  for (int e = tid; e < m * nq; e += QR_THREADS) {
+    const int i = e % m, j = e / m;
+    E[e] = (i == j) ? sone(T()) : szero<T>();
+  }
+  __syncthreads();
+  for (int k = kmax - 1; k >= 0; --k) {
+    const T tau = s_tau[k];
+    for (int j = warp; j < nq; j += nw) {
+      T w = szero<T>();
+      for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
+        macc(w, vi, E[i + (size_t)m * j]);
+      }
+      w = warp_sum(w);
+      const T f = smul(tau, w);
+      for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
+        E[i + (size_t)m * j] = ssub(E[i + (size_t)m * j], smul(vi, f));
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * nq; e += QR_THREADS) Q[e] = E[e];
+}
+
 // ---------------------------------------------------------------- step 2
 // B1[a + r0 (i + 2 (q + Pout t))] = sum_b X[a + r0 (i + 2 b)] C[(b + r1 q) + ldc t]
 template <typename T>
@@ -201,13 +295,9 @@ __global__ void k_gram_cols(const T* S, int ls, int n, double2* G, int ldg) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
   const int u = e % n, v = e / n;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int s2 = 0; s2 < ls; ++s2) {
-    const double2 a = to_d2(S[s2 + (size_t)ls * u]), b = to_d2(S[s2 + (size_t)ls * v]);
-    acc.x += a.x * b.x + a.y * b.y;     // conj(a) b
-    acc.y += a.x * b.y - a.y * b.x;
-  }
-  G[u + (size_t)ldg * v] = acc;
+  typename KAccOf<T>::type acc;
+  for (int s2 = 0; s2 < ls; ++s2) acc.add_cmul(S[s2 + (size_t)ls * u], S[s2 + (size_t)ls * v]);
+  G[u + (size_t)ldg * v] = to_d2(acc.get());
 }
 // SV[s + ls w] = sum_u S[s + ls u] V[u + n w]
 template <typename T>
@@ -265,13 +355,9 @@ __global__ void k_gram_rows(const T* Zt, const int* mptr, int mul, int mcap, int
   if (e >= mcap * mcap) return;
   const int a = e % mcap, b = e / mcap;
   if (a >= m || b >= m) return;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int u = 0; u < ncol; ++u) {
-    const double2 x = to_d2(Zt[a + (size_t)m * u]), y = to_d2(Zt[b + (size_t)m * u]);
-    acc.x += x.x * y.x + x.y * y.y;     // x conj(y)
-    acc.y += x.y * y.x - x.x * y.y;
-  }
-  G[a + (size_t)ldg * b] = acc;
+  typename KAccOf<T>::type acc;
+  for (int u = 0; u < ncol; ++u) acc.add_cmul(Zt[b + (size_t)m * u], Zt[a + (size_t)m * u]);
+  G[a + (size_t)ldg * b] = to_d2(acc.get());
 }
 // W[c + m u] = sum_a conj(U[a + m c]) Z[a + m u],  c < rows (= rmul * *rptr or m)
 template <typename T>
@@ -377,21 +463,31 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   // --- 1. Gaussian sketch cores and left sketches
   for (int k = 1; k < d; ++k) {
     const long long n = (long long)l[k - 1] * 2 * l[k];
+    { QTT_PROF("round_sketch", s);
     gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
                                                                               (uint32_t)k);
+    }
   }
   cudaMemcpyAsync(WL + wloff[0], one, sizeof(T), cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k < d; ++k) {
     const int l0 = l[k - 1], lk = l[k];
     const R* Ok = Oc + op->off[k - 1];
     const T* Xk = Xc + x->off[k - 1];
+    { QTT_PROF("round_sketch", s);
     k_a1<T, R><<<GRID1((long long)lk * 2 * Rc[k - 1])>>>(Om + omoff[k], l0, lk, WL + wloff[k - 1],
                                                          x->ranks, k, P[k - 1], Rc[k - 1], A1);
+    }
+    { QTT_PROF("round_sketch", s);
     k_a2<T><<<GRID1((long long)lk * 2 * P[k - 1] * 2 * xcap[k])>>>(A1, lk, Xk, x->ranks, k, P[k - 1],
                                                                    xcap[k], A2);
+    }
+    { QTT_PROF("round_sketch", s);
     k_wl<T, R><<<GRID1((long long)lk * Rc[k])>>>(Ok, P[k - 1], P[k], A2, lk, x->ranks, k, Rc[k],
                                                  WL + wloff[k]);
+    }
+    { QTT_PROF("round_sketch", s);
     k_normalize<T><<<1, 1024, 0, s>>>(WL + wloff[k], (long long)lk * Rc[k]);
+    }
   }
   // --- 2. right-to-left orthogonalising pass
   T* Ccur = C0;
@@ -402,29 +498,40 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     const R* Ok = Oc + op->off[k - 1];
     const T* Xk = Xc + x->off[k - 1];
     const int n2 = 2 * lq[k];
+    { QTT_PROF("round_orth", s);
     k_b1<T><<<GRID1((long long)xcap[k - 1] * 2 * P[k] * lq[k])>>>(Xk, x->ranks, k, xcap[k - 1], P[k],
                                                                    Ccur, ldc, lq[k], d, A2);
+    }
     const int ldz = Rc[k - 1];
     T* Zdst = (k == 1) ? Tpc + Tp->off[0] : Z;
+    { QTT_PROF("round_orth", s);
     k_z<T, R><<<GRID1((long long)xcap[k - 1] * P[k - 1] * 2 * lq[k])>>>(Ok, P[k - 1], P[k], A2, x->ranks,
                                                                         k, xcap[k - 1], lq[k], ldz, Zdst);
+    }
     if (k == 1) break;
     const int l0 = l[k - 1];
+    { QTT_PROF("round_orth", s);
     k_s<T><<<GRID1((long long)l0 * n2)>>>(WL + wloff[k - 1], l0, Z, ldz, x->ranks, k, P[k - 1], n2, S);
-    k_gram_cols<T><<<GRID1(n2 * n2)>>>(S, l0, n2, G, 128);
-    launch_eig_dense<T>(G, 128, nullptr, 0, n2, n2, 0 /*ALL*/, 0.0, d, 0, nullptr, 0, n2, nullptr,
-                        V1, nullptr, nullptr, nullptr, nullptr, 0, y->status, s);
-    const T* Vuse = V1;
-    if (refine) {
-      k_sv<T><<<GRID1(l0 * n2)>>>(S, l0, n2, V1, SV);
-      k_gram_cols<T><<<GRID1(n2 * n2)>>>(SV, l0, n2, G, 128);
-      launch_eig_dense<T>(G, 128, nullptr, 0, n2, n2, 0, 0.0, d, 0, nullptr, 0, n2, V1, SV2, V,
-                          nullptr, nullptr, nullptr, 0, y->status, s);
-      Vuse = V;
     }
     const int lq0 = lq[k - 1];
+    {
+      QTT_PROF("round_qr", s);
+      const size_t sm = sizeof(T) * ((size_t)n2 * l0 + (size_t)n2 * lq0);
+      static bool qr_cfg = false;
+      if (!qr_cfg) {
+        cudaFuncSetAttribute(k_house_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 2 * 128 * 64));
+        qr_cfg = true;
+      }
+      k_house_q<T><<<1, QR_THREADS, sm, s>>>(S, l0, n2, l0, lq0, V);
+    }
+    const T* Vuse = V;
+    { QTT_PROF("round_orth", s);
     k_qcore<T><<<GRID1(lq0 * n2)>>>(Vuse, n2, lq0, Tpc + Tp->off[k - 1]);
+    }
+    { QTT_PROF("round_orth", s);
     k_c<T><<<GRID1((long long)ldz * lq0)>>>(Z, ldz, Vuse, n2, lq0, x->ranks, k, P[k - 1], ldz, Cnext);
+    }
     std::swap(Ccur, Cnext);
     ldc = ldz;
   }
@@ -437,17 +544,25 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     const int lq0 = lq[k - 1], lqk = lq[k];
     const int tcap0 = ocap[k - 1];
     T* Ztd = (k == d) ? yc + y->off[d - 1] : Zt;
+    { QTT_PROF("round_trunc", s);
     k_zt<T><<<GRID1(2 * tcap0 * lqk)>>>(Lc, y->ranks, k, tcap0, Tpc + Tp->off[k - 1], lq0, lqk, Ztd);
+    }
     if (k == d) break;
     const int mcap = 2 * tcap0;
+    { QTT_PROF("round_trunc", s);
     k_gram_rows<T><<<GRID1(mcap * mcap)>>>(Zt, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
+    }
     T* corek = yc + y->off[k - 1];
     if (refine) {
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 0 /*ALL*/, tr.eps, d, rmax_eff,
                           nullptr, 0, lqk, nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1,
                           y->status, s);
+      { QTT_PROF("round_trunc", s);
       k_proj_rows<T><<<GRID1(mcap * lqk)>>>(V1, Zt, y->ranks + (k - 1), 2, nullptr, mcap, lqk, W1);
+      }
+      { QTT_PROF("round_trunc", s);
       k_gram_rows<T><<<GRID1(mcap * mcap)>>>(W1, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
+      }
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, tr.eps, d, rmax_eff,
                           nullptr, 0, lqk, V1, V, corek, y->ranks + k, nullptr, y->norm2, 0,
                           y->status, s);
@@ -457,8 +572,10 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
                           y->status, s);
     }
     // Lc = core_k^H Zt  (t_k x lq_k)
+    { QTT_PROF("round_trunc", s);
     k_proj_rows<T><<<GRID1(mcap * lqk)>>>(corek, Zt, y->ranks + (k - 1), 2, y->ranks + k, mcap, lqk,
                                           Lc);
+    }
   }
   st = cuda_check(cudaGetLastError(), "round launch");
   scratch_free(WL, s); scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);

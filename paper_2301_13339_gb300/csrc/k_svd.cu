@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   __shared__ int s_pp[EIG_MAXN / 2], s_pq[EIG_MAXN / 2];
   __shared__ R s_c[EIG_MAXN / 2], s_s[EIG_MAXN / 2];
   __shared__ T s_u[EIG_MAXN / 2];
-  __shared__ double s_d[EIG_MAXN / 2][2];
+  __shared__ R s_d[EIG_MAXN / 2][2];
   __shared__ int s_rot[EIG_MAXN / 2];
   __shared__ int s_nrot;
   __shared__ double s_lam[EIG_MAXN];
@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     if (a.write_norm2) *a.norm2 = t;
   }
 
-  const double tol = Sc<T>::eps;
-  const int maxsweep = Sc<T>::cplx ? 30 : 40;
+  const double tol = 4.0 * Sc<T>::eps;
+  const int maxsweep = Sc<T>::cplx ? 20 : 40;
   const int nb = np * (np + 1) / 2;
   bool converged = (n <= 1);
   for (int sweep = 0; sweep < maxsweep && !converged; ++sweep) {
@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
         s_c[tid] = (R)c;
         s_s[tid] = (R)s;
         s_u[tid] = u;
-        s_d[tid][0] = app - t * b;
-        s_d[tid][1] = aqq + t * b;
+        s_d[tid][0] = (R)(app - t * b);
+        s_d[tid][1] = (R)(aqq + t * b);
       }
       __syncthreads();
       for (int bi = tid; bi < nb; bi += EIG_THREADS) {
@@ -474,6 +474,7 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
                          (int)eig_smem_bytes<T>(EIG_MAXN));
     configured = true;
   }
+  QTT_PROF(mg_cap <= 32 ? "jacobi_eig_le32" : mg_cap <= 64 ? "jacobi_eig_le64" : "jacobi_eig_le128", s);
   gram_eig_kernel<T><<<1, EIG_THREADS, sm, s>>>(a);
 }
 
@@ -494,6 +495,7 @@ static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const 
                          (int)pg_smem_bytes<T>(true, 128, 128));
     configured = true;
   }
+  QTT_PROF("proj_gram", s);
   proj_gram_kernel<T, TM><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp,
                                                        ldp, mcap, rcap);
 }
@@ -524,6 +526,7 @@ static int launch_proj_gram(const T* M, const int* m_ptr, int m_mul, int mcap, l
 template <typename T>
 static void launch_reduce(const T* gp, int nparts, int ldp, double2* out, cudaStream_t s) {
   const int tot = ldp * ldp;
+  QTT_PROF("gram_reduce", s);
   gram_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(gp, nparts, ldp, out);
 }
 

@@ -81,6 +81,23 @@ __device__ __forceinline__ void rmac(float2& acc, float r, float2 b) {
   acc.y = fmaf(r, b.y, acc.y);
 }
 
+// Warp-wide sum of a T value with float shuffles for the FP32 path.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 // Compensated (Kahan) accumulation for the FP32 path: acc + comp carries the
 // sum of rounded products to ~1 ulp instead of ~sqrt(K) ulp.  FP64 sums are
 // plain.
@@ -211,6 +228,20 @@ qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc&
 void set_ranks_from_host(int* dev_ranks, const std::vector<int>& r, cudaStream_t s);
 // stream-ordered release of a handle
 void tensor_free_async(qtt_tensor* t, cudaStream_t s);
+
+// optional per-launch CUDA-event timing (qtt_profile_enable)
+struct ProfScope {
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+  const char* name_;
+  cudaStream_t s_;
+  bool active_;
+  void* a_ = nullptr;
+  void* b_ = nullptr;
+};
+#define QTT_PROF_CAT2(a, b) a##b
+#define QTT_PROF_CAT(a, b) QTT_PROF_CAT2(a, b)
+#define QTT_PROF(name, s) ::qtt::ProfScope QTT_PROF_CAT(_qtt_prof_, __LINE__)(name, s)
 
 // stream-ordered scratch allocation
 void* scratch_alloc(size_t bytes, cudaStream_t s);

@@ -175,7 +175,7 @@ def test_pipeline_c64_1d(qlib):
 
 @pytest.mark.parametrize("n", [16, 32])
 def test_pipeline_c64_2d(qlib, n):
-    # sizes whose rounding ranks stay below the sketch capacity (see DESIGN.md)
+    # sizes whose rounding ranks stay below the sketch capacity
     rng = synth.config_rng(2)
     x, _ = synth.image_2d_scene(rng, n, n, nscat=10, nrect=2, rect_min=4, rect_max=16)
     x = x.astype(np.complex64)
