@@ -121,6 +121,25 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
  * written back in row-major array order).  Asynchronous. */
 qtt_status qtt_to_full(const qtt_tensor* t, void* y, void* stream);
 
+/* qtt_to_full_noalloc -- the same expansion as qtt_to_full, for callers that
+ * must not allocate device memory after start-up: latency-critical loops in
+ * which a cudaMalloc (it can synchronise the device and its latency is
+ * unbounded) is not acceptable, and processes whose device memory is already
+ * reserved by another allocator, where a cudaMalloc could fail.  The paper
+ * has no counterpart: this is an interface variant, not a step of the method.
+ *   t, y    as qtt_to_full (the caller owns y; t is read only).
+ * Scratch: a static 16 MiB device array inside the library (every GPU that
+ * loads the library holds it until the process exits).  The expansion needs
+ * 2 (2^a + 2^(d-a)) rmax elements plus 8 (2^a + 2^(d-a)) bytes of index
+ * tables (a = d/2); QTT_EINVAL with a message when that exceeds 16 MiB.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (no allocation); make that first call before any
+ * stream capture.  No call allocates: no cudaMalloc, cudaFree or allocating
+ * library routine.  All calls share the one array and it keeps the last
+ * call's contents: calls that overlap on the GPU (different streams or
+ * threads) race and must be serialised by the caller.  Asynchronous. */
+qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* stream);
+
 /* qtt_conv_adjoint -- adjoint of qtt_conv_sinc's operator applied to r in
  * QTT (for the real even sinc kernel T^H = T: correlation with the flipped
  * kernel), rounded with round_tr.  If grad_cores is not NULL it must hold

@@ -18,7 +18,8 @@ from . import _build
 
 __all__ = [
     "QTTError", "QTTTensor", "QTTOperator", "lib", "load", "qtt_decompose", "qtt_conv_sinc",
-    "qtt_round", "qtt_to_full", "qtt_conv_adjoint", "qtt_matvec", "qtt_op_create",
+    "qtt_round", "qtt_to_full", "qtt_to_full_noalloc", "qtt_conv_adjoint", "qtt_matvec",
+    "qtt_op_create",
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
 ]
 
@@ -30,8 +31,8 @@ _STATUS = {0: "QTT_OK", -1: "QTT_EINVAL", -2: "QTT_ENOMEM", -3: "QTT_ECUDA",
            -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED"}
 
 EXPORTED_SYMBOLS = [
-    "qtt_decompose", "qtt_conv_sinc", "qtt_round", "qtt_to_full", "qtt_conv_adjoint",
-    "qtt_get_ranks", "qtt_get_info", "qtt_get_cores", "qtt_from_cores", "qtt_free",
+    "qtt_decompose", "qtt_conv_sinc", "qtt_round", "qtt_to_full", "qtt_to_full_noalloc",
+    "qtt_conv_adjoint", "qtt_get_ranks", "qtt_get_info", "qtt_get_cores", "qtt_from_cores", "qtt_free",
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version",
 ]
@@ -70,6 +71,7 @@ def load(path=None):
         "qtt_conv_sinc": (i, [vp, dp, i, d, tp, i, ull, vp, pp]),
         "qtt_round": (i, [vp, tp, i, ull, vp]),
         "qtt_to_full": (i, [vp, vp, vp]),
+        "qtt_to_full_noalloc": (i, [vp, vp, vp]),
         "qtt_conv_adjoint": (i, [vp, vp, dp, i, d, tp, i, ull, pp, pp, vp]),
         "qtt_get_ranks": (i, [vp, ip, vp]),
         "qtt_get_info": (i, [vp, ip, ip, ip, ip, ip]),
@@ -271,6 +273,19 @@ def qtt_to_full(t, out=None, stream=None):
     if out.dtype != dt or tuple(out.shape) != t.shape or not out.is_contiguous():
         raise ValueError("out has the wrong dtype/shape or is not contiguous")
     _check(_lib.qtt_to_full(t.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def qtt_to_full_noalloc(t, out, stream=None):
+    """Full into the caller's CUDA tensor ``out`` without any device
+    allocation by the library (scratch is a static device array; calls that
+    overlap on the GPU must be serialised by the caller)."""
+    import torch
+    load()
+    dt = torch.float64 if t.dtype_code == QTT_F64 else torch.complex64
+    if out.dtype != dt or tuple(out.shape) != t.shape or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype/shape or is not contiguous")
+    _check(_lib.qtt_to_full_noalloc(t.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

@@ -278,4 +278,120 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
 template qtt_status tt_full<double>(const qtt_tensor*, double*, cudaStream_t);
 template qtt_status tt_full<float2>(const qtt_tensor*, float2*, cudaStream_t);
 
+// --------------------------------------------------------------------------
+// Allocation-free variant of Full for callers that must not allocate device
+// memory after start-up: latency-critical loops where a cudaMalloc (which can
+// synchronise the device and has unbounded latency) is not acceptable, and
+// processes whose device memory is already reserved by another allocator,
+// where a cudaMalloc could fail.  The scratch (left/right partial products,
+// index tables) lives in the file-scope device array below; every GPU that
+// loads the library holds it until the process exits.
+constexpr size_t FULL_NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_full_noalloc_scratch[FULL_NOALLOC_SCRATCH_BYTES];
+
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device with that device current; the host-side symbol is only a
+// stand-in and must never be passed to a kernel).
+static qtt_status noalloc_scratch_ptr(void** out) {
+  int dev = 0;
+  qtt_status st = cuda_check(cudaGetDevice(&dev), "to_full_noalloc: cudaGetDevice");
+  if (st != QTT_OK) return st;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_error("to_full_noalloc: device index %d not supported", dev);
+    return QTT_EUNSUPPORTED;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    st = cuda_check(cudaGetSymbolAddress(&p, g_full_noalloc_scratch),
+                    "to_full_noalloc: cudaGetSymbolAddress");
+    if (st != QTT_OK) return st;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QTT_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename T>
+static qtt_status tt_full_noalloc_t(const qtt_tensor* t, T* y, cudaStream_t s) {
+  const TensorDesc& desc = t->desc;
+  const int d = desc.d;
+  ModeMap mm = make_mode_map(desc);
+  int a = d / 2;
+  if (desc.ndim == 2 && desc.interleave) a &= ~1;
+  if (a < 1) a = 1;
+  const long long nlo = 1LL << a, nhi = 1LL << (d - a);
+  int rmaxcap = 1;
+  for (int c : t->rcap) rmaxcap = std::max(rmaxcap, c);
+  const size_t lb = align256(sizeof(T) * (size_t)nlo * rmaxcap);
+  const size_t rb = align256(sizeof(T) * (size_t)nhi * rmaxcap);
+  const size_t tl = align256(sizeof(long long) * (size_t)nlo);
+  const size_t th = align256(sizeof(long long) * (size_t)nhi);
+  const size_t need = 2 * lb + 2 * rb + tl + th + align256(sizeof(int) * 64);
+  if (need > FULL_NOALLOC_SCRATCH_BYTES) {
+    set_error("qtt_to_full_noalloc: needs %zu bytes of scratch, the static limit is %zu bytes "
+              "(use qtt_to_full)", need, FULL_NOALLOC_SCRATCH_BYTES);
+    return QTT_EINVAL;
+  }
+  void* base = nullptr;
+  qtt_status st = noalloc_scratch_ptr(&base);
+  if (st != QTT_OK) return st;
+  char* p = (char*)base;
+  T* Lb0 = (T*)p; p += lb;
+  T* Lb1 = (T*)p; p += lb;
+  T* Rb0 = (T*)p; p += rb;
+  T* Rb1 = (T*)p; p += rb;
+  long long* tlo = (long long*)p; p += tl;
+  long long* thi = (long long*)p; p += th;
+  int* order = (int*)p;
+  // Every scratch element that is read below is first written in this call,
+  // so nothing has to be cleared between calls.
+  const T* cores = (const T*)t->cores;
+  T* Lcur = nullptr;
+  for (int k = 1; k <= a; ++k) {
+    T* Lnext = (k & 1) ? Lb0 : Lb1;
+    const long long tot = (1LL << (k - 1)) * 2 * t->rcap[k];
+    left_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(Lcur, cores + t->off[k - 1],
+                                                                     t->ranks, k, t->rcap[k], Lnext);
+    Lcur = Lnext;
+  }
+  T* Rcur = nullptr;
+  int ldcur = 0;
+  for (int k = d; k >= a + 1; --k) {
+    T* Rnext = ((d - k) & 1) ? Rb1 : Rb0;
+    const int ldo = t->rcap[k - 1];
+    const long long tot = (long long)ldo << (d - k + 1);
+    right_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(
+        Rcur, ldcur, cores + t->off[k - 1], t->ranks, k, d, ldo, Rnext);
+    Rcur = Rnext;
+    ldcur = ldo;
+  }
+  offset_table_kernel<<<(int)((nlo + 255) / 256), 256, 0, s>>>(mm, 0, a, tlo);
+  offset_table_kernel<<<(int)((nhi + 255) / 256), 256, 0, s>>>(mm, a, d - a, thi);
+  order64_kernel<<<1, 64, 0, s>>>(tlo, a, order);
+  dim3 grid((unsigned)((nlo + FX_TL - 1) / FX_TL), (unsigned)((nhi + FX_TH - 1) / FX_TH));
+  expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, tlo, thi, order,
+                                        y);
+  return cuda_check(cudaGetLastError(), "to_full_noalloc launch");
+}
+
+}  // namespace qtt
+
+extern "C" qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* stream) {
+  using namespace qtt;
+  if (!t || !y) {
+    set_error("qtt_to_full_noalloc: NULL argument");
+    return QTT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t->desc.dt == QTT_F64) return tt_full_noalloc_t<double>(t, (double*)y, s);
+  return tt_full_noalloc_t<float2>(t, (float2*)y, s);
+}
+
+namespace qtt {
+
 }  // namespace qtt
