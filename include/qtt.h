@@ -203,6 +203,19 @@ void qtt_profile_enable(int on);
 int qtt_profile_read(char* names, int name_stride, double* ms, int* counts, int cap);
 void qtt_profile_reset(void);
 
+/* qtt_small_eigh -- the one-CTA Hermitian eigen-decomposition behind every
+ * truncation (Alg. 1 "compute truncated SVD", done as eigen-decomposition of
+ * the unfolding's Gram matrix).  G: device n x n Hermitian as interleaved
+ * double pairs (re, im), column-major, n <= 128.  U: device, element type dt
+ * (QTT_C64: FP32 arithmetic, QTT_F64: real part of G, FP64 arithmetic),
+ * column-major n x n, columns ordered by descending eigenvalue.  lam: device
+ * double[n], descending.  Asynchronous. */
+qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam, void* stream);
+
+/* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
+ * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */
+void qtt_debug_set_eig_solver(int which);
+
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);
 

@@ -34,7 +34,8 @@ EXPORTED_SYMBOLS = [
     "qtt_decompose", "qtt_conv_sinc", "qtt_round", "qtt_to_full", "qtt_to_full_noalloc",
     "qtt_conv_adjoint", "qtt_get_ranks", "qtt_get_info", "qtt_get_cores", "qtt_from_cores", "qtt_free",
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
-    "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version",
+    "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
+    "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
 ]
 
 
@@ -85,6 +86,8 @@ def load(path=None):
         "qtt_op_free": (None, [vp]),
         "qtt_matvec": (i, [vp, vp, vp, pp]),
         "qtt_release_workspace": (None, []),
+        "qtt_small_eigh": (i, [vp, i, i, vp, vp, vp]),
+        "qtt_debug_set_eig_solver": (None, [i]),
         "qtt_last_error": (ctypes.c_char_p, []),
         "qtt_version": (ctypes.c_char_p, []),
     }
@@ -335,6 +338,28 @@ def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):
     _check(_lib.qtt_from_cores(buf.ctypes.data_as(ctypes.c_void_p), r, d, code, len(shape_log2),
                                sh, int(interleave), _stream(stream), ctypes.byref(out)))
     return QTTTensor(out)
+
+
+def qtt_small_eigh(G, dtype_code=QTT_C64, stream=None):
+    """Eigen-decomposition of a small Hermitian matrix with the library's
+    one-CTA solver: G (n x n, numpy or CUDA tensor) -> (lam desc, U)."""
+    import torch
+    load()
+    G = np.asarray(G.cpu().numpy() if hasattr(G, "cpu") else G, dtype=np.complex128)
+    n = G.shape[0]
+    Gd = torch.from_numpy(np.ascontiguousarray(G.T)).cuda()       # column-major
+    dt = torch.float64 if dtype_code == QTT_F64 else torch.complex64
+    U = torch.empty((n, n), dtype=dt, device="cuda")
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(_lib.qtt_small_eigh(ctypes.c_void_p(Gd.data_ptr()), n, int(dtype_code),
+                               ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                               _stream(stream)))
+    return lam.cpu().numpy(), U.cpu().numpy().T.copy()            # U[:, c] = eigenvector c
+
+
+def qtt_debug_set_eig_solver(which):
+    load()
+    _lib.qtt_debug_set_eig_solver(int(which))
 
 
 def version():

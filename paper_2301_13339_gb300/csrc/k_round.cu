@@ -22,14 +22,6 @@
 
 namespace qtt {
 
-// launch helpers implemented in k_svd.cu
-template <typename T>
-void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, int mg_const,
-                      int mg_cap, int mode, double eps, int dmodes, int rmax,
-                      const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
-                      T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
-                      int write_norm2, int* status, cudaStream_t s);
-
 // ---------------------------------------------------------------- Philox
 __host__ __device__ inline void philox_round(uint32_t c[4], const uint32_t k[2]) {
   const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
@@ -124,7 +116,9 @@ __global__ void k_wl(const R* O, int Pin, int Pout, const T* A2, int lk, const i
 // sketch of Y_{<=k} grows like (sqrt(l) ||Y_k||)^k; any scaling of a sketch
 // leaves its row space unchanged, so each WL_k is rescaled as it is formed.
 template <typename T>
-__global__ void k_normalize(T* A, long long n) {
+__global__ void k_normalize(T* A, int lk, const int* xr, int k, int Pout) {
+  // only the written prefix: columns c < P_k r_k (actual ranks)
+  const long long n = (long long)lk * Pout * xr[k];
   __shared__ float red[32];
   float mx = 0.f;
   for (long long e = threadIdx.x; e < n; e += blockDim.x) mx = fmaxf(mx, sqrtf((float)sabs2(A[e])));
@@ -486,7 +480,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
                                                  WL + wloff[k]);
     }
     { QTT_PROF("round_sketch", s);
-    k_normalize<T><<<1, 1024, 0, s>>>(WL + wloff[k], (long long)lk * Rc[k]);
+    k_normalize<T><<<1, 1024, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k]);
     }
   }
   // --- 2. right-to-left orthogonalising pass
@@ -563,9 +557,10 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
       { QTT_PROF("round_trunc", s);
       k_gram_rows<T><<<GRID1(mcap * mcap)>>>(W1, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
       }
+      // rank decision at eps_round: small eigenvalues to relative accuracy
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, tr.eps, d, rmax_eff,
                           nullptr, 0, lqk, V1, V, corek, y->ranks + k, nullptr, y->norm2, 0,
-                          y->status, s);
+                          y->status, s, 1);
     } else {
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1, tr.eps, d, rmax_eff, nullptr, 0,
                           lqk, nullptr, corek, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,

@@ -174,32 +174,6 @@ __global__ void gram_reduce_kernel(const T* __restrict__ part, int nparts, int l
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_MAXN = 128;
 
-enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
-
-template <typename T>
-struct EigArgs {
-  const double2* G;     // dense, ld = ldp
-  int ldp;
-  const int* mg_ptr;    // mg = mg_mul * *mg_ptr, or mg_const when mg_ptr is null
-  int mg_mul;
-  int mg_const;
-  int mode;
-  double eps;           // relative accuracy for the rank decision
-  int dmodes;           // d (number of modes) for tau = eps / sqrt(d-1) * ||A||
-  int rmax;             // cap (> 0)
-  const int* ncols_ptr; // ncols = ncols_mul * *ncols_ptr, or ncols_const if null
-  int ncols_mul;
-  long long ncols_const;
-  const T* U1;          // optional: core = U1 * U[:, :r] (U1 is mg x mg, ld mg)
-  T* Uout;              // sorted eigenvectors (ld = mg): all (MODE_ALL) or first r
-  T* core_out;          // optional: core (ld = mg, r columns)
-  int* rank_out;        // MODE_DECIDE: receives r
-  double* sig_out;      // optional: sorted eigenvalues
-  double* norm2;        // squared norm (read for tau; written when write_norm2)
-  int write_norm2;
-  int* status;
-};
-
 __device__ __forceinline__ int pk_idx(int i, int j) { return (j * (j + 1)) / 2 + i; }  // i <= j
 
 template <typename T>
@@ -465,8 +439,15 @@ static size_t eig_smem_bytes(int mg_cap) {
   return sizeof(T) * ((size_t)n * (n + 1) / 2 + (size_t)n * n);
 }
 
+static int g_eig_solver = 0;   // 0: tridiagonal solver for FP32, Jacobi for FP64; 1: Jacobi
+
 template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
+  if (Sc<T>::cplx && g_eig_solver == 0 && !a.relative) {
+    QTT_PROF(mg_cap <= 32 ? "heev_le32" : mg_cap <= 64 ? "heev_le64" : "heev_le128", s);
+    launch_heev_tri(reinterpret_cast<const EigArgs<float2>&>(a), mg_cap, s);
+    return;
+  }
   const size_t sm = eig_smem_bytes<T>(mg_cap);
   static bool configured = false;
   if (!configured) {
@@ -543,8 +524,9 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       int mg_cap, int mode, double eps, int dmodes, int rmax,
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
-                      int write_norm2, int* status, cudaStream_t s) {
-  EigArgs<T> a;
+                      int write_norm2, int* status, cudaStream_t s, int relative) {
+  EigArgs<T> a{};
+  a.relative = relative;
   a.G = G; a.ldp = ldp; a.mg_ptr = mg_ptr; a.mg_mul = mg_mul; a.mg_const = mg_const;
   a.mode = mode; a.eps = eps; a.dmodes = dmodes; a.rmax = rmax; a.ncols_ptr = ncols_ptr;
   a.ncols_mul = ncols_mul; a.ncols_const = ncols_const; a.U1 = U1; a.Uout = Uout;
@@ -638,11 +620,11 @@ template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_ten
 template void launch_eig_dense<double>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const double*,
                                        double*, double*, int*, double*, double*, int, int*,
-                                       cudaStream_t);
+                                       cudaStream_t, int);
 template void launch_eig_dense<float2>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const float2*,
                                        float2*, float2*, int*, double*, double*, int, int*,
-                                       cudaStream_t);
+                                       cudaStream_t, int);
 template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const double*, double*,
                                       double*, int*, double*, double*, int, int*, cudaStream_t);
@@ -651,3 +633,34 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
                                       float2*, int*, double*, double*, int, int*, cudaStream_t);
 
 }  // namespace qtt
+
+// Diagnostics: choose the FP32 eigen-solver (0 = tridiagonal, 1 = Jacobi).
+extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
+
+// Hermitian eigen-decomposition of one n x n matrix (n <= 128) with the
+// one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U
+// (device, element type of dt, ld n, columns by descending eigenvalue) and
+// lam (device, double, descending) out.
+extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam,
+                                     void* stream) {
+  using namespace qtt;
+  if (!G || !U || !lam || n < 1 || n > EIG_MAXN) {
+    set_error("qtt_small_eigh: bad argument");
+    return QTT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* nrm = (double*)scratch_alloc(sizeof(double), s);
+  if (dt == QTT_F64) {
+    EigArgs<double> a{};
+    a.G = (const double2*)G; a.ldp = n; a.mg_const = n; a.mode = EIG_MODE_ALL;
+    a.dmodes = 2; a.Uout = (double*)U; a.sig_out = lam; a.norm2 = nrm; a.write_norm2 = 1;
+    launch_eig<double>(a, n, s);
+  } else {
+    EigArgs<float2> a{};
+    a.G = (const double2*)G; a.ldp = n; a.mg_const = n; a.mode = EIG_MODE_ALL;
+    a.dmodes = 2; a.Uout = (float2*)U; a.sig_out = lam; a.norm2 = nrm; a.write_norm2 = 1;
+    launch_eig<float2>(a, n, s);
+  }
+  scratch_free(nrm, s);
+  return cuda_check(cudaGetLastError(), "qtt_small_eigh");
+}

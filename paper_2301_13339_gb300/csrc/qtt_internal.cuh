@@ -204,6 +204,49 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
                      int* status, cudaStream_t s);
 
+// ------------------------------------------------------------- eigen
+enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
+
+template <typename T>
+struct EigArgs {
+  const double2* G;     // dense, ld = ldp
+  int ldp;
+  const int* mg_ptr;    // mg = mg_mul * *mg_ptr, or mg_const when mg_ptr is null
+  int mg_mul;
+  int mg_const;
+  int mode;
+  double eps;           // relative accuracy for the rank decision
+  int dmodes;           // d (number of modes) for tau = eps / sqrt(d-1) * ||A||
+  int rmax;             // cap (> 0)
+  const int* ncols_ptr; // ncols = ncols_mul * *ncols_ptr, or ncols_const if null
+  int ncols_mul;
+  long long ncols_const;
+  const T* U1;          // optional: core = U1 * U[:, :r] (U1 is mg x mg, ld mg)
+  T* Uout;              // sorted eigenvectors (ld = mg): all (MODE_ALL) or first r
+  T* core_out;          // optional: core (ld = mg, r columns)
+  int* rank_out;        // MODE_DECIDE: receives r
+  double* sig_out;      // optional: sorted eigenvalues
+  double* norm2;        // squared norm (read for tau; written when write_norm2)
+  int write_norm2;
+  int* status;
+  int relative;         // 1: small eigenvalues needed to relative accuracy (Jacobi)
+};
+
+
+// one-CTA Hermitian eigensolvers (k_svd.cu: Jacobi; k_heev.cu: Householder
+// tridiagonalisation + bisection + twisted factorisation, FP32 path)
+void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s);
+size_t heev_tri_smem_bytes(int mg_cap);
+
+// eigen-decomposition of a dense double2 Gram (k_svd.cu); relative = 1 asks
+// for small eigenvalues to relative accuracy (Jacobi)
+template <typename T>
+void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, int mg_const,
+                      int mg_cap, int mode, double eps, int dmodes, int rmax,
+                      const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
+                      T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
+                      int write_norm2, int* status, cudaStream_t s, int relative = 0);
+
 // ------------------------------------------------------------- full
 template <typename T>
 qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s);
