@@ -245,16 +245,20 @@ def roofline(kernels, wl, peaks, peak_kind):
     # FP32 CUDA-core peak of the whole GPU: 152 SMs x 128 FMA/clk x 2 flop
     fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     N = 2 ** wl["d"]
-    if name.startswith("jacobi_eig"):
-        # one complex Hermitian eigen-decomposition of a 128 x 128 Gram per
-        # launch at the capped levels; algorithmic work counted as the
-        # LAPACK-style 9 n^3 real flops x 4 (complex)
+    if name.startswith("jacobi_eig") or name.startswith("heev"):
+        # one complex Hermitian eigen-decomposition of an n x n Gram per
+        # launch (n = 2 R_max at the capped levels); algorithmic work counted
+        # as LAPACK's ~9 n^3 real flop per real eigen-decomposition with
+        # vectors, x4 for complex arithmetic.  The kernel runs on one SM, so
+        # its peak is one SM's FP32 rate; the whole-GPU fraction is frac/152.
         n = 2 * wl["rmax"]
         flops = 9 * n ** 3 * 4
         ach = flops / (avg_ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "traffic": None,
-                "avg_launch_ms": avg_ms, "peak_source": f"152 SM x 128 FP32 FMA/clk at {sm_mhz:.0f} MHz"}
+        sm_peak = fp32_peak_tflops / 152
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": sm_peak,
+                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
+                "avg_launch_ms": avg_ms, "frac_of_gpu": ach / fp32_peak_tflops,
+                "peak_source": f"one SM: 128 FP32 FMA/clk at {sm_mhz:.0f} MHz (single-CTA kernel)"}
     if name in ("proj_gram", "full_expand", "morton_gather"):
         # algorithmic bytes: every launch streams its input unfolding once
         bytes_per_launch = 8.0 * N * 2 / max(kinfo["launches_per_step"], 1)

@@ -86,7 +86,7 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   if (fabsf(q) < pivmin) q = -pivmin;
   c += (q < 0.f);
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += (q < 0.f);
   }
@@ -103,11 +103,17 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __shared__ float2 s_scal, s_alpha2;
   __shared__ float s_xn2, s_glo, s_ghi, s_pivmin;
   __shared__ int s_r, s_clu[HMAX], s_pack[HT / 32];
+  __shared__ float2 s_part[4][HMAX];
+  __shared__ int s_bad[HMAX], s_clu0[HMAX];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+#define HEEV_STAMP(i) \
+  do { if (a.phase_clk && tid == 0) a.phase_clk[i] = clock64(); } while (0)
+  HEEV_STAMP(0);
   float2* A = reinterpret_cast<float2*>(smem_raw);        // n x n, ld n
-  float* Z = reinterpret_cast<float*>(A + (size_t)n * n);  // n x n, ld n
+  float* Z = reinterpret_cast<float*>(A + (size_t)n * n);  // n x n, ld ldz = n + 1
+  const int ldz = n + 1;
 
   // ---- load the Gram (double) and its trace
   double trl = 0.0;
@@ -129,6 +135,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     if (a.write_norm2) *a.norm2 = t;
   }
 
+  HEEV_STAMP(1);
   // ---- 1. Householder tridiagonalisation (lower)
   for (int k = 0; k < n - 1; ++k) {
     float part = 0.f;
@@ -171,21 +178,25 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     }
     __syncthreads();
     if (tau.x == 0.f && tau.y == 0.f) continue;
-    // p = tau * A22 v   (4 threads per row)
+    // p = tau * A22 v: thread t owns row k+1+(t & 127) and the columns
+    // congruent to (t >> 7) mod 4; lanes of a warp read consecutive rows
     {
-      const int g = tid >> 2, sub = tid & 3, i = k + 1 + g;
+      const int i = k + 1 + (tid & 127), ph = tid >> 7;
       float2 acc = make_float2(0.f, 0.f);
       if (i < n)
-        for (int j = k + 1 + sub; j < n; j += 4) {
+        for (int j = k + 1 + ph; j < n; j += 4) {
           const float2 aij = A[i + (size_t)n * j], vj = s_v[j];
           acc.x = fmaf(aij.x, vj.x, fmaf(-aij.y, vj.y, acc.x));
           acc.y = fmaf(aij.x, vj.y, fmaf(aij.y, vj.x, acc.y));
         }
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-      if (i < n && sub == 0) s_p[i] = cmulf(tau, acc);
+      s_part[ph][tid & 127] = acc;
+    }
+    __syncthreads();
+    for (int i = k + 1 + tid; i < n; i += HT) {
+      const int il = i - k - 1;
+      float2 acc = s_part[0][il];
+      for (int ph = 1; ph < 4; ++ph) { acc.x += s_part[ph][il].x; acc.y += s_part[ph][il].y; }
+      s_p[i] = cmulf(tau, acc);
     }
     __syncthreads();
     // alpha2 = -1/2 tau (p^H v)
@@ -218,17 +229,20 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       }
     }
     __syncthreads();
-    // A22 -= v w^H + w v^H
+    // A22 -= v w^H + w v^H: thread t owns row k+1+(t & 127), columns in
+    // steps of 4 from k+1+(t >> 7)
     {
-      const int L = n - k - 1;
-      for (int e = tid; e < L * L; e += HT) {
-        const int i = k + 1 + e % L, j = k + 1 + e / L;
-        const float2 vi = s_v[i], wi = s_p[i], vj = s_v[j], wj = s_p[j];
-        float2 x = A[i + (size_t)n * j];
-        // x -= vi conj(wj) + wi conj(vj)
-        x.x -= vi.x * wj.x + vi.y * wj.y + wi.x * vj.x + wi.y * vj.y;
-        x.y -= vi.y * wj.x - vi.x * wj.y + wi.y * vj.x - wi.x * vj.y;
-        A[i + (size_t)n * j] = x;
+      const int i = k + 1 + (tid & 127);
+      if (i < n) {
+        const float2 vi = s_v[i], wi = s_p[i];
+        for (int j = k + 1 + (tid >> 7); j < n; j += 4) {
+          const float2 vj = s_v[j], wj = s_p[j];
+          float2 x = A[i + (size_t)n * j];
+          // x -= vi conj(wj) + wi conj(vj)
+          x.x -= vi.x * wj.x + vi.y * wj.y + wi.x * vj.x + wi.y * vj.y;
+          x.y -= vi.y * wj.x - vi.x * wj.y + wi.y * vj.x - wi.x * vj.y;
+          A[i + (size_t)n * j] = x;
+        }
       }
     }
     __syncthreads();
@@ -252,6 +266,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   }
   __syncthreads();
 
+  HEEV_STAMP(2);
   // ---- 2. eigenvalues: 5-section with 4 threads per eigenvalue (ascending index)
   {
     const int g = tid >> 2, sub = tid & 3;
@@ -312,7 +327,10 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     s_r = r;
     // clusters over the descending order: c joins c-1's cluster when close
     const float tn = fmaxf(fabsf(s_glo), fabsf(s_ghi));
-    const float ortol = 1e-3f * tn;
+    // clusters for Gram-Schmidt: gaps at which FP32 eigenvectors are not
+    // resolved (eps ||T|| / gap of order one); wider gaps are handled by
+    // the Newton-Schulz orthonormalisation below
+    const float ortol = 1e-6f * tn;
     int cid = 0;
     for (int c = 0; c < n; ++c) {
       if (c > 0 && fabsf(s_lam[n - 1 - c] - s_lam[n - c]) > ortol) cid = c;
@@ -325,9 +343,10 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   if (a.sig_out)
     for (int c = tid; c < n; c += HT) a.sig_out[c] = (double)s_lam[n - 1 - c];
 
+  HEEV_STAMP(3);
   // ---- 3. eigenvectors of T (descending order, one thread per vector)
   for (int c = tid; c < ncopy; c += HT)
-    twisted_vector(s_d, s_e, n, s_lam[n - 1 - c], s_pivmin, Z + (size_t)n * c);
+    twisted_vector(s_d, s_e, n, s_lam[n - 1 - c], s_pivmin, Z + (size_t)ldz * c);
   __syncthreads();
 
   // ---- 4. Gram-Schmidt (twice) of every vector against all earlier ones, in
@@ -336,14 +355,17 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   // eigenvalues of a rank-deficient Gram: the twisted factorisation returns
   // the same vector for equal shifts) is completed at the end from unit
   // vectors orthogonalised against all the others.
+  HEEV_STAMP(4);
   float* coef = reinterpret_cast<float*>(s_p);   // s_p is free after step 1
-  int* bad = s_clu;                              // flags (cluster ids no longer needed)
-  for (int c = tid; c < ncopy; c += HT) bad[c] = 0;
+  int* bad = s_bad;
+  for (int c = tid; c < ncopy; c += HT) { bad[c] = 0; s_clu0[c] = s_clu[c]; }
   __syncthreads();
   for (int sweep = 0; sweep < 2; ++sweep) {
     // sweep 0: all vectors in order; sweep 1: complete the flagged ones
     for (int c = 0; c < ncopy; ++c) {
       if (sweep == 1 && !bad[c]) continue;               // uniform (smem flag)
+      const int clu0 = s_clu0[c];
+      if (sweep == 0 && clu0 == c) continue;             // first of its cluster: kept as is
       {
         if (sweep == 1) {
           // candidate: the unit vector e_i with the largest component outside
@@ -354,7 +376,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           for (int i = tid; i < n; i += HT) {
             float pr = 0.f;
             for (int j = 0; j < ncopy; ++j)
-              if (j != c && !bad[j]) pr = fmaf(Z[i + (size_t)n * j], Z[i + (size_t)n * j], pr);
+              if (j != c && !bad[j]) pr = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * j], pr);
             const float res = 1.f - pr;
             if (res > best) { best = res; bi = i; }
           }
@@ -375,30 +397,38 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           }
           __syncthreads();
           const int ui = s_pack[0];
-          for (int i = tid; i < n; i += HT) Z[i + (size_t)n * c] = (i == ui) ? 1.f : 0.f;
+          for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] = (i == ui) ? 1.f : 0.f;
           __syncthreads();
         }
         for (int pass = 0; pass < 2; ++pass) {
           for (int j = warp; j < ncopy; j += HT / 32) {
             float h = 0.f;
-            const bool use = (j != c) && !bad[j] && (sweep == 1 || j < c);
+            const bool use = (j != c) && !bad[j] && (sweep == 1 || (j < c && j >= clu0));
             if (use)
-              for (int i = lane; i < n; i += 32) h = fmaf(Z[i + (size_t)n * j], Z[i + (size_t)n * c], h);
+              for (int i = lane; i < n; i += 32) h = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * c], h);
             h = warp_sum(h);
             if (lane == 0) coef[j] = use ? h : 0.f;
           }
           __syncthreads();
-          for (int i = tid; i < n; i += HT) {
-            float acc = Z[i + (size_t)n * c];
+          {
+            // 4 partial sums per row (thread t: row t & 127, j = t >> 7 mod 4)
+            const int i = tid & 127, ph = tid >> 7;
             const int jend = (sweep == 0) ? c : ncopy;
-            for (int j = 0; j < jend; ++j) acc = fmaf(-coef[j], Z[i + (size_t)n * j], acc);
-            Z[i + (size_t)n * c] = acc;
+            float acc = 0.f;
+            if (i < n)
+              for (int j = ph; j < jend; j += 4) acc = fmaf(coef[j], Z[i + (size_t)ldz * j], acc);
+            ((float*)s_part)[ph * HMAX + i] = acc;
+          }
+          __syncthreads();
+          for (int i = tid; i < n; i += HT) {
+            const float* pp = (const float*)s_part;
+            Z[i + (size_t)ldz * c] -= pp[i] + pp[HMAX + i] + pp[2 * HMAX + i] + pp[3 * HMAX + i];
           }
           __syncthreads();
         }
         float part = 0.f;
         for (int i = tid; i < n; i += HT) {
-          const float z = Z[i + (size_t)n * c];
+          const float z = Z[i + (size_t)ldz * c];
           part = fmaf(z, z, part);
         }
         part = warp_sum(part);
@@ -417,12 +447,13 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
         __syncthreads();
         const float sc = s_xn2;
         if (sc > 0.f)
-          for (int i = tid; i < n; i += HT) Z[i + (size_t)n * c] *= sc;
+          for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] *= sc;
         __syncthreads();
       }
     }
   }
 
+  HEEV_STAMP(5);
   // ---- 5. U = Q Z: compact the reflectors, then transform column chunks
   // packed reflector k (rows k+2..n-1) at offset P_k = sum_{k'<k} (n - k' - 2)
   const int npack = (n >= 2) ? (n - 2) * (n - 1) / 2 : 0;
@@ -441,22 +472,103 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     for (int e = tid; e < npack && cnt < 16; e += HT, ++cnt) A[e] = buf[cnt];
     __syncthreads();
   }
+  // ---- 4b. Newton-Schulz orthonormalisation Z <- Z (3 I - Z^T Z) / 2.
+  // The vectors of distinct eigenvalues are orthogonal to O(eps ||T|| / gap)
+  // (the accuracy order of any backward-stable solver); each step squares
+  // the defect.  G = Z^T Z (dense) sits in the part of A freed by packing
+  // the reflectors; the new Z passes through Uout (global, this kernel's own
+  // output, overwritten by the back-transformation).  Both products use
+  // 4 x 8 register tiles per thread.
+  {
+    float* Gd = reinterpret_cast<float*>(A + npack);             // ncopy x ncopy
+    float* Zn = reinterpret_cast<float*>(a.Uout);                 // n x ncopy floats
+    // tile: 4 rows spaced 32 apart (consecutive across the lanes of a warp)
+    // x 8 columns (uniform across the warp: broadcast loads)
+    const int nrb = (ncopy + 127) / 128, ncb = (ncopy + 7) / 8;
+    for (int it = 0; it < 3; ++it) {
+      // G = Z^T Z
+      for (int t = warp; t < nrb * ncb; t += HT / 32) {
+        const int i0 = (t % nrb) * 128 + lane, j0 = (t / nrb) * 8;
+        float acc[4][8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+        for (int l = 0; l < n; ++l) {
+          float zi[4], zj[8];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int i = i0 + 32 * x;
+            zi[x] = (i < ncopy) ? Z[l + (size_t)ldz * i] : 0.f;
+          }
+#pragma unroll
+          for (int y = 0; y < 8; ++y) zj[y] = (j0 + y < ncopy) ? Z[l + (size_t)ldz * (j0 + y)] : 0.f;
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(zi[x], zj[y], acc[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) {
+            const int i = i0 + 32 * x;
+            if (i < ncopy && j0 + y < ncopy) Gd[i + (size_t)ncopy * (j0 + y)] = acc[x][y];
+          }
+      }
+      __syncthreads();
+      // Zn = 1.5 Z - 0.5 Z G
+      const int nrz = (n + 127) / 128;
+      for (int t = warp; t < nrz * ncb; t += HT / 32) {
+        const int i0 = (t % nrz) * 128 + lane, c0 = (t / nrz) * 8;
+        float acc[4][8];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+        for (int l = 0; l < ncopy; ++l) {
+          float zl[4], gl[8];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int i = i0 + 32 * x;
+            zl[x] = (i < n) ? Z[i + (size_t)ldz * l] : 0.f;
+          }
+#pragma unroll
+          for (int y = 0; y < 8; ++y) gl[y] = (c0 + y < ncopy) ? Gd[l + (size_t)ncopy * (c0 + y)] : 0.f;
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(zl[x], gl[y], acc[x][y]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) {
+            const int i = i0 + 32 * x, c = c0 + y;
+            if (i < n && c < ncopy) Zn[i + (size_t)n * c] = 1.5f * Z[i + (size_t)ldz * c] - 0.5f * acc[x][y];
+          }
+      }
+      __syncthreads();
+      for (int e = tid; e < n * ncopy; e += HT) Z[(e % n) + (size_t)ldz * (e / n)] = Zn[e];
+      __syncthreads();
+    }
+  }
   float2* Vp = A;                                  // packed reflectors
   float2* Uc = A + npack;                          // column chunk after them
   // columns per chunk: what fits in the rest of the n x n region, at most 64
-  // (the back-transformation maps 8 threads to a column)
-  const int cw = min(64, (n * n - npack) / n);
+  // (the back-transformation maps 8 threads to a column); leading dimension
+  // n + 1 keeps the 4 column groups of a warp on different banks
+  const int ldu = n + 1;
+  const int cw = max(1, min(64, (n * n - npack) / ldu));
   for (int cb = 0; cb < ncopy; cb += cw) {
     const int nc = min(cw, ncopy - cb);
-    for (int e = tid; e < n * nc; e += HT) {
-      const int i = e % n, c = e / n;
-      Uc[e] = make_float2(Z[i + (size_t)n * (cb + c)], 0.f);
-    }
+    for (int c = tid >> 7; c < nc; c += HT / 128)
+      for (int i = tid & 127; i < n; i += 128) Uc[i + (size_t)ldu * c] = make_float2(Z[i + (size_t)ldz * (cb + c)], 0.f);
     __syncthreads();
     // 8 threads per column; the group owns the column for all reflectors
     const int c = tid >> 3, sub = tid & 7;
     if (c < nc) {
-      float2* u = Uc + (size_t)n * c;
+      float2* u = Uc + (size_t)ldu * c;
       for (int k = n - 2; k >= 0; --k) {
         const float2 tau = s_tau[k];
         if (tau.x == 0.f && tau.y == 0.f) continue;
@@ -487,10 +599,12 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       }
     }
     __syncthreads();
-    for (int e = tid; e < n * nc; e += HT) a.Uout[(size_t)n * cb + e] = Uc[e];
+    for (int c = tid >> 7; c < nc; c += HT / 128)
+      for (int i = tid & 127; i < n; i += 128) a.Uout[(size_t)n * (cb + c) + i] = Uc[i + (size_t)ldu * c];
     __syncthreads();
   }
   __syncthreads();
+  HEEV_STAMP(6);
   if (a.core_out) {
     if (a.U1) {
       for (int e = tid; e < n * r; e += HT) {
@@ -503,10 +617,11 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       for (int e = tid; e < n * r; e += HT) a.core_out[e] = a.Uout[e];
     }
   }
+  HEEV_STAMP(7);
 }
 
 size_t heev_tri_smem_bytes(int mg_cap) {
-  return (size_t)mg_cap * mg_cap * (sizeof(float2) + sizeof(float));
+  return (size_t)mg_cap * mg_cap * sizeof(float2) + (size_t)mg_cap * (mg_cap + 1) * sizeof(float);
 }
 
 void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s) {

@@ -511,6 +511,18 @@ static void launch_reduce(const T* gp, int nparts, int ldp, double2* out, cudaSt
   gram_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(gp, nparts, ldp, out);
 }
 
+// Identity core of a level that keeps full rank: r_{k-1} = rp, r_k = 2 rp,
+// core (alpha, i, beta) = [beta == alpha + rp i]  (U = I of the 2rp x 2rp unfolding).
+template <typename T>
+__global__ void identity_level_kernel(T* core, int rp, int* ranks, int k) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = 2 * rp;
+  if (e == 0) ranks[k] = m;
+  if (e >= m * m) return;
+  const int row = e % m, col = e / m;
+  core[e] = (row == col) ? sone(T()) : szero<T>();
+}
+
 __global__ void set_boundary_ranks_kernel(int* ranks, int d) {
   if (threadIdx.x == 0) {
     ranks[0] = 1;
@@ -569,12 +581,26 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   set_boundary_ranks_kernel<<<1, 32, 0, s>>>(t->ranks, d);
   T* cores = (T*)t->cores;
   int* rk = t->ranks;
-  // Gram of the first unfolding (2 x 2^{d-1})
-  int nparts = launch_proj_gram<T>(v, rk + 0, 2, 2, N / 2, nullptr, nullptr, 0, nullptr, 0, gp,
-                                   2, max_parts, s);
-  int ldp = 2;
+  // Cap-only truncation (eps = 0): a level whose unfolding has
+  // m = 2^k <= min(R_max, n_k) rows keeps every singular value (Alg. 1 with
+  // tau = 0 keeps min(m, n) of them), so U can be the identity and
+  // Sigma V^* is the unfolding itself: no factorisation, no data pass.
+  int skip = 0;
+  if (tr.eps == 0.0)
+    while (skip + 1 <= d - 2 && (1LL << (skip + 1)) <= std::min<long long>(rmax_eff, 1LL << (d - skip - 1)))
+      ++skip;
+  for (int k = 1; k <= skip; ++k) {
+    const int rp = 1 << (k - 1);
+    QTT_PROF("identity_level", s);
+    identity_level_kernel<T><<<(4 * rp * rp + 255) / 256, 256, 0, s>>>(cores + t->off[k - 1], rp, rk, k);
+  }
+  // Gram of the first factored unfolding (2^{skip+1} x 2^{d-skip-1})
+  const int m0cap = 2 * t->rcap[skip];
+  int nparts = launch_proj_gram<T>(v, rk + skip, 2, m0cap, N >> (skip + 1), nullptr, nullptr, 0,
+                                   nullptr, 0, gp, m0cap, max_parts, s);
+  int ldp = m0cap;
   const T* M = v;
-  for (int k = 1; k <= d - 1; ++k) {
+  for (int k = skip + 1; k <= d - 1; ++k) {
     const long long n = N >> k;
     const int mcap = 2 * t->rcap[k - 1];
     const int rcapk = t->rcap[k];
@@ -586,7 +612,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       // pass 1: all eigenvectors of M M^H
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
                          nullptr, 0, n, nullptr, U1, nullptr, nullptr, nullptr, t->norm2,
-                         k == 1, t->status, s);
+                         k == skip + 1, t->status, s);
       // W1 = U1^H M, Gram of W1
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
                                    mcap, max_parts, s);
@@ -600,7 +626,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
     } else {
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
-                         t->norm2, k == 1, t->status, s);
+                         t->norm2, k == skip + 1, t->status, s);
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, core_k, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     }
@@ -641,6 +667,9 @@ extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which;
 // one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U
 // (device, element type of dt, ld n, columns by descending eigenvalue) and
 // lam (device, double, descending) out.
+static long long* g_small_eigh_clk = nullptr;   // diagnostics: phase clocks of the next call
+extern "C" void qtt_debug_small_eigh_clocks(long long* dev8) { g_small_eigh_clk = dev8; }
+
 extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam,
                                      void* stream) {
   using namespace qtt;
@@ -659,6 +688,7 @@ extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U
     EigArgs<float2> a{};
     a.G = (const double2*)G; a.ldp = n; a.mg_const = n; a.mode = EIG_MODE_ALL;
     a.dmodes = 2; a.Uout = (float2*)U; a.sig_out = lam; a.norm2 = nrm; a.write_norm2 = 1;
+    a.phase_clk = g_small_eigh_clk;
     launch_eig<float2>(a, n, s);
   }
   scratch_free(nrm, s);

@@ -230,6 +230,7 @@ struct EigArgs {
   int write_norm2;
   int* status;
   int relative;         // 1: small eigenvalues needed to relative accuracy (Jacobi)
+  long long* phase_clk; // optional: clock64() at phase boundaries (diagnostics)
 };
 
 
