@@ -279,7 +279,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="line_2p20_c64", choices=sorted(WORKLOADS))
-    ap.add_argument("--refine", type=int, default=0, help="second Gram pass in the TT-SVD")
+    ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -87,3 +87,66 @@ def conv_dense(x, B, normalize=True):
     Bx, By = (B, B) if np.isscalar(B) else B
     return C.conv2d_fft(x.astype(np.result_type(x, np.float64)),
                         C.sinc_taps(nx, Bx, normalize), C.sinc_taps(ny, By, normalize))
+
+
+# --------------------------------------------------------------------------
+# Deconvolution loss and its gradient (the differentiable use of the
+# convolution step): L(F) = || full(T F) - g ||_2^2 for a QTT tensor F.
+# T is the sinc Toeplitz operator; for the real even kernel T^H = T.
+# Gradient convention: the one PyTorch uses for complex leaves, i.e.
+# 2 dL/d conj(F_k); for real data it is the ordinary gradient.
+# --------------------------------------------------------------------------
+def apply_T_dense(v, shape, B, normalize=True):
+    """T v on the dense array (Eq. dconv via FFT)."""
+    return conv_dense(np.asarray(v).reshape(shape), B, normalize)
+
+
+def deconv_loss(cores, shape, B, g, normalize=True, interleave=True):
+    f = to_array(cores, shape, interleave)
+    r = apply_T_dense(f, shape, B, normalize) - g
+    return float(np.vdot(r, r).real)
+
+
+def deconv_dense_grad(cores, shape, B, g, normalize=True, interleave=True):
+    """w = 2 T^H (T f - g) on the dense array (T^H = T for the even real sinc)."""
+    f = to_array(cores, shape, interleave)
+    r = apply_T_dense(f, shape, B, normalize) - g
+    return 2.0 * apply_T_dense(r, shape, B, normalize)
+
+
+def core_grads(cores, w_qtt_vector):
+    """grad_k[a, i, b] = sum over the other indices of w * conj(left partial)
+    * conj(right partial): the chain rule through f = F_1 ... F_d.
+
+    w_qtt_vector: the dense w in QTT order (length 2^d).
+    """
+    d = len(cores)
+    grads = []
+    for k in range(d):
+        # left partial products of modes < k: (2^k, r_{k-1}); right: (r_k, 2^{d-k-1})
+        Lp = np.ones((1, 1), dtype=cores[0].dtype) if k == 0 else _left_partial(cores[:k])
+        Rp = _right_partial(cores[k + 1:]) if k < d - 1 else np.ones((1, 1), dtype=cores[0].dtype)
+        nl, nr = Lp.shape[0], Rp.shape[1]
+        W = w_qtt_vector.reshape((nl, 2, nr), order='F')
+        gk = np.einsum('lir,la,br->aib', W, np.conj(Lp), np.conj(Rp))
+        grads.append(gk)
+    return grads
+
+
+def _left_partial(cores):
+    """(2^k, r_k) matrix of the first k cores, row index low bits first."""
+    A = cores[0].reshape((2, -1), order='F')
+    for c in cores[1:]:
+        rp = c.shape[0]
+        A = A.reshape((-1, rp), order='F') @ c.reshape((rp, -1), order='F')
+    return A.reshape((-1, cores[-1].shape[2]), order='F')
+
+
+def _right_partial(cores):
+    """(r_k, 2^{d-k}) matrix of the cores after the cut, column index low bits first."""
+    R = cores[-1].reshape((cores[-1].shape[0], 2), order='F')
+    for c in reversed(cores[:-1]):
+        r0, _, r1 = c.shape
+        # R_new[a, i + 2 rest] = sum_b c[a, i, b] R[b, rest]
+        R = np.einsum('aib,bz->aiz', c, R).reshape((r0, -1), order='F')
+    return R
