@@ -50,7 +50,8 @@ typedef enum {
   QTT_ECUDA = -3,         /* a CUDA runtime call failed                        */
   QTT_ETIMEOUT = -4,      /* a device iteration limit was reached              */
   QTT_ERANK = -5,         /* a rank exceeded its capacity                      */
-  QTT_EUNSUPPORTED = -6   /* valid request this build does not implement       */
+  QTT_EUNSUPPORTED = -6,  /* valid request this build does not implement       */
+  QTT_ENUMERIC = -7       /* non-finite values (NaN / Inf) met in the data     */
 } qtt_status;
 
 typedef enum { QTT_F64 = 0, QTT_C64 = 2 } qtt_dtype;
@@ -140,17 +141,68 @@ qtt_status qtt_to_full(const qtt_tensor* t, void* y, void* stream);
  * threads) race and must be serialised by the caller.  Asynchronous. */
 qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* stream);
 
-/* qtt_conv_adjoint -- adjoint of qtt_conv_sinc's operator applied to r in
- * QTT (for the real even sinc kernel T^H = T: correlation with the flipped
- * kernel), rounded with round_tr.  If grad_cores is not NULL it must hold
- * d device pointers; core k receives dL/dconj(F_k) of
- * L(F) = ||full(T F) - g||^2 where r = full(T F) - g is given in QTT:
- * the contraction of w = 2 T^H r with the left/right partial products of
- * f's cores (environment sweeps).  adj_out (may be NULL) receives T^H r. */
+/* qtt_conv_adjoint -- the adjoint of qtt_conv_sinc's operator applied to a
+ * QTT tensor r, then TT-rounded with round_tr, and optionally the core
+ * gradients of the least-squares deconvolution loss.  This is the
+ * differentiation of the convolution step (Alg. 2 step 3) for gradient-based
+ * deconvolution with the kernel of Eq. GAF; the paper itself only applies T.
+ *   f          QTT tensor whose core gradients are wanted (may be NULL when
+ *              grad_cores is NULL); same shape, type and mode order as r.
+ *   r          the residual full(T f) - g in QTT form (read only).
+ *   B, normalize, eps_op   the forward operator's parameters, as in
+ *              qtt_conv_sinc.  T^H is built from the forward operator's
+ *              cores with j and i swapped (the cores are real), so it is the
+ *              exact adjoint of the discrete operator qtt_conv_sinc applies;
+ *              for the even sinc it is correlation with the flipped kernel
+ *              and equals T up to eps_op.  2D: T^H = T_x^H T_y^H, each
+ *              factor followed by a rounding.
+ *   round_tr, sketch, seed  rounding of T^H r, as in qtt_conv_sinc.
+ *   grad_cores NULL, or d device pointers; pointer k receives, in f's core
+ *              layout at f's current ranks (r_{k-1} x 2 x r_k column-major),
+ *              the gradient 2 dL/dconj(F_k) of L(F) = ||full(T F) - g||^2,
+ *              i.e. the contraction of w = 2 T^H r with the left and right
+ *              partial products of f's cores (environment sweeps).  For real
+ *              data this is the ordinary gradient; for complex data it is
+ *              the convention of PyTorch's complex autograd.
+ *   adj_out    NULL, or receives a new handle holding round(T^H r).
+ * Asynchronous.  QTT_EINVAL on mismatched handles or NULL grad pointers;
+ * QTT_EUNSUPPORTED when f's and the adjoint's rank capacities exceed the
+ * environment sweep's shared memory (max rank product above 64 x 64 for
+ * complex64 / real float64 handles with wider products). */
 qtt_status qtt_conv_adjoint(const qtt_tensor* f, const qtt_tensor* r, const double* B,
                             int normalize, double eps_op, const qtt_trunc* round_tr,
                             int sketch, unsigned long long seed, void* const* grad_cores,
                             qtt_tensor** adj_out, void* stream);
+
+/* qtt_core_grads -- the chain rule through Full (Alg. 3) alone: for a QTT
+ * vector w of f's shape, grad_k = alpha * C_k(f, w) + beta * grad_k where
+ * C_k(f, w)[a, i, b] = sum over the other modes of w * conj(left partial
+ * product of f up to core k-1)[., a] * conj(right partial product of f from
+ * core k+1)[b, .].  Used with w = T^H g to subtract the target's share from
+ * the gradient.  grad_cores as in qtt_conv_adjoint (beta = 0: overwrite).
+ * Asynchronous. */
+qtt_status qtt_core_grads(const qtt_tensor* f, const qtt_tensor* w, double alpha, double beta,
+                          void* const* grad_cores, void* stream);
+
+/* qtt_dot -- <x, y> = sum_n conj(x[n]) y[n] of two QTT tensors of the same
+ * shape (left-to-right environment sweep, O(d r^3)).  out_dev: DEVICE
+ * memory for two doubles (real, imaginary part).  Asynchronous.  The sum is
+ * carried in the handles' arithmetic (FP32 for QTT_C64). */
+qtt_status qtt_dot(const qtt_tensor* x, const qtt_tensor* y, double* out_dev, void* stream);
+
+/* qtt_add -- new handle alpha x + beta y (the TT sum: block-diagonal
+ * cores, ranks r_x + r_y in the interior, each at most QTT_PRODUCT_CAP; no
+ * rounding -- follow with qtt_round).  Asynchronous. */
+qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_tensor* y,
+                   void* stream, qtt_tensor** out);
+
+/* qtt_from_device_cores -- new handle holding copies of d cores given in
+ * DEVICE memory, core k at cores[k] in the packed column-major layout
+ * r_{k-1} x 2 x r_k (ranks: d+1 host ints, r_0 = r_d = 1).  The caller keeps
+ * ownership of its buffers.  Asynchronous (stream-ordered copies). */
+qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int d, qtt_dtype dt,
+                                 int ndim, const int* log2_shape, int interleave, void* stream,
+                                 qtt_tensor** out);
 
 /* Handle inspection and construction (tests, checkpoints). */
 /* ranks_host: d+1 ints r_0..r_d.  Synchronises; returns the device status. */

@@ -28,7 +28,7 @@ QTT_C64 = 2
 QTT_RANK_CAP = 64
 
 _STATUS = {0: "QTT_OK", -1: "QTT_EINVAL", -2: "QTT_ENOMEM", -3: "QTT_ECUDA",
-           -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED"}
+           -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED", -7: "QTT_ENUMERIC"}
 
 EXPORTED_SYMBOLS = [
     "qtt_decompose", "qtt_conv_sinc", "qtt_round", "qtt_to_full", "qtt_to_full_noalloc",
@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = [
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
+    "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
 ]
 
 
@@ -74,6 +75,10 @@ def load(path=None):
         "qtt_to_full": (i, [vp, vp, vp]),
         "qtt_to_full_noalloc": (i, [vp, vp, vp]),
         "qtt_conv_adjoint": (i, [vp, vp, dp, i, d, tp, i, ull, pp, pp, vp]),
+        "qtt_core_grads": (i, [vp, vp, d, d, pp, vp]),
+        "qtt_dot": (i, [vp, vp, vp, vp]),
+        "qtt_add": (i, [d, vp, d, vp, vp, pp]),
+        "qtt_from_device_cores": (i, [pp, ip, i, i, i, ip, i, vp, pp]),
         "qtt_get_ranks": (i, [vp, ip, vp]),
         "qtt_get_info": (i, [vp, ip, ip, ip, ip, ip]),
         "qtt_get_cores": (i, [vp, vp, vp]),
@@ -292,20 +297,104 @@ def qtt_to_full_noalloc(t, out, stream=None):
     return out
 
 
+def _grad_ptrs(grad_cores, d):
+    if grad_cores is None:
+        return None
+    if len(grad_cores) != d:
+        raise ValueError(f"need {d} gradient buffers, got {len(grad_cores)}")
+    for g in grad_cores:
+        if not g.is_cuda or not _colmajor(g):
+            raise ValueError("gradient buffers must be CUDA tensors (r0, 2, r1) in column-major storage")
+    return (ctypes.c_void_p * d)(*[g.data_ptr() for g in grad_cores])
+
+
+def _colmajor(c):
+    """True when the (r0, 2, r1) tensor c is stored column-major (r0 fastest)."""
+    return c.dim() == 3 and c.permute(2, 1, 0).is_contiguous()
+
+
 def qtt_conv_adjoint(f, r, B, normalize=True, eps_op=1e-7, eps_round=1e-7, rround=0,
-                     refine=True, sketch=0, seed=20230131, grad_cores=None, stream=None):
+                     refine=True, sketch=0, seed=20230131, grad_cores=None, want_adj=True,
+                     stream=None):
+    """round(T^H r) and, if ``grad_cores`` (d CUDA tensors in f's core shapes,
+    column-major) is given, the core gradients 2 dL/dconj(F_k) of
+    L = ||T full(f) - g||^2 for the residual r = T f - g in QTT."""
     load()
-    Bs = [float(B)] * f.ndim if np.isscalar(B) else [float(b) for b in B]
+    Bs = [float(B)] * r.ndim if np.isscalar(B) else [float(b) for b in B]
     Barr = (ctypes.c_double * 2)(*(Bs + [0.0] * (2 - len(Bs))))
     tr = _trunc(eps_round, rround, refine)
     adj = ctypes.c_void_p()
-    gp = None
-    if grad_cores is not None:
-        gp = (ctypes.c_void_p * len(grad_cores))(*[g.data_ptr() for g in grad_cores])
-    _check(_lib.qtt_conv_adjoint(f.handle, r.handle, Barr, int(bool(normalize)), float(eps_op),
-                                 ctypes.byref(tr), int(sketch), int(seed), gp, ctypes.byref(adj),
+    gp = _grad_ptrs(grad_cores, r.d)
+    _check(_lib.qtt_conv_adjoint(f.handle if f is not None else None, r.handle, Barr,
+                                 int(bool(normalize)), float(eps_op), ctypes.byref(tr), int(sketch),
+                                 int(seed), gp, ctypes.byref(adj) if want_adj else None,
                                  _stream(stream)))
-    return QTTTensor(adj) if adj.value else None
+    return QTTTensor(adj) if (want_adj and adj.value) else None
+
+
+def qtt_core_grads(f, w, grad_cores, alpha=1.0, beta=0.0, stream=None):
+    """grad_k = alpha * C_k(f, w) + beta * grad_k (chain rule through Full)."""
+    load()
+    gp = _grad_ptrs(grad_cores, f.d)
+    _check(_lib.qtt_core_grads(f.handle, w.handle, float(alpha), float(beta), gp, _stream(stream)))
+    return grad_cores
+
+
+def qtt_dot(x, y, out=None, stream=None):
+    """<x, y> = sum conj(x) y as a CUDA float64 tensor [re, im] (no sync)."""
+    import torch
+    load()
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(_lib.qtt_dot(x.handle, y.handle, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def qtt_add(alpha, x, beta, y, stream=None):
+    """alpha x + beta y as a new handle (TT sum, ranks add; not rounded)."""
+    load()
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_add(float(alpha), x.handle, float(beta), y.handle, _stream(stream),
+                        ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_from_device_cores(cores, shape_log2, interleave=True, stream=None):
+    """Handle holding copies of CUDA core tensors (r_{k-1}, 2, r_k), each in
+    column-major storage (see ``core_tensors``)."""
+    import torch
+    load()
+    d = len(cores)
+    code = _dtype_code(cores[0])
+    for c in cores:
+        if not c.is_cuda or not _colmajor(c) or _dtype_code(c) != code:
+            raise ValueError("cores must be CUDA tensors of one dtype in column-major storage")
+    ranks = [1] + [int(c.shape[2]) for c in cores]
+    r = (ctypes.c_int * (d + 1))(*ranks)
+    sh = (ctypes.c_int * 2)(*(list(shape_log2) + [0] * (2 - len(shape_log2))))
+    ptrs = (ctypes.c_void_p * d)(*[c.data_ptr() for c in cores])
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_from_device_cores(ptrs, r, d, code, len(shape_log2), sh, int(interleave),
+                                      _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def empty_cores(ranks, dtype, device="cuda"):
+    """Uninitialised CUDA core tensors (r_{k-1}, 2, r_k) in column-major storage."""
+    import torch
+    return [torch.empty_strided((ranks[k], 2, ranks[k + 1]), (1, ranks[k], 2 * ranks[k]),
+                                dtype=dtype, device=device) for k in range(len(ranks) - 1)]
+
+
+def core_tensors(t, stream=None):
+    """The cores of handle t as CUDA tensors (r_{k-1}, 2, r_k), column-major."""
+    import torch
+    host = t.cores(stream)
+    dt = torch.float64 if t.dtype_code == QTT_F64 else torch.complex64
+    out = empty_cores([1] + [c.shape[2] for c in host], dt)
+    for o, c in zip(out, host):
+        o.copy_(torch.from_numpy(c))
+    return out
 
 
 def qtt_op_create(d, B, normalize=True, eps_op=1e-7, dtype_code=QTT_C64, stream=None):

@@ -125,6 +125,19 @@ static std::mutex g_cache_mu;
 static std::map<OpKey, qtt_op*> g_op_cache;
 static std::map<EmbKey, qtt_op*> g_emb_cache;
 static std::map<std::pair<int, int>, qtt_op*> g_id_cache;
+static std::map<const qtt_op*, qtt_op*> g_tr_cache;   // forward operator -> its transpose
+
+static qtt_status cached_transpose(const qtt_op* op, cudaStream_t s, qtt_op** out) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_tr_cache.find(op);
+  if (it != g_tr_cache.end()) { *out = it->second; return QTT_OK; }
+  qtt_op* t = nullptr;
+  qtt_status st = op_transpose(op, s, &t);
+  if (st != QTT_OK) return st;
+  g_tr_cache[op] = t;
+  *out = t;
+  return QTT_OK;
+}
 
 static qtt_status cached_op(int d, double B, int normalize, double eps_op, qtt_dtype dt,
                             cudaStream_t s, qtt_op** out) {
@@ -338,6 +351,10 @@ qtt_status qtt_get_ranks(const qtt_tensor* t, int* ranks_host, void* stream) {
     return QTT_ETIMEOUT;
   }
   if (status & DEV_ST_RANK_OVERFLOW) { set_error("a rank exceeded its capacity"); return QTT_ERANK; }
+  if (status & DEV_ST_NONFINITE) {
+    set_error("an eigen-solve met a non-finite value (NaN or Inf in the data)");
+    return QTT_ENUMERIC;
+  }
   return QTT_OK;
 }
 
@@ -460,6 +477,8 @@ void qtt_release_workspace(void) {
   for (auto& kv : g_op_cache) op_free(kv.second);
   for (auto& kv : g_emb_cache) op_free(kv.second);
   for (auto& kv : g_id_cache) op_free(kv.second);
+  for (auto& kv : g_tr_cache) op_free(kv.second);
+  g_tr_cache.clear();
   g_op_cache.clear();
   g_emb_cache.clear();
   g_id_cache.clear();
@@ -470,14 +489,125 @@ void qtt_release_workspace(void) {
   }
 }
 
+static bool same_layout(const qtt_tensor* a, const qtt_tensor* b) {
+  if (a->desc.d != b->desc.d || a->desc.dt != b->desc.dt || a->desc.ndim != b->desc.ndim) return false;
+  for (int i = 0; i < a->desc.ndim; ++i)
+    if (a->desc.log2_shape[i] != b->desc.log2_shape[i]) return false;
+  return a->desc.ndim == 1 || a->desc.interleave == b->desc.interleave;
+}
+
 qtt_status qtt_conv_adjoint(const qtt_tensor* f, const qtt_tensor* r, const double* B,
                             int normalize, double eps_op, const qtt_trunc* round_tr, int sketch,
                             unsigned long long seed, void* const* grad_cores,
                             qtt_tensor** adj_out, void* stream) {
-  (void)f; (void)r; (void)B; (void)normalize; (void)eps_op; (void)round_tr; (void)sketch;
-  (void)seed; (void)grad_cores; (void)adj_out; (void)stream;
-  set_error("qtt_conv_adjoint: not implemented in this build");
-  return QTT_EUNSUPPORTED;
+  g_err[0] = 0;
+  if (!r || !B) { set_error("qtt_conv_adjoint: NULL argument"); return QTT_EINVAL; }
+  if (grad_cores && !f) { set_error("qtt_conv_adjoint: gradients need f"); return QTT_EINVAL; }
+  if (f && !same_layout(f, r)) { set_error("qtt_conv_adjoint: f and r differ in shape or type"); return QTT_EINVAL; }
+  if (grad_cores)
+    for (int k = 0; k < r->desc.d; ++k)
+      if (!grad_cores[k]) { set_error("qtt_conv_adjoint: grad_cores[%d] is NULL", k); return QTT_EINVAL; }
+  qtt_status st = check_trunc(round_tr);
+  if (st != QTT_OK) return st;
+  if (!(eps_op > 0.0) || eps_op >= 1.0) { set_error("qtt_conv_adjoint: eps_op must be in (0, 1)"); return QTT_EINVAL; }
+  for (int a = 0; a < r->desc.ndim; ++a)
+    if (!(B[a] > 0.0)) { set_error("qtt_conv_adjoint: B must be positive"); return QTT_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nrm = normalize ? 1 : 0;
+  qtt_tensor* adj = nullptr;
+  if (r->desc.ndim == 1) {
+    qtt_op* op = nullptr;
+    qtt_op* opT = nullptr;
+    st = cached_op(r->desc.d, B[0], nrm, eps_op, r->desc.dt, s, &op);
+    if (st == QTT_OK) st = cached_transpose(op, s, &opT);
+    if (st == QTT_OK) st = round_product(opT, r, *round_tr, sketch, seed, s, &adj);
+  } else {
+    // (T_y T_x)^H = T_x^H T_y^H: the y adjoint first
+    qtt_op *ox = nullptr, *oy = nullptr, *oxT = nullptr, *oyT = nullptr;
+    st = cached_embed(r->desc, 0, B[0], nrm, eps_op, s, &ox);
+    if (st == QTT_OK) st = cached_embed(r->desc, 1, B[1], nrm, eps_op, s, &oy);
+    if (st == QTT_OK) st = cached_transpose(ox, s, &oxT);
+    if (st == QTT_OK) st = cached_transpose(oy, s, &oyT);
+    qtt_tensor* a1 = nullptr;
+    if (st == QTT_OK) st = round_product(oyT, r, *round_tr, sketch, seed, s, &a1);
+    if (st == QTT_OK) {
+      st = round_product(oxT, a1, *round_tr, sketch, seed + 0x9E3779B97F4A7C15ULL, s, &adj);
+      tensor_free_async(a1, s);
+    }
+  }
+  if (st != QTT_OK) return st;
+  if (grad_cores) {
+    st = env_sweep(f, adj, 2.0, 0.0, grad_cores, nullptr, s);
+    if (st != QTT_OK) { tensor_free_async(adj, s); return st; }
+  }
+  if (adj_out) *adj_out = adj;
+  else tensor_free_async(adj, s);
+  return QTT_OK;
+}
+
+qtt_status qtt_core_grads(const qtt_tensor* f, const qtt_tensor* w, double alpha, double beta,
+                          void* const* grad_cores, void* stream) {
+  g_err[0] = 0;
+  if (!f || !w || !grad_cores) { set_error("qtt_core_grads: NULL argument"); return QTT_EINVAL; }
+  if (!same_layout(f, w)) { set_error("qtt_core_grads: f and w differ in shape or type"); return QTT_EINVAL; }
+  for (int k = 0; k < f->desc.d; ++k)
+    if (!grad_cores[k]) { set_error("qtt_core_grads: grad_cores[%d] is NULL", k); return QTT_EINVAL; }
+  return env_sweep(f, w, alpha, beta, grad_cores, nullptr, (cudaStream_t)stream);
+}
+
+qtt_status qtt_dot(const qtt_tensor* x, const qtt_tensor* y, double* out_dev, void* stream) {
+  g_err[0] = 0;
+  if (!x || !y || !out_dev) { set_error("qtt_dot: NULL argument"); return QTT_EINVAL; }
+  if (!same_layout(x, y)) { set_error("qtt_dot: tensors differ in shape or type"); return QTT_EINVAL; }
+  return env_sweep(x, y, 0.0, 0.0, nullptr, (double2*)out_dev, (cudaStream_t)stream);
+}
+
+qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_tensor* y,
+                   void* stream, qtt_tensor** out) {
+  g_err[0] = 0;
+  if (!x || !y || !out) { set_error("qtt_add: NULL argument"); return QTT_EINVAL; }
+  if (!same_layout(x, y)) { set_error("qtt_add: tensors differ in shape or type"); return QTT_EINVAL; }
+  return tt_add(alpha, x, beta, y, (cudaStream_t)stream, out);
+}
+
+qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int d, qtt_dtype dt,
+                                 int ndim, const int* log2_shape, int interleave, void* stream,
+                                 qtt_tensor** out) {
+  g_err[0] = 0;
+  if (!cores || !ranks || !log2_shape || !out) { set_error("qtt_from_device_cores: NULL argument"); return QTT_EINVAL; }
+  if (!valid_dtype(dt) || d < 2 || d > 30 || (ndim != 1 && ndim != 2)) {
+    set_error("qtt_from_device_cores: bad dtype/d/ndim");
+    return QTT_EINVAL;
+  }
+  if (ranks[0] != 1 || ranks[d] != 1) { set_error("qtt_from_device_cores: boundary ranks must be 1"); return QTT_EINVAL; }
+  int dsum = 0;
+  for (int a = 0; a < ndim; ++a) dsum += log2_shape[a];
+  if (dsum != d) { set_error("qtt_from_device_cores: log2 shape does not add up to d"); return QTT_EINVAL; }
+  for (int k = 1; k < d; ++k)
+    if (ranks[k] < 1 || ranks[k] > QTT_PRODUCT_CAP) { set_error("qtt_from_device_cores: rank %d out of range", ranks[k]); return QTT_EINVAL; }
+  for (int k = 0; k < d; ++k)
+    if (!cores[k]) { set_error("qtt_from_device_cores: cores[%d] is NULL", k); return QTT_EINVAL; }
+  TensorDesc desc;
+  desc.d = d;
+  desc.dt = dt;
+  desc.ndim = ndim;
+  desc.interleave = interleave ? 1 : 0;
+  for (int a = 0; a < ndim; ++a) desc.log2_shape[a] = log2_shape[a];
+  std::vector<int> rc(ranks, ranks + d + 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  qtt_tensor* t = nullptr;
+  qtt_status st = tensor_alloc(desc, rc, s, &t);
+  if (st != QTT_OK) return st;
+  const size_t esz = elem_size(dt);
+  for (int k = 0; k < d; ++k) {
+    st = cuda_check(cudaMemcpyAsync((char*)t->cores + esz * t->off[k], cores[k],
+                                    esz * (size_t)rc[k] * 2 * rc[k + 1], cudaMemcpyDeviceToDevice, s),
+                    "qtt_from_device_cores");
+    if (st != QTT_OK) { tensor_free_async(t, s); return st; }
+  }
+  set_ranks_from_host(t->ranks, rc, s);
+  *out = t;
+  return QTT_OK;
 }
 
 }  // extern "C"

@@ -72,9 +72,26 @@ __device__ void twisted_vector(const float* d, const float* e, int n, float sigm
     z[i + 1] = v;
     prev = v;
   }
+  // normalise with a scaling by the largest entry (the recurrences can
+  // reach ~1/pivmin next to a tiny pivot); an overflow falls back to e_k,
+  // which the orthogonalisation step then treats as a degenerate copy
+  float zmax = 0.f;
+  bool finite = true;
+  for (int i = 0; i < n; ++i) {
+    finite = finite && isfinite(z[i]);
+    zmax = fmaxf(zmax, fabsf(z[i]));
+  }
+  if (!finite || !(zmax > 0.f)) {
+    for (int i = 0; i < n; ++i) z[i] = (i == k) ? 1.f : 0.f;
+    return;
+  }
+  const float inv = 1.f / zmax;
   float s2 = 0.f;
-  for (int i = 0; i < n; ++i) s2 = fmaf(z[i], z[i], s2);
-  zn = rsqrtf(s2);
+  for (int i = 0; i < n; ++i) {
+    const float t = z[i] * inv;
+    s2 = fmaf(t, t, s2);
+  }
+  zn = inv * rsqrtf(s2);
   for (int i = 0; i < n; ++i) z[i] *= zn;
 }
 
@@ -102,6 +119,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __shared__ double s_redd[HT / 32];
   __shared__ float2 s_scal, s_alpha2;
   __shared__ float s_xn2, s_glo, s_ghi, s_pivmin;
+  __shared__ double s_trace;
   __shared__ int s_r, s_clu[HMAX], s_pack[HT / 32];
   __shared__ float2 s_part[4][HMAX];
   __shared__ int s_bad[HMAX], s_clu0[HMAX];
@@ -115,17 +133,11 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   float* Z = reinterpret_cast<float*>(A + (size_t)n * n);  // n x n, ld ldz = n + 1
   const int ldz = n + 1;
 
-  // ---- load the Gram (double) and its trace
+  // ---- trace, then the Gram (double) scaled to unit trace in FP32: the
+  // solver works on O(1) numbers whatever the data's scale (no overflow or
+  // underflow in the reflectors); eigenvalues are scaled back by the trace
   double trl = 0.0;
-  for (int e = tid; e < n * n; e += HT) {
-    const int i = e % n, j = e / n;
-    double2 g = a.G[i + (size_t)a.ldp * j];
-    if (i == j) {
-      g.y = 0.0;
-      trl += g.x;
-    }
-    A[e] = make_float2((float)g.x, (float)g.y);
-  }
+  for (int i = tid; i < n; i += HT) trl += a.G[i + (size_t)a.ldp * i].x;
   for (int off = 16; off > 0; off >>= 1) trl += __shfl_xor_sync(0xffffffffu, trl, off);
   if (lane == 0) s_redd[warp] = trl;
   __syncthreads();
@@ -133,7 +145,17 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     double t = 0.0;
     for (int w = 0; w < HT / 32; ++w) t += s_redd[w];
     if (a.write_norm2) *a.norm2 = t;
+    s_trace = (t > 0.0 && isfinite(t)) ? t : 1.0;
   }
+  __syncthreads();
+  const double gsc = 1.0 / s_trace;
+  for (int e = tid; e < n * n; e += HT) {
+    const int i = e % n, j = e / n;
+    double2 g = a.G[i + (size_t)a.ldp * j];
+    if (i == j) g.y = 0.0;
+    A[e] = make_float2((float)(g.x * gsc), (float)(g.y * gsc));
+  }
+  __syncthreads();
 
   HEEV_STAMP(1);
   // ---- 1. Householder tridiagonalisation (lower)
@@ -147,17 +169,22 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     if (lane == 0) s_redf[warp] = part;
     __syncthreads();
     if (tid == 0) {
-      float xn2 = 0.f;
-      for (int w = 0; w < HT / 32; ++w) xn2 += s_redf[w];
+      // reflector scalars in FP64 (|alpha - beta|^2 underflows FP32 for
+      // columns near 1e-19); columns below 1e-30 of the unit trace are
+      // negligible and are left as they are
+      double xn2 = 0.0;
+      for (int w = 0; w < HT / 32; ++w) xn2 += (double)s_redf[w];
       const float2 al = A[(k + 1) + (size_t)n * k];
+      const double ar = al.x, ai = al.y;
       float2 tau = make_float2(0.f, 0.f), scal = make_float2(0.f, 0.f);
       float beta = al.x;
-      if (xn2 > 0.f || al.y != 0.f) {
-        const float nrm = sqrtf(al.x * al.x + al.y * al.y + xn2);
-        beta = (al.x >= 0.f) ? -nrm : nrm;
-        tau = make_float2((beta - al.x) / beta, -al.y / beta);
-        const float dr = al.x - beta, di = al.y, den = dr * dr + di * di;
-        scal = make_float2(dr / den, -di / den);
+      const double nrm = sqrt(ar * ar + ai * ai + xn2);
+      if ((xn2 > 0.0 || ai != 0.0) && nrm > 1e-30) {
+        const double b = (ar >= 0.0) ? -nrm : nrm;
+        beta = (float)b;
+        tau = make_float2((float)((b - ar) / b), (float)(-ai / b));
+        const double dr = ar - b, di = ai, den = dr * dr + di * di;
+        scal = make_float2((float)(dr / den), (float)(-di / den));
       }
       s_e[k] = beta;
       s_d[k] = A[k + (size_t)n * k].x;
@@ -298,7 +325,11 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           else lo = x3;
         }
       }
-      if (act && sub == 0) s_lam[idx] = 0.5f * (lo + hi);
+      if (act && sub == 0) {
+        const float lam = 0.5f * (lo + hi);
+        if (!isfinite(lam) && a.status) atomicOr(a.status, DEV_ST_NONFINITE);
+        s_lam[idx] = lam;
+      }
     }
   }
   __syncthreads();
@@ -315,7 +346,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       double tail = 0.0;
       r = kmax;
       for (int c = kmax - 1; c >= 1; --c) {
-        const double l = (double)s_lam[n - 1 - c];
+        const double l = (double)s_lam[n - 1 - c] * s_trace;
         tail += (l > 0.0 ? l : 0.0);
         if (tail <= tau2) r = c;
         else break;
@@ -341,7 +372,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   const int r = s_r;
   const int ncopy = (a.mode == EIG_MODE_ALL) ? n : r;
   if (a.sig_out)
-    for (int c = tid; c < n; c += HT) a.sig_out[c] = (double)s_lam[n - 1 - c];
+    for (int c = tid; c < n; c += HT) a.sig_out[c] = (double)s_lam[n - 1 - c] * s_trace;
 
   HEEV_STAMP(3);
   // ---- 3. eigenvectors of T (descending order, one thread per vector)

@@ -59,6 +59,66 @@ __global__ void gauss_fill_kernel(R* out, long long n, unsigned long long seed, 
 
 #define GRID1(n) (unsigned)(((n) + 255) / 256), 256, 0, s
 
+// Orthonormal sketch cores.  Each Gaussian core Omega_k, read as the
+// (2 l_{k-1}) x l_k matrix Om[s' + l0 (j + 2 s)] (l_k <= 2 l_{k-1}), is
+// replaced by the Q factor of its Gram-Schmidt orthonormalisation (classical
+// Gram-Schmidt applied twice per column).  The left sketch Omega_{<=k} then
+// has orthonormal columns: a random isometry of the 2^k-dimensional left
+// space, exactly an orthogonal change of basis at cuts where l_k = 2^k.  With
+// plain Gaussian cores the TT sketch's condition number grows with k, and in
+// FP32 that loses digits in the range finder of step 2.
+constexpr int OS_THREADS = 256;
+constexpr int OS_MAXD = 32;
+struct SketchCores {
+  long long off[OS_MAXD];
+  int m[OS_MAXD];   // 2 l_{k-1}
+  int n[OS_MAXD];   // l_k
+};
+template <typename R>
+__global__ void __launch_bounds__(OS_THREADS) k_orth_sketch(R* Om, SketchCores sc) {
+  extern __shared__ __align__(16) unsigned char os_smem[];
+  R* M = reinterpret_cast<R*>(os_smem);
+  __shared__ R s_c[128];
+  __shared__ R s_red[OS_THREADS / 32];
+  const int k = blockIdx.x + 1;
+  const int m = sc.m[k], n = sc.n[k];
+  R* G = Om + sc.off[k];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = OS_THREADS / 32;
+  for (int e = tid; e < m * n; e += OS_THREADS) M[e] = G[e];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    R* v = M + (size_t)m * j;
+    for (int pass = 0; pass < 2; ++pass) {
+      // c_i = <M_i, v> for i < j: one warp per coefficient
+      for (int i = warp; i < j; i += nw) {
+        const R* qi = M + (size_t)m * i;
+        R a = 0;
+        for (int r = lane; r < m; r += 32) a += qi[r] * v[r];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) s_c[i] = a;
+      }
+      __syncthreads();
+      for (int r = tid; r < m; r += OS_THREADS) {
+        R a = v[r];
+        for (int i = 0; i < j; ++i) a -= s_c[i] * M[r + (size_t)m * i];
+        v[r] = a;
+      }
+      __syncthreads();
+    }
+    R a = 0;
+    for (int r = tid; r < m; r += OS_THREADS) a += v[r] * v[r];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if (lane == 0) s_red[warp] = a;
+    __syncthreads();
+    R nrm2 = 0;
+    for (int w = 0; w < nw; ++w) nrm2 += s_red[w];
+    const R inv = nrm2 > (R)0 ? (R)1 / sqrt(nrm2) : (R)0;
+    for (int r = tid; r < m; r += OS_THREADS) v[r] *= inv;
+    __syncthreads();
+  }
+  for (int e = tid; e < m * n; e += OS_THREADS) G[e] = M[e];
+}
+
 // ---------------------------------------------------------------- step 1
 // A1[s + lk (j + 2 c)] = sum_{s'} Om[s' + l0 (j + 2 s)] WL0[s' + l0 c],  c < R0
 template <typename T, typename R>
@@ -396,6 +456,8 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     l[k] = (int)std::min<long long>({(long long)sketch, lim, (long long)Rc[k]});
   }
   l[0] = l[d] = 1;
+  // the left sketch at cut k spans at most 2 l_{k-1} directions
+  for (int k = 1; k < d; ++k) l[k] = std::min(l[k], 2 * l[k - 1]);
   lq[d] = 1;
   for (int k = d; k >= 2; --k) lq[k - 1] = std::min(l[k - 1], 2 * lq[k]);
   lq[0] = 1;
@@ -461,6 +523,24 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
                                                                               (uint32_t)k);
     }
+  }
+  if (d > 1) {
+    SketchCores sc{};
+    int mmax = 1;
+    for (int k = 1; k < d && k < OS_MAXD; ++k) {
+      sc.off[k] = (long long)omoff[k];
+      sc.m[k] = 2 * l[k - 1];
+      sc.n[k] = l[k];
+      mmax = std::max(mmax, sc.m[k] * sc.n[k]);
+    }
+    static bool os_cfg = false;
+    if (!os_cfg) {
+      cudaFuncSetAttribute(k_orth_sketch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(R) * 128 * 64));
+      os_cfg = true;
+    }
+    QTT_PROF("round_sketch", s);
+    k_orth_sketch<R><<<d - 1, OS_THREADS, sizeof(R) * (size_t)mmax, s>>>(Om, sc);
   }
   cudaMemcpyAsync(WL + wloff[0], one, sizeof(T), cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k < d; ++k) {

@@ -350,7 +350,17 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   if (!converged && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
 
   // eigenvalues and descending order (ties by index)
-  for (int i = tid; i < mg; i += EIG_THREADS) s_lam[i] = (double)sreal(A[pk_idx(i, i)]);
+  // a NaN compares false both ways and would break the rank count below
+  // (two indices with the same rank, an unset slot): such eigenvalues sort
+  // last as -inf and the device status records the non-finite input
+  for (int i = tid; i < mg; i += EIG_THREADS) {
+    double l = (double)sreal(A[pk_idx(i, i)]);
+    if (!isfinite(l)) {
+      if (a.status) atomicOr(a.status, DEV_ST_NONFINITE);
+      if (isnan(l)) l = -INFINITY;
+    }
+    s_lam[i] = l;
+  }
   __syncthreads();
   for (int i = tid; i < mg; i += EIG_THREADS) {
     const double li = s_lam[i];

@@ -143,6 +143,7 @@ __host__ __device__ __forceinline__ void from_d2(double2 v, float2& o) { o = mak
 enum : int {
   DEV_ST_JACOBI_LIMIT = 1,   // Jacobi sweep limit reached before convergence
   DEV_ST_RANK_OVERFLOW = 2,  // a rank larger than its capacity was requested
+  DEV_ST_NONFINITE = 4,      // an eigen-solve met a non-finite value (NaN / Inf input)
 };
 
 // ---------------------------------------------------------------- handles
@@ -267,6 +268,17 @@ void op_free(qtt_op* op);
 qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_tensor** out);
 qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,
                          unsigned long long seed, cudaStream_t s, qtt_tensor** out);
+
+// environment sweeps (k_env.cu): dot_out (device, may be null) receives
+// <f, w> = sum conj(f) w; grad (d device pointers, may be null) receives
+// grad_k = alpha * E_{k-1} W_k R_k + beta * grad_k
+qtt_status env_sweep(const qtt_tensor* f, const qtt_tensor* w, double alpha, double beta,
+                     void* const* grad, double2* dot_out, cudaStream_t s);
+// alpha x + beta y (ranks add)
+qtt_status tt_add(double alpha, const qtt_tensor* x, double beta, const qtt_tensor* y,
+                  cudaStream_t s, qtt_tensor** out);
+// operator with j and i swapped in every core (the adjoint of a real operator)
+qtt_status op_transpose(const qtt_op* op, cudaStream_t s, qtt_op** out);
 
 // write host-known ranks (<= 32 modes) to a device rank array, stream-ordered
 void set_ranks_from_host(int* dev_ranks, const std::vector<int>& r, cudaStream_t s);
