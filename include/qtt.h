@@ -264,10 +264,12 @@ void qtt_profile_reset(void);
  * double[n], descending.  Asynchronous. */
 qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam, void* stream);
 
-/* Diagnostics: if dev8 is not NULL, the next qtt_small_eigh calls (FP32
- * tridiagonal solver) store clock64() at their 8 phase boundaries in dev8
- * (device, 8 long long); NULL switches it off. */
-void qtt_debug_small_eigh_clocks(long long* dev8);
+/* Diagnostics: if dev10 is not NULL, the next qtt_small_eigh calls (FP32
+ * tridiagonal solver) store clock64() at their 10 phase boundaries (start,
+ * load, tridiagonalisation, eigenvalues, eigenvectors, orthogonalisation,
+ * reflector packing, Newton-Schulz, back-transformation, output) in dev10
+ * (device, 10 long long); NULL switches it off. */
+void qtt_debug_small_eigh_clocks(long long* dev10);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
  * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */

@@ -479,6 +479,7 @@ void qtt_release_workspace(void) {
   for (auto& kv : g_id_cache) op_free(kv.second);
   for (auto& kv : g_tr_cache) op_free(kv.second);
   g_tr_cache.clear();
+  sketch_cache_clear();
   g_op_cache.clear();
   g_emb_cache.clear();
   g_id_cache.clear();

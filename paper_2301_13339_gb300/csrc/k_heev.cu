@@ -169,22 +169,20 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     if (lane == 0) s_redf[warp] = part;
     __syncthreads();
     if (tid == 0) {
-      // reflector scalars in FP64 (|alpha - beta|^2 underflows FP32 for
-      // columns near 1e-19); columns below 1e-30 of the unit trace are
-      // negligible and are left as they are
-      double xn2 = 0.0;
-      for (int w = 0; w < HT / 32; ++w) xn2 += (double)s_redf[w];
+      // on the unit-trace matrix a column below 1e-18 is negligible (and
+      // would underflow |alpha - beta|^2): it is left as it is
+      float xn2 = 0.f;
+      for (int w = 0; w < HT / 32; ++w) xn2 += s_redf[w];
       const float2 al = A[(k + 1) + (size_t)n * k];
-      const double ar = al.x, ai = al.y;
       float2 tau = make_float2(0.f, 0.f), scal = make_float2(0.f, 0.f);
       float beta = al.x;
-      const double nrm = sqrt(ar * ar + ai * ai + xn2);
-      if ((xn2 > 0.0 || ai != 0.0) && nrm > 1e-30) {
-        const double b = (ar >= 0.0) ? -nrm : nrm;
-        beta = (float)b;
-        tau = make_float2((float)((b - ar) / b), (float)(-ai / b));
-        const double dr = ar - b, di = ai, den = dr * dr + di * di;
-        scal = make_float2((float)(dr / den), (float)(-di / den));
+      const float nrm = sqrtf(al.x * al.x + al.y * al.y + xn2);
+      if ((xn2 > 0.f || al.y != 0.f) && nrm > 1e-18f) {
+        beta = (al.x >= 0.f) ? -nrm : nrm;
+        const float rb = 1.f / beta;
+        tau = make_float2((beta - al.x) * rb, -al.y * rb);
+        const float dr = al.x - beta, di = al.y, rden = 1.f / (dr * dr + di * di);
+        scal = make_float2(dr * rden, -di * rden);
       }
       s_e[k] = beta;
       s_d[k] = A[k + (size_t)n * k].x;
@@ -503,6 +501,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     for (int e = tid; e < npack && cnt < 16; e += HT, ++cnt) A[e] = buf[cnt];
     __syncthreads();
   }
+  HEEV_STAMP(6);
   // ---- 4b. Newton-Schulz orthonormalisation Z <- Z (3 I - Z^T Z) / 2.
   // The vectors of distinct eigenvalues are orthogonal to O(eps ||T|| / gap)
   // (the accuracy order of any backward-stable solver); each step squares
@@ -584,6 +583,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       __syncthreads();
     }
   }
+  HEEV_STAMP(7);
   float2* Vp = A;                                  // packed reflectors
   float2* Uc = A + npack;                          // column chunk after them
   // columns per chunk: what fits in the rest of the n x n region, at most 64
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     __syncthreads();
   }
   __syncthreads();
-  HEEV_STAMP(6);
+  HEEV_STAMP(8);
   if (a.core_out) {
     if (a.U1) {
       for (int e = tid; e < n * r; e += HT) {
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       for (int e = tid; e < n * r; e += HT) a.core_out[e] = a.Uout[e];
     }
   }
-  HEEV_STAMP(7);
+  HEEV_STAMP(9);
 }
 
 size_t heev_tri_smem_bytes(int mg_cap) {

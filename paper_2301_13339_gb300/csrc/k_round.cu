@@ -19,6 +19,9 @@
 // All factorisations are Gram + Jacobi (+ refinement) on <= 128 x 128.
 #include "qtt_internal.cuh"
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace qtt {
 
@@ -437,6 +440,109 @@ __global__ void k_set_ranks_one(int* r, int d) {
   if (threadIdx.x == 0) { r[0] = 1; r[d] = 1; }
 }
 
+// ---------------------------------------------------------------- sketch cache
+// The orthonormalised sketch cores are a function of (device, element type,
+// seed, l profile) only, so they are generated once per key and kept (up to
+// SK_CACHE_MAX bytes in total; beyond that, or while the stream is being
+// captured into a CUDA graph, a miss generates them into per-call scratch).
+// The entry's event orders the generation before uses on other streams.
+struct SketchEntry {
+  void* ptr = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool ready = false;
+  size_t bytes = 0;
+};
+typedef std::tuple<int, int, unsigned long long, std::vector<int>> SketchKey;
+static std::mutex g_sk_mu;
+static std::map<SketchKey, SketchEntry> g_sk_cache;
+static size_t g_sk_bytes = 0;
+constexpr size_t SK_CACHE_MAX = (size_t)64 << 20;
+
+void sketch_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_sk_mu);
+  for (auto& kv : g_sk_cache) {
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+  }
+  g_sk_cache.clear();
+  g_sk_bytes = 0;
+}
+
+template <typename R>
+static void generate_sketch(R* Om, const std::vector<int>& l, const std::vector<size_t>& omoff,
+                            int d, unsigned long long seed, cudaStream_t s) {
+  for (int k = 1; k < d; ++k) {
+    const long long n = (long long)l[k - 1] * 2 * l[k];
+    QTT_PROF("round_sketch", s);
+    gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
+                                                                              (uint32_t)k);
+  }
+  if (d > 1) {
+    SketchCores sc{};
+    int mmax = 1;
+    for (int k = 1; k < d && k < OS_MAXD; ++k) {
+      sc.off[k] = (long long)omoff[k];
+      sc.m[k] = 2 * l[k - 1];
+      sc.n[k] = l[k];
+      mmax = std::max(mmax, sc.m[k] * sc.n[k]);
+    }
+    static bool os_cfg = false;
+    if (!os_cfg) {
+      cudaFuncSetAttribute(k_orth_sketch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(R) * 128 * 64));
+      os_cfg = true;
+    }
+    QTT_PROF("round_sketch", s);
+    k_orth_sketch<R><<<d - 1, OS_THREADS, sizeof(R) * (size_t)mmax, s>>>(Om, sc);
+  }
+}
+
+// Returns the sketch cores for (seed, l); *owned = true when the caller must
+// scratch_free them after use.
+template <typename R>
+static R* get_sketch(const std::vector<int>& l, const std::vector<size_t>& omoff, size_t omtot,
+                     int d, unsigned long long seed, cudaStream_t s, bool* owned) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  SketchKey key(dev, (int)sizeof(R), seed, l);
+  const size_t bytes = sizeof(R) * std::max<size_t>(omtot, 1);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  {
+    std::lock_guard<std::mutex> lk(g_sk_mu);
+    auto it = g_sk_cache.find(key);
+    if (it != g_sk_cache.end()) {
+      SketchEntry& en = it->second;
+      if (!en.ready) {
+        if (cudaEventQuery(en.ev) == cudaSuccess) en.ready = true;
+        else cudaStreamWaitEvent(s, en.ev, 0);
+      }
+      *owned = false;
+      return (R*)en.ptr;
+    }
+    if (cs == cudaStreamCaptureStatusNone && g_sk_bytes + bytes <= SK_CACHE_MAX) {
+      SketchEntry en;
+      if (cudaMalloc(&en.ptr, bytes) == cudaSuccess &&
+          cudaEventCreateWithFlags(&en.ev, cudaEventDisableTiming) == cudaSuccess) {
+        generate_sketch<R>((R*)en.ptr, l, omoff, d, seed, s);
+        cudaEventRecord(en.ev, s);
+        en.bytes = bytes;
+        g_sk_bytes += bytes;
+        g_sk_cache[key] = en;
+        *owned = false;
+        return (R*)en.ptr;
+      }
+      cudaGetLastError();
+      if (en.ptr) cudaFree(en.ptr);
+    }
+  }
+  R* Om = (R*)scratch_alloc(bytes, s);
+  if (!Om) return nullptr;
+  generate_sketch<R>(Om, l, omoff, d, seed, s);
+  *owned = true;
+  return Om;
+}
+
 template <typename T>
 static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr,
                                   int sketch, unsigned long long seed, cudaStream_t s,
@@ -479,7 +585,8 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   size_t omtot = 0;
   for (int k = 1; k < d; ++k) { omoff[k] = omtot; omtot += (size_t)l[k - 1] * 2 * l[k]; }
   T* WL = (T*)scratch_alloc(sizeof(T) * std::max<size_t>(wltot, 1), s);
-  R* Om = (R*)scratch_alloc(sizeof(R) * std::max<size_t>(omtot, 1), s);
+  bool om_owned = false;
+  R* Om = get_sketch<R>(l, omoff, omtot, d, seed, s, &om_owned);
   const size_t a1sz = (size_t)lmax * 2 * Rmax;
   const size_t a2sz = (size_t)lmax * 2 * Pmax * 2 * xmax;
   T* A1 = (T*)scratch_alloc(sizeof(T) * a1sz, s);
@@ -516,32 +623,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   if (st != QTT_OK) { qtt_free(Tp); return st; }
   k_set_ranks_one<<<1, 32, 0, s>>>(y->ranks, d);
 
-  // --- 1. Gaussian sketch cores and left sketches
-  for (int k = 1; k < d; ++k) {
-    const long long n = (long long)l[k - 1] * 2 * l[k];
-    { QTT_PROF("round_sketch", s);
-    gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
-                                                                              (uint32_t)k);
-    }
-  }
-  if (d > 1) {
-    SketchCores sc{};
-    int mmax = 1;
-    for (int k = 1; k < d && k < OS_MAXD; ++k) {
-      sc.off[k] = (long long)omoff[k];
-      sc.m[k] = 2 * l[k - 1];
-      sc.n[k] = l[k];
-      mmax = std::max(mmax, sc.m[k] * sc.n[k]);
-    }
-    static bool os_cfg = false;
-    if (!os_cfg) {
-      cudaFuncSetAttribute(k_orth_sketch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(R) * 128 * 64));
-      os_cfg = true;
-    }
-    QTT_PROF("round_sketch", s);
-    k_orth_sketch<R><<<d - 1, OS_THREADS, sizeof(R) * (size_t)mmax, s>>>(Om, sc);
-  }
+  // --- 1. left sketches through the (cached) orthonormal sketch cores
   cudaMemcpyAsync(WL + wloff[0], one, sizeof(T), cudaMemcpyDeviceToDevice, s);
   for (int k = 1; k < d; ++k) {
     const int l0 = l[k - 1], lk = l[k];
@@ -653,7 +735,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     }
   }
   st = cuda_check(cudaGetLastError(), "round launch");
-  scratch_free(WL, s); scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
+  scratch_free(WL, s); if (om_owned) scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
   scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
   scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s); scratch_free(G, s);
   scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s); scratch_free(one, s);

@@ -678,7 +678,7 @@ extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which;
 // (device, element type of dt, ld n, columns by descending eigenvalue) and
 // lam (device, double, descending) out.
 static long long* g_small_eigh_clk = nullptr;   // diagnostics: phase clocks of the next call
-extern "C" void qtt_debug_small_eigh_clocks(long long* dev8) { g_small_eigh_clk = dev8; }
+extern "C" void qtt_debug_small_eigh_clocks(long long* dev10) { g_small_eigh_clk = dev10; }
 
 extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam,
                                      void* stream) {

@@ -280,6 +280,9 @@ qtt_status tt_add(double alpha, const qtt_tensor* x, double beta, const qtt_tens
 // operator with j and i swapped in every core (the adjoint of a real operator)
 qtt_status op_transpose(const qtt_op* op, cudaStream_t s, qtt_op** out);
 
+// drop the cached sketch cores of the rounding (k_round.cu)
+void sketch_cache_clear();
+
 // write host-known ranks (<= 32 modes) to a device rank array, stream-ordered
 void set_ranks_from_host(int* dev_ranks, const std::vector<int>& r, cudaStream_t s);
 // stream-ordered release of a handle
