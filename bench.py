@@ -23,6 +23,13 @@ scaling); the time is the max over ranks.
 
 --impl reference: the FP64 oracle (numpy, host cores) on the same workload,
 one line per step.
+
+--workload batch_256_c64: 256 complex64 range lines of uneven length
+(2^14..2^18), 10-40 scatterers each, SNR 15 dB, per-line B ~ U[128, 1024] and
+R_max from {8, 16, 32, 64}.  A step is one CUDA-graph launch of the whole
+batch (the stream count picked by the autotuner); also reported: the same
+lines as 256 separate single-line calls on one stream.  The inputs (~210 MB)
+exceed L2; L2 is flushed before each step anyway.
 """
 import argparse
 import json
@@ -39,6 +46,8 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "line_2p20_c64": dict(d=20, B=1024.0, rmax=64, eps=0.0, eps_op=1e-7, eps_round=1e-7,
                           nscat=50, nbumps=3, snr_db=20.0, tol=1e-5),
+    "batch_256_c64": dict(kind="batch", nlines=256, dmin=14, dmax=18, snr_db=15.0, bmin=128.0,
+                          bmax=1024.0, eps=0.0, eps_op=1e-7, eps_round=1e-7, tol=1e-5),
 }
 
 
@@ -251,7 +260,9 @@ def roofline(kernels, wl, peaks, peak_kind):
         # as LAPACK's ~9 n^3 real flop per real eigen-decomposition with
         # vectors, x4 for complex arithmetic.  The kernel runs on one SM, so
         # its peak is one SM's FP32 rate; the whole-GPU fraction is frac/152.
-        n = 2 * wl["rmax"]
+        import re
+        m = re.search(r"le(\d+)", name)
+        n = min(2 * wl["rmax"], int(m.group(1))) if m else 2 * wl["rmax"]
         flops = 9 * n ** 3 * 4
         ach = flops / (avg_ms * 1e-3) / 1e12
         sm_peak = fp32_peak_tflops / 152
@@ -272,6 +283,204 @@ def roofline(kernels, wl, peaks, peak_kind):
             "peak_source": "fp32 cuda cores"}
 
 
+# ------------------------------------------------------------------ batch
+def make_batch(wl, rank=0):
+    import synth
+    rng = synth.config_rng(3, sub=rank if rank else None)
+    return synth.batch_lines(rng, nlines=wl["nlines"], dmin=wl["dmin"], dmax=wl["dmax"],
+                             snr_db=wl["snr_db"], bmin=wl["bmin"], bmax=wl["bmax"])
+
+
+def run_oracle_line(ln, wl):
+    from oracle import pipeline as P
+    t0 = time.perf_counter()
+    out = P.conv_sinc_qtt(ln["x"].astype(np.complex128), ln["B"], wl["eps"], ln["rmax"],
+                          eps_op=wl["eps_op"], eps_round=wl["eps_round"])
+    return out, time.perf_counter() - t0
+
+
+def oracle_sample(lines, wl, budget_s=15.0):
+    """The oracle on lines taken in order until ~budget_s of CPU time."""
+    done, t, n = 0, 0.0, 0
+    for ln in lines:
+        _, dt = run_oracle_line(ln, wl)
+        t += dt
+        n += ln["x"].size
+        done += 1
+        if t >= budget_s:
+            break
+    return n, t, done
+
+
+def batch_main(args, wl, metric):
+    import torch
+    import torch.distributed as dist
+    import paper_2301_13339_gb300 as q
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": args.workload, "nlines": wl["nlines"],
+              "log2_len": [wl["dmin"], wl["dmax"]], "B": [wl["bmin"], wl["bmax"]],
+              "rmax_choices": [8, 16, 32, 64], "eps": wl["eps"], "eps_op": wl["eps_op"],
+              "eps_round": wl["eps_round"], "snr_db": wl["snr_db"],
+              "l2": "inputs exceed L2; flushed (512 MiB write) before every timed step anyway"}
+    lines = make_batch(wl, rank)
+    N = sum(ln["x"].size for ln in lines)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n, t, done = oracle_sample(lines, wl)
+        v = n / t / 1e6
+        cores = len(os.sched_getaffinity(0))
+        sample = f"the first {done} of {len(lines)} lines ({n} samples), numpy FP64"
+        print(json.dumps({
+            "impl": "reference", "metric": metric, "value": v, "unit": "Msamples/s",
+            "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    q.load()
+    L = q.lib()
+    stream = torch.cuda.Stream(device=dev)
+    xs = [torch.from_numpy(ln["x"].astype(np.complex64)).to(dev) for ln in lines]
+    ys = [torch.empty_like(x) for x in xs]
+    Bs = [ln["B"] for ln in lines]
+    rms = [ln["rmax"] for ln in lines]
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    kw = dict(eps=wl["eps"], eps_op=wl["eps_op"], eps_round=wl["eps_round"])
+
+    # 256 separate single-line calls on one stream (the plain path)
+    def plain(s):
+        for i, ln in enumerate(lines):
+            f = q.qtt_decompose(xs[i], eps=wl["eps"], rmax=ln["rmax"], refine=True, stream=s)
+            y = q.qtt_conv_sinc(f, ln["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"],
+                                seed=20230131 + i, stream=s)
+            q.qtt_to_full(y, out=ys[i], stream=s)
+            f.free(stream=s)
+            y.free(stream=s)
+    with torch.cuda.stream(stream):
+        plain(stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        plain(stream)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    plain_out = [y.clone() for y in ys]
+
+    # autotuned concurrency, captured as one graph
+    best, tune = q.autotune_batch(xs, ys, Bs, rms, candidates=(8, 16, 32, 64), reps=1,
+                                  stream=stream, **kw)
+    info = best.info()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            best.launch(stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dev.index)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            best.launch(stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    same = all(torch.equal(a, b) for a, b in zip(plain_out, ys))
+    # e2e: pinned host inputs copied in and outputs copied back inside the events
+    xh = [torch.from_numpy(ln["x"].astype(np.complex64)).pin_memory() for ln in lines]
+    yh = [torch.empty_like(x).pin_memory() for x in xh]
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            eve[i][0].record(stream)
+            for xd, xhh in zip(xs, xh):
+                xd.copy_(xhh, non_blocking=True)
+            best.launch(stream)
+            for yd, yhh in zip(ys, yh):
+                yhh.copy_(yd, non_blocking=True)
+            eve[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eve)
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+    # per-kernel times from a profiled eager pass (concurrent streams: shares)
+    import ctypes
+    L.qtt_profile_enable.argtypes = [ctypes.c_int]
+    L.qtt_profile_read.restype = ctypes.c_int
+    L.qtt_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.qtt_profile_reset()
+    L.qtt_profile_enable(1)
+    with torch.cuda.stream(stream):
+        best.run(xs, ys, stream)
+    torch.cuda.synchronize(dev)
+    L.qtt_profile_enable(0)
+    cap, stride = 64, 64
+    names = ctypes.create_string_buffer(cap * stride)
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int * cap)()
+    nk = L.qtt_profile_read(names, stride, ms, cnt, cap)
+    kern = {}
+    for i in range(nk):
+        nm = names.raw[i * stride:(i + 1) * stride].split(b"\0")[0].decode()
+        kern[nm] = {"ms_per_step": ms[i], "launches_per_step": cnt[i]}
+    L.qtt_profile_reset()
+    if rank != 0:
+        return
+    peaks, peak_kind = _peaks()
+    value = world * N * args.steps / (total_ms * 1e-3) / 1e6
+    line = {"metric": metric, "value": value, "unit": "Msamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 arithmetic)", "data": "synthetic", "config": config,
+            "e2e": {"value": world * N * args.steps / (e2e_ms * 1e-3) / 1e6, "unit": "Msamples/s",
+                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": int(info["graph_nodes"]) * args.steps,
+            "graph": {"nodes": info["graph_nodes"], "nstreams": info["nstreams"],
+                      "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()}},
+            "plain_single_stream": {"ms": plain_ms, "value": N / (plain_ms * 1e-3) / 1e6,
+                                    "unit": "Msamples/s", "bit_identical_to_graph": bool(same)},
+            "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in kern.items()},
+            "roofline": roofline(kern, {"d": 18, "rmax": 64}, peaks, peak_kind),
+            "clocks": clk}
+    if not args.no_cpu_baseline:
+        from oracle import conv as C
+        # parity on three sampled lines (the two shortest and the longest)
+        order = sorted(range(len(lines)), key=lambda i: lines[i]["d"])
+        worst = 0.0
+        for i in [order[0], order[1], order[-1]]:
+            ref, _ = run_oracle_line(lines[i], wl)
+            worst = max(worst, C.rel_l2(ys[i].cpu().numpy().astype(np.complex128), ref))
+        line["parity"] = {"e2_vs_oracle_max_sampled": worst, "lines_sampled": 3,
+                          "tol": wl["tol"], "ok": bool(worst <= wl["tol"])}
+        n, t, done = oracle_sample(lines, wl)
+        line["cpu_baseline"] = {"value": n / t / 1e6, "unit": "Msamples/s",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"the first {done} of {len(lines)} lines ({n} samples)"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,8 +493,13 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     wl = WORKLOADS[args.workload]
-    N = 2 ** wl["d"]
     metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"
+    if wl.get("kind") == "batch":
+        # more hardware work queues for the concurrent line chains (process-local)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+        batch_main(args, wl, metric)
+        return
+    N = 2 ** wl["d"]
     config = {"workload": args.workload, "samples_per_line": N, "dtype_in": "complex64",
               "B": wl["B"], "rmax": wl["rmax"], "eps": wl["eps"], "eps_op": wl["eps_op"],
               "eps_round": wl["eps_round"], "snr_db": wl["snr_db"],

@@ -204,6 +204,44 @@ qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int
                                  int ndim, const int* log2_shape, int interleave, void* stream,
                                  qtt_tensor** out);
 
+/* Batched lines (many independent 1D signals of uneven length, bandwidth
+ * and rank cap): Alg. 2 steps 1-4 for every line -- qtt_decompose with
+ * (eps, rmax[i], refine), qtt_conv_sinc with (B[i], normalize, eps_op,
+ * round_tr) and qtt_to_full -- with the lines spread over internal streams
+ * so that their chains run concurrently.  Lines are independent; the paper's
+ * method is applied to each unchanged.
+ *
+ * qtt_batch_create: plans for nlines lines (log2_len[i], B[i], rmax[i]; host
+ *   arrays, copied).  nstreams <= 0: 16.  Builds every line's operator plan
+ *   (synchronises `stream` once per distinct (log2_len, B)).
+ * qtt_batch_run: eager submission.  x[i] / y[i]: caller-owned device arrays
+ *   of 2^log2_len[i] elements of dt (y written).  Forks from and joins back
+ *   to `stream`; asynchronous.
+ * qtt_batch_capture: runs the batch once eagerly (synchronising `stream`),
+ *   then captures the same submission for these x / y buffers into a CUDA
+ *   graph (relaxed capture mode); `stream` must not be the legacy default
+ *   stream.  The buffers must stay valid while the graph is used.
+ * qtt_batch_launch: replays the captured graph on `stream` (one launch for
+ *   the whole batch); asynchronous.
+ * qtt_batch_info: internal stream count and graph node count (0 if none).
+ * qtt_batch_free: synchronises the device and releases streams and graph.
+ * qtt_batch_conv_sinc: create + run + release in one call (asynchronous;
+ *   the internal streams are released when their work completes). */
+typedef struct qtt_batch qtt_batch;
+qtt_status qtt_batch_create(int nlines, const int* log2_len, const double* B, const int* rmax,
+                            double eps, int refine, int normalize, double eps_op,
+                            const qtt_trunc* round_tr, qtt_dtype dt, int nstreams, void* stream,
+                            qtt_batch** out);
+qtt_status qtt_batch_run(qtt_batch* b, const void* const* x, void* const* y, void* stream);
+qtt_status qtt_batch_capture(qtt_batch* b, const void* const* x, void* const* y, void* stream);
+qtt_status qtt_batch_launch(qtt_batch* b, void* stream);
+qtt_status qtt_batch_info(const qtt_batch* b, int* nstreams, int* graph_nodes);
+void qtt_batch_free(qtt_batch* b);
+qtt_status qtt_batch_conv_sinc(int nlines, const void* const* x, const int* log2_len,
+                               const double* B, const int* rmax, double eps, int refine,
+                               int normalize, double eps_op, const qtt_trunc* round_tr,
+                               void* const* y, qtt_dtype dt, void* stream);
+
 /* Handle inspection and construction (tests, checkpoints). */
 /* ranks_host: d+1 ints r_0..r_d.  Synchronises; returns the device status. */
 qtt_status qtt_get_ranks(const qtt_tensor* t, int* ranks_host, void* stream);

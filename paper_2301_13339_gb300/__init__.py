@@ -21,6 +21,8 @@ __all__ = [
     "qtt_round", "qtt_to_full", "qtt_to_full_noalloc", "qtt_conv_adjoint", "qtt_matvec",
     "qtt_op_create",
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
+    "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
+    "qtt_from_device_cores", "empty_cores", "core_tensors",
 ]
 
 QTT_F64 = 0
@@ -37,6 +39,8 @@ EXPORTED_SYMBOLS = [
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
+    "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
+    "qtt_batch_free", "qtt_batch_conv_sinc",
 ]
 
 
@@ -79,6 +83,13 @@ def load(path=None):
         "qtt_dot": (i, [vp, vp, vp, vp]),
         "qtt_add": (i, [d, vp, d, vp, vp, pp]),
         "qtt_from_device_cores": (i, [pp, ip, i, i, i, ip, i, vp, pp]),
+        "qtt_batch_create": (i, [i, ip, dp, ip, d, i, i, d, tp, i, i, vp, pp]),
+        "qtt_batch_run": (i, [vp, pp, pp, vp]),
+        "qtt_batch_capture": (i, [vp, pp, pp, vp]),
+        "qtt_batch_launch": (i, [vp, vp]),
+        "qtt_batch_info": (i, [vp, ip, ip]),
+        "qtt_batch_free": (None, [vp]),
+        "qtt_batch_conv_sinc": (i, [i, pp, ip, dp, ip, d, i, i, d, tp, pp, i, vp]),
         "qtt_get_ranks": (i, [vp, ip, vp]),
         "qtt_get_info": (i, [vp, ip, ip, ip, ip, ip]),
         "qtt_get_cores": (i, [vp, vp, vp]),
@@ -427,6 +438,132 @@ def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):
     _check(_lib.qtt_from_cores(buf.ctypes.data_as(ctypes.c_void_p), r, d, code, len(shape_log2),
                                sh, int(interleave), _stream(stream), ctypes.byref(out)))
     return QTTTensor(out)
+
+
+def _line_arrays(xs, ys):
+    if len(xs) != len(ys):
+        raise ValueError("xs and ys differ in length")
+    code = _dtype_code(xs[0])
+    lg = []
+    for x, y in zip(xs, ys):
+        if (not x.is_cuda or not y.is_cuda or not x.is_contiguous() or not y.is_contiguous()
+                or x.dim() != 1 or x.shape != y.shape or x.dtype != y.dtype or _dtype_code(x) != code):
+            raise ValueError("lines must be contiguous 1D CUDA tensors of one dtype, y like x")
+        n = int(x.shape[0])
+        ln = n.bit_length() - 1
+        if n < 4 or (1 << ln) != n:
+            raise ValueError(f"line length {n} is not a power of two >= 4")
+        lg.append(ln)
+    xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+    yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+    return code, lg, xp, yp
+
+
+class QTTBatch:
+    """Independent 1D lines of uneven length, bandwidth and rank cap through
+    decompose -> sinc convolution -> Full, spread over ``nstreams`` internal
+    streams; ``capture`` records the whole batch as one CUDA graph that
+    ``launch`` replays."""
+
+    def __init__(self, log2_len, B, rmax, eps=0.0, refine=True, normalize=True, eps_op=1e-7,
+                 eps_round=1e-7, rround=0, dtype_code=QTT_C64, nstreams=0, stream=None):
+        load()
+        n = len(log2_len)
+        self.n = n
+        self.log2_len = [int(v) for v in log2_len]
+        tr = _trunc(eps_round, rround, True)
+        out = ctypes.c_void_p()
+        _check(_lib.qtt_batch_create(n, (ctypes.c_int * n)(*self.log2_len),
+                                     (ctypes.c_double * n)(*[float(b) for b in B]),
+                                     (ctypes.c_int * n)(*[int(r) for r in rmax]), float(eps),
+                                     int(bool(refine)), int(bool(normalize)), float(eps_op),
+                                     ctypes.byref(tr), int(dtype_code), int(nstreams),
+                                     _stream(stream), ctypes.byref(out)))
+        self._h = out
+        self._bufs = None
+
+    def run(self, xs, ys, stream=None):
+        _, lg, xp, yp = _line_arrays(xs, ys)
+        if lg != self.log2_len:
+            raise ValueError("line lengths differ from the batch plan")
+        _check(_lib.qtt_batch_run(self._h, xp, yp, _stream(stream)))
+        return ys
+
+    def capture(self, xs, ys, stream):
+        _, lg, xp, yp = _line_arrays(xs, ys)
+        if lg != self.log2_len:
+            raise ValueError("line lengths differ from the batch plan")
+        _check(_lib.qtt_batch_capture(self._h, xp, yp, _stream(stream)))
+        self._bufs = (xs, ys)      # the graph reads and writes these buffers
+
+    def launch(self, stream=None):
+        _check(_lib.qtt_batch_launch(self._h, _stream(stream)))
+
+    def info(self):
+        ns, nn = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.qtt_batch_info(self._h, ctypes.byref(ns), ctypes.byref(nn)))
+        return {"nstreams": ns.value, "graph_nodes": nn.value}
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.qtt_batch_free(self._h)
+        self._h = None
+        self._bufs = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def qtt_batch_conv_sinc(xs, B, rmax, ys=None, eps=0.0, refine=True, normalize=True, eps_op=1e-7,
+                        eps_round=1e-7, rround=0, stream=None):
+    """One-shot batched decompose -> convolve -> Full of the 1D lines xs."""
+    import torch
+    load()
+    if ys is None:
+        ys = [torch.empty_like(x) for x in xs]
+    code, lg, xp, yp = _line_arrays(xs, ys)
+    n = len(xs)
+    tr = _trunc(eps_round, rround, True)
+    _check(_lib.qtt_batch_conv_sinc(n, xp, (ctypes.c_int * n)(*lg),
+                                    (ctypes.c_double * n)(*[float(b) for b in B]),
+                                    (ctypes.c_int * n)(*[int(r) for r in rmax]), float(eps),
+                                    int(bool(refine)), int(bool(normalize)), float(eps_op),
+                                    ctypes.byref(tr), yp, code, _stream(stream)))
+    return ys
+
+
+def autotune_batch(xs, ys, B, rmax, candidates=(8, 16, 32, 64), reps=2, stream=None, **kw):
+    """Pick the internal stream count of a captured batch by timing graph
+    launches (CUDA events on ``stream``); returns (best QTTBatch, {S: ms})."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.Stream()
+    lg = [int(x.shape[0]).bit_length() - 1 for x in xs]
+    best, best_ms, times = None, None, {}
+    for S in candidates:
+        if S > len(xs) and times:
+            continue
+        b = QTTBatch(lg, B, rmax, nstreams=S, stream=stream, **kw)
+        b.capture(xs, ys, stream)
+        b.launch(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        times[b.info()["nstreams"]] = ms
+        if best is None or ms < best_ms:
+            if best is not None:
+                best.free()
+            best, best_ms = b, ms
+        else:
+            b.free()
+    return best, times
 
 
 def qtt_small_eigh(G, dtype_code=QTT_C64, stream=None):

@@ -153,6 +153,11 @@ static qtt_status cached_op(int d, double B, int normalize, double eps_op, qtt_d
   return QTT_OK;
 }
 
+qtt_status cached_op_plan(int d, double B, int normalize, double eps_op, qtt_dtype dt,
+                          cudaStream_t s, qtt_op** out) {
+  return cached_op(d, B, normalize ? 1 : 0, eps_op, dt, s, out);
+}
+
 static qtt_status cached_embed(const TensorDesc& desc, int axis, double B, int normalize,
                                double eps_op, cudaStream_t s, qtt_op** out) {
   const int dax = desc.log2_shape[axis == 0 ? 1 : 0];

@@ -445,7 +445,8 @@ __global__ void k_set_ranks_one(int* r, int d) {
 // seed, l profile) only, so they are generated once per key and kept (up to
 // SK_CACHE_MAX bytes in total; beyond that, or while the stream is being
 // captured into a CUDA graph, a miss generates them into per-call scratch).
-// The entry's event orders the generation before uses on other streams.
+// A new entry is complete before it is returned (one wait per key), so any
+// stream or graph may use it.
 struct SketchEntry {
   void* ptr = nullptr;
   cudaEvent_t ev = nullptr;
@@ -512,20 +513,18 @@ static R* get_sketch(const std::vector<int>& l, const std::vector<size_t>& omoff
     std::lock_guard<std::mutex> lk(g_sk_mu);
     auto it = g_sk_cache.find(key);
     if (it != g_sk_cache.end()) {
-      SketchEntry& en = it->second;
-      if (!en.ready) {
-        if (cudaEventQuery(en.ev) == cudaSuccess) en.ready = true;
-        else cudaStreamWaitEvent(s, en.ev, 0);
-      }
       *owned = false;
-      return (R*)en.ptr;
+      return (R*)it->second.ptr;
     }
     if (cs == cudaStreamCaptureStatusNone && g_sk_bytes + bytes <= SK_CACHE_MAX) {
       SketchEntry en;
       if (cudaMalloc(&en.ptr, bytes) == cudaSuccess &&
           cudaEventCreateWithFlags(&en.ev, cudaEventDisableTiming) == cudaSuccess) {
         generate_sketch<R>((R*)en.ptr, l, omoff, d, seed, s);
+        // complete before any stream (or graph) can use the entry
         cudaEventRecord(en.ev, s);
+        cudaEventSynchronize(en.ev);
+        en.ready = true;
         en.bytes = bytes;
         g_sk_bytes += bytes;
         g_sk_cache[key] = en;

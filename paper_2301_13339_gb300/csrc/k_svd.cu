@@ -266,28 +266,35 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
         if (p > q) { int t = p; p = q; q = t; }
         s_pp[tid] = p;
         s_pq[tid] = q;
-        const double app = (double)sreal(A[pk_idx(p, p)]);
-        const double aqq = (double)sreal(A[pk_idx(q, q)]);
+        // rotation parameters in the data's own precision (FP64 is 1/64 of
+        // the FP32 rate on this GPU and sat on the critical path of every
+        // step); sqrt(app) sqrt(aqq) instead of sqrt(app aqq) avoids the
+        // FP32 underflow of the product, and t = 1/(2 zeta) for huge zeta
+        // avoids the overflow of zeta^2
+        const R app = sreal(A[pk_idx(p, p)]);
+        const R aqq = sreal(A[pk_idx(q, q)]);
         const T apq = A[pk_idx(p, q)];
-        const double b = sqrt((double)sabs2(apq));
+        const R b = sqrt(sabs2(apq));
         int rot = 0;
-        double c = 1.0, s = 0.0, t = 0.0;
+        R c = (R)1, s = (R)0, t = (R)0;
         T u = sone(T());
-        if (b > 0.0 && b > tol * sqrt(fabs(app) * fabs(aqq))) {
-          const double zeta = (aqq - app) / (2.0 * b);
-          t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c = 1.0 / sqrt(1.0 + t * t);
+        if (b > (R)0 && b > (R)tol * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
+          const R zeta = (aqq - app) / ((R)2 * b);
+          const R az = fabs(zeta);
+          const R tt = (az > (R)1e15) ? (R)0.5 / az : (R)1 / (az + sqrt((R)1 + zeta * zeta));
+          t = (zeta >= (R)0) ? tt : -tt;
+          c = (R)1 / sqrt((R)1 + t * t);
           s = t * c;
-          u = rscale(apq, (R)(1.0 / b));
+          u = rscale(apq, (R)1 / b);
           rot = 1;
           atomicAdd(&s_nrot, 1);
         }
         s_rot[tid] = rot;
-        s_c[tid] = (R)c;
-        s_s[tid] = (R)s;
+        s_c[tid] = c;
+        s_s[tid] = s;
         s_u[tid] = u;
-        s_d[tid][0] = (R)(app - t * b);
-        s_d[tid][1] = (R)(aqq + t * b);
+        s_d[tid][0] = app - t * b;
+        s_d[tid][1] = aqq + t * b;
       }
       __syncthreads();
       for (int bi = tid; bi < nb; bi += EIG_THREADS) {
@@ -563,12 +570,12 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s) {
+                     int* status, cudaStream_t s, int relative) {
   double2* gfin = (double2*)scratch_alloc(sizeof(double2) * ldp * ldp, s);
   launch_reduce<T>(gram_part, nparts, ldp, gfin, s);
   launch_eig_dense<T>(gfin, ldp, mg_ptr, mg_mul, 0, mg_cap, mode, eps, dmodes, rmax, ncols_ptr,
                       ncols_mul, ncols_const, U1, Uout, core_out, rank_out, sig_out, norm2,
-                      write_norm2, status, s);
+                      write_norm2, status, s, relative);
   scratch_free(gfin, s);
 }
 
@@ -626,10 +633,11 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       // W1 = U1^H M, Gram of W1
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
                                    mcap, max_parts, s);
-      // pass 2: decide the rank; core = U1 * U2[:, :r]
+      // pass 2: decide the rank on the projected Gram, whose small
+      // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
       launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
-                         t->status, s);
+                         t->status, s, 1);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
@@ -663,10 +671,10 @@ template void launch_eig_dense<float2>(const double2*, int, const int*, int, int
                                        cudaStream_t, int);
 template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const double*, double*,
-                                      double*, int*, double*, double*, int, int*, cudaStream_t);
+                                      double*, int*, double*, double*, int, int*, cudaStream_t, int);
 template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const float2*, float2*,
-                                      float2*, int*, double*, double*, int, int*, cudaStream_t);
+                                      float2*, int*, double*, double*, int, int*, cudaStream_t, int);
 
 }  // namespace qtt
 

@@ -203,7 +203,7 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s);
+                     int* status, cudaStream_t s, int relative = 0);
 
 // ------------------------------------------------------------- eigen
 enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
@@ -279,6 +279,10 @@ qtt_status tt_add(double alpha, const qtt_tensor* x, double beta, const qtt_tens
                   cudaStream_t s, qtt_tensor** out);
 // operator with j and i swapped in every core (the adjoint of a real operator)
 qtt_status op_transpose(const qtt_op* op, cudaStream_t s, qtt_op** out);
+
+// the cached 1D sinc operator plan for (d, B, normalize, eps_op, dt) (api.cu)
+qtt_status cached_op_plan(int d, double B, int normalize, double eps_op, qtt_dtype dt,
+                          cudaStream_t s, qtt_op** out);
 
 // drop the cached sketch cores of the rounding (k_round.cu)
 void sketch_cache_clear();
