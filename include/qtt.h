@@ -306,7 +306,9 @@ qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* l
  * tridiagonal solver) store clock64() at their 10 phase boundaries (start,
  * load, tridiagonalisation, eigenvalues, eigenvectors, orthogonalisation,
  * reflector packing, Newton-Schulz, back-transformation, output) in dev10
- * (device, 10 long long); NULL switches it off. */
+ * (device, 10 long long); with the Jacobi solver selected, slots 0-3 get
+ * start, load, end of the sweeps and end, and slot 4 the sweep count.
+ * NULL switches it off. */
 void qtt_debug_small_eigh_clocks(long long* dev10);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal

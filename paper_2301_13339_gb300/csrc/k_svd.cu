@@ -203,31 +203,31 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   __shared__ unsigned short s_blk[(EIG_MAXN / 2) * (EIG_MAXN / 2 + 1) / 2][2];
 
   const int tid = threadIdx.x;
+  if (a.phase_clk && tid == 0) a.phase_clk[0] = clock64();
   const int mg = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
   const int n = (mg + 1) & ~1;            // even
   const int np = n / 2;
   T* A = reinterpret_cast<T*>(smem_raw);  // packed, n(n+1)/2
-  T* V = A + (n * (n + 1)) / 2;           // n x n, column-major
+  T* V = A + (n * (n + 1)) / 2;           // n x n, column-major, ld n + 1
 
-  // load + identity
+  // load + identity.  V has leading dimension n + 1: the column-pair
+  // products of the orthonormalisation below then read 32 different banks.
+  const int ldv = n + 1;
   double tr_local = 0.0;
-  for (int e = tid; e < (n * (n + 1)) / 2; e += EIG_THREADS) {
-    // invert pk_idx: find j with j(j+1)/2 <= e
-    int j = (int)floor((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-    while ((j + 1) * (j + 2) / 2 <= e) ++j;
-    while (j * (j + 1) / 2 > e) --j;
-    const int i = e - j * (j + 1) / 2;
-    T v = szero<T>();
-    if (i < mg && j < mg) {
-      double2 g = a.G[i + (size_t)a.ldp * j];
-      if (i == j) { g.y = 0.0; tr_local += g.x; }
-      from_d2(g, v);
+  for (int j = tid >> 5; j < n; j += EIG_THREADS / 32) {
+    for (int i = tid & 31; i <= j; i += 32) {
+      T v = szero<T>();
+      if (i < mg && j < mg) {
+        double2 g = a.G[i + (size_t)a.ldp * j];
+        if (i == j) { g.y = 0.0; tr_local += g.x; }
+        from_d2(g, v);
+      }
+      A[pk_idx(i, j)] = v;
     }
-    A[e] = v;
   }
   for (int e = tid; e < n * n; e += EIG_THREADS) {
     const int i = e % n, j = e / n;
-    V[e] = (i == j) ? sone(T()) : szero<T>();
+    V[i + ldv * j] = (i == j) ? sone(T()) : szero<T>();
   }
   // block table (P <= Q)
   {
@@ -251,11 +251,13 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     if (a.write_norm2) *a.norm2 = t;
   }
 
+  if (a.phase_clk && tid == 0) a.phase_clk[1] = clock64();
   const double tol = 4.0 * Sc<T>::eps;
   const int maxsweep = Sc<T>::cplx ? 20 : 40;
   const int nb = np * (np + 1) / 2;
   bool converged = (n <= 1);
-  for (int sweep = 0; sweep < maxsweep && !converged; ++sweep) {
+  int nsweep = 0;
+  for (int sweep = 0; sweep < maxsweep && !converged; ++sweep, ++nsweep) {
     if (tid == 0) s_nrot = 0;
     __syncthreads();
     for (int step = 0; step < n - 1; ++step) {
@@ -344,10 +346,10 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
         const int p = s_pp[P], q = s_pq[P];
         const R c = s_c[P], s = s_s[P];
         const T u = s_u[P];
-        const T vp = V[row + n * p], vq = V[row + n * q];
+        const T vp = V[row + ldv * p], vq = V[row + ldv * q];
         // [vp, vq] J = [c vp - s conj(u) vq, s u vp + c vq]
-        V[row + n * p] = ssub(rscale(vp, c), smul(rscale(conjg(u), s), vq));
-        V[row + n * q] = sadd(smul(rscale(u, s), vp), rscale(vq, c));
+        V[row + ldv * p] = ssub(rscale(vp, c), smul(rscale(conjg(u), s), vq));
+        V[row + ldv * q] = sadd(smul(rscale(u, s), vp), rscale(vq, c));
       }
       __syncthreads();
     }
@@ -355,6 +357,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     __syncthreads();
   }
   if (!converged && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
+  if (a.phase_clk && tid == 0) { a.phase_clk[2] = clock64(); a.phase_clk[4] = nsweep; }
 
   // eigenvalues and descending order (ties by index)
   // a NaN compares false both ways and would break the rank count below
@@ -410,29 +413,27 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     // FP32: the accumulated rotations leave V orthonormal only to
     // ~sqrt(#rotations) eps; one Newton-Schulz step V (3 I - V^H V) / 2
     // squares that error.  G = V^H V goes into the (no longer needed) packed A.
-    const int ng = n * (n + 1) / 2;
-    for (int e = tid; e < ng; e += EIG_THREADS) {
-      int j = (int)floor((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while ((j + 1) * (j + 2) / 2 <= e) ++j;
-      while (j * (j + 1) / 2 > e) --j;
-      const int i = e - j * (j + 1) / 2;
-      T acc = szero<T>();
-      for (int l = 0; l < n; ++l) macc(acc, V[l + n * i], V[l + n * j]);
-      A[e] = acc;
+    // G = V^H V (upper triangle, packed): a warp per column j, lanes over i
+    for (int j = tid >> 5; j < n; j += EIG_THREADS / 32) {
+      for (int i = tid & 31; i <= j; i += 32) {
+        T acc = szero<T>();
+        for (int l = 0; l < n; ++l) macc(acc, V[l + ldv * i], V[l + ldv * j]);
+        A[pk_idx(i, j)] = acc;
+      }
     }
     __syncthreads();
     for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
       const int i = e % mg, c = e / mg;
       const int pc = s_perm[c];
-      T acc = rscale(V[i + n * pc], (typename Sc<T>::R)1.5);
+      T acc = rscale(V[i + ldv * pc], (typename Sc<T>::R)1.5);
       T corr = szero<T>();
-      for (int l = 0; l < n; ++l) mac(corr, V[i + n * l], pk_get(A, l, pc));
+      for (int l = 0; l < n; ++l) mac(corr, V[i + ldv * l], pk_get(A, l, pc));
       a.Uout[e] = ssub(acc, rscale(corr, (typename Sc<T>::R)0.5));
     }
   } else {
     for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
       const int i = e % mg, c = e / mg;
-      a.Uout[e] = V[i + n * s_perm[c]];
+      a.Uout[e] = V[i + ldv * s_perm[c]];
     }
   }
   __syncthreads();
@@ -448,12 +449,13 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
       for (int e = tid; e < mg * r; e += EIG_THREADS) a.core_out[e] = a.Uout[e];
     }
   }
+  if (a.phase_clk && tid == 0) a.phase_clk[3] = clock64();
 }
 
 template <typename T>
 static size_t eig_smem_bytes(int mg_cap) {
   const int n = (mg_cap + 1) & ~1;
-  return sizeof(T) * ((size_t)n * (n + 1) / 2 + (size_t)n * n);
+  return sizeof(T) * ((size_t)n * (n + 1) / 2 + (size_t)n * (n + 1));
 }
 
 static int g_eig_solver = 0;   // 0: tridiagonal solver for FP32, Jacobi for FP64; 1: Jacobi
