@@ -24,6 +24,14 @@ scaling); the time is the max over ranks.
 --impl reference: the FP64 oracle (numpy, host cores) on the same workload,
 one line per step.
 
+--workload deconv_2048sq_c64: gradient-based deconvolution of a 2048 x 2048
+complex64 image (100 scatterers convolved with the separable sinc, B = 256,
+complex noise at SNR 20 dB; target g = its TT-SVD at rank 64, f of rank 32):
+a step is one forward + adjoint + core-gradient evaluation through the
+autograd Function plus the core update; reported in s/step.  At this size the
+rounded ranks hit the library's capacity of 64, so the numbers time the
+kernels; parity of the gradient is tested at smaller sizes.
+
 --workload batch_256_c64: 256 complex64 range lines of uneven length
 (2^14..2^18), 10-40 scatterers each, SNR 15 dB, per-line B ~ U[128, 1024] and
 R_max from {8, 16, 32, 64}.  A step is one CUDA-graph launch of the whole
@@ -48,6 +56,8 @@ WORKLOADS = {
                           nscat=50, nbumps=3, snr_db=20.0, tol=1e-5),
     "batch_256_c64": dict(kind="batch", nlines=256, dmin=14, dmax=18, snr_db=15.0, bmin=128.0,
                           bmax=1024.0, eps=0.0, eps_op=1e-7, eps_round=1e-7, tol=1e-5),
+    "deconv_2048sq_c64": dict(kind="deconv", dy=11, dx=11, B=256.0, nscat=100, snr_db=20.0,
+                              rank_f=32, rank_g=64, eps_op=1e-7, eps_round=1e-7),
 }
 
 
@@ -241,6 +251,12 @@ def gpu_arm(args, wl):
                 clocks=clk, kernels=kern, out=out_host, x=x, dev=dev)
 
 
+# DRAM bytes (read + write) per launch from the committed ncu captures in
+# profiles/ (gram_eig_kernel_n128_line_2p20_c64.md); valid while that kernel
+# is unchanged.
+NCU_TRAFFIC = {"jacobi_eig_le128": 333056.0}
+
+
 def roofline(kernels, wl, peaks, peak_kind):
     """Dominant kernel's achieved rate against its bound."""
     if not kernels:
@@ -267,7 +283,7 @@ def roofline(kernels, wl, peaks, peak_kind):
         ach = flops / (avg_ms * 1e-3) / 1e12
         sm_peak = fp32_peak_tflops / 152
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": sm_peak,
-                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": NCU_TRAFFIC.get(name),
                 "avg_launch_ms": avg_ms, "frac_of_gpu": ach / fp32_peak_tflops,
                 "peak_source": f"one SM: 128 FP32 FMA/clk at {sm_mhz:.0f} MHz (single-CTA kernel)"}
     if name in ("proj_gram", "full_expand", "morton_gather"):
@@ -481,6 +497,112 @@ def batch_main(args, wl, metric):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ deconvolution
+def deconv_main(args, wl):
+    import torch
+    import synth
+    import paper_2301_13339_gb300 as q
+    from paper_2301_13339_gb300.deconv import SincDeconvProblem, default_step, lipschitz_estimate
+    ny, nx = 2 ** wl["dy"], 2 ** wl["dx"]
+    config = {"workload": args.workload, "shape": [ny, nx], "B": wl["B"], "nscat": wl["nscat"],
+              "snr_db": wl["snr_db"], "rank_f": wl["rank_f"], "rank_g": wl["rank_g"],
+              "eps_op": wl["eps_op"], "eps_round": wl["eps_round"]}
+    metric = "QTT deconvolution gradient step (forward + adjoint + core gradients + update)"
+    rng = synth.config_rng(4)
+    scene = synth.deconv_scene_2d(rng, ny, nx, nscat=wl["nscat"]).astype(np.complex64)
+    noise = (rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))).astype(np.complex64)
+    if args.impl == "reference":
+        from oracle import pipeline as P
+        cores, _, _ = P.decompose(scene.astype(np.complex128), 0.0, wl["rank_f"])
+        obs = P.conv_dense(scene.astype(np.complex128), wl["B"])
+        t0 = time.perf_counter()
+        w = P.deconv_dense_grad(cores, (ny, nx), wl["B"], obs)
+        from oracle import qtt as Q
+        P.core_grads(cores, Q.image_to_qtt_vector(w))
+        t = time.perf_counter() - t0
+        print(json.dumps({"impl": "reference", "metric": metric, "value": t, "unit": "s/step",
+                          "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t,
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": t, "unit": "s/step",
+                                           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                           "sample": "one dense gradient (FFT adjoint + core contractions)"},
+                          "e2e": {"value": t, "unit": "s/step", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    dev = torch.device("cuda", 0)
+    q.load()
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        # observation: the scene through the library's own forward operator, plus noise
+        sd = torch.from_numpy(scene).to(dev)
+        fs = q.qtt_decompose(sd, eps=0.0, rmax=64, refine=True, stream=stream)
+        ys = q.qtt_conv_sinc(fs, wl["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"], stream=stream)
+        obs = q.qtt_to_full(ys, stream=stream)
+        p_sig = float((obs.abs() ** 2).mean())
+        sigma = (p_sig / 10 ** (wl["snr_db"] / 10)) ** 0.5
+        obs_h = (obs.cpu().numpy() + noise * np.float32(sigma / np.sqrt(2))).astype(np.complex64)
+        xd = torch.from_numpy(obs_h).to(dev)
+        g = q.qtt_decompose(xd, eps=0.0, rmax=wl["rank_g"], refine=True, stream=stream)
+        f0 = q.qtt_decompose(xd, eps=0.0, rmax=wl["rank_f"], refine=True, stream=stream)
+        prob = SincDeconvProblem(g, wl["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"])
+        L_hat = lipschitz_estimate(prob)
+        cores = [c.detach().clone().requires_grad_(True) for c in q.core_tensors(f0)]
+        step = default_step(prob, cores, L_hat)
+
+        def gd_step():
+            L = prob.loss(cores)
+            grads = torch.autograd.grad(L, cores)
+            with torch.no_grad():
+                for c, gr in zip(cores, grads):
+                    c.sub_(step * gr)
+            return L.detach()
+        for _ in range(args.warmup):
+            gd_step()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        losses = []
+        clocks = Clocks(dev.index)
+        clocks.start()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            losses.append(gd_step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        # e2e: the observation from pinned host memory, its TT-SVD, the steps,
+        # and the deconvolved image back to the host
+        xh = torch.from_numpy(obs_h).pin_memory()
+        out_h = torch.empty_like(xh).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        g2 = q.qtt_decompose(xd, eps=0.0, rmax=wl["rank_g"], refine=True, stream=stream)
+        prob.g = g2
+        for i in range(args.steps):
+            gd_step()
+        fh = prob.handle(cores)
+        out_h.copy_(q.qtt_to_full(fh, stream=stream), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1)
+    Ls = torch.stack(losses).cpu().numpy().tolist()
+    line = {"metric": metric, "value": total_ms / args.steps * 1e-3, "unit": "s/step",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
+            "config": config,
+            "e2e": {"value": e2e_ms / args.steps * 1e-3, "unit": "s/step",
+                    "h2d_bytes_per_step": 8 * ny * nx / args.steps,
+                    "d2h_bytes_per_step": 8 * ny * nx / args.steps},
+            "loss_first_last": [Ls[0], Ls[-1]], "loss_monotone": bool(all(b <= a * (1 + 1e-6) for a, b in zip(Ls, Ls[1:]))),
+            "step_size": step, "lipschitz_estimate": L_hat, "clocks": clk,
+            "note": "rounded ranks capped at 64 at this size; gradient parity is tested at 32x32 and 1024-sample lines"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +616,9 @@ def main():
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     wl = WORKLOADS[args.workload]
     metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"
+    if wl.get("kind") == "deconv":
+        deconv_main(args, wl)
+        return
     if wl.get("kind") == "batch":
         # more hardware work queues for the concurrent line chains (process-local)
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
@@ -551,6 +676,10 @@ def main():
             "gpu_launches": int(round(launches)),
             "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in kern.items()},
             "roofline": roofline(kern, wl, peaks, peak_kind),
+            # the end-to-end floor: each input sample read and each output
+            # sample written once (16 B per complex64 sample)
+            "hbm_floor": {"bytes_per_sample": 16,
+                          "frac": 16.0 * N * args.steps / (res["total_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"]},
             "clocks": res["clocks"], "refine": args.refine}
     if not args.no_cpu_baseline:
         ref, t = run_oracle(res["x"], wl)
