@@ -115,9 +115,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __shared__ float s_d[HMAX], s_e[HMAX], s_e2[HMAX], s_lam[HMAX];
   __shared__ float2 s_tau[HMAX], s_v[HMAX], s_p[HMAX];
   __shared__ float s_redf[HT / 32];
-  __shared__ float2 s_redc[HT / 32];
   __shared__ double s_redd[HT / 32];
-  __shared__ float2 s_scal, s_alpha2;
   __shared__ float s_xn2, s_glo, s_ghi, s_pivmin;
   __shared__ double s_trace;
   __shared__ int s_r, s_clu[HMAX], s_pack[HT / 32];
@@ -158,21 +156,21 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __syncthreads();
 
   HEEV_STAMP(1);
-  // ---- 1. Householder tridiagonalisation (lower)
+  // ---- 1. Householder tridiagonalisation (lower).  Per column k: warp 0
+  // forms the reflector and v (shuffle reductions, no block-wide sum); all
+  // threads form the partial products of p = A22 v; warp 0 finishes
+  // p, alpha2 = -tau (p^H v) / 2 and w = tau A22 v + alpha2 v; all threads
+  // apply A22 -= v w^H + w v^H.  Four barriers per column.
   for (int k = 0; k < n - 1; ++k) {
-    float part = 0.f;
-    for (int i = k + 2 + tid; i < n; i += HT) {
-      const float2 x = A[i + (size_t)n * k];
-      part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
-    }
-    part = warp_sum(part);
-    if (lane == 0) s_redf[warp] = part;
-    __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
+      float part = 0.f;
+      for (int i = k + 2 + lane; i < n; i += 32) {
+        const float2 x = A[i + (size_t)n * k];
+        part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
+      }
+      const float xn2 = warp_sum(part);
       // on the unit-trace matrix a column below 1e-18 is negligible (and
       // would underflow |alpha - beta|^2): it is left as it is
-      float xn2 = 0.f;
-      for (int w = 0; w < HT / 32; ++w) xn2 += s_redf[w];
       const float2 al = A[(k + 1) + (size_t)n * k];
       float2 tau = make_float2(0.f, 0.f), scal = make_float2(0.f, 0.f);
       float beta = al.x;
@@ -184,73 +182,87 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
         const float dr = al.x - beta, di = al.y, rden = 1.f / (dr * dr + di * di);
         scal = make_float2(dr * rden, -di * rden);
       }
-      s_e[k] = beta;
-      s_d[k] = A[k + (size_t)n * k].x;
-      s_tau[k] = tau;
-      s_scal = scal;
+      const bool act = (tau.x != 0.f || tau.y != 0.f);
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        float2 v;
+        if (i == k + 1) v = make_float2(1.f, 0.f);
+        else {
+          v = A[i + (size_t)n * k];
+          if (act) {
+            v = cmulf(v, scal);
+            A[i + (size_t)n * k] = v;
+          }
+        }
+        s_v[i] = v;
+      }
+      if (lane == 0) {
+        s_e[k] = beta;
+        s_d[k] = A[k + (size_t)n * k].x;
+        s_tau[k] = tau;
+      }
     }
     __syncthreads();
     const float2 tau = s_tau[k];
-    const float2 scal = s_scal;
-    for (int i = k + 1 + tid; i < n; i += HT) {
-      float2 v;
-      if (i == k + 1) v = make_float2(1.f, 0.f);
-      else {
-        v = cmulf(A[i + (size_t)n * k], scal);
-        A[i + (size_t)n * k] = v;
-      }
-      s_v[i] = v;
-    }
-    __syncthreads();
-    if (tau.x == 0.f && tau.y == 0.f) continue;
-    // p = tau * A22 v: thread t owns row k+1+(t & 127) and the columns
-    // congruent to (t >> 7) mod 4; lanes of a warp read consecutive rows
+    if (tau.x == 0.f && tau.y == 0.f) continue;   // uniform: s_tau is shared
+    // partial products of A22 v: thread t owns row k+1+(t & 127) and the
+    // columns congruent to (t >> 7) mod 4; lanes of a warp read consecutive rows
     {
       const int i = k + 1 + (tid & 127), ph = tid >> 7;
-      float2 acc = make_float2(0.f, 0.f);
-      if (i < n)
-        for (int j = k + 1 + ph; j < n; j += 4) {
-          const float2 aij = A[i + (size_t)n * j], vj = s_v[j];
-          acc.x = fmaf(aij.x, vj.x, fmaf(-aij.y, vj.y, acc.x));
-          acc.y = fmaf(aij.x, vj.y, fmaf(aij.y, vj.x, acc.y));
+      float2 acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+      if (i < n) {
+        int j = k + 1 + ph;
+        // four independent chains (columns j, j+4, j+8, j+12)
+        for (; j + 12 < n; j += 16) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 aij = A[i + (size_t)n * (j + 4 * u)], vj = s_v[j + 4 * u];
+            acc[u].x = fmaf(aij.x, vj.x, fmaf(-aij.y, vj.y, acc[u].x));
+            acc[u].y = fmaf(aij.x, vj.y, fmaf(aij.y, vj.x, acc[u].y));
+          }
         }
-      s_part[ph][tid & 127] = acc;
+        for (; j < n; j += 4) {
+          const float2 aij = A[i + (size_t)n * j], vj = s_v[j];
+          acc[0].x = fmaf(aij.x, vj.x, fmaf(-aij.y, vj.y, acc[0].x));
+          acc[0].y = fmaf(aij.x, vj.y, fmaf(aij.y, vj.x, acc[0].y));
+        }
+      }
+      s_part[ph][tid & 127] = make_float2(acc[0].x + acc[1].x + acc[2].x + acc[3].x,
+                                          acc[0].y + acc[1].y + acc[2].y + acc[3].y);
     }
     __syncthreads();
-    for (int i = k + 1 + tid; i < n; i += HT) {
-      const int il = i - k - 1;
-      float2 acc = s_part[0][il];
-      for (int ph = 1; ph < 4; ++ph) { acc.x += s_part[ph][il].x; acc.y += s_part[ph][il].y; }
-      s_p[i] = cmulf(tau, acc);
-    }
-    __syncthreads();
-    // alpha2 = -1/2 tau (p^H v)
-    {
+    if (warp == 0) {
+      // p = tau A22 v (rows k+1..n-1, 4 per lane), p^H v, w = p + alpha2 v
+      float2 pl[4];
       float2 pd = make_float2(0.f, 0.f);
-      for (int i = k + 1 + tid; i < n; i += HT) {
-        const float2 pi = s_p[i], vi = s_v[i];
-        pd.x = fmaf(pi.x, vi.x, fmaf(pi.y, vi.y, pd.x));
-        pd.y = fmaf(pi.x, vi.y, fmaf(-pi.y, vi.x, pd.y));
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = k + 1 + lane + 32 * t;
+        pl[t] = make_float2(0.f, 0.f);
+        if (i < n) {
+          const int il = i - k - 1;
+          float2 acc = s_part[0][il];
+          for (int ph = 1; ph < 4; ++ph) { acc.x += s_part[ph][il].x; acc.y += s_part[ph][il].y; }
+          const float2 pi = cmulf(tau, acc), vi = s_v[i];
+          pl[t] = pi;
+          pd.x = fmaf(pi.x, vi.x, fmaf(pi.y, vi.y, pd.x));
+          pd.y = fmaf(pi.x, vi.y, fmaf(-pi.y, vi.x, pd.y));
+        }
       }
       pd = warp_sum(pd);
-      if (lane == 0) s_redc[warp] = pd;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float2 dot = make_float2(0.f, 0.f);
-      for (int w = 0; w < HT / 32; ++w) { dot.x += s_redc[w].x; dot.y += s_redc[w].y; }
-      const float2 t = cmulf(tau, dot);
-      s_alpha2 = make_float2(-0.5f * t.x, -0.5f * t.y);
-    }
-    __syncthreads();
-    {
-      const float2 al2 = s_alpha2;
-      for (int i = k + 1 + tid; i < n; i += HT) {
-        const float2 vi = s_v[i];
-        float2 w = s_p[i];
-        w.x = fmaf(al2.x, vi.x, fmaf(-al2.y, vi.y, w.x));
-        w.y = fmaf(al2.x, vi.y, fmaf(al2.y, vi.x, w.y));
-        s_p[i] = w;
+      const float2 t2 = cmulf(tau, pd);
+      const float2 al2 = make_float2(-0.5f * t2.x, -0.5f * t2.y);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = k + 1 + lane + 32 * t;
+        if (i < n) {
+          const float2 vi = s_v[i];
+          float2 w = pl[t];
+          w.x = fmaf(al2.x, vi.x, fmaf(-al2.y, vi.y, w.x));
+          w.y = fmaf(al2.x, vi.y, fmaf(al2.y, vi.x, w.y));
+          s_p[i] = w;
+        }
       }
     }
     __syncthreads();
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       const int i = k + 1 + (tid & 127);
       if (i < n) {
         const float2 vi = s_v[i], wi = s_p[i];
+#pragma unroll 4
         for (int j = k + 1 + (tid >> 7); j < n; j += 4) {
           const float2 vj = s_v[j], wj = s_p[j];
           float2 x = A[i + (size_t)n * j];
@@ -547,6 +560,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           }
       }
       __syncthreads();
+
       // Zn = 1.5 Z - 0.5 Z G
       const int nrz = (n + 127) / 128;
       for (int t = warp; t < nrz * ncb; t += HT / 32) {
@@ -596,8 +610,12 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     for (int c = tid >> 7; c < nc; c += HT / 128)
       for (int i = tid & 127; i < n; i += 128) Uc[i + (size_t)ldu * c] = make_float2(Z[i + (size_t)ldz * (cb + c)], 0.f);
     __syncthreads();
-    // 8 threads per column; the group owns the column for all reflectors
-    const int c = tid >> 3, sub = tid & 7;
+    // 8 threads per column; the group owns the column for all reflectors.
+    // The 4 groups of a warp take columns 8 apart: with ldu = n + 1 (n even)
+    // their 16-word windows then start 16 banks apart (2 wavefronts per warp
+    // access, the minimum for 32 float2)
+    const int grp = tid >> 3, sub = tid & 7, gw = grp >> 2;
+    const int c = (gw & 7) + 8 * (grp & 3) + 32 * (gw >> 3);
     if (c < nc) {
       float2* u = Uc + (size_t)ldu * c;
       for (int k = n - 2; k >= 0; --k) {
