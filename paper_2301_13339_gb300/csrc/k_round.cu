@@ -215,8 +215,6 @@ k_house_q(const T* __restrict__ S, int ls, int m, int nc, int nq, T* __restrict_
   T* A = reinterpret_cast<T*>(smem_raw);      // m x nc, ld m
   T* E = A + (size_t)m * nc;                  // m x nq, ld m
   __shared__ T s_tau[128];
-  __shared__ R s_red[QR_THREADS / 32];
-  __shared__ T s_scal;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_THREADS / 32;
   for (int e = tid; e < m * nc; e += QR_THREADS) {
     const int i = e % m, j = e / m;
@@ -225,32 +223,40 @@ k_house_q(const T* __restrict__ S, int ls, int m, int nc, int nq, T* __restrict_
   __syncthreads();
   const int kmax = min(m, nc);
   for (int k = 0; k < kmax; ++k) {
-    R part = (R)0;
-    for (int i = k + 1 + tid; i < m; i += QR_THREADS) part += sabs2(A[i + (size_t)m * k]);
-    part = warp_sum(part);
-    if (lane == 0) s_red[warp] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double xn2 = 0.0;
-      for (int w = 0; w < nw; ++w) xn2 += (double)s_red[w];
-      const double2 al = to_d2(A[k + (size_t)m * k]);
-      T tau = szero<T>(), scal = szero<T>();
-      if (xn2 > 0.0 || al.y != 0.0) {
-        const double nrm = sqrt(al.x * al.x + al.y * al.y + xn2);
-        const double beta = (al.x >= 0.0) ? -nrm : nrm;
-        from_d2(make_double2((beta - al.x) / beta, -al.y / beta), tau);
-        // scal = 1 / (alpha - beta)
-        const double dr = al.x - beta, di = al.y, den = dr * dr + di * di;
-        from_d2(make_double2(dr / den, -di / den), scal);
-        from_d2(make_double2(beta, 0.0), A[k + (size_t)m * k]);
+    // warp 0 forms the reflector and v in the data's precision, on the
+    // column scaled by its largest entry (no underflow or overflow of
+    // |alpha - beta|^2 whatever the data's scale; tau and v are scale free)
+    if (warp == 0) {
+      R amax = (R)0;
+      for (int i = k + lane; i < m; i += 32) {
+        const T x = A[i + (size_t)m * k];
+        amax = rmax(amax, rmax(rabs(sreal(x)), rabs(simag(x))));
       }
-      s_tau[k] = tau;
-      s_scal = scal;
+      for (int off = 16; off > 0; off >>= 1) amax = rmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+      T tau = szero<T>(), scal = szero<T>();
+      if (amax > (R)0) {
+        const R inv = (R)1 / amax;
+        R part = (R)0;
+        for (int i = k + 1 + lane; i < m; i += 32) part += sabs2(rscale(A[i + (size_t)m * k], inv));
+        part = warp_sum(part);
+        const T al = rscale(A[k + (size_t)m * k], inv);
+        const R ax = sreal(al), ay = simag(al);
+        if (part > (R)0 || ay != (R)0) {
+          const R nrm = sqrt(ax * ax + ay * ay + part);
+          const R beta = (ax >= (R)0) ? -nrm : nrm;
+          const R rb = (R)1 / beta;
+          tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
+          const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
+          scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
+          for (int i = k + 1 + lane; i < m; i += 32)
+            A[i + (size_t)m * k] = smul(A[i + (size_t)m * k], scal);
+          if (lane == 0) A[k + (size_t)m * k] = make_scalar<T>(beta * amax, (R)0);
+        }
+      }
+      if (lane == 0) s_tau[k] = tau;
     }
     __syncthreads();
-    const T scal = s_scal, tau = s_tau[k];
-    for (int i = k + 1 + tid; i < m; i += QR_THREADS) A[i + (size_t)m * k] = smul(A[i + (size_t)m * k], scal);
-    __syncthreads();
+    const T tau = s_tau[k];
     // trailing columns: A <- (I - conj(tau) v v^H) A, v = [1; A[k+1:, k]]
     const T ctau = conjg(tau);
     for (int j = k + 1 + warp; j < nc; j += nw) {

@@ -47,6 +47,15 @@ __host__ __device__ __forceinline__ double rscale(double a, double s) { return a
 __host__ __device__ __forceinline__ float2 rscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ double sreal(double a) { return a; }
 __host__ __device__ __forceinline__ float sreal(float2 a) { return a.x; }
+__host__ __device__ __forceinline__ double simag(double) { return 0.0; }
+__host__ __device__ __forceinline__ float simag(float2 a) { return a.y; }
+template <typename T> __host__ __device__ __forceinline__ T make_scalar(typename Sc<T>::R re, typename Sc<T>::R im);
+template <> __host__ __device__ __forceinline__ double make_scalar<double>(double re, double) { return re; }
+template <> __host__ __device__ __forceinline__ float2 make_scalar<float2>(float re, float im) { return make_float2(re, im); }
+__host__ __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
+__host__ __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
+__host__ __device__ __forceinline__ double rabs(double a) { return fabs(a); }
+__host__ __device__ __forceinline__ float rabs(float a) { return fabsf(a); }
 __host__ __device__ __forceinline__ double sabs2(double a) { return a * a; }
 __host__ __device__ __forceinline__ float sabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
