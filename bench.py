@@ -254,7 +254,7 @@ def gpu_arm(args, wl):
 # DRAM bytes (read + write) per launch from the committed ncu captures in
 # profiles/ (gram_eig_kernel_n128_line_2p20_c64.md); valid while that kernel
 # is unchanged.
-NCU_TRAFFIC = {"jacobi_eig_le128": 333056.0}
+NCU_TRAFFIC = {}
 
 
 def roofline(kernels, wl, peaks, peak_kind):

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
           s = t * c;
           u = rscale(apq, (R)1 / b);
           rot = 1;
-          atomicAdd(&s_nrot, 1);
+          s_nrot = 1;   // any rotation this sweep (same value from every writer)
         }
         s_rot[tid] = rot;
         s_c[tid] = c;
@@ -340,16 +340,22 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
         pk_set(A, i1, j0, b10);
         pk_set(A, i1, j1, b11);
       }
-      for (int e = tid; e < n * np; e += EIG_THREADS) {
-        const int P = e / n, row = e % n;
-        if (!s_rot[P]) continue;
-        const int p = s_pp[P], q = s_pq[P];
-        const R c = s_c[P], s = s_s[P];
-        const T u = s_u[P];
-        const T vp = V[row + ldv * p], vq = V[row + ldv * q];
-        // [vp, vq] J = [c vp - s conj(u) vq, s u vp + c vq]
-        V[row + ldv * p] = ssub(rscale(vp, c), smul(rscale(conjg(u), s), vq));
-        V[row + ldv * q] = sadd(smul(rscale(u, s), vp), rscale(vq, c));
+      // V <- V J: 16 threads per pair, each over rows r, r + 16, ... (the
+      // pair's parameters are read once per thread)
+      {
+        const int P = tid >> 4;
+        if (P < np && s_rot[P]) {
+          const int p = s_pp[P], q = s_pq[P];
+          const R c = s_c[P], s = s_s[P];
+          const T u = s_u[P];
+          const T su = rscale(u, s), scu = rscale(conjg(u), s);
+          for (int row = tid & 15; row < n; row += 16) {
+            const T vp = V[row + ldv * p], vq = V[row + ldv * q];
+            // [vp, vq] J = [c vp - s conj(u) vq, s u vp + c vq]
+            V[row + ldv * p] = ssub(rscale(vp, c), smul(scu, vq));
+            V[row + ldv * q] = sadd(smul(su, vp), rscale(vq, c));
+          }
+        }
       }
       __syncthreads();
     }
