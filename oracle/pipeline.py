@@ -17,15 +17,16 @@ from . import conv as C
 from . import toeplitz as T
 
 
-def decompose(x, eps, rmax, interleave=True):
-    """Steps 1-2.  x: 1D vector of length 2^d or 2D image (2^dy, 2^dx)."""
+def decompose(x, eps, rmax, interleave=True, delta=None):
+    """Steps 1-2.  x: 1D vector of length 2^d or 2D image (2^dy, 2^dx).
+    delta: SV drop-off rule instead of eps (Sec. 5 modification (3))."""
     x = np.asarray(x)
     if x.ndim == 1:
         v = x.astype(np.result_type(x, np.float64))
     else:
         v = Q.image_to_qtt_vector(x.astype(np.result_type(x, np.float64)), interleave)
     d = int(np.log2(v.size))
-    cores, ranks, sig = Q.tt_svd(v, d, eps, rmax)
+    cores, ranks, sig = Q.tt_svd(v, d, eps, rmax, delta)
     return cores, ranks, sig
 
 

@@ -102,7 +102,23 @@ def eps_rank(s, tau, rmax=None):
     return max(r, 1)
 
 
-def tt_svd(v, d, eps, rmax=None):
+def drop_rank(s, delta, rmax=None):
+    """Sec. 5 modification (3), "SV drop off": the first k (1-based) with
+    sigma_{k+1} / sigma_k < delta keeps sigma_1..sigma_k; with no such drop
+    every singular value is kept.  Then the cap R_max.  (Reading: the FIRST
+    drop below delta, scanning from the largest singular value.)"""
+    s = np.asarray(s, dtype=np.float64)
+    r = len(s)
+    for k in range(1, len(s)):
+        if s[k - 1] > 0 and s[k] / s[k - 1] < delta:
+            r = k
+            break
+    if rmax is not None and rmax > 0:
+        r = min(r, rmax)
+    return max(r, 1)
+
+
+def tt_svd(v, d, eps, rmax=None, delta=None):
     """Alg. 1 (TT-SVD) with the max-rank modification (1) of Sec. 5.
 
     v    : vector of length 2^d in QTT order.
@@ -111,6 +127,8 @@ def tt_svd(v, d, eps, rmax=None):
            ||A - A~||_F <= eps ||A||_F of Sec. 4; the printed sqrt(M-1) with
            M = 2 would give eps*||A|| per step instead).
     rmax : rank cap R_max (None or <= 0: no cap).
+    delta: if given (0 < delta < 1), the SV drop-off rule (``drop_rank``,
+           Sec. 5 modification (3)) replaces the eps rule.
     Returns (cores, ranks, sigmas) where sigmas[k] are the singular values of
     the k-th unfolding (for tests of the error bound).
     """
@@ -124,7 +142,7 @@ def tt_svd(v, d, eps, rmax=None):
         m = 2 * r_prev
         A = rest.reshape((m, -1), order='F')          # unfolding m_k x n_k
         U, s, Vh = np.linalg.svd(A, full_matrices=False)
-        r = eps_rank(s, tau, rmax)
+        r = drop_rank(s, delta, rmax) if delta else eps_rank(s, tau, rmax)
         cores.append(U[:, :r].reshape((r_prev, 2, r), order='F'))
         rest = s[:r, None] * Vh[:r, :]                 # A := Sigma V^*
         sigmas.append(s)

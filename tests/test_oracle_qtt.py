@@ -187,3 +187,26 @@ def test_norm_matches_full():
     v = rng.standard_normal(2 ** 9) + 1j * rng.standard_normal(2 ** 9)
     cores, _, _ = Q.tt_svd(v, 9, 0.0)
     assert abs(Q.norm(cores) - np.linalg.norm(v)) <= 1e-12 * np.linalg.norm(v)
+
+
+def test_drop_rank_rule():
+    # Sec. 5 modification (3): the first relative drop below delta
+    s = np.array([10.0, 9.0, 8.0, 0.1, 0.09, 0.001])
+    assert Q.drop_rank(s, 0.5) == 3
+    assert Q.drop_rank(s, 0.05) == 3          # 0.1 / 8 is the first ratio below 0.05
+    assert Q.drop_rank(s, 0.012) == 5         # 0.1 / 8 = 0.0125 passes, 0.001 / 0.09 does not
+    assert Q.drop_rank(s, 0.01) == 6          # no ratio below 0.01: keep all
+    assert Q.drop_rank(s, 0.5, rmax=2) == 2
+    assert Q.drop_rank(np.array([1.0, 0.0]), 0.5) == 1
+
+
+def test_drop_rule_recovers_exact_qtt_ranks():
+    # a sum of two exponentials has QTT rank 2 at every cut; with a small
+    # perturbation the singular values drop by many orders after the 2nd
+    rng = np.random.default_rng(9)
+    d = 10
+    i = np.arange(2 ** d)
+    v = np.exp(-i / 300.0) + 0.5 * np.exp(-i / 37.0) + 1e-9 * rng.standard_normal(2 ** d)
+    cores, ranks, sig = Q.tt_svd(v, d, 0.0, None, delta=1e-3)
+    assert ranks[1:-1] == [2] * (d - 1)
+    assert np.linalg.norm(Q.full(cores) - v) <= 1e-6 * np.linalg.norm(v)
