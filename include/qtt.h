@@ -64,11 +64,16 @@ typedef enum { QTT_F64 = 0, QTT_C64 = 2 } qtt_dtype;
  *          library's capacity QTT_RANK_CAP.
  *   refine 1: second Gram pass on the projected unfolding before the rank
  *          decision (relative accuracy of small singular values); 0: single
- *          pass.  FP64 calls always refine. */
+ *          pass.  FP64 calls always refine.
+ *   delta  0 < delta < 1: the SV drop-off rule (Sec. 5 modification (3))
+ *          replaces the eps rule: rank = the first k with
+ *          sigma_{k+1}/sigma_k < delta, all singular values if there is no
+ *          such drop, then the cap rmax.  <= 0: off. */
 typedef struct {
   double eps;
   int rmax;
   int refine;
+  double delta;
 } qtt_trunc;
 
 /* Largest TT rank any handle can hold (capacity of the per-cut Jacobi). */

@@ -51,7 +51,8 @@ class QTTError(RuntimeError):
 
 
 class _Trunc(ctypes.Structure):
-    _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int)]
+    _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int),
+                ("delta", ctypes.c_double)]
 
 
 _lib = None
@@ -236,13 +237,14 @@ class QTTOperator:
             pass
 
 
-def _trunc(eps, rmax, refine):
-    return _Trunc(float(eps), int(rmax or 0), int(bool(refine)))
+def _trunc(eps, rmax, refine, delta=0.0):
+    return _Trunc(float(eps), int(rmax or 0), int(bool(refine)), float(delta or 0.0))
 
 
-def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None):
+def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None, delta=0.0):
     """QTT reshape + TT-SVD (Alg. 1 with the max-rank cap of Sec. 5) of a
-    contiguous CUDA tensor (1D length 2^d, or 2D 2^dy x 2^dx row-major)."""
+    contiguous CUDA tensor (1D length 2^d, or 2D 2^dy x 2^dx row-major).
+    delta > 0: the SV drop-off rule (Sec. 5 (3)) instead of eps."""
     load()
     if not x.is_cuda or not x.is_contiguous():
         raise ValueError("x must be a contiguous CUDA tensor")
@@ -254,7 +256,7 @@ def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None
             raise ValueError(f"sizes must be powers of two >= 2, got {tuple(x.shape)}")
         shape.append(ln)
     sh = (ctypes.c_int * 2)(*(shape + [0] * (2 - len(shape))))
-    tr = _trunc(eps, rmax, refine)
+    tr = _trunc(eps, rmax, refine, delta)
     out = ctypes.c_void_p()
     _check(_lib.qtt_decompose(ctypes.c_void_p(x.data_ptr()), code, x.dim(), sh, int(interleave),
                               ctypes.byref(tr), _stream(stream), ctypes.byref(out)))

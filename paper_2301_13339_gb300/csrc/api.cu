@@ -213,6 +213,7 @@ static qtt_status cached_identity(int d, qtt_dtype dt, cudaStream_t s, qtt_op** 
 static qtt_status check_trunc(const qtt_trunc* tr) {
   if (!tr) { set_error("truncation parameters are NULL"); return QTT_EINVAL; }
   if (!(tr->eps >= 0.0) || tr->eps >= 1.0) { set_error("eps must be in [0, 1)"); return QTT_EINVAL; }
+  if (tr->delta >= 1.0 || tr->delta != tr->delta) { set_error("delta must be < 1 (<= 0: off)"); return QTT_EINVAL; }
   return QTT_OK;
 }
 

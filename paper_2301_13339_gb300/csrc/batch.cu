@@ -38,7 +38,7 @@ struct qtt_batch {
 namespace qtt {
 
 static qtt_status run_line(qtt_batch* b, int i, const void* x, void* y, cudaStream_t s) {
-  qtt_trunc tr{b->eps, b->rmax[i], b->refine};
+  qtt_trunc tr{b->eps, b->rmax[i], b->refine, 0.0};
   const int lg = b->d[i];
   qtt_tensor* f = nullptr;
   qtt_status st = qtt_decompose(x, b->dt, 1, &lg, 1, &tr, s, &f);

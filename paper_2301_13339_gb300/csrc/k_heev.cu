@@ -356,11 +356,20 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       const double tau2 = (a.dmodes > 1) ? a.eps * a.eps / (double)(a.dmodes - 1) * nrm2 : 0.0;
       double tail = 0.0;
       r = kmax;
-      for (int c = kmax - 1; c >= 1; --c) {
-        const double l = (double)s_lam[n - 1 - c] * s_trace;
-        tail += (l > 0.0 ? l : 0.0);
-        if (tail <= tau2) r = c;
-        else break;
+      if (a.delta > 0.0) {
+        // SV drop-off: the first lambda_{c+1} < delta^2 lambda_c
+        const double d2 = a.delta * a.delta;
+        for (int c = 1; c < kmax; ++c) {
+          const double lp = (double)s_lam[n - c], lc = (double)s_lam[n - 1 - c];
+          if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
+        }
+      } else {
+        for (int c = kmax - 1; c >= 1; --c) {
+          const double l = (double)s_lam[n - 1 - c] * s_trace;
+          tail += (l > 0.0 ? l : 0.0);
+          if (tail <= tau2) r = c;
+          else break;
+        }
       }
       if (a.rmax > 0 && r > a.rmax) r = a.rmax;
       if (r < 1) r = 1;

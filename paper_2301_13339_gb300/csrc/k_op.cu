@@ -114,7 +114,7 @@ qtt_status op_sinc_create(int d, double B, int normalize, double eps_op, qtt_dty
   qtt_tensor* G = nullptr;
   qtt_status st = tensor_alloc(gd, rank_caps(d + 1, 0, QTT_RANK_CAP), s, &G);
   if (st != QTT_OK) return st;
-  qtt_trunc tr{eps_op, 0, 1};
+  qtt_trunc tr{eps_op, 0, 1, 0.0};
   st = tt_svd<double>(chat, d + 1, tr, G, s);
   if (st != QTT_OK) { qtt_free(G); return st; }
   std::vector<int> rho(d + 2);

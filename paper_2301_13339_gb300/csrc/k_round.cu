@@ -727,11 +727,11 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
       // rank decision at eps_round: small eigenvalues to relative accuracy
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, tr.eps, d, rmax_eff,
                           nullptr, 0, lqk, V1, V, corek, y->ranks + k, nullptr, y->norm2, 0,
-                          y->status, s, 1);
+                          y->status, s, 1, tr.delta);
     } else {
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1, tr.eps, d, rmax_eff, nullptr, 0,
                           lqk, nullptr, corek, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,
-                          y->status, s);
+                          y->status, s, 0, tr.delta);
     }
     // Lc = core_k^H Zt  (t_k x lq_k)
     { QTT_PROF("round_trunc", s);

@@ -398,11 +398,21 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
       const double tau2 = (a.dmodes > 1) ? a.eps * a.eps / (double)(a.dmodes - 1) * nrm2 : 0.0;
       double tail = 0.0;
       r = kmax;
-      for (int c = kmax - 1; c >= 1; --c) {
-        const double l = s_lam[s_perm[c]];
-        tail += (l > 0.0 ? l : 0.0);
-        if (tail <= tau2) r = c;
-        else break;
+      if (a.delta > 0.0) {
+        // SV drop-off: the first sigma_{c+1} / sigma_c < delta, i.e.
+        // lambda_{c+1} < delta^2 lambda_c (eigenvalues of the Gram)
+        const double d2 = a.delta * a.delta;
+        for (int c = 1; c < kmax; ++c) {
+          const double lp = s_lam[s_perm[c - 1]], lc = s_lam[s_perm[c]];
+          if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
+        }
+      } else {
+        for (int c = kmax - 1; c >= 1; --c) {
+          const double l = s_lam[s_perm[c]];
+          tail += (l > 0.0 ? l : 0.0);
+          if (tail <= tau2) r = c;
+          else break;
+        }
       }
       if (a.rmax > 0 && r > a.rmax) r = a.rmax;
       if (r < 1) r = 1;
@@ -561,9 +571,11 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       int mg_cap, int mode, double eps, int dmodes, int rmax,
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
-                      int write_norm2, int* status, cudaStream_t s, int relative) {
+                      int write_norm2, int* status, cudaStream_t s, int relative,
+                      double delta) {
   EigArgs<T> a{};
   a.relative = relative;
+  a.delta = delta;
   a.G = G; a.ldp = ldp; a.mg_ptr = mg_ptr; a.mg_mul = mg_mul; a.mg_const = mg_const;
   a.mode = mode; a.eps = eps; a.dmodes = dmodes; a.rmax = rmax; a.ncols_ptr = ncols_ptr;
   a.ncols_mul = ncols_mul; a.ncols_const = ncols_const; a.U1 = U1; a.Uout = Uout;
@@ -578,12 +590,12 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s, int relative) {
+                     int* status, cudaStream_t s, int relative, double delta) {
   double2* gfin = (double2*)scratch_alloc(sizeof(double2) * ldp * ldp, s);
   launch_reduce<T>(gram_part, nparts, ldp, gfin, s);
   launch_eig_dense<T>(gfin, ldp, mg_ptr, mg_mul, 0, mg_cap, mode, eps, dmodes, rmax, ncols_ptr,
                       ncols_mul, ncols_const, U1, Uout, core_out, rank_out, sig_out, norm2,
-                      write_norm2, status, s, relative);
+                      write_norm2, status, s, relative, delta);
   scratch_free(gfin, s);
 }
 
@@ -611,7 +623,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   // tau = 0 keeps min(m, n) of them), so U can be the identity and
   // Sigma V^* is the unfolding itself: no factorisation, no data pass.
   int skip = 0;
-  if (tr.eps == 0.0)
+  if (tr.eps == 0.0 && !(tr.delta > 0.0))
     while (skip + 1 <= d - 2 && (1LL << (skip + 1)) <= std::min<long long>(rmax_eff, 1LL << (d - skip - 1)))
       ++skip;
   for (int k = 1; k <= skip; ++k) {
@@ -645,14 +657,14 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
       launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
-                         t->status, s, 1);
+                         t->status, s, 1, tr.delta);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     } else {
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
-                         t->norm2, k == skip + 1, t->status, s);
+                         t->norm2, k == skip + 1, t->status, s, 0, tr.delta);
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, core_k, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     }
@@ -672,17 +684,17 @@ template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_ten
 template void launch_eig_dense<double>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const double*,
                                        double*, double*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int);
+                                       cudaStream_t, int, double);
 template void launch_eig_dense<float2>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const float2*,
                                        float2*, float2*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int);
+                                       cudaStream_t, int, double);
 template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const double*, double*,
-                                      double*, int*, double*, double*, int, int*, cudaStream_t, int);
+                                      double*, int*, double*, double*, int, int*, cudaStream_t, int, double);
 template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const float2*, float2*,
-                                      float2*, int*, double*, double*, int, int*, cudaStream_t, int);
+                                      float2*, int*, double*, double*, int, int*, cudaStream_t, int, double);
 
 }  // namespace qtt
 

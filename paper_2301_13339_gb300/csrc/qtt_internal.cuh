@@ -212,7 +212,7 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s, int relative = 0);
+                     int* status, cudaStream_t s, int relative = 0, double delta = 0.0);
 
 // ------------------------------------------------------------- eigen
 enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
@@ -240,6 +240,7 @@ struct EigArgs {
   int write_norm2;
   int* status;
   int relative;         // 1: small eigenvalues needed to relative accuracy (Jacobi)
+  double delta;         // > 0: SV drop-off rank rule instead of eps (MODE_DECIDE)
   long long* phase_clk; // optional: clock64() at phase boundaries (diagnostics)
 };
 
@@ -256,7 +257,8 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       int mg_cap, int mode, double eps, int dmodes, int rmax,
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
-                      int write_norm2, int* status, cudaStream_t s, int relative = 0);
+                      int write_norm2, int* status, cudaStream_t s, int relative = 0,
+                      double delta = 0.0);
 
 // ------------------------------------------------------------- full
 template <typename T>

@@ -188,3 +188,25 @@ def test_pipeline_c64_2d(qlib, n):
     out = qlib.qtt_to_full(y).cpu().numpy().astype(np.complex128)
     ref = P.conv_sinc_qtt(x.astype(np.complex128), B, 3e-2, 64, eps_op=1e-7, eps_round=1e-7)
     assert C.rel_l2(out, ref) <= TOL32
+
+
+@pytest.mark.parametrize("dtype,noise,delta,tol", [(np.float64, 1e-9, 1e-3, 1e-12),
+                                                    (np.complex64, 1e-4, 1e-2, 1e-5)])
+def test_decompose_sv_dropoff(qlib, dtype, noise, delta, tol):
+    """Sec. 5 modification (3): ranks and reconstruction equal the oracle's."""
+    import torch
+    q = qlib
+    rng = np.random.default_rng(17)
+    d = 12
+    i = np.arange(2 ** d)
+    v = np.exp(-i / 700.0) + 0.5 * np.exp(-i / 90.0) + 0.25 * np.cos(i / 33.0)
+    if dtype == np.complex64:
+        v = v * np.exp(1j * i / 50.0)
+    v = v + noise * np.linalg.norm(v) / np.sqrt(v.size) * rng.standard_normal(v.size)
+    x = v.astype(dtype)
+    cores, ranks, _ = P.decompose(x.astype(np.complex128 if dtype == np.complex64 else np.float64),
+                                  0.0, None, delta=delta)
+    t = q.qtt_decompose(torch.from_numpy(x).cuda(), eps=0.0, rmax=0, refine=True, delta=delta)
+    assert t.ranks() == ranks
+    got = q.qtt_to_full(t).cpu().numpy()
+    assert C.rel_l2(got, Q.full(cores)) <= tol
