@@ -61,6 +61,19 @@ WORKLOADS = {
 }
 
 
+def max_over_ranks(values, device):
+    """Elementwise max of per-rank timings (the slowest rank sets the job
+    time); identity on one process.  `device` is the tensor device of the
+    process group's backend (cuda for NCCL, cpu for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -194,9 +207,7 @@ def gpu_arm(args, wl):
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms, = max_over_ranks([total_ms], dev)
         dist.barrier()
 
     # ---- e2e through the C ABI with host buffers
@@ -217,9 +228,7 @@ def gpu_arm(args, wl):
     torch.cuda.synchronize(dev)
     e2e_ms = sum(a.elapsed_time(b) for a, b in eve)
     if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, = max_over_ranks([e2e_ms], dev)
 
     # ---- profiled pass: per-kernel CUDA-event times on the same workload
     import ctypes
@@ -437,9 +446,7 @@ def batch_main(args, wl, metric):
     torch.cuda.synchronize(dev)
     e2e_ms = sum(a.elapsed_time(b) for a, b in eve)
     if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
+        total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], dev)
     # per-kernel times from a profiled eager pass (concurrent streams: shares)
     import ctypes
     L.qtt_profile_enable.argtypes = [ctypes.c_int]
