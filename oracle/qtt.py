@@ -88,13 +88,17 @@ def qtt_vector_to_image(v, ny, nx, interleave=True):
 # (1), "max rank TT-SVD").
 # --------------------------------------------------------------------------
 def eps_rank(s, tau, rmax=None):
+    """Sec. 4 eps-rank: the smallest r >= 1 with sqrt(sum_{i>r} s_i^2) <= tau,
+    then the cap.  tau = 0 (eps = 0) is the max rank TT-SVD of Sec. 5
+    modification (1): no threshold at all, every singular value up to the cap
+    is kept (exact zeros included), so the ranks follow Lemma 5.1's shapes."""
     s = np.asarray(s, dtype=np.float64)
     n = len(s)
     # tail[r] = sqrt(sum_{i >= r} s_i^2), r = 0..n
     tail2 = np.concatenate([np.cumsum((s ** 2)[::-1])[::-1], [0.0]])
     r = n
     for cand in range(1, n + 1):
-        if tail2[cand] <= tau * tau:
+        if tau > 0 and tail2[cand] <= tau * tau:
             r = cand
             break
     if rmax is not None and rmax > 0:

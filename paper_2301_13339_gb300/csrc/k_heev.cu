@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           const double lp = (double)s_lam[n - c], lc = (double)s_lam[n - 1 - c];
           if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
         }
-      } else {
+      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
         for (int c = kmax - 1; c >= 1; --c) {
           const double l = (double)s_lam[n - 1 - c] * s_trace;
           tail += (l > 0.0 ? l : 0.0);

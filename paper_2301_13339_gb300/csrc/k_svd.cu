@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
           const double lp = s_lam[s_perm[c - 1]], lc = s_lam[s_perm[c]];
           if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
         }
-      } else {
+      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
         for (int c = kmax - 1; c >= 1; --c) {
           const double l = s_lam[s_perm[c]];
           tail += (l > 0.0 ? l : 0.0);

@@ -151,6 +151,9 @@ def test_eps_rank_definition():
     assert Q.eps_rank(s, np.sqrt(0.5 ** 2 + 0.25 ** 2)) == 3
     assert Q.eps_rank(s, 100.0) == 1
     assert Q.eps_rank(s, 0.0, rmax=2) == 2
+    # eps = 0 is the cap-only TT-SVD: exact zeros are kept up to the cap
+    assert Q.eps_rank(np.array([3.0, 0.0, 0.0]), 0.0) == 3
+    assert Q.eps_rank(np.array([3.0, 0.0, 0.0]), 1e-300) == 1
 
 
 def test_round_exact_and_bounded():
