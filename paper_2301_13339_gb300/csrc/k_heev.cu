@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __shared__ float s_d[HMAX], s_e[HMAX], s_e2[HMAX], s_lam[HMAX];
   __shared__ float2 s_tau[HMAX], s_v[HMAX], s_p[HMAX];
   __shared__ float s_redf[HT / 32];
+  __shared__ float s_red4[4];
+  __shared__ float2 s_pdw[HT / 32];
   __shared__ double s_redd[HT / 32];
   __shared__ float s_xn2, s_glo, s_ghi, s_pivmin;
   __shared__ double s_trace;
@@ -124,8 +126,13 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+#ifdef QTT_HEEV_TRI_PROFILE
+#define HEEV_STAMP(i) \
+  do { if (a.phase_clk && tid == 0 && (i) < 6) a.phase_clk[i] = clock64(); } while (0)
+#else
 #define HEEV_STAMP(i) \
   do { if (a.phase_clk && tid == 0) a.phase_clk[i] = clock64(); } while (0)
+#endif
   HEEV_STAMP(0);
   float2* A = reinterpret_cast<float2*>(smem_raw);        // n x n, ld n
   float* Z = reinterpret_cast<float*>(A + (size_t)n * n);  // n x n, ld ldz = n + 1
@@ -156,54 +163,64 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __syncthreads();
 
   HEEV_STAMP(1);
-  // ---- 1. Householder tridiagonalisation (lower).  Per column k: warp 0
-  // forms the reflector and v (shuffle reductions, no block-wide sum); all
-  // threads form the partial products of p = A22 v; warp 0 finishes
-  // p, alpha2 = -tau (p^H v) / 2 and w = tau A22 v + alpha2 v; all threads
-  // apply A22 -= v w^H + w v^H.  Four barriers per column.
+  // ---- 1. Householder tridiagonalisation (lower).  Per column k, all
+  // phases spread over the block (5 barriers): the column norm by the 128
+  // row threads; the reflector scalars computed redundantly by every thread
+  // (no serial section) and v formed by the row threads; the partial
+  // products of A22 v together with the partial sums of (A22 v)^H v (p^H v
+  // is linear in them); w = p + alpha2 v by the row threads; the rank-2
+  // update A22 -= v w^H + w v^H.
+#ifdef QTT_HEEV_TRI_PROFILE
+  long long tp_acc[4] = {0, 0, 0, 0}, tp_t = clock64();
+#define TRI_MARK(i) do { if (tid == 0) { const long long t_ = clock64(); tp_acc[i] += t_ - tp_t; tp_t = t_; } } while (0)
+#else
+#define TRI_MARK(i) do { } while (0)
+#endif
   for (int k = 0; k < n - 1; ++k) {
-    if (warp == 0) {
+    const int irow = k + 1 + tid;                 // row of the threads tid < 128
+    const bool rowt = (tid < 128) && (irow < n);
+    float2 xk = make_float2(0.f, 0.f);
+    if (tid < 128) {
       float part = 0.f;
-      for (int i = k + 2 + lane; i < n; i += 32) {
-        const float2 x = A[i + (size_t)n * k];
-        part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
+      if (rowt) {
+        xk = A[irow + (size_t)n * k];
+        if (irow >= k + 2) part = fmaf(xk.x, xk.x, xk.y * xk.y);
       }
-      const float xn2 = warp_sum(part);
-      // on the unit-trace matrix a column below 1e-18 is negligible (and
-      // would underflow |alpha - beta|^2): it is left as it is
-      const float2 al = A[(k + 1) + (size_t)n * k];
-      float2 tau = make_float2(0.f, 0.f), scal = make_float2(0.f, 0.f);
-      float beta = al.x;
-      const float nrm = sqrtf(al.x * al.x + al.y * al.y + xn2);
-      if ((xn2 > 0.f || al.y != 0.f) && nrm > 1e-18f) {
-        beta = (al.x >= 0.f) ? -nrm : nrm;
-        const float rb = 1.f / beta;
-        tau = make_float2((beta - al.x) * rb, -al.y * rb);
-        const float dr = al.x - beta, di = al.y, rden = 1.f / (dr * dr + di * di);
-        scal = make_float2(dr * rden, -di * rden);
-      }
-      const bool act = (tau.x != 0.f || tau.y != 0.f);
-      for (int i = k + 1 + lane; i < n; i += 32) {
-        float2 v;
-        if (i == k + 1) v = make_float2(1.f, 0.f);
-        else {
-          v = A[i + (size_t)n * k];
-          if (act) {
-            v = cmulf(v, scal);
-            A[i + (size_t)n * k] = v;
-          }
-        }
-        s_v[i] = v;
-      }
-      if (lane == 0) {
-        s_e[k] = beta;
-        s_d[k] = A[k + (size_t)n * k].x;
-        s_tau[k] = tau;
-      }
+      part = warp_sum(part);
+      if (lane == 0) s_red4[warp] = part;
     }
     __syncthreads();
-    const float2 tau = s_tau[k];
-    if (tau.x == 0.f && tau.y == 0.f) continue;   // uniform: s_tau is shared
+    // on the unit-trace matrix a column below 1e-18 is negligible (and
+    // would underflow |alpha - beta|^2): it is left as it is
+    const float xn2 = (s_red4[0] + s_red4[1]) + (s_red4[2] + s_red4[3]);
+    const float2 al = A[(k + 1) + (size_t)n * k];
+    float2 tau = make_float2(0.f, 0.f), scal = make_float2(0.f, 0.f);
+    float beta = al.x;
+    const float nrm = sqrtf(al.x * al.x + al.y * al.y + xn2);
+    if ((xn2 > 0.f || al.y != 0.f) && nrm > 1e-18f) {
+      beta = (al.x >= 0.f) ? -nrm : nrm;
+      const float rb = 1.f / beta;
+      tau = make_float2((beta - al.x) * rb, -al.y * rb);
+      const float dr = al.x - beta, di = al.y, rden = 1.f / (dr * dr + di * di);
+      scal = make_float2(dr * rden, -di * rden);
+    }
+    const bool act = (tau.x != 0.f || tau.y != 0.f);   // identical in every thread
+    if (rowt) {
+      float2 v = make_float2(1.f, 0.f);
+      if (irow > k + 1) {
+        v = act ? cmulf(xk, scal) : xk;
+        if (act) A[irow + (size_t)n * k] = v;
+      }
+      s_v[irow] = v;
+    }
+    if (tid == 0) {
+      s_e[k] = beta;
+      s_d[k] = A[k + (size_t)n * k].x;
+      s_tau[k] = tau;
+    }
+    __syncthreads();
+    TRI_MARK(0);
+    if (!act) continue;   // uniform; the barrier above ends every read of s_red4
     // partial products of A22 v: thread t owns row k+1+(t & 127) and the
     // columns congruent to (t >> 7) mod 4; lanes of a warp read consecutive rows
     {
@@ -211,7 +228,9 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       float2 acc[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+      float2 vi = make_float2(0.f, 0.f);
       if (i < n) {
+        vi = s_v[i];
         int j = k + 1 + ph;
         // four independent chains (columns j, j+4, j+8, j+12)
         for (; j + 12 < n; j += 16) {
@@ -228,44 +247,35 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
           acc[0].y = fmaf(aij.x, vj.y, fmaf(aij.y, vj.x, acc[0].y));
         }
       }
-      s_part[ph][tid & 127] = make_float2(acc[0].x + acc[1].x + acc[2].x + acc[3].x,
-                                          acc[0].y + acc[1].y + acc[2].y + acc[3].y);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      // p = tau A22 v (rows k+1..n-1, 4 per lane), p^H v, w = p + alpha2 v
-      float2 pl[4];
-      float2 pd = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = k + 1 + lane + 32 * t;
-        pl[t] = make_float2(0.f, 0.f);
-        if (i < n) {
-          const int il = i - k - 1;
-          float2 acc = s_part[0][il];
-          for (int ph = 1; ph < 4; ++ph) { acc.x += s_part[ph][il].x; acc.y += s_part[ph][il].y; }
-          const float2 pi = cmulf(tau, acc), vi = s_v[i];
-          pl[t] = pi;
-          pd.x = fmaf(pi.x, vi.x, fmaf(pi.y, vi.y, pd.x));
-          pd.y = fmaf(pi.x, vi.y, fmaf(-pi.y, vi.x, pd.y));
-        }
-      }
+      const float2 a4 = make_float2(acc[0].x + acc[1].x + acc[2].x + acc[3].x,
+                                    acc[0].y + acc[1].y + acc[2].y + acc[3].y);
+      s_part[ph][tid & 127] = a4;
+      // conj(a4) v_i, summed over the block = (A22 v)^H v
+      float2 pd = make_float2(fmaf(a4.x, vi.x, a4.y * vi.y), fmaf(a4.x, vi.y, -a4.y * vi.x));
       pd = warp_sum(pd);
-      const float2 t2 = cmulf(tau, pd);
-      const float2 al2 = make_float2(-0.5f * t2.x, -0.5f * t2.y);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = k + 1 + lane + 32 * t;
-        if (i < n) {
-          const float2 vi = s_v[i];
-          float2 w = pl[t];
-          w.x = fmaf(al2.x, vi.x, fmaf(-al2.y, vi.y, w.x));
-          w.y = fmaf(al2.x, vi.y, fmaf(al2.y, vi.x, w.y));
-          s_p[i] = w;
-        }
-      }
+      if (lane == 0) s_pdw[warp] = pd;
     }
     __syncthreads();
+    TRI_MARK(1);
+    if (rowt) {
+      // p = tau A22 v; p^H v = conj(tau) (A22 v)^H v; w = p + alpha2 v with
+      // alpha2 = -tau (p^H v) / 2
+      const int il = irow - k - 1;
+      float2 acc = s_part[0][il];
+      for (int ph = 1; ph < 4; ++ph) { acc.x += s_part[ph][il].x; acc.y += s_part[ph][il].y; }
+      float2 sv = make_float2(0.f, 0.f);
+      for (int w = 0; w < HT / 32; ++w) { sv.x += s_pdw[w].x; sv.y += s_pdw[w].y; }
+      const float2 pdt = cmulf(cconjf(tau), sv);
+      const float2 t2 = cmulf(tau, pdt);
+      const float2 al2 = make_float2(-0.5f * t2.x, -0.5f * t2.y);
+      const float2 pi = cmulf(tau, acc), vi = s_v[irow];
+      float2 w = pi;
+      w.x = fmaf(al2.x, vi.x, fmaf(-al2.y, vi.y, w.x));
+      w.y = fmaf(al2.x, vi.y, fmaf(al2.y, vi.x, w.y));
+      s_p[irow] = w;
+    }
+    __syncthreads();
+    TRI_MARK(2);
     // A22 -= v w^H + w v^H: thread t owns row k+1+(t & 127), columns in
     // steps of 4 from k+1+(t >> 7)
     {
@@ -284,7 +294,13 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       }
     }
     __syncthreads();
+    TRI_MARK(3);
   }
+#ifdef QTT_HEEV_TRI_PROFILE
+  // diagnostic build only: the four sub-phase totals of the reduction
+  if (tid == 0 && a.phase_clk) for (int i = 0; i < 4; ++i) a.phase_clk[6 + i] = tp_acc[i];
+#endif
+#undef TRI_MARK
   if (tid == 0) {
     s_d[n - 1] = A[(n - 1) + (size_t)n * (n - 1)].x;
     float glo = FLT_MAX, ghi = -FLT_MAX, me2 = 0.f;
