@@ -320,6 +320,11 @@ void qtt_debug_small_eigh_clocks(long long* dev10);
  * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */
 void qtt_debug_set_eig_solver(int which);
 
+/* Diagnostics: sweep count of the FP32 relative-accuracy Jacobi passes
+ * (refinement pass of the TT-SVD and of the rounding); default 3; 0 = run
+ * to the convergence test; negative = back to the default. */
+void qtt_debug_set_refine_sweeps(int sweeps);
+
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);
 

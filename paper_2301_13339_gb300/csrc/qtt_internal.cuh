@@ -241,6 +241,7 @@ struct EigArgs {
   int* status;
   int relative;         // 1: small eigenvalues needed to relative accuracy (Jacobi)
   double delta;         // > 0: SV drop-off rank rule instead of eps (MODE_DECIDE)
+  int max_sweeps;       // Jacobi sweep limit (0: the default, flagged when reached)
   long long* phase_clk; // optional: clock64() at phase boundaries (diagnostics)
 };
 
