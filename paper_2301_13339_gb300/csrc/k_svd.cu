@@ -425,7 +425,39 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   if (a.sig_out)
     for (int c = tid; c < mg; c += EIG_THREADS) a.sig_out[c] = s_lam[s_perm[c]];
   const int ncopy = (a.mode == EIG_MODE_ALL) ? mg : r;
-  if (Sc<T>::cplx) {
+  if (Sc<T>::cplx && ncopy * n <= (n * (n + 1)) / 2) {
+    // FP32, the kept columns only (rank decisions): one Newton-Schulz step on
+    // V_r = V[:, perm[:ncopy]] (gathered into the free packed region),
+    // G_r = V_r^H V_r in the free V region, U = V_r (3 I - G_r) / 2
+    T* Vr = A;
+    for (int e = tid; e < n * ncopy; e += EIG_THREADS) {
+      const int i = e % n, c = e / n;
+      Vr[e] = V[i + ldv * s_perm[c]];
+    }
+    __syncthreads();
+    T* Gr = V;
+    {
+      const int wp = tid >> 5, ln = tid & 31;
+      for (int e = wp; e < ncopy * ncopy; e += EIG_THREADS / 32) {
+        const int c1 = e % ncopy, c2 = e / ncopy;
+        if (c1 > c2) continue;                       // uniform per warp
+        T acc = szero<T>();
+        for (int i = ln; i < n; i += 32) macc(acc, Vr[i + n * c1], Vr[i + n * c2]);
+        acc = warp_sum(acc);
+        if (ln == 0) {
+          Gr[c1 + ncopy * c2] = acc;
+          Gr[c2 + ncopy * c1] = conjg(acc);
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
+      const int i = e % mg, c = e / mg;
+      T corr = szero<T>();
+      for (int l = 0; l < ncopy; ++l) mac(corr, Vr[i + n * l], Gr[l + ncopy * c]);
+      a.Uout[e] = ssub(rscale(Vr[i + n * c], (typename Sc<T>::R)1.5), rscale(corr, (typename Sc<T>::R)0.5));
+    }
+  } else if (Sc<T>::cplx) {
     // FP32: the accumulated rotations leave V orthonormal only to
     // ~sqrt(#rotations) eps; one Newton-Schulz step V (3 I - V^H V) / 2
     // squares that error.  G = V^H V goes into the (no longer needed) packed A.
