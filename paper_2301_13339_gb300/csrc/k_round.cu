@@ -340,17 +340,28 @@ __global__ void k_z(const R* O, int Pin, int Pout, const T* B1, const int* xr, i
     }
   Z[(a + r0 * p) + (size_t)ldz * (j + 2 * tt)] = acc.get();
 }
-// S[s + l0 u] = sum_{c < R0} WL[s + l0 c] Z[c + ldz u]
+// S[s + l0 u] = sum_{c < R0} WL[s + l0 c] Z[c + ldz u]  (R0 = P r up to ~1e3):
+// KS_SPLIT threads share one output, each a compensated partial sum over
+// every KS_SPLIT-th c, combined by shuffles within the group
+constexpr int KS_SPLIT = 8;
 template <typename T>
 __global__ void k_s(const T* WL, int l0, const T* Z, int ldz, const int* xr, int k, int Pin,
                     int ncolu, T* S) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)l0 * ncolu) return;
+  const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const long long e = g / KS_SPLIT;
+  const int part = (int)(g % KS_SPLIT);
+  const bool live = e < (long long)l0 * ncolu;
   const int R0 = Pin * xr[k - 1];
-  const int s = (int)(e % l0), u = (int)(e / l0);
   typename KAccOf<T>::type acc;
-  for (int c = 0; c < R0; ++c) acc.add_mul(WL[s + (size_t)l0 * c], Z[c + (size_t)ldz * u]);
-  S[e] = acc.get();
+  if (live) {
+    const int s = (int)(e % l0), u = (int)(e / l0);
+    for (int c = part; c < R0; c += KS_SPLIT)
+      acc.add_mul(WL[s + (size_t)l0 * c], Z[c + (size_t)ldz * u]);
+  }
+  T v = acc.get();
+  // groups of KS_SPLIT consecutive lanes (blockDim is a multiple of 32)
+  for (int off = 1; off < KS_SPLIT; off <<= 1) v = sadd(v, shfl_xor_s(v, off));
+  if (live && part == 0) S[e] = v;
 }
 // column Gram  G[u + ldg v] = sum_s conj(S[s + ls u]) S[s + ls v],  u, v < n (rows ls)
 template <typename T>
@@ -672,7 +683,8 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     if (k == 1) break;
     const int l0 = l[k - 1];
     { QTT_PROF("round_orth", s);
-    k_s<T><<<GRID1((long long)l0 * n2)>>>(WL + wloff[k - 1], l0, Z, ldz, x->ranks, k, P[k - 1], n2, S);
+    k_s<T><<<GRID1((long long)l0 * n2 * KS_SPLIT)>>>(WL + wloff[k - 1], l0, Z, ldz, x->ranks, k,
+                                                    P[k - 1], n2, S);
     }
     const int lq0 = lq[k - 1];
     {

@@ -102,6 +102,11 @@ __device__ __forceinline__ float2 warp_sum(float2 v) {
   }
   return v;
 }
+// one shuffle of a T value (full-warp mask; all lanes must take part)
+__device__ __forceinline__ double shfl_xor_s(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ float2 shfl_xor_s(float2 v, int off) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+}
 __device__ __forceinline__ float warp_sum(float v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
