@@ -168,8 +168,14 @@ def gpu_arm(args, wl):
     L = q.lib()
     stream = torch.cuda.Stream(device=dev)
     N = 2 ** wl["d"]
-    x, _ = make_input(wl, rank)
+    x, clean = make_input(wl, rank)
     xd = torch.from_numpy(x).to(dev)
+    # operator plan (built once per (n, B, eps_op); reported apart from the steps)
+    torch.cuda.synchronize(dev)
+    t_plan = time.perf_counter()
+    q.qtt_op_create(wl["d"], wl["B"], True, wl["eps_op"], q.QTT_C64)
+    torch.cuda.synchronize(dev)
+    plan_ms = 1e3 * (time.perf_counter() - t_plan)
     out = torch.empty(N, dtype=torch.complex64, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     refine = args.refine
@@ -257,13 +263,14 @@ def gpu_arm(args, wl):
     L.qtt_profile_reset()
     out_host = out.cpu().numpy()
     return dict(world=world, rank=rank, total_ms=total_ms, e2e_ms=e2e_ms, wall_s=t_wall,
-                clocks=clk, kernels=kern, out=out_host, x=x, dev=dev)
+                clocks=clk, kernels=kern, out=out_host, x=x, clean=clean, dev=dev,
+                plan_ms=plan_ms)
 
 
 # DRAM bytes (read + write) per launch from the committed ncu captures in
-# profiles/ (gram_eig_kernel_n128_line_2p20_c64.md); valid while that kernel
+# profiles/ (heev_tri_kernel_n128_line_2p20_c64.md); valid while that kernel
 # is unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"heev_le128": 380416.0}
 
 
 def roofline(kernels, wl, peaks, peak_kind):
@@ -687,12 +694,18 @@ def main():
             # sample written once (16 B per complex64 sample)
             "hbm_floor": {"bytes_per_sample": 16,
                           "frac": 16.0 * N * args.steps / (res["total_ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-            "clocks": res["clocks"], "refine": args.refine}
+            "clocks": res["clocks"], "refine": args.refine,
+            "plan_ms": res["plan_ms"]}
     if not args.no_cpu_baseline:
         ref, t = run_oracle(res["x"], wl)
         from oracle import conv as C
         e2 = C.rel_l2(res["out"].astype(np.complex128), ref)
         line["parity"] = {"e2_vs_oracle": e2, "tol": wl["tol"], "ok": bool(e2 <= wl["tol"])}
+        # the paper's denoising metric: E2 against the noise-free convolution
+        from oracle import pipeline as P
+        ref_clean = P.conv_dense(res["clean"], wl["B"])
+        line["e2_vs_noise_free"] = C.rel_l2(res["out"].astype(np.complex128), ref_clean)
+        line["e2_noisy_input_vs_noise_free"] = C.rel_l2(P.conv_dense(res["x"].astype(np.complex128), wl["B"]), ref_clean)
         line["cpu_baseline"] = {"value": N / t / 1e6, "unit": "Msamples/s",
                                 "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                                 "sample": f"one full line (2^{wl['d']} samples), numpy FP64"}
