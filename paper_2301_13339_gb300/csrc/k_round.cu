@@ -18,6 +18,7 @@
 //                    the deterministic rounding step.
 // All factorisations are Gram + Jacobi (+ refinement) on <= 128 x 128.
 #include "qtt_internal.cuh"
+#include "house_qr.cuh"
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -205,99 +206,23 @@ __global__ void k_normalize(T* A, int lk, const int* xr, int k, int Pout) {
 // read from S (nc x m, ld ls); writes the first nq columns of Q (m x nq, ld m)
 // with orthonormal columns spanning the row space of S (Householder QR is
 // backward stable and keeps Q orthonormal also when S is rank deficient).
-// H_k = I - tau_k v_k v_k^H (LAPACK's convention), Q = H_1 ... H_kmax.
-constexpr int QR_THREADS = 256;
+// The factorisation and the formation of Q are in house_qr.cuh.
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS)
 k_house_q(const T* __restrict__ S, int ls, int m, int nc, int nq, T* __restrict__ Q) {
-  using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);      // m x nc, ld m
   T* E = A + (size_t)m * nc;                  // m x nq, ld m
   __shared__ T s_tau[128];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = QR_THREADS / 32;
-  for (int e = tid; e < m * nc; e += QR_THREADS) {
+  for (int e = threadIdx.x; e < m * nc; e += QR_THREADS) {
     const int i = e % m, j = e / m;
     A[e] = conjg(S[j + (size_t)ls * i]);
   }
   __syncthreads();
   const int kmax = min(m, nc);
-  for (int k = 0; k < kmax; ++k) {
-    // warp 0 forms the reflector and v in the data's precision, on the
-    // column scaled by its largest entry (no underflow or overflow of
-    // |alpha - beta|^2 whatever the data's scale; tau and v are scale free)
-    if (warp == 0) {
-      R amax = (R)0;
-      for (int i = k + lane; i < m; i += 32) {
-        const T x = A[i + (size_t)m * k];
-        amax = rmax(amax, rmax(rabs(sreal(x)), rabs(simag(x))));
-      }
-      for (int off = 16; off > 0; off >>= 1) amax = rmax(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-      T tau = szero<T>(), scal = szero<T>();
-      if (amax > (R)0) {
-        const R inv = (R)1 / amax;
-        R part = (R)0;
-        for (int i = k + 1 + lane; i < m; i += 32) part += sabs2(rscale(A[i + (size_t)m * k], inv));
-        part = warp_sum(part);
-        const T al = rscale(A[k + (size_t)m * k], inv);
-        const R ax = sreal(al), ay = simag(al);
-        if (part > (R)0 || ay != (R)0) {
-          const R nrm = sqrt(ax * ax + ay * ay + part);
-          const R beta = (ax >= (R)0) ? -nrm : nrm;
-          const R rb = (R)1 / beta;
-          tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
-          const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
-          scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
-          for (int i = k + 1 + lane; i < m; i += 32)
-            A[i + (size_t)m * k] = smul(A[i + (size_t)m * k], scal);
-          if (lane == 0) A[k + (size_t)m * k] = make_scalar<T>(beta * amax, (R)0);
-        }
-      }
-      if (lane == 0) s_tau[k] = tau;
-    }
-    __syncthreads();
-    const T tau = s_tau[k];
-    // trailing columns: A <- (I - conj(tau) v v^H) A, v = [1; A[k+1:, k]]
-    const T ctau = conjg(tau);
-    for (int j = k + 1 + warp; j < nc; j += nw) {
-      T w = szero<T>();
-      for (int i = k + lane; i < m; i += 32) {
-        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
-        macc(w, vi, A[i + (size_t)m * j]);
-      }
-      w = warp_sum(w);
-      const T f = smul(ctau, w);
-      for (int i = k + lane; i < m; i += 32) {
-        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
-        A[i + (size_t)m * j] = ssub(A[i + (size_t)m * j], smul(vi, f));
-      }
-    }
-    __syncthreads();
-  }
-  // Q = H_1 ... H_kmax applied to the first nq columns of I
-  for (int e = tid; e < m * nq; e += QR_THREADS) {
-    const int i = e % m, j = e / m;
-    E[e] = (i == j) ? sone(T()) : szero<T>();
-  }
-  __syncthreads();
-  for (int k = kmax - 1; k >= 0; --k) {
-    const T tau = s_tau[k];
-    for (int j = warp; j < nq; j += nw) {
-      T w = szero<T>();
-      for (int i = k + lane; i < m; i += 32) {
-        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
-        macc(w, vi, E[i + (size_t)m * j]);
-      }
-      w = warp_sum(w);
-      const T f = smul(tau, w);
-      for (int i = k + lane; i < m; i += 32) {
-        const T vi = (i == k) ? sone(T()) : A[i + (size_t)m * k];
-        E[i + (size_t)m * j] = ssub(E[i + (size_t)m * j], smul(vi, f));
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < m * nq; e += QR_THREADS) Q[e] = E[e];
+  house_qr_factor(A, m, nc, s_tau);
+  house_form_q(A, m, kmax, nq, s_tau, E);
+  for (int e = threadIdx.x; e < m * nq; e += QR_THREADS) Q[e] = E[e];
 }
 
 // ---------------------------------------------------------------- step 2

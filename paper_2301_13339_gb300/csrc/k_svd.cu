@@ -15,6 +15,7 @@
 // Ranks live on the device: every kernel reads the ranks it needs, grids are
 // sized for the host-side capacities.
 #include "qtt_internal.cuh"
+#include "house_qr.cuh"
 #include <cstdio>
 #include <algorithm>
 
@@ -596,6 +597,32 @@ __global__ void identity_level_kernel(T* core, int rp, int* ranks, int k) {
   core[e] = (row == col) ? sone(T()) : szero<T>();
 }
 
+// A TT-SVD level that keeps every singular value (cap-only truncation with
+// n_k no larger than the cap): any orthonormal basis of the unfolding's
+// column space gives the same tensor, so the level is M = Q R by Householder
+// (one CTA): core_k = Q, and R (n x n, upper triangular) is the next
+// unfolding -- the same memory layout, since the column-major reshape of an
+// r_k x n_k remainder to 2 r_k x n_k / 2 moves nothing.  The rank is n.
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) qr_level_kernel(const T* M, int* rk, int k, int n,
+                                                              T* core, T* Rnext) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_tau[128];
+  const int m = 2 * rk[k - 1];
+  T* A = reinterpret_cast<T*>(smem_raw);      // m x n
+  T* E = A + (size_t)m * n;                   // m x n
+  for (int e = threadIdx.x; e < m * n; e += QR_THREADS) A[e] = M[e];
+  __syncthreads();                            // M is read in full before Rnext (may alias) is written
+  house_qr_factor(A, m, n, s_tau);
+  for (int e = threadIdx.x; e < n * n; e += QR_THREADS) {
+    const int i = e % n, j = e / n;
+    Rnext[e] = (i <= j) ? A[i + (size_t)m * j] : szero<T>();
+  }
+  house_form_q(A, m, n, n, s_tau, E);
+  for (int e = threadIdx.x; e < m * n; e += QR_THREADS) core[e] = E[e];
+  if (threadIdx.x == 0) rk[k] = n;
+}
+
 __global__ void set_boundary_ranks_kernel(int* ranks, int d) {
   if (threadIdx.x == 0) {
     ranks[0] = 1;
@@ -684,6 +711,20 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
     T* Wout = (k == d - 1) ? cores + t->off[d - 1] : (refine ? bufB : (M == bufA ? bufB : bufA));
     const int fold_next = (k < d - 1) ? 1 : -1;
     const int ldp_next = 2 * rcapk;
+    if (tr.eps == 0.0 && !(tr.delta > 0.0) && k > skip + 1 && n <= 64 && n == rcapk) {
+      // every singular value is kept from here on (n_k halves each level)
+      static bool qr_cfg = false;
+      if (!qr_cfg) {
+        cudaFuncSetAttribute(qr_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 2 * 128 * 64));
+        qr_cfg = true;
+      }
+      QTT_PROF("qr_level", s);
+      qr_level_kernel<T><<<1, QR_THREADS, sizeof(T) * 2 * (size_t)mcap * n, s>>>(
+          M, rk, k, (int)n, core_k, Wout);
+      M = Wout;
+      continue;
+    }
     if (refine) {
       // pass 1: all eigenvectors of M M^H
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
