@@ -372,6 +372,46 @@ __global__ void k_proj_rows(const T* U, const T* Zt, const int* mptr, int mul, c
   for (int a = 0; a < m; ++a) acc.add_cmul(U[a + (size_t)m * c], Zt[a + (size_t)m * u]);
   W[c + (size_t)rr * u] = acc.get();
 }
+// Step 3 with more rows than columns (m = 2 t_{k-1} > lq_k): Zt = Q R by
+// Householder (one CTA) first, so the rank decision factors the
+// lq_k x lq_k Gram of R instead of the m x m Gram of Zt (whose rank is at
+// most lq_k).  Q: m x kk (ld m), R: kk x nc (ld kk), kk = min(m, nc) also
+// written to *kdev for the kernels that follow.
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS)
+k_qr_rows(const T* __restrict__ Zt, const int* mptr, int mul, int nc, T* __restrict__ Q,
+          T* __restrict__ R, int* kdev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_tau[128];
+  const int m = mul * (*mptr);
+  const int kk = min(m, nc);
+  T* A = reinterpret_cast<T*>(smem_raw);     // m x nc
+  T* E = A + (size_t)m * nc;                 // m x kk
+  for (int e = threadIdx.x; e < m * nc; e += QR_THREADS) A[e] = Zt[e];
+  __syncthreads();
+  house_qr_factor(A, m, nc, s_tau);
+  for (int e = threadIdx.x; e < kk * nc; e += QR_THREADS) {
+    const int i = e % kk, j = e / kk;
+    R[e] = (i <= j) ? A[i + (size_t)m * j] : szero<T>();
+  }
+  house_form_q(A, m, kk, kk, s_tau, E);
+  for (int e = threadIdx.x; e < m * kk; e += QR_THREADS) Q[e] = E[e];
+  if (threadIdx.x == 0) *kdev = kk;
+}
+// core[i + m c] = sum_a Q[i + m a] Ur[a + kk c],  i < m = 2 t_{k-1}, c < r_k
+template <typename T>
+__global__ void k_qu(const T* Q, const int* mptr, const int* kdev, const T* Ur, const int* rptr,
+                     int mcap, int rcap, T* core) {
+  const int m = 2 * (*mptr), kk = *kdev, r = *rptr;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mcap * rcap) return;
+  const int i = e % mcap, c = e / mcap;
+  if (i >= m || c >= r) return;
+  typename KAccOf<T>::type acc;
+  for (int a = 0; a < kk; ++a) acc.add_mul(Q[i + (size_t)m * a], Ur[a + (size_t)kk * c]);
+  core[i + (size_t)m * c] = acc.get();
+}
+
 __global__ void k_one(void* p, int is_f64) {
   if (threadIdx.x == 0) {
     if (is_f64) *(double*)p = 1.0;
@@ -545,8 +585,12 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   T* W1 = (T*)scratch_alloc(sizeof(T) * 128 * 64, s);
   T* Lc = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
   T* one = (T*)scratch_alloc(sizeof(T), s);
+  T* Qz = (T*)scratch_alloc(sizeof(T) * 128 * 64, s);
+  T* Rz = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
+  T* Ur = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
+  int* kd = (int*)scratch_alloc(sizeof(int), s);
   if (!WL || !Om || !A1 || !A2 || !Z || !C0 || !C1 || !S || !SV || !SV2 || !V1 || !V || !G || !Zt ||
-      !W1 || !Lc || !one) {
+      !W1 || !Lc || !one || !Qz || !Rz || !Ur || !kd) {
     set_error("round: scratch allocation failed");
     return QTT_ENOMEM;
   }
@@ -647,10 +691,54 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     }
     if (k == d) break;
     const int mcap = 2 * tcap0;
+    T* corek = yc + y->off[k - 1];
+    if (lqk < mcap) {
+      // more rows than columns: QR first, then the rank decision on R
+      {
+        QTT_PROF("round_trunc_qr", s);
+        static bool qr_rows_cfg = false;
+        if (!qr_rows_cfg) {
+          cudaFuncSetAttribute(k_qr_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(T) * 2 * 128 * 64));
+          qr_rows_cfg = true;
+        }
+        const size_t sm = sizeof(T) * ((size_t)mcap * lqk + (size_t)mcap * lqk);
+        k_qr_rows<T><<<1, QR_THREADS, sm, s>>>(Zt, y->ranks + (k - 1), 2, lqk, Qz, Rz, kd);
+      }
+      { QTT_PROF("round_trunc", s);
+      k_gram_rows<T><<<GRID1(lqk * lqk)>>>(Rz, kd, 1, lqk, lqk, G, 128);
+      }
+      if (refine) {
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 0 /*ALL*/, tr.eps, d, rmax_eff, nullptr, 0, lqk,
+                            nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1, y->status, s);
+        { QTT_PROF("round_trunc", s);
+        k_proj_rows<T><<<GRID1(lqk * lqk)>>>(V1, Rz, kd, 1, nullptr, lqk, lqk, W1);
+        }
+        { QTT_PROF("round_trunc", s);
+        k_gram_rows<T><<<GRID1(lqk * lqk)>>>(W1, kd, 1, lqk, lqk, G, 128);
+        }
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1 /*DECIDE*/, tr.eps, d, rmax_eff, nullptr, 0,
+                            lqk, V1, V, Ur, y->ranks + k, nullptr, y->norm2, 0, y->status, s, 1,
+                            tr.delta);
+      } else {
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1, tr.eps, d, rmax_eff, nullptr, 0, lqk,
+                            nullptr, Ur, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,
+                            y->status, s, 0, tr.delta);
+      }
+      const int rcapk = ocap[k];
+      { QTT_PROF("round_trunc", s);
+      k_qu<T><<<GRID1(mcap * rcapk)>>>(Qz, y->ranks + (k - 1), kd, Ur, y->ranks + k, mcap, rcapk,
+                                       corek);
+      }
+      // Lc = Ur^H R  (t_k x lq_k)
+      { QTT_PROF("round_trunc", s);
+      k_proj_rows<T><<<GRID1(lqk * lqk)>>>(Ur, Rz, kd, 1, y->ranks + k, lqk, lqk, Lc);
+      }
+      continue;
+    }
     { QTT_PROF("round_trunc", s);
     k_gram_rows<T><<<GRID1(mcap * mcap)>>>(Zt, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
     }
-    T* corek = yc + y->off[k - 1];
     if (refine) {
       launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 0 /*ALL*/, tr.eps, d, rmax_eff,
                           nullptr, 0, lqk, nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1,
@@ -681,6 +769,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
   scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s); scratch_free(G, s);
   scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s); scratch_free(one, s);
+  scratch_free(Qz, s); scratch_free(Rz, s); scratch_free(Ur, s); scratch_free(kd, s);
   tensor_free_async(Tp, s);
   if (st != QTT_OK) { qtt_free(y); return st; }
   *out = y;
