@@ -307,14 +307,17 @@ void qtt_profile_reset(void);
  * double[n], descending.  Asynchronous. */
 qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam, void* stream);
 
-/* Diagnostics: if dev10 is not NULL, the next qtt_small_eigh calls (FP32
- * tridiagonal solver) store clock64() at their 10 phase boundaries (start,
+/* Diagnostics: if dev16 is not NULL, the following FP32 tridiagonal solves
+ * (qtt_small_eigh and the solves inside decompose and round; the last one
+ * leaves its values) store clock64() at their 10 phase boundaries (start,
  * load, tridiagonalisation, eigenvalues, eigenvectors, orthogonalisation,
- * reflector packing, Newton-Schulz, back-transformation, output) in dev10
- * (device, 10 long long); with the Jacobi solver selected, slots 0-3 get
- * start, load, end of the sweeps and end, and slot 4 the sweep count.
- * NULL switches it off. */
-void qtt_debug_small_eigh_clocks(long long* dev10);
+ * reflector packing, Newton-Schulz, back-transformation, output) in slots
+ * 0-9 of dev16 (device, 16 long long), and in slots 10-12 the end of the
+ * Gram-Schmidt sweeps, the number of degenerate copies replaced and the
+ * number of vectors in clusters of more than one member; with the Jacobi
+ * solver selected (qtt_small_eigh), slots 0-3 get start, load, end of the
+ * sweeps and end, and slot 4 the sweep count.  NULL switches it off. */
+void qtt_debug_small_eigh_clocks(long long* dev16);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
  * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */

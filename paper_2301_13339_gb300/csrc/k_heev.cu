@@ -8,12 +8,14 @@
 //      eigenvalue evaluating 4 interior points (5-section) per round;
 //   3. eigenvectors of T for the wanted eigenvalues by the twisted
 //      factorisation T - lambda I = N_k D_k N_k^T (one thread per vector);
-//   4. classical Gram-Schmidt, twice, inside clusters of close eigenvalues;
+//   4. modified Gram-Schmidt, twice, inside clusters of close eigenvalues;
 //   5. U = Q Z, each column transformed by its own group of 8 threads (no
 //      block-wide barrier per reflector).
 // About 10-20x fewer dependent steps than cyclic Jacobi (n-1 steps per sweep,
 // ~8 sweeps).  Same EigArgs contract as the Jacobi kernel in k_svd.cu.
 #include "qtt_internal.cuh"
+#include <cooperative_groups.h>
+#include <algorithm>
 #include <cfloat>
 
 namespace qtt {
@@ -110,7 +112,17 @@ __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int 
   return c;
 }
 
-__global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
+// Hand-off of a split solve: the tridiagonal eigenvectors Z (n x ncopy, ld n),
+// the packed reflectors (reflector k, rows k+2..n-1, at sum_{k'<k}(n-k'-2)),
+// tau, and hdr[0] = ncopy.  Z == nullptr: one kernel does everything.
+struct HeevSplit {
+  float* Z;
+  float2* V;
+  float2* tau;
+  int* hdr;
+};
+
+__global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a, HeevSplit hs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_d[HMAX], s_e[HMAX], s_e2[HMAX], s_lam[HMAX];
   __shared__ float2 s_tau[HMAX], s_v[HMAX], s_p[HMAX];
@@ -122,7 +134,8 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   __shared__ double s_trace;
   __shared__ int s_r, s_clu[HMAX], s_pack[HT / 32];
   __shared__ float2 s_part[4][HMAX];
-  __shared__ int s_bad[HMAX], s_clu0[HMAX];
+  __shared__ int s_bad[HMAX], s_cend[HMAX];
+  __shared__ float s_inv[HMAX];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
@@ -403,6 +416,12 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
       if (c > 0 && fabsf(s_lam[n - 1 - c] - s_lam[n - c]) > ortol) cid = c;
       s_clu[c] = cid;    // first member of c's cluster
     }
+    const int nc = (a.mode == EIG_MODE_ALL) ? n : r;
+    int cend = nc;
+    for (int c = nc - 1; c >= 0; --c) {
+      s_cend[c] = cend;  // one past the last member of c's cluster (among the copied)
+      if (s_clu[c] == c) cend = c;
+    }
   }
   __syncthreads();
   const int r = s_r;
@@ -416,111 +435,190 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
     twisted_vector(s_d, s_e, n, s_lam[n - 1 - c], s_pivmin, Z + (size_t)ldz * c);
   __syncthreads();
 
-  // ---- 4. Gram-Schmidt (twice) of every vector against all earlier ones, in
-  // descending order (the span of the leading vectors is kept).  A vector
-  // whose residual is small (an exactly degenerate eigenvalue, e.g. the zero
-  // eigenvalues of a rank-deficient Gram: the twisted factorisation returns
-  // the same vector for equal shifts) is completed at the end from unit
-  // vectors orthogonalised against all the others.
+  // ---- 4. orthogonalisation inside clusters, in descending order (the span
+  // of the leading vectors of a cluster is kept).
+  // 4a. modified Gram-Schmidt, right-looking, two sweeps: at step c every
+  // warp loads z_c, forms q = z_c / |z_c| in registers (the same bits in
+  // every warp: same data, same butterfly order) and removes q from its share
+  // of the later members of c's cluster; one barrier per step, none for a
+  // vector alone in its cluster.  A member whose residual norm in the first
+  // sweep is below 1/4 is a degenerate copy (an exactly repeated eigenvalue,
+  // e.g. the zero eigenvalues of a rank-deficient Gram, for which the twisted
+  // factorisation returns the same vector): it projects nothing and is
+  // replaced in 4b.
   HEEV_STAMP(4);
-  float* coef = reinterpret_cast<float*>(s_p);   // s_p is free after step 1
   int* bad = s_bad;
-  for (int c = tid; c < ncopy; c += HT) { bad[c] = 0; s_clu0[c] = s_clu[c]; }
+  for (int c = tid; c < ncopy; c += HT) bad[c] = 0;
   __syncthreads();
   for (int sweep = 0; sweep < 2; ++sweep) {
-    // sweep 0: all vectors in order; sweep 1: complete the flagged ones
     for (int c = 0; c < ncopy; ++c) {
-      if (sweep == 1 && !bad[c]) continue;               // uniform (smem flag)
-      const int clu0 = s_clu0[c];
-      if (sweep == 0 && clu0 == c) continue;             // first of its cluster: kept as is
-      {
-        if (sweep == 1) {
-          // candidate: the unit vector e_i with the largest component outside
-          // the span of the accepted vectors (residual 1 - sum_j Z[i,j]^2);
-          // some e_i has at least (missing dimension)/n there.
-          float best = -1.f;
-          int bi = 0;
-          for (int i = tid; i < n; i += HT) {
-            float pr = 0.f;
-            for (int j = 0; j < ncopy; ++j)
-              if (j != c && !bad[j]) pr = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * j], pr);
-            const float res = 1.f - pr;
-            if (res > best) { best = res; bi = i; }
-          }
-          // block argmax (ties: smallest index)
-          for (int off = 16; off > 0; off >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          if (lane == 0) { s_redf[warp] = best; s_pack[warp] = bi; }
-          __syncthreads();
-          if (tid == 0) {
-            float bb = -1.f;
-            int ii = 0;
-            for (int w = 0; w < HT / 32; ++w)
-              if (s_redf[w] > bb || (s_redf[w] == bb && s_pack[w] < ii)) { bb = s_redf[w]; ii = s_pack[w]; }
-            s_pack[0] = ii;
-          }
-          __syncthreads();
-          const int ui = s_pack[0];
-          for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] = (i == ui) ? 1.f : 0.f;
-          __syncthreads();
-        }
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int j = warp; j < ncopy; j += HT / 32) {
-            float h = 0.f;
-            const bool use = (j != c) && !bad[j] && (sweep == 1 || (j < c && j >= clu0));
-            if (use)
-              for (int i = lane; i < n; i += 32) h = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * c], h);
-            h = warp_sum(h);
-            if (lane == 0) coef[j] = use ? h : 0.f;
-          }
-          __syncthreads();
-          {
-            // 4 partial sums per row (thread t: row t & 127, j = t >> 7 mod 4)
-            const int i = tid & 127, ph = tid >> 7;
-            const int jend = (sweep == 0) ? c : ncopy;
-            float acc = 0.f;
-            if (i < n)
-              for (int j = ph; j < jend; j += 4) acc = fmaf(coef[j], Z[i + (size_t)ldz * j], acc);
-            ((float*)s_part)[ph * HMAX + i] = acc;
-          }
-          __syncthreads();
-          for (int i = tid; i < n; i += HT) {
-            const float* pp = (const float*)s_part;
-            Z[i + (size_t)ldz * c] -= pp[i] + pp[HMAX + i] + pp[2 * HMAX + i] + pp[3 * HMAX + i];
-          }
-          __syncthreads();
-        }
-        float part = 0.f;
-        for (int i = tid; i < n; i += HT) {
-          const float z = Z[i + (size_t)ldz * c];
-          part = fmaf(z, z, part);
-        }
-        part = warp_sum(part);
-        if (lane == 0) s_redf[warp] = part;
-        __syncthreads();
-        if (tid == 0) {
-          float t = 0.f;
-          for (int w = 0; w < HT / 32; ++w) t += s_redf[w];
-          // sweep 0: a residual norm below 1/4 of the unit vector marks a
-          // degenerate copy; sweep 1: the best candidate is always accepted
-          const bool ok = (sweep == 0) ? (t > 0.0625f) : (t > 0.f);
-          if (sweep == 0) bad[c] = ok ? 0 : 1;
-          else bad[c] = 0;
-          s_xn2 = ok ? rsqrtf(t) : 0.f;
-        }
-        __syncthreads();
-        const float sc = s_xn2;
-        if (sc > 0.f)
-          for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] *= sc;
-        __syncthreads();
+      const int cend = s_cend[c];
+      if (cend - s_clu[c] <= 1) continue;                 // alone in its cluster (uniform)
+      if (sweep == 1 && bad[c]) continue;                  // decided in sweep 0 (uniform)
+      float q[4], nn = 0.f;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int i = lane + 32 * x;
+        q[x] = (i < n) ? Z[i + (size_t)ldz * c] : 0.f;
+        nn = fmaf(q[x], q[x], nn);
       }
+      nn = warp_sum(nn);
+      if (sweep == 0 && !(nn > 0.0625f)) {                 // uniform: every warp has nn
+        if (tid == 0) bad[c] = 1;
+        continue;
+      }
+      const float inv = rsqrtf(nn);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) q[x] *= inv;
+      if (tid == 0) s_inv[c] = inv;
+      // four members per warp at a time: independent dot/butterfly chains
+      for (int j0 = c + 1 + warp; j0 < cend; j0 += 4 * (HT / 32)) {
+        float zr[4][4], h[4];
+        bool act[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * (HT / 32);
+          act[u] = (j < cend) && !(sweep == 1 && bad[j]);
+          h[u] = 0.f;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int i = lane + 32 * x;
+            zr[u][x] = (act[u] && i < n) ? Z[i + (size_t)ldz * j] : 0.f;
+            h[u] = fmaf(q[x], zr[u][x], h[u]);
+          }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) h[u] += __shfl_xor_sync(0xffffffffu, h[u], off);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!act[u]) continue;
+          float* zj = Z + (size_t)ldz * (j0 + u * (HT / 32));
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int i = lane + 32 * x;
+            if (i < n) zj[i] = fmaf(-h[u], q[x], zr[u][x]);
+          }
+        }
+      }
+      __syncthreads();
     }
+    // normalise what the sweep orthogonalised (z_c is not read again after
+    // its own step, so the scaling waits until here)
+    for (int c = warp; c < ncopy; c += HT / 32) {
+      if (s_cend[c] - s_clu[c] <= 1 || bad[c]) continue;
+      const float inv = s_inv[c];
+      for (int i = lane; i < n; i += 32) Z[i + (size_t)ldz * c] *= inv;
+    }
+    __syncthreads();
+  }
+
+  if (a.phase_clk && tid == 0) {
+    a.phase_clk[10] = clock64();
+    int nb = 0, nm = 0;
+    for (int c = 0; c < ncopy; ++c) {
+      nb += bad[c];
+      nm += (s_cend[c] - s_clu[c] > 1);
+    }
+    a.phase_clk[11] = nb;
+    a.phase_clk[12] = nm;
+  }
+  // 4b. each degenerate copy becomes the unit vector e_i with the largest
+  // component outside the span of the accepted vectors (residual
+  // 1 - sum_j Z[i,j]^2; some e_i has at least (missing dimension)/n there),
+  // orthogonalised twice against all accepted vectors (classical
+  // Gram-Schmidt) and normalised; it is accepted from then on.
+  float* coef = reinterpret_cast<float*>(s_p);   // s_p is free after step 1
+  for (int c = 0; c < ncopy; ++c) {
+    if (!bad[c]) continue;                               // uniform (smem flag)
+    float best = -1.f;
+    int bi = 0;
+    for (int i = tid; i < n; i += HT) {
+      float pr = 0.f;
+      for (int j = 0; j < ncopy; ++j)
+        if (j != c && !bad[j]) pr = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * j], pr);
+      const float res = 1.f - pr;
+      if (res > best) { best = res; bi = i; }
+    }
+    // block argmax (ties: smallest index)
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_redf[warp] = best; s_pack[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float bb = -1.f;
+      int ii = 0;
+      for (int w = 0; w < HT / 32; ++w)
+        if (s_redf[w] > bb || (s_redf[w] == bb && s_pack[w] < ii)) { bb = s_redf[w]; ii = s_pack[w]; }
+      s_pack[0] = ii;
+    }
+    __syncthreads();
+    const int ui = s_pack[0];
+    for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] = (i == ui) ? 1.f : 0.f;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = warp; j < ncopy; j += HT / 32) {
+        float h = 0.f;
+        const bool use = (j != c) && !bad[j];
+        if (use)
+          for (int i = lane; i < n; i += 32) h = fmaf(Z[i + (size_t)ldz * j], Z[i + (size_t)ldz * c], h);
+        h = warp_sum(h);
+        if (lane == 0) coef[j] = use ? h : 0.f;
+      }
+      __syncthreads();
+      {
+        // 4 partial sums per row (thread t: row t & 127, j = t >> 7 mod 4)
+        const int i = tid & 127, ph = tid >> 7;
+        float acc = 0.f;
+        if (i < n)
+          for (int j = ph; j < ncopy; j += 4) acc = fmaf(coef[j], Z[i + (size_t)ldz * j], acc);
+        ((float*)s_part)[ph * HMAX + i] = acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += HT) {
+        const float* pp = (const float*)s_part;
+        Z[i + (size_t)ldz * c] -= pp[i] + pp[HMAX + i] + pp[2 * HMAX + i] + pp[3 * HMAX + i];
+      }
+      __syncthreads();
+    }
+    float part = 0.f;
+    for (int i = tid; i < n; i += HT) {
+      const float z = Z[i + (size_t)ldz * c];
+      part = fmaf(z, z, part);
+    }
+    part = warp_sum(part);
+    if (lane == 0) s_redf[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < HT / 32; ++w) t += s_redf[w];
+      bad[c] = 0;
+      s_xn2 = (t > 0.f) ? rsqrtf(t) : 0.f;
+    }
+    __syncthreads();
+    const float sc = s_xn2;
+    if (sc > 0.f)
+      for (int i = tid; i < n; i += HT) Z[i + (size_t)ldz * c] *= sc;
+    __syncthreads();
   }
 
   HEEV_STAMP(5);
+  if (hs.Z) {
+    // split solve: the Newton-Schulz step and U = Q Z run in
+    // heev_back_kernel over a cluster of CTAs
+    for (int e = tid; e < n * ncopy; e += HT) hs.Z[e] = Z[(e % n) + (size_t)ldz * (e / n)];
+    for (int k = warp; k < n - 2; k += HT / 32) {
+      const int pk = k * (n - 2) - k * (k - 1) / 2;
+      for (int i = k + 2 + lane; i < n; i += 32) hs.V[pk + (i - k - 2)] = A[i + (size_t)n * k];
+    }
+    for (int k = tid; k < n - 1; k += HT) hs.tau[k] = s_tau[k];
+    if (tid == 0) hs.hdr[0] = ncopy;
+    return;
+  }
   // ---- 5. U = Q Z: compact the reflectors, then transform column chunks
   // packed reflector k (rows k+2..n-1) at offset P_k = sum_{k'<k} (n - k' - 2)
   const int npack = (n >= 2) ? (n - 2) * (n - 1) / 2 : 0;
@@ -694,8 +792,200 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a) {
   HEEV_STAMP(9);
 }
 
+// ---------------------------------------------------------------------------
+// Second half of a split solve, over a cluster of HB_CTAS CTAs (one SM each):
+// every CTA holds all of Z and owns a slice of at most 16 columns.
+//   Newton-Schulz, 3 steps: G_s = Z^T Z_s, Z'_s = 1.5 Z_s - 0.5 Z G_s for the
+//     own slice s, then Z'_s is stored into every CTA's second Z buffer
+//     (distributed shared memory) and the cluster synchronises;
+//   U_s = Q Z_s: the reflectors, newest first, on the own columns, the
+//     column held in registers by 16 threads (8 rows each, fixed ownership:
+//     no barrier between reflectors);
+//   optionally core_s = U1 U_s for the kept columns.
+// The column products reduce in the same order as the one-CTA kernel's tiles.
+constexpr int HB_CTAS = 8;
+constexpr int HB_THREADS = 256;
+
+__global__ void __cluster_dims__(HB_CTAS, 1, 1) __launch_bounds__(HB_THREADS)
+    heev_back_kernel(EigArgs<float2> a, HeevSplit hs, int mg_cap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_tau[HMAX];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int rank = (int)cluster.block_rank();
+  const long long t0 = clock64();
+  const int n = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+  const int ncopy = hs.hdr[0];
+  const int ldz = n + 1;
+  const size_t zcap = (size_t)mg_cap * (mg_cap + 1);
+  float* Zb0 = reinterpret_cast<float*>(smem_raw);
+  float* Zb1 = Zb0 + zcap;
+  float2* Vp = reinterpret_cast<float2*>(Zb1 + zcap);
+  const int npack = (n >= 2) ? (n - 2) * (n - 1) / 2 : 0;
+  const int nvcap = (mg_cap >= 2) ? (mg_cap - 2) * (mg_cap - 1) / 2 : 0;
+  float2* Uc = Vp + nvcap;                       // 16 x (n + 1) float2 (also G_s)
+  float* Gs = reinterpret_cast<float*>(Uc);      // ncopy x 16 floats, ld ncopy
+
+  const int cw = (ncopy + HB_CTAS - 1) / HB_CTAS;  // <= 16
+  const int c0 = rank * cw;
+  const int nc = max(0, min(cw, ncopy - c0));
+
+  for (int e = tid; e < n * ncopy; e += HB_THREADS) Zb0[(e % n) + (size_t)ldz * (e / n)] = hs.Z[e];
+  for (int e = tid; e < npack; e += HB_THREADS) Vp[e] = hs.V[e];
+  for (int k = tid; k < n - 1; k += HB_THREADS) s_tau[k] = hs.tau[k];
+  cluster.sync();   // every CTA has started and loaded (remote stores follow)
+  const long long t1 = clock64();
+
+  float* Z = Zb0;
+  float* Zn = Zb1;
+  // thread -> (row i = tid & 127, columns jg, jg + 2, ..., jg + 14)
+  const int ti = tid & 127, jg = tid >> 7;
+  for (int it = 0; it < 3; ++it) {
+    for (int i = ti; i < ncopy; i += 128) {
+      float acc[8];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[y] = 0.f;
+      for (int l = 0; l < n; ++l) {
+        const float zi = Z[l + (size_t)ldz * i];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int j = jg + 2 * y;
+          const float zj = (j < nc) ? Z[l + (size_t)ldz * (c0 + j)] : 0.f;
+          acc[y] = fmaf(zi, zj, acc[y]);
+        }
+      }
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const int j = jg + 2 * y;
+        if (j < nc) Gs[i + (size_t)ncopy * j] = acc[y];
+      }
+    }
+    __syncthreads();
+    for (int i = ti; i < n; i += 128) {
+      float acc[8];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[y] = 0.f;
+      for (int l = 0; l < ncopy; ++l) {
+        const float zl = Z[i + (size_t)ldz * l];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int j = jg + 2 * y;
+          const float g = (j < nc) ? Gs[l + (size_t)ncopy * j] : 0.f;
+          acc[y] = fmaf(zl, g, acc[y]);
+        }
+      }
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const int j = jg + 2 * y;
+        if (j < nc) acc[y] = 1.5f * Z[i + (size_t)ldz * (c0 + j)] - 0.5f * acc[y];
+      }
+      for (int dst = 0; dst < HB_CTAS; ++dst) {
+        float* Zr = cluster.map_shared_rank(Zn, dst);
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int j = jg + 2 * y;
+          if (j < nc) Zr[i + (size_t)ldz * (c0 + j)] = acc[y];
+        }
+      }
+    }
+    cluster.sync();   // all slices stored everywhere; the old buffer is free
+    float* t = Z;
+    Z = Zn;
+    Zn = t;
+  }
+  const long long t2 = clock64();
+
+  // U_s = Q Z_s; thread (column cc = tid >> 4, sub = tid & 15) owns rows
+  // sub + 16 m
+  const int cc = tid >> 4, sub = tid & 15;
+  float2 u[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = sub + 16 * m;
+    u[m] = make_float2((cc < nc && i < n) ? Z[i + (size_t)ldz * (c0 + cc)] : 0.f, 0.f);
+  }
+  const unsigned gm = 0xffffu << (lane & 16);
+  for (int k = n - 2; k >= 0; --k) {
+    const float2 tau = s_tau[k];
+    if (tau.x == 0.f && tau.y == 0.f) continue;
+    const int pk = k * (n - 2) - k * (k - 1) / 2;
+    float2 v[8];
+    float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = sub + 16 * m;
+      v[m] = (i == k + 1) ? make_float2(1.f, 0.f)
+             : (i > k + 1 && i < n) ? Vp[pk + (i - k - 2)] : make_float2(0.f, 0.f);
+      w.x = fmaf(v[m].x, u[m].x, fmaf(v[m].y, u[m].y, w.x));   // conj(v) u
+      w.y = fmaf(v[m].x, u[m].y, fmaf(-v[m].y, u[m].x, w.y));
+    }
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+      w.x += __shfl_xor_sync(gm, w.x, off);
+      w.y += __shfl_xor_sync(gm, w.y, off);
+    }
+    const float2 f = cmulf(tau, w);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      u[m].x -= v[m].x * f.x - v[m].y * f.y;
+      u[m].y -= v[m].x * f.y + v[m].y * f.x;
+    }
+  }
+  const long long t3 = clock64();
+  if (cc < nc) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = sub + 16 * m;
+      if (i < n) a.Uout[(size_t)n * (c0 + cc) + i] = u[m];
+    }
+  }
+  if (a.core_out) {
+    const int r = ncopy;   // all columns (MODE_ALL) or the decided rank
+    if (a.U1) {
+      // Gs is free: stage the own columns, ld n + 1
+      if (cc < nc) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = sub + 16 * m;
+          if (i < n) Uc[i + (size_t)ldz * cc] = u[m];
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < n * nc; e += HB_THREADS) {
+        const int i = e % n, c = e / n;
+        if (c0 + c >= r) continue;
+        KAcc32 acc;
+        for (int l = 0; l < n; ++l) acc.add_mul(a.U1[i + (size_t)n * l], Uc[l + (size_t)ldz * c]);
+        a.core_out[i + (size_t)n * (c0 + c)] = acc.get();
+      }
+    } else if (a.core_out != a.Uout && cc < nc && c0 + cc < r) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i = sub + 16 * m;
+        if (i < n) a.core_out[(size_t)n * (c0 + cc) + i] = u[m];
+      }
+    }
+  }
+  if (a.phase_clk && rank == 0 && tid == 0) {
+    // this SM's clock differs from the first kernel's: durations are added
+    // to the first kernel's last stamp
+    const long long p5 = a.phase_clk[5];
+    a.phase_clk[6] = p5 + (t1 - t0);
+    a.phase_clk[7] = p5 + (t2 - t0);
+    a.phase_clk[8] = p5 + (t3 - t0);
+    a.phase_clk[9] = p5 + (clock64() - t0);
+  }
+}
+
 size_t heev_tri_smem_bytes(int mg_cap) {
   return (size_t)mg_cap * mg_cap * sizeof(float2) + (size_t)mg_cap * (mg_cap + 1) * sizeof(float);
+}
+
+static size_t heev_back_smem_bytes(int mg_cap) {
+  const size_t nv = (mg_cap >= 2) ? (size_t)(mg_cap - 2) * (mg_cap - 1) / 2 : 0;
+  const size_t gs = std::max((size_t)16 * (mg_cap + 1) * sizeof(float2), (size_t)16 * mg_cap * sizeof(float));
+  return 2 * (size_t)mg_cap * (mg_cap + 1) * sizeof(float) + nv * sizeof(float2) + gs;
 }
 
 void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s) {
@@ -703,9 +993,32 @@ void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s) {
   if (!configured) {
     cudaFuncSetAttribute(heev_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)heev_tri_smem_bytes(HMAX));
+    cudaFuncSetAttribute(heev_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)heev_back_smem_bytes(HMAX));
     configured = true;
   }
-  heev_tri_kernel<<<1, HT, heev_tri_smem_bytes(mg_cap), s>>>(a);
+  HeevSplit hs{nullptr, nullptr, nullptr, nullptr};
+  void* buf = nullptr;
+  if (mg_cap > 32) {
+    // Z (floats) | reflectors | tau | header
+    auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    const size_t zb = al16((size_t)mg_cap * mg_cap * sizeof(float));
+    const size_t vb = al16((size_t)mg_cap * mg_cap / 2 * sizeof(float2));
+    const size_t tb = al16((size_t)mg_cap * sizeof(float2));
+    buf = scratch_alloc(zb + vb + tb + 16, s);
+    if (buf) {
+      char* p = (char*)buf;
+      hs.Z = (float*)p;
+      hs.V = (float2*)(p + zb);
+      hs.tau = (float2*)(p + zb + vb);
+      hs.hdr = (int*)(p + zb + vb + tb);
+    }
+  }
+  heev_tri_kernel<<<1, HT, heev_tri_smem_bytes(mg_cap), s>>>(a, hs);
+  if (buf) {
+    heev_back_kernel<<<HB_CTAS, HB_THREADS, heev_back_smem_bytes(mg_cap), s>>>(a, hs, mg_cap);
+    scratch_free(buf, s);
+  }
 }
 
 }  // namespace qtt

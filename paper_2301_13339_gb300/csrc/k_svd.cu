@@ -508,6 +508,9 @@ static size_t eig_smem_bytes(int mg_cap) {
 }
 
 static int g_eig_solver = 0;   // 0: tridiagonal solver for FP32, Jacobi for FP64; 1: Jacobi
+// diagnostics: phase clocks of every following FP32 tridiagonal solve (the
+// last one leaves its clocks), set by qtt_debug_small_eigh_clocks
+static long long* g_small_eigh_clk = nullptr;
 // FP32 relative-accuracy Jacobi (refinement passes): a fixed number of
 // sweeps.  On a Gram already projected on the first pass's eigenvectors the
 // error against the FP64 oracle is the same after 2 sweeps as at the
@@ -518,6 +521,13 @@ static int g_refine_sweeps = 3;
 template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   if (Sc<T>::cplx && g_eig_solver == 0 && !a.relative) {
+    if (g_small_eigh_clk && !a.phase_clk) {
+      EigArgs<T> b = a;
+      b.phase_clk = g_small_eigh_clk;
+      QTT_PROF(mg_cap <= 32 ? "heev_le32" : mg_cap <= 64 ? "heev_le64" : "heev_le128", s);
+      launch_heev_tri(reinterpret_cast<const EigArgs<float2>&>(b), mg_cap, s);
+      return;
+    }
     QTT_PROF(mg_cap <= 32 ? "heev_le32" : mg_cap <= 64 ? "heev_le64" : "heev_le128", s);
     launch_heev_tri(reinterpret_cast<const EigArgs<float2>&>(a), mg_cap, s);
     return;
@@ -786,8 +796,7 @@ extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps =
 // one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U
 // (device, element type of dt, ld n, columns by descending eigenvalue) and
 // lam (device, double, descending) out.
-static long long* g_small_eigh_clk = nullptr;   // diagnostics: phase clocks of the next call
-extern "C" void qtt_debug_small_eigh_clocks(long long* dev10) { g_small_eigh_clk = dev10; }
+extern "C" void qtt_debug_small_eigh_clocks(long long* dev16) { qtt::g_small_eigh_clk = dev16; }
 
 extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam,
                                      void* stream) {
