@@ -314,9 +314,12 @@ qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* l
  * reflector packing, Newton-Schulz, back-transformation, output) in slots
  * 0-9 of dev16 (device, 16 long long), and in slots 10-12 the end of the
  * Gram-Schmidt sweeps, the number of degenerate copies replaced and the
- * number of vectors in clusters of more than one member; with the Jacobi
- * solver selected (qtt_small_eigh), slots 0-3 get start, load, end of the
- * sweeps and end, and slot 4 the sweep count.  NULL switches it off. */
+ * number of vectors in clusters of more than one member.  The Jacobi
+ * solves (qtt_small_eigh with that solver selected, the refinement passes
+ * of decompose and round) store start, load, end of the sweeps and end in
+ * slots 0-3, the sweep count in slot 4, and the ends of the ordering, of
+ * the Newton-Schulz Gram and of the output in slots 13-15.  NULL switches
+ * it off. */
 void qtt_debug_small_eigh_clocks(long long* dev16);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
@@ -324,7 +327,7 @@ void qtt_debug_small_eigh_clocks(long long* dev16);
 void qtt_debug_set_eig_solver(int which);
 
 /* Diagnostics: sweep count of the FP32 relative-accuracy Jacobi passes
- * (refinement pass of the TT-SVD and of the rounding); default 3; 0 = run
+ * (refinement pass of the TT-SVD and of the rounding); default 2; 0 = run
  * to the convergence test; negative = back to the default. */
 void qtt_debug_set_refine_sweeps(int sweeps);
 

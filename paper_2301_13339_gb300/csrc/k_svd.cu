@@ -422,41 +422,61 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     s_r = r;
   }
   __syncthreads();
+  if (a.phase_clk && tid == 0) a.phase_clk[13] = clock64();
   const int r = s_r;
   if (a.sig_out)
     for (int c = tid; c < mg; c += EIG_THREADS) a.sig_out[c] = s_lam[s_perm[c]];
   const int ncopy = (a.mode == EIG_MODE_ALL) ? mg : r;
-  if (Sc<T>::cplx && ncopy * n <= (n * (n + 1)) / 2) {
+  if (Sc<T>::cplx && ncopy * (n + 1) <= (n * (n + 1)) / 2) {
     // FP32, the kept columns only (rank decisions): one Newton-Schulz step on
     // V_r = V[:, perm[:ncopy]] (gathered into the free packed region),
     // G_r = V_r^H V_r in the free V region, U = V_r (3 I - G_r) / 2
+    // (ld n + 1: the columns of a warp's lanes fall on different banks)
     T* Vr = A;
+    const int lv = n + 1;
     for (int e = tid; e < n * ncopy; e += EIG_THREADS) {
       const int i = e % n, c = e / n;
-      Vr[e] = V[i + ldv * s_perm[c]];
+      Vr[i + lv * c] = V[i + ldv * s_perm[c]];
     }
     __syncthreads();
     T* Gr = V;
-    {
-      const int wp = tid >> 5, ln = tid & 31;
-      for (int e = wp; e < ncopy * ncopy; e += EIG_THREADS / 32) {
-        const int c1 = e % ncopy, c2 = e / ncopy;
-        if (c1 > c2) continue;                       // uniform per warp
-        T acc = szero<T>();
-        for (int i = ln; i < n; i += 32) macc(acc, Vr[i + n * c1], Vr[i + n * c2]);
-        acc = warp_sum(acc);
-        if (ln == 0) {
-          Gr[c1 + ncopy * c2] = acc;
-          Gr[c2 + ncopy * c1] = conjg(acc);
-        }
+    // G_r: a thread per (c1, 4 consecutive c2), lanes over c1
+    for (int t = tid; t < ncopy * ((ncopy + 3) / 4); t += EIG_THREADS) {
+      const int c1 = t % ncopy, c2 = (t / ncopy) * 4;
+      T acc[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[y] = szero<T>();
+      for (int l = 0; l < n; ++l) {
+        const T x = Vr[l + lv * c1];
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (c2 + y < ncopy) macc(acc[y], x, Vr[l + lv * (c2 + y)]);
       }
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (c2 + y < ncopy) Gr[c1 + ncopy * (c2 + y)] = acc[y];
     }
     __syncthreads();
-    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
-      const int i = e % mg, c = e / mg;
-      T corr = szero<T>();
-      for (int l = 0; l < ncopy; ++l) mac(corr, Vr[i + n * l], Gr[l + ncopy * c]);
-      a.Uout[e] = ssub(rscale(Vr[i + n * c], (typename Sc<T>::R)1.5), rscale(corr, (typename Sc<T>::R)0.5));
+    if (a.phase_clk && tid == 0) a.phase_clk[14] = clock64();
+    // U = 1.5 V_r - 0.5 V_r G_r: a thread per (row i, 8 consecutive columns)
+    for (int t = tid; t < mg * ((ncopy + 7) / 8); t += EIG_THREADS) {
+      const int i = t % mg, c0 = (t / mg) * 8;
+      T acc[8];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[y] = szero<T>();
+      for (int l = 0; l < ncopy; ++l) {
+        const T x = Vr[i + lv * l];
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+          if (c0 + y < ncopy) mac(acc[y], x, Gr[l + ncopy * (c0 + y)]);
+      }
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const int c = c0 + y;
+        if (c < ncopy)
+          a.Uout[i + (size_t)mg * c] = ssub(rscale(Vr[i + lv * c], (typename Sc<T>::R)1.5),
+                                            rscale(acc[y], (typename Sc<T>::R)0.5));
+      }
     }
   } else if (Sc<T>::cplx) {
     // FP32: the accumulated rotations leave V orthonormal only to
@@ -486,6 +506,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     }
   }
   __syncthreads();
+  if (a.phase_clk && tid == 0) a.phase_clk[15] = clock64();
   if (a.core_out) {
     if (a.U1) {
       for (int e = tid; e < mg * r; e += EIG_THREADS) {
@@ -499,6 +520,26 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
     }
   }
   if (a.phase_clk && tid == 0) a.phase_clk[3] = clock64();
+}
+
+// core[:, c] = U1 U[:, c] for the first r columns (r = *r_ptr, or mg),
+// compensated sums: one CTA per column, a thread per row.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    core_product_kernel(const T* __restrict__ U1, const T* __restrict__ U, const int* mg_ptr,
+                        int mg_mul, int mg_const, const int* r_ptr, T* __restrict__ core) {
+  __shared__ T s_u[EIG_MAXN];
+  const int mg = mg_ptr ? mg_mul * (*mg_ptr) : mg_const;
+  const int r = r_ptr ? *r_ptr : mg;
+  const int c = blockIdx.x;
+  if (c >= r) return;
+  for (int l = threadIdx.x; l < mg; l += 128) s_u[l] = U[l + (size_t)mg * c];
+  __syncthreads();
+  for (int i = threadIdx.x; i < mg; i += 128) {
+    typename KAccOf<T>::type acc;
+    for (int l = 0; l < mg; ++l) acc.add_mul(U1[i + (size_t)mg * l], s_u[l]);
+    core[i + (size_t)mg * c] = acc.get();
+  }
 }
 
 template <typename T>
@@ -515,8 +556,10 @@ static long long* g_small_eigh_clk = nullptr;
 // sweeps.  On a Gram already projected on the first pass's eigenvectors the
 // error against the FP64 oracle is the same after 2 sweeps as at the
 // convergence test (measured: 6.2e-6 worst of 20 batch lines, 1.3e-6 on the
-// 2^20 line, for 2, 3, 4, 5 sweeps and full convergence); 3 keeps a margin.
-static int g_refine_sweeps = 3;
+// 2^20 line, for 2, 3, 4, 5 sweeps and full convergence; the same again for
+// 1, 2 and 3 sweeps after the first pass's orthogonalisation changed); 2 keep
+// one squaring of the rotation angles as margin.
+static int g_refine_sweeps = 2;
 
 template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
@@ -539,8 +582,23 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
                          (int)eig_smem_bytes<T>(EIG_MAXN));
     configured = true;
   }
-  QTT_PROF(mg_cap <= 32 ? "jacobi_eig_le32" : mg_cap <= 64 ? "jacobi_eig_le64" : "jacobi_eig_le128", s);
-  gram_eig_kernel<T><<<1, EIG_THREADS, sm, s>>>(a);
+  const char* pname =
+      mg_cap <= 32 ? "jacobi_eig_le32" : mg_cap <= 64 ? "jacobi_eig_le64" : "jacobi_eig_le128";
+  EigArgs<T> b = a;
+  if (g_small_eigh_clk && !b.phase_clk) b.phase_clk = g_small_eigh_clk;
+  // core = U1 U[:, :r] over many CTAs instead of inside the one-CTA solve
+  const bool split_core = a.U1 && a.core_out && (a.mode == EIG_MODE_ALL || a.rank_out);
+  if (split_core) b.core_out = nullptr;
+  {
+    QTT_PROF(pname, s);
+    gram_eig_kernel<T><<<1, EIG_THREADS, sm, s>>>(b);
+  }
+  if (split_core) {
+    QTT_PROF("core_product", s);
+    core_product_kernel<T><<<mg_cap, 128, 0, s>>>(a.U1, a.Uout, a.mg_ptr, a.mg_mul, a.mg_const,
+                                                  a.mode == EIG_MODE_ALL ? nullptr : a.rank_out,
+                                                  a.core_out);
+  }
 }
 
 template <typename T>
@@ -790,7 +848,7 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 
 // Diagnostics: choose the FP32 eigen-solver (0 = tridiagonal, 1 = Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
-extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps = sweeps >= 0 ? sweeps : 3; }
+extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps = sweeps >= 0 ? sweeps : 2; }
 
 // Hermitian eigen-decomposition of one n x n matrix (n <= 128) with the
 // one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U
