@@ -331,6 +331,12 @@ void qtt_debug_set_eig_solver(int which);
  * to the convergence test; negative = back to the default. */
 void qtt_debug_set_refine_sweeps(int sweeps);
 
+/* Diagnostics: FP32 tridiagonal solver's orthogonalisation.  Eigenvalues
+ * closer than ortol_rel * ||T|| chain into clusters orthogonalised by
+ * Gram-Schmidt (default 1e-6); ns_steps Newton-Schulz steps follow
+ * (default 3).  Non-positive values restore the defaults. */
+void qtt_debug_set_heev_cluster(double ortol_rel, int ns_steps);
+
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);
 

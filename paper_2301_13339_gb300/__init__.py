@@ -105,6 +105,8 @@ def load(path=None):
         "qtt_release_workspace": (None, []),
         "qtt_small_eigh": (i, [vp, i, i, vp, vp, vp]),
         "qtt_debug_set_eig_solver": (None, [i]),
+        "qtt_debug_set_heev_cluster": (None, [d, i]),
+        "qtt_debug_set_refine_sweeps": (None, [i]),
         "qtt_last_error": (ctypes.c_char_p, []),
         "qtt_version": (ctypes.c_char_p, []),
     }

@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a, HeevSpl
     // clusters for Gram-Schmidt: gaps at which FP32 eigenvectors are not
     // resolved (eps ||T|| / gap of order one); wider gaps are handled by
     // the Newton-Schulz orthonormalisation below
-    const float ortol = 1e-6f * tn;
+    const float ortol = a.ortol_rel * tn;
     int cid = 0;
     for (int c = 0; c < n; ++c) {
       if (c > 0 && fabsf(s_lam[n - 1 - c] - s_lam[n - c]) > ortol) cid = c;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a, HeevSpl
     // tile: 4 rows spaced 32 apart (consecutive across the lanes of a warp)
     // x 8 columns (uniform across the warp: broadcast loads)
     const int nrb = (ncopy + 127) / 128, ncb = (ncopy + 7) / 8;
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < a.ns_steps; ++it) {
       // G = Z^T Z
       for (int t = warp; t < nrb * ncb; t += HT / 32) {
         const int i0 = (t % nrb) * 128 + lane, j0 = (t / nrb) * 8;
@@ -841,7 +841,7 @@ __global__ void __cluster_dims__(HB_CTAS, 1, 1) __launch_bounds__(HB_THREADS)
   float* Zn = Zb1;
   // thread -> (row i = tid & 127, columns jg, jg + 2, ..., jg + 14)
   const int ti = tid & 127, jg = tid >> 7;
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < a.ns_steps; ++it) {
     for (int i = ti; i < ncopy; i += 128) {
       float acc[8];
 #pragma unroll
@@ -988,7 +988,18 @@ static size_t heev_back_smem_bytes(int mg_cap) {
   return 2 * (size_t)mg_cap * (mg_cap + 1) * sizeof(float) + nv * sizeof(float2) + gs;
 }
 
-void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s) {
+static float g_heev_ortol = 1e-6f;
+static int g_heev_ns = 3;
+
+void heev_set_cluster_params(double ortol_rel, int ns_steps) {
+  g_heev_ortol = ortol_rel > 0.0 ? (float)ortol_rel : 1e-6f;
+  g_heev_ns = ns_steps > 0 ? ns_steps : 3;
+}
+
+void launch_heev_tri(const EigArgs<float2>& a_in, int mg_cap, cudaStream_t s) {
+  EigArgs<float2> a = a_in;
+  a.ortol_rel = g_heev_ortol;
+  a.ns_steps = g_heev_ns;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(heev_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -187,6 +187,172 @@ __device__ __forceinline__ void pk_set(T* A, int i, int j, T v) {
   else A[pk_idx(j, i)] = conjg(v);
 }
 
+// After the sweeps (both Jacobi kernels): eigenvalues from the diagonal of
+// the packed A, descending order, rank decision, orthonormalised output
+// columns and the optional core = U1 U[:, :r].  A and V are shared memory
+// (V: n x n, ld ldv); the whole block takes part.
+template <typename T>
+__device__ void eig_post(const EigArgs<T>& a, T* A, T* V, int n, int mg, int ldv) {
+  __shared__ double s_lam[EIG_MAXN];
+  __shared__ int s_perm[EIG_MAXN];
+  __shared__ int s_r;
+  const int tid = threadIdx.x;
+  // eigenvalues and descending order (ties by index)
+  // a NaN compares false both ways and would break the rank count below
+  // (two indices with the same rank, an unset slot): such eigenvalues sort
+  // last as -inf and the device status records the non-finite input
+  for (int i = tid; i < mg; i += EIG_THREADS) {
+    double l = (double)sreal(A[pk_idx(i, i)]);
+    if (!isfinite(l)) {
+      if (a.status) atomicOr(a.status, DEV_ST_NONFINITE);
+      if (isnan(l)) l = -INFINITY;
+    }
+    s_lam[i] = l;
+  }
+  __syncthreads();
+  for (int i = tid; i < mg; i += EIG_THREADS) {
+    const double li = s_lam[i];
+    int rk = 0;
+    for (int j = 0; j < mg; ++j) {
+      const double lj = s_lam[j];
+      rk += (lj > li) || (lj == li && j < i);
+    }
+    s_perm[rk] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r = mg;
+    if (a.mode == EIG_MODE_DECIDE) {
+      const long long ncols = a.ncols_ptr ? (long long)a.ncols_mul * (*a.ncols_ptr) : a.ncols_const;
+      int kmax = mg < ncols ? mg : (int)ncols;
+      if (kmax < 1) kmax = 1;
+      const double nrm2 = *a.norm2;
+      const double tau2 = (a.dmodes > 1) ? a.eps * a.eps / (double)(a.dmodes - 1) * nrm2 : 0.0;
+      double tail = 0.0;
+      r = kmax;
+      if (a.delta > 0.0) {
+        // SV drop-off: the first sigma_{c+1} / sigma_c < delta, i.e.
+        // lambda_{c+1} < delta^2 lambda_c (eigenvalues of the Gram)
+        const double d2 = a.delta * a.delta;
+        for (int c = 1; c < kmax; ++c) {
+          const double lp = s_lam[s_perm[c - 1]], lc = s_lam[s_perm[c]];
+          if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
+        }
+      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
+        for (int c = kmax - 1; c >= 1; --c) {
+          const double l = s_lam[s_perm[c]];
+          tail += (l > 0.0 ? l : 0.0);
+          if (tail <= tau2) r = c;
+          else break;
+        }
+      }
+      if (a.rmax > 0 && r > a.rmax) r = a.rmax;
+      if (r < 1) r = 1;
+      if (a.rank_out) *a.rank_out = r;
+    }
+    s_r = r;
+  }
+  __syncthreads();
+  if (a.phase_clk && tid == 0) a.phase_clk[13] = clock64();
+  const int r = s_r;
+  if (a.sig_out)
+    for (int c = tid; c < mg; c += EIG_THREADS) a.sig_out[c] = s_lam[s_perm[c]];
+  const int ncopy = (a.mode == EIG_MODE_ALL) ? mg : r;
+  if (Sc<T>::cplx && ncopy * (n + 1) <= (n * (n + 1)) / 2) {
+    // FP32, the kept columns only (rank decisions): one Newton-Schulz step on
+    // V_r = V[:, perm[:ncopy]] (gathered into the free packed region),
+    // G_r = V_r^H V_r in the free V region, U = V_r (3 I - G_r) / 2
+    // (ld n + 1: the columns of a warp's lanes fall on different banks)
+    T* Vr = A;
+    const int lv = n + 1;
+    for (int e = tid; e < n * ncopy; e += EIG_THREADS) {
+      const int i = e % n, c = e / n;
+      Vr[i + lv * c] = V[i + ldv * s_perm[c]];
+    }
+    __syncthreads();
+    T* Gr = V;
+    // G_r: a thread per (c1, 4 consecutive c2), lanes over c1
+    for (int t = tid; t < ncopy * ((ncopy + 3) / 4); t += EIG_THREADS) {
+      const int c1 = t % ncopy, c2 = (t / ncopy) * 4;
+      T acc[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[y] = szero<T>();
+      for (int l = 0; l < n; ++l) {
+        const T x = Vr[l + lv * c1];
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (c2 + y < ncopy) macc(acc[y], x, Vr[l + lv * (c2 + y)]);
+      }
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (c2 + y < ncopy) Gr[c1 + ncopy * (c2 + y)] = acc[y];
+    }
+    __syncthreads();
+    if (a.phase_clk && tid == 0) a.phase_clk[14] = clock64();
+    // U = 1.5 V_r - 0.5 V_r G_r: a thread per (row i, 8 consecutive columns)
+    for (int t = tid; t < mg * ((ncopy + 7) / 8); t += EIG_THREADS) {
+      const int i = t % mg, c0 = (t / mg) * 8;
+      T acc[8];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[y] = szero<T>();
+      for (int l = 0; l < ncopy; ++l) {
+        const T x = Vr[i + lv * l];
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+          if (c0 + y < ncopy) mac(acc[y], x, Gr[l + ncopy * (c0 + y)]);
+      }
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const int c = c0 + y;
+        if (c < ncopy)
+          a.Uout[i + (size_t)mg * c] = ssub(rscale(Vr[i + lv * c], (typename Sc<T>::R)1.5),
+                                            rscale(acc[y], (typename Sc<T>::R)0.5));
+      }
+    }
+  } else if (Sc<T>::cplx) {
+    // FP32: the accumulated rotations leave V orthonormal only to
+    // ~sqrt(#rotations) eps; one Newton-Schulz step V (3 I - V^H V) / 2
+    // squares that error.  G = V^H V goes into the (no longer needed) packed A.
+    // G = V^H V (upper triangle, packed): a warp per column j, lanes over i
+    for (int j = tid >> 5; j < n; j += EIG_THREADS / 32) {
+      for (int i = tid & 31; i <= j; i += 32) {
+        T acc = szero<T>();
+        for (int l = 0; l < n; ++l) macc(acc, V[l + ldv * i], V[l + ldv * j]);
+        A[pk_idx(i, j)] = acc;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
+      const int i = e % mg, c = e / mg;
+      const int pc = s_perm[c];
+      T acc = rscale(V[i + ldv * pc], (typename Sc<T>::R)1.5);
+      T corr = szero<T>();
+      for (int l = 0; l < n; ++l) mac(corr, V[i + ldv * l], pk_get(A, l, pc));
+      a.Uout[e] = ssub(acc, rscale(corr, (typename Sc<T>::R)0.5));
+    }
+  } else {
+    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
+      const int i = e % mg, c = e / mg;
+      a.Uout[e] = V[i + ldv * s_perm[c]];
+    }
+  }
+  __syncthreads();
+  if (a.phase_clk && tid == 0) a.phase_clk[15] = clock64();
+  if (a.core_out) {
+    if (a.U1) {
+      for (int e = tid; e < mg * r; e += EIG_THREADS) {
+        const int i = e % mg, c = e / mg;
+        typename KAccOf<T>::type acc;
+        for (int l = 0; l < mg; ++l) acc.add_mul(a.U1[i + (size_t)mg * l], a.Uout[l + (size_t)mg * c]);
+        a.core_out[e] = acc.get();
+      }
+    } else if (a.core_out != a.Uout) {
+      for (int e = tid; e < mg * r; e += EIG_THREADS) a.core_out[e] = a.Uout[e];
+    }
+  }
+  if (a.phase_clk && tid == 0) a.phase_clk[3] = clock64();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   using R = typename Sc<T>::R;
@@ -197,10 +363,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   __shared__ R s_d[EIG_MAXN / 2][2];
   __shared__ int s_rot[EIG_MAXN / 2];
   __shared__ int s_nrot;
-  __shared__ double s_lam[EIG_MAXN];
-  __shared__ int s_perm[EIG_MAXN];
   __shared__ double s_red[32];
-  __shared__ int s_r;
   __shared__ unsigned short s_blk[(EIG_MAXN / 2) * (EIG_MAXN / 2 + 1) / 2][2];
 
   const int tid = threadIdx.x;
@@ -366,160 +529,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   if (!converged && a.max_sweeps == 0 && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
   if (a.phase_clk && tid == 0) { a.phase_clk[2] = clock64(); a.phase_clk[4] = nsweep; }
 
-  // eigenvalues and descending order (ties by index)
-  // a NaN compares false both ways and would break the rank count below
-  // (two indices with the same rank, an unset slot): such eigenvalues sort
-  // last as -inf and the device status records the non-finite input
-  for (int i = tid; i < mg; i += EIG_THREADS) {
-    double l = (double)sreal(A[pk_idx(i, i)]);
-    if (!isfinite(l)) {
-      if (a.status) atomicOr(a.status, DEV_ST_NONFINITE);
-      if (isnan(l)) l = -INFINITY;
-    }
-    s_lam[i] = l;
-  }
-  __syncthreads();
-  for (int i = tid; i < mg; i += EIG_THREADS) {
-    const double li = s_lam[i];
-    int rk = 0;
-    for (int j = 0; j < mg; ++j) {
-      const double lj = s_lam[j];
-      rk += (lj > li) || (lj == li && j < i);
-    }
-    s_perm[rk] = i;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int r = mg;
-    if (a.mode == EIG_MODE_DECIDE) {
-      const long long ncols = a.ncols_ptr ? (long long)a.ncols_mul * (*a.ncols_ptr) : a.ncols_const;
-      int kmax = mg < ncols ? mg : (int)ncols;
-      if (kmax < 1) kmax = 1;
-      const double nrm2 = *a.norm2;
-      const double tau2 = (a.dmodes > 1) ? a.eps * a.eps / (double)(a.dmodes - 1) * nrm2 : 0.0;
-      double tail = 0.0;
-      r = kmax;
-      if (a.delta > 0.0) {
-        // SV drop-off: the first sigma_{c+1} / sigma_c < delta, i.e.
-        // lambda_{c+1} < delta^2 lambda_c (eigenvalues of the Gram)
-        const double d2 = a.delta * a.delta;
-        for (int c = 1; c < kmax; ++c) {
-          const double lp = s_lam[s_perm[c - 1]], lc = s_lam[s_perm[c]];
-          if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
-        }
-      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
-        for (int c = kmax - 1; c >= 1; --c) {
-          const double l = s_lam[s_perm[c]];
-          tail += (l > 0.0 ? l : 0.0);
-          if (tail <= tau2) r = c;
-          else break;
-        }
-      }
-      if (a.rmax > 0 && r > a.rmax) r = a.rmax;
-      if (r < 1) r = 1;
-      if (a.rank_out) *a.rank_out = r;
-    }
-    s_r = r;
-  }
-  __syncthreads();
-  if (a.phase_clk && tid == 0) a.phase_clk[13] = clock64();
-  const int r = s_r;
-  if (a.sig_out)
-    for (int c = tid; c < mg; c += EIG_THREADS) a.sig_out[c] = s_lam[s_perm[c]];
-  const int ncopy = (a.mode == EIG_MODE_ALL) ? mg : r;
-  if (Sc<T>::cplx && ncopy * (n + 1) <= (n * (n + 1)) / 2) {
-    // FP32, the kept columns only (rank decisions): one Newton-Schulz step on
-    // V_r = V[:, perm[:ncopy]] (gathered into the free packed region),
-    // G_r = V_r^H V_r in the free V region, U = V_r (3 I - G_r) / 2
-    // (ld n + 1: the columns of a warp's lanes fall on different banks)
-    T* Vr = A;
-    const int lv = n + 1;
-    for (int e = tid; e < n * ncopy; e += EIG_THREADS) {
-      const int i = e % n, c = e / n;
-      Vr[i + lv * c] = V[i + ldv * s_perm[c]];
-    }
-    __syncthreads();
-    T* Gr = V;
-    // G_r: a thread per (c1, 4 consecutive c2), lanes over c1
-    for (int t = tid; t < ncopy * ((ncopy + 3) / 4); t += EIG_THREADS) {
-      const int c1 = t % ncopy, c2 = (t / ncopy) * 4;
-      T acc[4];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) acc[y] = szero<T>();
-      for (int l = 0; l < n; ++l) {
-        const T x = Vr[l + lv * c1];
-#pragma unroll
-        for (int y = 0; y < 4; ++y)
-          if (c2 + y < ncopy) macc(acc[y], x, Vr[l + lv * (c2 + y)]);
-      }
-#pragma unroll
-      for (int y = 0; y < 4; ++y)
-        if (c2 + y < ncopy) Gr[c1 + ncopy * (c2 + y)] = acc[y];
-    }
-    __syncthreads();
-    if (a.phase_clk && tid == 0) a.phase_clk[14] = clock64();
-    // U = 1.5 V_r - 0.5 V_r G_r: a thread per (row i, 8 consecutive columns)
-    for (int t = tid; t < mg * ((ncopy + 7) / 8); t += EIG_THREADS) {
-      const int i = t % mg, c0 = (t / mg) * 8;
-      T acc[8];
-#pragma unroll
-      for (int y = 0; y < 8; ++y) acc[y] = szero<T>();
-      for (int l = 0; l < ncopy; ++l) {
-        const T x = Vr[i + lv * l];
-#pragma unroll
-        for (int y = 0; y < 8; ++y)
-          if (c0 + y < ncopy) mac(acc[y], x, Gr[l + ncopy * (c0 + y)]);
-      }
-#pragma unroll
-      for (int y = 0; y < 8; ++y) {
-        const int c = c0 + y;
-        if (c < ncopy)
-          a.Uout[i + (size_t)mg * c] = ssub(rscale(Vr[i + lv * c], (typename Sc<T>::R)1.5),
-                                            rscale(acc[y], (typename Sc<T>::R)0.5));
-      }
-    }
-  } else if (Sc<T>::cplx) {
-    // FP32: the accumulated rotations leave V orthonormal only to
-    // ~sqrt(#rotations) eps; one Newton-Schulz step V (3 I - V^H V) / 2
-    // squares that error.  G = V^H V goes into the (no longer needed) packed A.
-    // G = V^H V (upper triangle, packed): a warp per column j, lanes over i
-    for (int j = tid >> 5; j < n; j += EIG_THREADS / 32) {
-      for (int i = tid & 31; i <= j; i += 32) {
-        T acc = szero<T>();
-        for (int l = 0; l < n; ++l) macc(acc, V[l + ldv * i], V[l + ldv * j]);
-        A[pk_idx(i, j)] = acc;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
-      const int i = e % mg, c = e / mg;
-      const int pc = s_perm[c];
-      T acc = rscale(V[i + ldv * pc], (typename Sc<T>::R)1.5);
-      T corr = szero<T>();
-      for (int l = 0; l < n; ++l) mac(corr, V[i + ldv * l], pk_get(A, l, pc));
-      a.Uout[e] = ssub(acc, rscale(corr, (typename Sc<T>::R)0.5));
-    }
-  } else {
-    for (int e = tid; e < mg * ncopy; e += EIG_THREADS) {
-      const int i = e % mg, c = e / mg;
-      a.Uout[e] = V[i + ldv * s_perm[c]];
-    }
-  }
-  __syncthreads();
-  if (a.phase_clk && tid == 0) a.phase_clk[15] = clock64();
-  if (a.core_out) {
-    if (a.U1) {
-      for (int e = tid; e < mg * r; e += EIG_THREADS) {
-        const int i = e % mg, c = e / mg;
-        typename KAccOf<T>::type acc;
-        for (int l = 0; l < mg; ++l) acc.add_mul(a.U1[i + (size_t)mg * l], a.Uout[l + (size_t)mg * c]);
-        a.core_out[e] = acc.get();
-      }
-    } else if (a.core_out != a.Uout) {
-      for (int e = tid; e < mg * r; e += EIG_THREADS) a.core_out[e] = a.Uout[e];
-    }
-  }
-  if (a.phase_clk && tid == 0) a.phase_clk[3] = clock64();
+  eig_post<T>(a, A, V, n, mg, ldv);
 }
 
 // core[:, c] = U1 U[:, c] for the first r columns (r = *r_ptr, or mg),
@@ -855,6 +865,9 @@ extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps =
 // (device, element type of dt, ld n, columns by descending eigenvalue) and
 // lam (device, double, descending) out.
 extern "C" void qtt_debug_small_eigh_clocks(long long* dev16) { qtt::g_small_eigh_clk = dev16; }
+extern "C" void qtt_debug_set_heev_cluster(double ortol_rel, int ns_steps) {
+  qtt::heev_set_cluster_params(ortol_rel, ns_steps);
+}
 
 extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam,
                                      void* stream) {

@@ -248,12 +248,15 @@ struct EigArgs {
   double delta;         // > 0: SV drop-off rank rule instead of eps (MODE_DECIDE)
   int max_sweeps;       // Jacobi sweep limit (0: the default, flagged when reached)
   long long* phase_clk; // optional: clock64() at phase boundaries (diagnostics)
+  float ortol_rel;      // tridiagonal solver: cluster gap / ||T|| for Gram-Schmidt
+  int ns_steps;         // tridiagonal solver: Newton-Schulz steps
 };
 
 
 // one-CTA Hermitian eigensolvers (k_svd.cu: Jacobi; k_heev.cu: Householder
 // tridiagonalisation + bisection + twisted factorisation, FP32 path)
 void launch_heev_tri(const EigArgs<float2>& a, int mg_cap, cudaStream_t s);
+void heev_set_cluster_params(double ortol_rel, int ns_steps);
 size_t heev_tri_smem_bytes(int mg_cap);
 
 // eigen-decomposition of a dense double2 Gram (k_svd.cu); relative = 1 asks
