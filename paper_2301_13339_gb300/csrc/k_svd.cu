@@ -532,6 +532,305 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   eig_post<T>(a, A, V, n, mg, ldv);
 }
 
+// --------------------------------------------------------------------------
+// FP32 refinement solve in three launches (n > 32, fixed sweep count).
+//
+// 1. jacobi_dm_kernel: the sweeps on the matrix alone.  Indices live in
+//    "positions": at every step pair P is positions (2P, 2P+1), and after the
+//    step every element moves to (pi(x), pi(y)), pi being the seat rotation
+//    of the round-robin tournament (position 0 fixed, the first members of
+//    the pairs move down one pair, the second members up one), so the players
+//    at (2P, 2P+1) in step t are the same pair as in the one-CTA kernel:
+//    (n-1, t) for P = 0, ((t+P) mod (n-1), (t-P) mod (n-1)) otherwise.  Each
+//    2 x 2 block is read from fixed addresses, rotated and written to fixed
+//    addresses of the other buffer (no index tables, no conjugation on the
+//    read side, no ordering inside a step); after n-1 steps every player is
+//    back at its first position.  Every step's rotations go to a log.
+// 2. jacobi_vapply_kernel: V = product of the logged rotations, one warp
+//    per row of V (the rows are independent), many CTAs.
+// 3. jacobi_finish_kernel: ordering, rank, Newton-Schulz step and output
+//    from the diagonal and V (the one-CTA kernel's final stage).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int dm_pi(int x, int n) {
+  if (n == 2 || x == 0) return x;
+  if (x == 2) return 1;
+  if ((x & 1) == 0) return x - 2;
+  if (x == n - 1) return n - 2;
+  return x + 2;
+}
+__device__ __forceinline__ int dm_pl0(int x, int n) {   // player at position x before step 0
+  if (x == 0) return n - 1;
+  if (x == 1) return 0;
+  return (x & 1) ? n - 1 - (x >> 1) : (x >> 1);
+}
+
+// packed upper triangle with every column starting at an even element, so
+// that rows (2P, 2P+1) of a column are one aligned 16-byte pair
+__device__ __forceinline__ int pkp(int i, int j) { return (j * (j + 1)) / 2 + (j + 1) / 2 + i; }
+
+__global__ void __launch_bounds__(EIG_THREADS)
+    jacobi_dm_kernel(EigArgs<float2> a, float4* __restrict__ rlog, float* __restrict__ dbuf,
+                     int* __restrict__ hdr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) float4 s_par[EIG_MAXN / 2];   // (c, s, u); s = 0: no rotation
+  __shared__ int s_pi[EIG_MAXN];
+  __shared__ int s_nrot;
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  if (a.phase_clk && tid == 0) a.phase_clk[0] = clock64();
+  const int mg = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+  const int n = (mg + 1) & ~1;
+  const int np = n / 2;
+  const int npkp = pkp(n - 1, n - 1) + 1;
+  float2* Acur = reinterpret_cast<float2*>(smem_raw);
+  float2* Anext = Acur + ((npkp + 1) & ~1);
+
+  for (int x = tid; x < n; x += EIG_THREADS) s_pi[x] = dm_pi(x, n);
+  double tr_local = 0.0;
+  for (int y = tid >> 5; y < n; y += EIG_THREADS / 32) {
+    const int py = dm_pl0(y, n);
+    for (int x = tid & 31; x <= y; x += 32) {
+      const int px = dm_pl0(x, n);
+      float2 v = make_float2(0.f, 0.f);
+      if (px < mg && py < mg) {
+        const double2 g = a.G[px + (size_t)a.ldp * py];
+        v = make_float2((float)g.x, x == y ? 0.f : (float)g.y);
+        if (x == y) tr_local += g.x;
+      }
+      Acur[pkp(x, y)] = v;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
+  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
+  // this thread's off-diagonal blocks (P < Q): source and destination
+  // addresses for the whole solve; bit 31 of a destination = store conj
+  const int nbo = np * (np - 1) / 2;
+  int bP[2], bQ[2], src0[2], src1[2], dst[2][4];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int bo = tid + k * EIG_THREADS;
+    bP[k] = -1;
+    bQ[k] = 0;
+    src0[k] = src1[k] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dst[k][e] = 0;
+    if (bo < nbo) {
+      int Q = (int)floor((1.0 + sqrt(1.0 + 8.0 * bo)) * 0.5);
+      while (Q * (Q - 1) / 2 > bo) --Q;
+      while ((Q + 1) * Q / 2 <= bo) ++Q;
+      const int P = bo - Q * (Q - 1) / 2;
+      bP[k] = P;
+      bQ[k] = Q;
+      src0[k] = pkp(2 * P, 2 * Q);
+      src1[k] = pkp(2 * P, 2 * Q + 1);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x2 = dm_pi(2 * P + (e & 1), n), y2 = dm_pi(2 * Q + (e >> 1), n);
+        dst[k][e] = (x2 <= y2) ? pkp(x2, y2) : (int)(pkp(y2, x2) | 0x80000000u);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
+    if (a.write_norm2) *a.norm2 = t;
+  }
+  if (a.phase_clk && tid == 0) a.phase_clk[1] = clock64();
+
+  const float tol = 4.0f * Sc<float2>::eps;
+  const int maxsweep = (a.max_sweeps > 0) ? a.max_sweeps : 20;
+  bool converged = (n <= 1);
+  int nsweep = 0;
+  for (int sweep = 0; sweep < maxsweep && !converged; ++sweep, ++nsweep) {
+    if (tid == 0) s_nrot = 0;
+    __syncthreads();
+    for (int step = 0; step < n - 1; ++step) {
+      if (tid < np) {
+        // pair P = positions (x, x + 1); the one-CTA kernel's arithmetic
+        const int x = 2 * tid, y = x + 1;
+        const float app = Acur[pkp(x, x)].x;
+        const float aqq = Acur[pkp(y, y)].x;
+        const float2 apq = Acur[pkp(x, y)];
+        const float b = sqrtf(sabs2(apq));
+        int rot = 0;
+        float c = 1.f, s = 0.f, t = 0.f;
+        float2 u = make_float2(1.f, 0.f);
+        if (b > 0.f && b > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+          const float zeta = (aqq - app) / (2.f * b);
+          const float az = fabsf(zeta);
+          const float tt = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta));
+          t = (zeta >= 0.f) ? tt : -tt;
+          c = 1.f / sqrtf(1.f + t * t);
+          s = t * c;
+          const float ib = 1.f / b;
+          u = make_float2(apq.x * ib, apq.y * ib);
+          rot = 1;
+          s_nrot = 1;
+        }
+        const float4 par = make_float4(c, s, u.x, u.y);
+        s_par[tid] = par;
+        rlog[(size_t)(nsweep * (n - 1) + step) * np + tid] = par;
+        // the diagonal block, rotated (or as it was), to its next place
+        const float d0 = rot ? app - t * b : app, d1 = rot ? aqq + t * b : aqq;
+        const float2 o = rot ? make_float2(0.f, 0.f) : apq;
+        const int x2 = s_pi[x], y2 = s_pi[y];
+        Anext[pkp(x2, x2)] = make_float2(d0, 0.f);
+        Anext[pkp(y2, y2)] = make_float2(d1, 0.f);
+        if (x2 <= y2) Anext[pkp(x2, y2)] = o;
+        else Anext[pkp(y2, x2)] = make_float2(o.x, -o.y);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (bP[k] < 0) continue;
+        const float4 c0 = *reinterpret_cast<const float4*>(Acur + src0[k]);   // rows 2P, 2P+1 of column 2Q
+        const float4 c1 = *reinterpret_cast<const float4*>(Acur + src1[k]);   // of column 2Q+1
+        float2 b00 = make_float2(c0.x, c0.y), b10 = make_float2(c0.z, c0.w);
+        float2 b01 = make_float2(c1.x, c1.y), b11 = make_float2(c1.z, c1.w);
+        const float4 pP = s_par[bP[k]];
+        if (pP.y != 0.f) {
+          const float c = pP.x, s = pP.y;
+          const float2 u = make_float2(pP.z, pP.w);
+          const float2 su = rscale(u, s), scu = rscale(conjg(u), s);
+          const float2 n00 = ssub(rscale(b00, c), smul(su, b10));
+          const float2 n01 = ssub(rscale(b01, c), smul(su, b11));
+          const float2 n10 = sadd(smul(scu, b00), rscale(b10, c));
+          const float2 n11 = sadd(smul(scu, b01), rscale(b11, c));
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        const float4 pQ = s_par[bQ[k]];
+        if (pQ.y != 0.f) {
+          const float c = pQ.x, s = pQ.y;
+          const float2 u = make_float2(pQ.z, pQ.w);
+          const float2 su = rscale(u, s), scu = rscale(conjg(u), s);
+          const float2 n00 = ssub(rscale(b00, c), smul(b01, scu));
+          const float2 n01 = sadd(smul(b00, su), rscale(b01, c));
+          const float2 n10 = ssub(rscale(b10, c), smul(b11, scu));
+          const float2 n11 = sadd(smul(b10, su), rscale(b11, c));
+          b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+        }
+        const float2 bv[4] = {b00, b10, b01, b11};   // e = (row bit) | (col bit) << 1
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int d = dst[k][e];
+          if (d < 0) Anext[d & 0x7fffffff] = make_float2(bv[e].x, -bv[e].y);
+          else Anext[d] = bv[e];
+        }
+      }
+      __syncthreads();
+      float2* tsw = Acur;
+      Acur = Anext;
+      Anext = tsw;
+    }
+    converged = (s_nrot == 0);
+    __syncthreads();
+  }
+  if (!converged && a.max_sweeps == 0 && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
+  if (a.phase_clk && tid == 0) { a.phase_clk[2] = clock64(); a.phase_clk[4] = nsweep; }
+  // every player is back at its first position
+  for (int x = tid; x < n; x += EIG_THREADS) dbuf[dm_pl0(x, n)] = Acur[pkp(x, x)].x;
+  if (tid == 0) hdr[0] = nsweep * (n - 1);
+}
+
+// two padded packed buffers (pkp layout) of an n x n matrix, n even
+static size_t dm_smem_bytes(int n) {
+  const size_t np1 = (size_t)(n - 1) * n / 2 + n / 2 + n;   // pkp(n-1, n-1) + 1
+  return 2 * ((np1 + 1) & ~(size_t)1) * sizeof(float2);
+}
+
+constexpr int VA_WARPS = 8;
+constexpr int VA_CHUNK = 16;   // log steps staged in shared memory at a time
+
+__device__ __forceinline__ void va_stage(float4* dst, const float4* src, int count) {
+  // cp.async 16-byte copies, one commit group per chunk
+  for (int i = threadIdx.x; i < count; i += VA_WARPS * 32) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(VA_WARPS * 32)
+    jacobi_vapply_kernel(const int* mg_ptr, int mg_mul, int mg_const,
+                         const float4* __restrict__ rlog, const int* __restrict__ hdr,
+                         float2* __restrict__ vbuf) {
+  __shared__ float2 s_row[VA_WARPS][EIG_MAXN];
+  __shared__ __align__(16) float4 s_log[2][VA_CHUNK * (EIG_MAXN / 2)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mg = mg_ptr ? mg_mul * (*mg_ptr) : mg_const;
+  const int n = (mg + 1) & ~1, np = n / 2, n1 = n - 1;
+  const int row = blockIdx.x * VA_WARPS + warp;
+  const bool has_row = row < n;   // every warp stays for the block barriers
+  float2* v = s_row[warp];
+  if (has_row)
+    for (int j = lane; j < n; j += 32) v[j] = make_float2(j == row ? 1.f : 0.f, 0.f);
+  __syncwarp();
+  const int nsteps = hdr[0];
+  const int nchunks = (nsteps + VA_CHUNK - 1) / VA_CHUNK;
+  auto chunk_count = [&](int c) { return min(VA_CHUNK, nsteps - c * VA_CHUNK) * np; };
+  if (nchunks > 0) va_stage(s_log[0], rlog, chunk_count(0));
+  int tl = 0;   // step within the sweep
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      va_stage(s_log[(c + 1) & 1], rlog + (size_t)(c + 1) * VA_CHUNK * np, chunk_count(c + 1));
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const float4* L = s_log[c & 1];
+    const int ns = min(VA_CHUNK, nsteps - c * VA_CHUNK);
+    for (int k = 0; k < ns; ++k) {
+      if (has_row) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int P = lane + 32 * h;
+          if (P >= np) continue;
+          const float4 r = L[k * np + P];
+          if (r.y == 0.f) continue;
+          int p, q;
+          if (P == 0) { p = n1; q = tl; }
+          else {
+            p = tl + P; if (p >= n1) p -= n1;
+            q = tl - P; if (q < 0) q += n1;
+          }
+          const float2 u = make_float2(r.z, r.w);
+          const float2 su = rscale(u, r.y), scu = rscale(conjg(u), r.y);
+          const float2 vp = v[p], vq = v[q];
+          // [vp, vq] J = [c vp - s conj(u) vq, s u vp + c vq]
+          v[p] = ssub(rscale(vp, r.x), smul(scu, vq));
+          v[q] = sadd(smul(su, vp), rscale(vq, r.x));
+        }
+      }
+      __syncwarp();
+      if (++tl == n1) tl = 0;
+    }
+    __syncthreads();   // the buffer is restaged two chunks later
+  }
+  if (has_row)
+    for (int j = lane; j < n; j += 32) vbuf[j + (size_t)n * row] = v[j];
+}
+
+__global__ void __launch_bounds__(EIG_THREADS)
+    jacobi_finish_kernel(EigArgs<float2> a, const float2* __restrict__ vbuf,
+                         const float* __restrict__ dbuf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int mg = a.mg_ptr ? a.mg_mul * (*a.mg_ptr) : a.mg_const;
+  const int n = (mg + 1) & ~1;
+  const int ldv = n + 1;
+  float2* A = reinterpret_cast<float2*>(smem_raw);
+  float2* V = A + (n * (n + 1)) / 2;
+  for (int e = tid; e < n * n; e += EIG_THREADS) {
+    const int i = e / n, j = e % n;
+    V[i + (size_t)ldv * j] = vbuf[e];
+  }
+  for (int i = tid; i < n; i += EIG_THREADS) A[pk_idx(i, i)] = make_float2(dbuf[i], 0.f);
+  __syncthreads();
+  eig_post<float2>(a, A, V, n, mg, ldv);
+}
+
 // core[:, c] = U1 U[:, c] for the first r columns (r = *r_ptr, or mg),
 // compensated sums: one CTA per column, a thread per row.
 template <typename T>
@@ -599,7 +898,46 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   // core = U1 U[:, :r] over many CTAs instead of inside the one-CTA solve
   const bool split_core = a.U1 && a.core_out && (a.mode == EIG_MODE_ALL || a.rank_out);
   if (split_core) b.core_out = nullptr;
-  {
+  bool done = false;
+  if (Sc<T>::cplx && a.relative && a.max_sweeps > 0 && mg_cap > 32) {
+    // FP32 refinement: sweeps, V and the final stage in three launches
+    const size_t ncap = (mg_cap + 1) & ~1;
+    auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t lb = al16((size_t)a.max_sweeps * (ncap - 1) * (ncap / 2) * sizeof(float4));
+    const size_t vb = al16(ncap * ncap * sizeof(float2)), db = al16(ncap * sizeof(float));
+    char* buf = (char*)scratch_alloc(lb + vb + db + 16, s);
+    if (buf) {
+      static bool dm_cfg = false;
+      if (!dm_cfg) {
+        cudaFuncSetAttribute(jacobi_dm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dm_smem_bytes(EIG_MAXN));
+        cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eig_smem_bytes<float2>(EIG_MAXN));
+        dm_cfg = true;
+      }
+      float4* rlog = (float4*)buf;
+      float2* vbuf = (float2*)(buf + lb);
+      float* dbuf = (float*)(buf + lb + vb);
+      int* hdr = (int*)(buf + lb + vb + db);
+      const EigArgs<float2>& bf = reinterpret_cast<const EigArgs<float2>&>(b);
+      {
+        QTT_PROF(pname, s);
+        jacobi_dm_kernel<<<1, EIG_THREADS, dm_smem_bytes((int)ncap), s>>>(bf, rlog, dbuf, hdr);
+      }
+      {
+        QTT_PROF("jacobi_vapply", s);
+        jacobi_vapply_kernel<<<(unsigned)((ncap + VA_WARPS - 1) / VA_WARPS), VA_WARPS * 32, 0, s>>>(
+            a.mg_ptr, a.mg_mul, a.mg_const, rlog, hdr, vbuf);
+      }
+      {
+        QTT_PROF("jacobi_finish", s);
+        jacobi_finish_kernel<<<1, EIG_THREADS, eig_smem_bytes<float2>(mg_cap), s>>>(bf, vbuf, dbuf);
+      }
+      scratch_free(buf, s);
+      done = true;
+    }
+  }
+  if (!done) {
     QTT_PROF(pname, s);
     gram_eig_kernel<T><<<1, EIG_THREADS, sm, s>>>(b);
   }
