@@ -268,9 +268,10 @@ def gpu_arm(args, wl):
 
 
 # DRAM bytes (read + write) per launch from the committed ncu captures in
-# profiles/ (heev_tri_kernel_n128_line_2p20_c64.md); valid while that kernel
-# is unchanged.
-NCU_TRAFFIC = {"heev_le128": 380416.0}
+# profiles/ (heev_tri_kernel_n128_line_2p20_c64.md: heev_tri_kernel +
+# heev_back_kernel; jacobi_dm_kernel_n128_line_2p20_c64.md); valid while
+# those kernels are unchanged.
+NCU_TRAFFIC = {"heev_le128": 354816.0 + 182272.0, "jacobi_eig_le128": 177920.0}
 
 
 def roofline(kernels, wl, peaks, peak_kind):
