@@ -307,20 +307,20 @@ void qtt_profile_reset(void);
  * double[n], descending.  Asynchronous. */
 qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* lam, void* stream);
 
-/* Diagnostics: if dev16 is not NULL, the following FP32 tridiagonal solves
- * (qtt_small_eigh and the solves inside decompose and round; the last one
- * leaves its values) store clock64() at their 10 phase boundaries (start,
- * load, tridiagonalisation, eigenvalues, eigenvectors, orthogonalisation,
- * reflector packing, Newton-Schulz, back-transformation, output) in slots
- * 0-9 of dev16 (device, 16 long long), and in slots 10-12 the end of the
- * Gram-Schmidt sweeps, the number of degenerate copies replaced and the
- * number of vectors in clusters of more than one member.  The Jacobi
- * solves (qtt_small_eigh with that solver selected, the refinement passes
- * of decompose and round) store start, load, end of the sweeps and end in
- * slots 0-3, the sweep count in slot 4, and the ends of the ordering, of
- * the Newton-Schulz Gram and of the output in slots 13-15.  NULL switches
- * it off. */
-void qtt_debug_small_eigh_clocks(long long* dev16);
+/* Diagnostics: if dev32 is not NULL (device, 32 long long), the following
+ * eigen-solves of the FP32 path store clock64() values there; the last
+ * solve of each kind leaves its values.  Tridiagonal solver (qtt_small_eigh
+ * and the solves inside decompose and round): slots 0-9 = its 10 phase
+ * boundaries (start, load, tridiagonalisation, eigenvalues, eigenvectors,
+ * orthogonalisation, hand-off, Newton-Schulz, back-transformation, output),
+ * slots 10-12 = the end of the Gram-Schmidt sweeps, the number of
+ * degenerate copies replaced and the number of vectors in clusters of more
+ * than one member.  Jacobi solver: through qtt_small_eigh (with that solver
+ * selected) slots 0-3 = start, load, end of the sweeps, end, slot 4 = sweep
+ * count, slots 13-15 = ends of the ordering, of the Newton-Schulz Gram and
+ * of the output; inside decompose and round the same at slots 16 + those.
+ * NULL switches it off. */
+void qtt_debug_small_eigh_clocks(long long* dev32);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
  * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */

@@ -894,7 +894,8 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   const char* pname =
       mg_cap <= 32 ? "jacobi_eig_le32" : mg_cap <= 64 ? "jacobi_eig_le64" : "jacobi_eig_le128";
   EigArgs<T> b = a;
-  if (g_small_eigh_clk && !b.phase_clk) b.phase_clk = g_small_eigh_clk;
+  // diagnostics: the Jacobi solves inside decompose / round use slots 16..
+  if (g_small_eigh_clk && !b.phase_clk) b.phase_clk = g_small_eigh_clk + 16;
   // core = U1 U[:, :r] over many CTAs instead of inside the one-CTA solve
   const bool split_core = a.U1 && a.core_out && (a.mode == EIG_MODE_ALL || a.rank_out);
   if (split_core) b.core_out = nullptr;
@@ -1202,7 +1203,7 @@ extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps =
 // one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U
 // (device, element type of dt, ld n, columns by descending eigenvalue) and
 // lam (device, double, descending) out.
-extern "C" void qtt_debug_small_eigh_clocks(long long* dev16) { qtt::g_small_eigh_clk = dev16; }
+extern "C" void qtt_debug_small_eigh_clocks(long long* dev32) { qtt::g_small_eigh_clk = dev32; }
 extern "C" void qtt_debug_set_heev_cluster(double ortol_rel, int ns_steps) {
   qtt::heev_set_cluster_params(ortol_rel, ns_steps);
 }
