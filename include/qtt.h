@@ -323,7 +323,10 @@ qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U, double* l
 void qtt_debug_small_eigh_clocks(long long* dev32);
 
 /* Diagnostics: eigen-solver of the FP32 path (0 = Householder tridiagonal
- * + bisection, the default; 1 = cyclic Jacobi).  FP64 always uses Jacobi. */
+ * + bisection, the default; 1 = cyclic Jacobi; 2 = for qtt_small_eigh only,
+ * the relative-accuracy Jacobi of the refinement passes, up to 20 sweeps
+ * and stopping at the first sweep without a rotation: for n > 32 the
+ * three-launch data-movement solve).  FP64 always uses Jacobi. */
 void qtt_debug_set_eig_solver(int which);
 
 /* Diagnostics: sweep count of the FP32 relative-accuracy Jacobi passes

@@ -1195,7 +1195,8 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 
 }  // namespace qtt
 
-// Diagnostics: choose the FP32 eigen-solver (0 = tridiagonal, 1 = Jacobi).
+// Diagnostics: choose the FP32 eigen-solver (0 = tridiagonal, 1 = Jacobi,
+// 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
 extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps = sweeps >= 0 ? sweeps : 2; }
 
@@ -1227,6 +1228,12 @@ extern "C" qtt_status qtt_small_eigh(const void* G, int n, qtt_dtype dt, void* U
     a.G = (const double2*)G; a.ldp = n; a.mg_const = n; a.mode = EIG_MODE_ALL;
     a.dmodes = 2; a.Uout = (float2*)U; a.sig_out = lam; a.norm2 = nrm; a.write_norm2 = 1;
     a.phase_clk = g_small_eigh_clk;
+    if (g_eig_solver == 2) {
+      // the refinement passes' solver on a dense matrix: up to 20 sweeps,
+      // stopping at the first sweep without a rotation
+      a.relative = 1;
+      a.max_sweeps = 20;
+    }
     launch_eig<float2>(a, n, s);
   }
   scratch_free(nrm, s);

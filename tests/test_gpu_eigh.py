@@ -1,5 +1,8 @@
-"""The one-CTA Hermitian eigen-solvers (behind every truncation of Alg. 1)
-against LAPACK (numpy.linalg.eigh, FP64), through the C ABI.
+"""The Hermitian eigen-solvers behind every truncation of Alg. 1 against
+LAPACK (numpy.linalg.eigh, FP64), through the C ABI: solver 0 = FP32
+tridiagonal (+ cluster back-transformation above n = 32), 1 = one-CTA
+Jacobi, 2 = the relative-accuracy refinement Jacobi (three launches with
+data-movement ordering above n = 32) run to convergence (at most 20 sweeps).
 
 Checked quantities are gauge-free: eigenvalues, residual ||G u - lam u||,
 orthonormality, and the projector onto the leading r-dimensional subspace
@@ -31,8 +34,8 @@ SPECTRA = {
 }
 
 
-@pytest.mark.parametrize("solver", [0, 1])
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 33, 64, 100, 128])
+@pytest.mark.parametrize("solver", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 33, 34, 64, 67, 100, 127, 128])
 @pytest.mark.parametrize("kind", sorted(SPECTRA))
 def test_small_eigh_c64(qlib, solver, n, kind):
     rng = np.random.default_rng(n)
