@@ -123,6 +123,12 @@ __global__ void __launch_bounds__(OS_THREADS) k_orth_sketch(R* Om, SketchCores s
   for (int e = tid; e < m * n; e += OS_THREADS) G[e] = M[e];
 }
 
+// The contractions below are one output per thread, summed in index order
+// with compensation; their operands come from L2, so the loops load KB
+// terms ahead (independent loads in flight) and then add them in the same
+// order as a plain loop would.
+constexpr int KB = 8;
+
 // ---------------------------------------------------------------- step 1
 // A1[s + lk (j + 2 c)] = sum_{s'} Om[s' + l0 (j + 2 s)] WL0[s' + l0 c],  c < R0
 template <typename T, typename R>
@@ -134,7 +140,20 @@ __global__ void k_a1(const R* Om, int l0, int lk, const T* WL0, const int* xr, i
   const int s = (int)(e % lk), j = (int)((e / lk) % 2), c = (int)(e / (2LL * lk));
   if (c >= R0) return;
   typename KAccOf<T>::type acc;
-  for (int sp = 0; sp < l0; ++sp) acc.add_rmul(Om[sp + l0 * (j + 2 * s)], WL0[sp + (size_t)l0 * c]);
+  const R* om = Om + (size_t)l0 * (j + 2 * s);
+  const T* wl = WL0 + (size_t)l0 * c;
+  for (int s0 = 0; s0 < l0; s0 += KB) {
+    R o[KB];
+    T w[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      o[t] = (s0 + t < l0) ? om[s0 + t] : (R)0;
+      w[t] = (s0 + t < l0) ? wl[s0 + t] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (s0 + t < l0) acc.add_rmul(o[t], w[t]);
+  }
   A1[s + (size_t)lk * (j + 2 * c)] = acc.get();
 }
 // A2[s + lk (j + 2 (p + Pin (i + 2 b)))] = sum_a A1[s + lk (j + 2 (a + r0 p))] X[a + r0 (i + 2 b)]
@@ -152,8 +171,18 @@ __global__ void k_a2(const T* A1, int lk, const T* X, const int* xr, int k, int 
   const int b = (int)t;
   if (b >= r1) return;
   typename KAccOf<T>::type acc;
-  for (int a = 0; a < r0; ++a)
-    acc.add_mul(A1[s + (size_t)lk * (j + 2 * (a + r0 * p))], X[a + (size_t)r0 * (i + 2 * b)]);
+  for (int a0 = 0; a0 < r0; a0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int a = a0 + t;
+      x1[t] = (a < r0) ? A1[s + (size_t)lk * (j + 2 * (a + r0 * p))] : szero<T>();
+      x2[t] = (a < r0) ? X[a + (size_t)r0 * (i + 2 * b)] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (a0 + t < r0) acc.add_mul(x1[t], x2[t]);
+  }
   A2[s + (size_t)lk * (j + 2 * (p + Pin * (i + 2 * b)))] = acc.get();
 }
 // WL1[s + lk (b + r1 q)] = sum_{j,p,i} O[p + Pin (j + 2 (i + 2 q))] A2[s + lk (j + 2 (p + Pin (i + 2 b)))]
@@ -240,8 +269,18 @@ __global__ void k_b1(const T* X, const int* xr, int k, int rcap0, int Pout, cons
   const int tt = (int)t;
   if (a >= r0) return;
   typename KAccOf<T>::type acc;
-  for (int b = 0; b < r1; ++b)
-    acc.add_mul(X[a + (size_t)r0 * (i + 2 * b)], C[(b + r1 * q) + (size_t)ldc * tt]);
+  for (int b0 = 0; b0 < r1; b0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int b = b0 + t;
+      x1[t] = (b < r1) ? X[a + (size_t)r0 * (i + 2 * b)] : szero<T>();
+      x2[t] = (b < r1) ? C[(b + r1 * q) + (size_t)ldc * tt] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (b0 + t < r1) acc.add_mul(x1[t], x2[t]);
+  }
   B1[a + (size_t)r0 * (i + 2 * (q + Pout * tt))] = acc.get();
 }
 // Z[(a + r0 p) + ldz (j + 2 t)] = sum_{q,i} O[p + Pin (j + 2 (i + 2 q))] B1[a + r0 (i + 2 (q + Pout t))]
@@ -280,8 +319,18 @@ __global__ void k_s(const T* WL, int l0, const T* Z, int ldz, const int* xr, int
   typename KAccOf<T>::type acc;
   if (live) {
     const int s = (int)(e % l0), u = (int)(e / l0);
-    for (int c = part; c < R0; c += KS_SPLIT)
-      acc.add_mul(WL[s + (size_t)l0 * c], Z[c + (size_t)ldz * u]);
+    for (int c0 = part; c0 < R0; c0 += KB * KS_SPLIT) {
+      T x1[KB], x2[KB];
+#pragma unroll
+      for (int t = 0; t < KB; ++t) {
+        const int c = c0 + t * KS_SPLIT;
+        x1[t] = (c < R0) ? WL[s + (size_t)l0 * c] : szero<T>();
+        x2[t] = (c < R0) ? Z[c + (size_t)ldz * u] : szero<T>();
+      }
+#pragma unroll
+      for (int t = 0; t < KB; ++t)
+        if (c0 + t * KS_SPLIT < R0) acc.add_mul(x1[t], x2[t]);
+    }
   }
   T v = acc.get();
   // groups of KS_SPLIT consecutive lanes (blockDim is a multiple of 32)
@@ -295,7 +344,18 @@ __global__ void k_gram_cols(const T* S, int ls, int n, double2* G, int ldg) {
   if (e >= n * n) return;
   const int u = e % n, v = e / n;
   typename KAccOf<T>::type acc;
-  for (int s2 = 0; s2 < ls; ++s2) acc.add_cmul(S[s2 + (size_t)ls * u], S[s2 + (size_t)ls * v]);
+  for (int q0 = 0; q0 < ls; q0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int s2 = q0 + t;
+      x1[t] = (s2 < ls) ? S[s2 + (size_t)ls * u] : szero<T>();
+      x2[t] = (s2 < ls) ? S[s2 + (size_t)ls * v] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (q0 + t < ls) acc.add_cmul(x1[t], x2[t]);
+  }
   G[u + (size_t)ldg * v] = to_d2(acc.get());
 }
 // SV[s + ls w] = sum_u S[s + ls u] V[u + n w]
@@ -305,7 +365,18 @@ __global__ void k_sv(const T* S, int ls, int n, const T* V, T* SV) {
   if (e >= ls * n) return;
   const int s2 = e % ls, w = e / ls;
   typename KAccOf<T>::type acc;
-  for (int u = 0; u < n; ++u) acc.add_mul(S[s2 + (size_t)ls * u], V[u + (size_t)n * w]);
+  for (int u0 = 0; u0 < n; u0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int u = u0 + t;
+      x1[t] = (u < n) ? S[s2 + (size_t)ls * u] : szero<T>();
+      x2[t] = (u < n) ? V[u + (size_t)n * w] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (u0 + t < n) acc.add_mul(x1[t], x2[t]);
+  }
   SV[e] = acc.get();
 }
 // Q[s + lq0 (j + 2 t)] = conj(V[(j + 2 t) + n s]),  n = 2 lq
@@ -325,7 +396,18 @@ __global__ void k_c(const T* Z, int ldz, const T* V, int n, int lq0, const int* 
   const int c = (int)(e % ldc), s2 = (int)(e / ldc);
   if (c >= Pin * xr[k - 1]) return;
   typename KAccOf<T>::type acc;
-  for (int u = 0; u < n; ++u) acc.add_mul(Z[c + (size_t)ldz * u], V[u + (size_t)n * s2]);
+  for (int u0 = 0; u0 < n; u0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int u = u0 + t;
+      x1[t] = (u < n) ? Z[c + (size_t)ldz * u] : szero<T>();
+      x2[t] = (u < n) ? V[u + (size_t)n * s2] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (u0 + t < n) acc.add_mul(x1[t], x2[t]);
+  }
   Cn[c + (size_t)ldc * s2] = acc.get();
 }
 
@@ -342,7 +424,18 @@ __global__ void k_zt(const T* Lc, const int* tr, int k, int tcap0, const T* Tp, 
   if (row >= m) return;
   const int s2 = row % t0, j = row / t0;
   typename KAccOf<T>::type acc;
-  for (int sp = 0; sp < lq0; ++sp) acc.add_mul(Lc[s2 + (size_t)t0 * sp], Tp[sp + (size_t)lq0 * (j + 2 * u)]);
+  for (int q0 = 0; q0 < lq0; q0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int sp = q0 + t;
+      x1[t] = (sp < lq0) ? Lc[s2 + (size_t)t0 * sp] : szero<T>();
+      x2[t] = (sp < lq0) ? Tp[sp + (size_t)lq0 * (j + 2 * u)] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (q0 + t < lq0) acc.add_mul(x1[t], x2[t]);
+  }
   Zt[row + (size_t)m * u] = acc.get();
 }
 // row Gram  G[a + ldg b] = sum_u Z[a + m u] conj(Z[b + m u]),  m = mul * *mptr
@@ -355,7 +448,18 @@ __global__ void k_gram_rows(const T* Zt, const int* mptr, int mul, int mcap, int
   const int a = e % mcap, b = e / mcap;
   if (a >= m || b >= m) return;
   typename KAccOf<T>::type acc;
-  for (int u = 0; u < ncol; ++u) acc.add_cmul(Zt[b + (size_t)m * u], Zt[a + (size_t)m * u]);
+  for (int u0 = 0; u0 < ncol; u0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int u = u0 + t;
+      x1[t] = (u < ncol) ? Zt[b + (size_t)m * u] : szero<T>();
+      x2[t] = (u < ncol) ? Zt[a + (size_t)m * u] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (u0 + t < ncol) acc.add_cmul(x1[t], x2[t]);
+  }
   G[a + (size_t)ldg * b] = to_d2(acc.get());
 }
 // W[c + m u] = sum_a conj(U[a + m c]) Z[a + m u],  c < rows (= rmul * *rptr or m)
@@ -369,7 +473,18 @@ __global__ void k_proj_rows(const T* U, const T* Zt, const int* mptr, int mul, c
   const int c = e % mcap, u = e / mcap;
   if (c >= rr) return;
   typename KAccOf<T>::type acc;
-  for (int a = 0; a < m; ++a) acc.add_cmul(U[a + (size_t)m * c], Zt[a + (size_t)m * u]);
+  for (int a0 = 0; a0 < m; a0 += KB) {
+    T x1[KB], x2[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int a = a0 + t;
+      x1[t] = (a < m) ? U[a + (size_t)m * c] : szero<T>();
+      x2[t] = (a < m) ? Zt[a + (size_t)m * u] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (a0 + t < m) acc.add_cmul(x1[t], x2[t]);
+  }
   W[c + (size_t)rr * u] = acc.get();
 }
 // Step 3 with more rows than columns (m = 2 t_{k-1} > lq_k): Zt = Q R by

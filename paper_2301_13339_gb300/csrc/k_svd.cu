@@ -845,8 +845,16 @@ __global__ void __launch_bounds__(128)
   for (int l = threadIdx.x; l < mg; l += 128) s_u[l] = U[l + (size_t)mg * c];
   __syncthreads();
   for (int i = threadIdx.x; i < mg; i += 128) {
+    // eight loads of U1 in flight, then the compensated sum in index order
     typename KAccOf<T>::type acc;
-    for (int l = 0; l < mg; ++l) acc.add_mul(U1[i + (size_t)mg * l], s_u[l]);
+    for (int l0 = 0; l0 < mg; l0 += 8) {
+      T x[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) x[t] = (l0 + t < mg) ? U1[i + (size_t)mg * (l0 + t)] : szero<T>();
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (l0 + t < mg) acc.add_mul(x[t], s_u[l0 + t]);
+    }
     core[i + (size_t)mg * c] = acc.get();
   }
 }
