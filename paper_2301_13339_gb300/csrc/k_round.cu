@@ -196,38 +196,50 @@ __global__ void k_wl(const R* O, int Pin, int Pout, const T* A2, int lk, const i
   if (c >= Pout * r1) return;
   const int b = c % r1, q = c / r1;
   typename KAccOf<T>::type acc;
-  for (int i = 0; i < 2; ++i)
-    for (int p = 0; p < Pin; ++p)
-      for (int j = 0; j < 2; ++j) {
-        const R o = O[p + Pin * (j + 2 * (i + 2 * q))];
-        if (o != (R)0) acc.add_rmul(o, A2[s + (size_t)lk * (j + 2 * (p + Pin * (i + 2 * b)))]);
-      }
+  // terms (i, p, j) in that nesting order, flattened: f = j + 2 (p + Pin i)
+  const int nf = 4 * Pin;
+  for (int f0 = 0; f0 < nf; f0 += KB) {
+    R o[KB];
+    T x[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int f = f0 + t;
+      const int j = f & 1, p = (f >> 1) % Pin, i = (f >> 1) / Pin;
+      o[t] = (f < nf) ? O[p + Pin * (j + 2 * (i + 2 * q))] : (R)0;
+      x[t] = (f < nf) ? A2[s + (size_t)lk * (j + 2 * (p + Pin * (i + 2 * b)))] : szero<T>();
+    }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (o[t] != (R)0) acc.add_rmul(o[t], x[t]);
+  }
   WL1[s + (size_t)lk * c] = acc.get();
 }
 
-// In-place scaling of a sketch block to unit max-abs entry (one CTA).  The
+// In-place scaling of a sketch block to unit max-abs entry.  The
 // sketch of Y_{<=k} grows like (sqrt(l) ||Y_k||)^k; any scaling of a sketch
 // leaves its row space unchanged, so each WL_k is rescaled as it is formed.
+// Over many CTAs: the largest |entry| (non-negative floats compare as their
+// bit patterns) by atomicMax into *mx (zeroed before), then the division by
+// it.
 template <typename T>
-__global__ void k_normalize(T* A, int lk, const int* xr, int k, int Pout) {
-  // only the written prefix: columns c < P_k r_k (actual ranks)
+__global__ void k_absmax(const T* A, int lk, const int* xr, int k, int Pout, unsigned* mx) {
   const long long n = (long long)lk * Pout * xr[k];
-  __shared__ float red[32];
-  float mx = 0.f;
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) mx = fmaxf(mx, sqrtf((float)sabs2(A[e])));
-  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, off));
-    if (threadIdx.x == 0) red[0] = v;
-  }
-  __syncthreads();
-  const float m = red[0];
+  float m = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, sqrtf((float)sabs2(A[e])));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(m));
+}
+template <typename T>
+__global__ void k_scale_max(T* A, int lk, const int* xr, int k, int Pout, const unsigned* mx) {
+  const float m = __uint_as_float(*mx);
   if (!(m > 0.f) || !(m < 3.0e38f)) return;
+  const long long n = (long long)lk * Pout * xr[k];
   const typename Sc<T>::R sc = (typename Sc<T>::R)(1.0 / (double)m);
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) A[e] = rscale(A[e], sc);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    A[e] = rscale(A[e], sc);
 }
 
 // ---------------------------------------------------------------- QR
@@ -297,11 +309,22 @@ __global__ void k_z(const R* O, int Pin, int Pout, const T* B1, const int* xr, i
   const int tt = (int)t;
   if (a >= r0) return;
   typename KAccOf<T>::type acc;
-  for (int q = 0; q < Pout; ++q)
-    for (int i = 0; i < 2; ++i) {
-      const R o = O[p + Pin * (j + 2 * (i + 2 * q))];
-      if (o != (R)0) acc.add_rmul(o, B1[a + (size_t)r0 * (i + 2 * (q + Pout * tt))]);
+  // terms (q, i) in that nesting order, flattened: f = i + 2 q
+  const int nf = 2 * Pout;
+  for (int f0 = 0; f0 < nf; f0 += KB) {
+    R o[KB];
+    T x[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) {
+      const int f = f0 + t;
+      const int i = f & 1, q = f >> 1;
+      o[t] = (f < nf) ? O[p + Pin * (j + 2 * (i + 2 * q))] : (R)0;
+      x[t] = (f < nf) ? B1[a + (size_t)r0 * (i + 2 * (q + Pout * tt))] : szero<T>();
     }
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (o[t] != (R)0) acc.add_rmul(o[t], x[t]);
+  }
   Z[(a + r0 * p) + (size_t)ldz * (j + 2 * tt)] = acc.get();
 }
 // S[s + l0 u] = sum_{c < R0} WL[s + l0 c] Z[c + ldz u]  (R0 = P r up to ~1e3):
@@ -704,13 +727,15 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   T* Rz = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
   T* Ur = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
   int* kd = (int*)scratch_alloc(sizeof(int), s);
+  unsigned* wmax = (unsigned*)scratch_alloc(sizeof(unsigned) * (d + 1), s);
   if (!WL || !Om || !A1 || !A2 || !Z || !C0 || !C1 || !S || !SV || !SV2 || !V1 || !V || !G || !Zt ||
-      !W1 || !Lc || !one || !Qz || !Rz || !Ur || !kd) {
+      !W1 || !Lc || !one || !Qz || !Rz || !Ur || !kd || !wmax) {
     set_error("round: scratch allocation failed");
     return QTT_ENOMEM;
   }
   const int is64 = Sc<T>::cplx ? 0 : 1;
   k_one<<<1, 32, 0, s>>>(one, is64);
+  cudaMemsetAsync(wmax, 0, sizeof(unsigned) * (d + 1), s);
   // intermediate right-orthonormal TT (host-known ranks lq)
   TensorDesc pd = x->desc;
   qtt_tensor* Tp = nullptr;
@@ -742,7 +767,9 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
                                                  WL + wloff[k]);
     }
     { QTT_PROF("round_sketch", s);
-    k_normalize<T><<<1, 1024, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k]);
+    const unsigned nbk = (unsigned)std::min<long long>(152, ((long long)lk * Rc[k] + 255) / 256);
+    k_absmax<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k], wmax + k);
+    k_scale_max<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k], wmax + k);
     }
   }
   // --- 2. right-to-left orthogonalising pass
@@ -885,6 +912,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s); scratch_free(G, s);
   scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s); scratch_free(one, s);
   scratch_free(Qz, s); scratch_free(Rz, s); scratch_free(Ur, s); scratch_free(kd, s);
+  scratch_free(wmax, s);
   tensor_free_async(Tp, s);
   if (st != QTT_OK) { qtt_free(y); return st; }
   *out = y;
