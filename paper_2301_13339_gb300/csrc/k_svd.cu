@@ -147,19 +147,43 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
 }
 
 // Sum of the per-CTA partial Grams in double: out[e] = sum_p part[p][e].
+// Sum of the per-CTA partial Grams in FP64.  Block = 32 elements x 8 part
+// lanes: lane y sums parts y, y+8, ... in order, then the 8 lane sums are
+// added in y order (a fixed order: the result does not depend on timing).
+constexpr int GR_SPLIT = 8;
 template <typename T>
-__global__ void gram_reduce_kernel(const T* __restrict__ part, int nparts, int ldp,
-                                   double2* __restrict__ out) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * GR_SPLIT)
+    gram_reduce_kernel(const T* __restrict__ part, int nparts, int ldp, double2* __restrict__ out) {
+  __shared__ double2 s_acc[GR_SPLIT][32];
   const int tot = ldp * ldp;
-  if (e >= tot) return;
-  double2 s = make_double2(0.0, 0.0);
-  for (int p = 0; p < nparts; ++p) {
-    double2 v = to_d2(part[(size_t)p * tot + e]);
-    s.x += v.x;
-    s.y += v.y;
+  const int e = blockIdx.x * 32 + threadIdx.x;
+  double2 acc = make_double2(0.0, 0.0);
+  if (e < tot) {
+    for (int p0 = threadIdx.y; p0 < nparts; p0 += 4 * GR_SPLIT) {
+      T x[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int p = p0 + t * GR_SPLIT;
+        x[t] = (p < nparts) ? part[(size_t)p * tot + e] : szero<T>();
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const double2 v = to_d2(x[t]);
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+    }
   }
-  out[e] = s;
+  s_acc[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && e < tot) {
+    double2 r = s_acc[0][threadIdx.x];
+    for (int y = 1; y < GR_SPLIT; ++y) {
+      r.x += s_acc[y][threadIdx.x].x;
+      r.y += s_acc[y][threadIdx.x].y;
+    }
+    out[e] = r;
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1007,7 +1031,7 @@ template <typename T>
 static void launch_reduce(const T* gp, int nparts, int ldp, double2* out, cudaStream_t s) {
   const int tot = ldp * ldp;
   QTT_PROF("gram_reduce", s);
-  gram_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(gp, nparts, ldp, out);
+  gram_reduce_kernel<T><<<(tot + 31) / 32, dim3(32, GR_SPLIT), 0, s>>>(gp, nparts, ldp, out);
 }
 
 // Identity core of a level that keeps full rank: r_{k-1} = rp, r_k = 2 rp,
