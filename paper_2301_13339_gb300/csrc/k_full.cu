@@ -232,6 +232,8 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
   long long* thi = (long long*)scratch_alloc(sizeof(long long) * nhi, s);
   int* order = (int*)scratch_alloc(sizeof(int) * 64, s);
   if (!Lb0 || !Lb1 || !Rb0 || !Rb1 || !tlo || !thi || !order) {
+    scratch_free(Lb0, s); scratch_free(Lb1, s); scratch_free(Rb0, s); scratch_free(Rb1, s);
+    scratch_free(tlo, s); scratch_free(thi, s); scratch_free(order, s);
     set_error("to_full: scratch allocation failed");
     return QTT_ENOMEM;
   }

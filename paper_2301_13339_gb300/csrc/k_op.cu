@@ -100,7 +100,12 @@ qtt_status op_sinc_create(int d, double B, int normalize, double eps_op, qtt_dty
   const long long n = 1LL << d;
   double* sum = (double*)scratch_alloc(sizeof(double), s);
   double* chat = (double*)scratch_alloc(sizeof(double) * 2 * n, s);
-  if (!sum || !chat) { set_error("op_sinc_create: alloc"); return QTT_ENOMEM; }
+  if (!sum || !chat) {
+    scratch_free(sum, s);
+    scratch_free(chat, s);
+    set_error("op_sinc_create: alloc");
+    return QTT_ENOMEM;
+  }
   cudaMemsetAsync(sum, 0, sizeof(double), s);
   int blocks = (int)std::min<long long>((2 * n + 255) / 256, 4096);
   sinc_sum_kernel<<<blocks, 256, 0, s>>>(n, B, sum);
@@ -137,6 +142,7 @@ qtt_status op_sinc_create(int d, double B, int normalize, double eps_op, qtt_dty
   op->total = tot;
   const size_t rsz = (dt == QTT_F64) ? sizeof(double) : sizeof(float);
   if (cudaMalloc(&op->cores, rsz * tot) != cudaSuccess) {
+    cudaGetLastError();
     delete op;
     qtt_free(G);
     set_error("op_sinc_create: cudaMalloc");
@@ -200,6 +206,7 @@ qtt_status op_embed_axis(const qtt_op* op1d, const TensorDesc& desc, int axis, c
   op->total = tot;
   const size_t rsz = (op->dt == QTT_F64) ? sizeof(double) : sizeof(float);
   if (cudaMalloc(&op->cores, rsz * tot) != cudaSuccess) {
+    cudaGetLastError();
     delete op;
     set_error("op_embed_axis: cudaMalloc");
     return QTT_ENOMEM;

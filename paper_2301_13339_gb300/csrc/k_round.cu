@@ -728,8 +728,18 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   T* Ur = (T*)scratch_alloc(sizeof(T) * 64 * 64, s);
   int* kd = (int*)scratch_alloc(sizeof(int), s);
   unsigned* wmax = (unsigned*)scratch_alloc(sizeof(unsigned) * (d + 1), s);
+  // every scratch buffer goes back to the pool on every exit
+  auto release = [&]() {
+    scratch_free(WL, s); if (om_owned) scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
+    scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
+    scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s);
+    scratch_free(G, s); scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s);
+    scratch_free(one, s); scratch_free(Qz, s); scratch_free(Rz, s); scratch_free(Ur, s);
+    scratch_free(kd, s); scratch_free(wmax, s);
+  };
   if (!WL || !Om || !A1 || !A2 || !Z || !C0 || !C1 || !S || !SV || !SV2 || !V1 || !V || !G || !Zt ||
       !W1 || !Lc || !one || !Qz || !Rz || !Ur || !kd || !wmax) {
+    release();
     set_error("round: scratch allocation failed");
     return QTT_ENOMEM;
   }
@@ -740,12 +750,12 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   TensorDesc pd = x->desc;
   qtt_tensor* Tp = nullptr;
   qtt_status st = tensor_alloc(pd, lq, s, &Tp);
-  if (st != QTT_OK) return st;
+  if (st != QTT_OK) { release(); return st; }
   T* Tpc = (T*)Tp->cores;
   // output
   qtt_tensor* y = nullptr;
   st = tensor_alloc(x->desc, ocap, s, &y);
-  if (st != QTT_OK) { qtt_free(Tp); return st; }
+  if (st != QTT_OK) { tensor_free_async(Tp, s); release(); return st; }
   k_set_ranks_one<<<1, 32, 0, s>>>(y->ranks, d);
 
   // --- 1. left sketches through the (cached) orthonormal sketch cores
@@ -907,12 +917,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     }
   }
   st = cuda_check(cudaGetLastError(), "round launch");
-  scratch_free(WL, s); if (om_owned) scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
-  scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
-  scratch_free(SV, s); scratch_free(SV2, s); scratch_free(V1, s); scratch_free(V, s); scratch_free(G, s);
-  scratch_free(Zt, s); scratch_free(W1, s); scratch_free(Lc, s); scratch_free(one, s);
-  scratch_free(Qz, s); scratch_free(Rz, s); scratch_free(Ur, s); scratch_free(kd, s);
-  scratch_free(wmax, s);
+  release();
   tensor_free_async(Tp, s);
   if (st != QTT_OK) { qtt_free(y); return st; }
   *out = y;

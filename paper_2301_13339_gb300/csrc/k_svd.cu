@@ -1127,6 +1127,8 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   T* U1 = (T*)scratch_alloc(sizeof(T) * LDP * LDP, s);
   T* U2 = (T*)scratch_alloc(sizeof(T) * LDP * LDP, s);
   if (!bufA || !bufB || !gp || !U1 || !U2) {
+    scratch_free(bufA, s); scratch_free(bufB, s); scratch_free(gp, s);
+    scratch_free(U1, s); scratch_free(U2, s);
     set_error("tt_svd: scratch allocation failed");
     return QTT_ENOMEM;
   }
