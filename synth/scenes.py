@@ -128,3 +128,58 @@ def deconv_scene_2d(rng, ny, nx, nscat=100):
     ix = np.clip(np.round(px * nx - 0.5).astype(np.int64), 0, nx - 1)
     np.add.at(scene, (iy, ix), amp)
     return scene
+
+
+# ---------------------------------------------------------------- Sec. 7 examples
+# The paper's analytic test signals (Examples 1-3), sampled at the cell
+# centres x_j = a + dx/2 + j dx, j < N = 2^(K-1) - 1, dx = (b - a)/N, and
+# zero-padded at the end to 2^K per axis.  The printed noise levels are read
+# as standard deviations.  Each returns (noisy, clean, N, B) with B = 2^K /
+# (Delta_x / dx), the sinc bandwidth in this library's units (the grid
+# spacing of the padded axis is 1 / 2^K).
+
+def _paper_grid(a, b, K):
+    N = 2 ** (K - 1) - 1
+    dx = (b - a) / N
+    return a + dx / 2 + dx * np.arange(N, dtype=np.float64), dx, N
+
+
+def paper_example_1d(example, K, rng):
+    """Example 1: f = exp(-(3x/10)^2) (0.4 sin 8 pi x - 0.7 cos 6 pi x) on
+    [-10, 10], noise 0.02, Delta_x = 4 dx.  Example 2: f = exp(-(3x)^2)
+    (0.9 sin(2 pi x / (5 dx)) + 1.4 cos(pi x / (3 dx))) on [-1, 1], noise 0.01,
+    Delta_x = 2 dx."""
+    if example == 1:
+        x, dx, N = _paper_grid(-10.0, 10.0, K)
+        f = np.exp(-(3 * x / 10) ** 2) * (0.4 * np.sin(8 * np.pi * x) - 0.7 * np.cos(6 * np.pi * x))
+        sd, lobe = 0.02, 4.0
+    elif example == 2:
+        x, dx, N = _paper_grid(-1.0, 1.0, K)
+        f = np.exp(-(3 * x) ** 2) * (0.9 * np.sin(2 * np.pi * x / (5 * dx))
+                                     + 1.4 * np.cos(np.pi * x / (3 * dx)))
+        sd, lobe = 0.01, 2.0
+    else:
+        raise ValueError("1D examples are 1 and 2")
+    n = 2 ** K
+    clean = np.zeros(n)
+    clean[:N] = f
+    noisy = clean.copy()
+    noisy[:N] += real_noise(rng, N, sd)
+    return noisy, clean, N, n / lobe
+
+
+def paper_example_2d(K, rng):
+    """Example 3: f = exp(-((2x)^2 + (2y)^2)) (sin 2 pi x - cos 7 pi y
+    + cos 4 pi x y - sin 3 pi x y) on [-1, 1]^2, noise 0.1, Delta_x = 2 dx;
+    rows are x, columns y."""
+    x, dx, N = _paper_grid(-1.0, 1.0, K)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    f = np.exp(-((2 * X) ** 2 + (2 * Y) ** 2)) * (np.sin(2 * np.pi * X) - np.cos(7 * np.pi * Y)
+                                                 + np.cos(4 * np.pi * X * Y)
+                                                 - np.sin(3 * np.pi * X * Y))
+    n = 2 ** K
+    clean = np.zeros((n, n))
+    clean[:N, :N] = f
+    noisy = clean.copy()
+    noisy[:N, :N] += rng.normal(0.0, 0.1, size=(N, N))
+    return noisy, clean, N, n / 2.0
