@@ -20,5 +20,7 @@ Modules
 ``pipeline`` -- decompose -> convolve in QTT -> round -> full (Alg. 2 with the
                 Toeplitz convolution step), and the deconvolution loss, its
                 dense adjoint and its core gradients.
+``rsvd``     -- the range finder and randomized SVD (App. A, Algs. 4-5) and the
+                max rank TT-RSVD (Sec. 5 modification (2)).
 """
-from . import qtt, conv, toeplitz, pipeline  # noqa: F401
+from . import qtt, conv, toeplitz, pipeline, rsvd  # noqa: F401

@@ -7,4 +7,5 @@ draws scenes and noise.
 from .scenes import (  # noqa: F401
     SEED, config_rng, line_1d_bumps, line_1d_scatterers, image_2d_scene,
     batch_lines, deconv_scene_2d, add_noise_snr, real_noise, paper_example_1d, paper_example_2d,
+    rsvd_omega_blocks,
 )

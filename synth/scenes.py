@@ -183,3 +183,22 @@ def paper_example_2d(K, rng):
     noisy = clean.copy()
     noisy[:N, :N] += rng.normal(0.0, 0.1, size=(N, N))
     return noisy, clean, N, n / 2.0
+
+
+# ---------------------------------------------------------------- TT-RSVD draws
+def rsvd_omega_blocks(d, rmax, p, rng, dtype=np.float64):
+    """Seeded N(0, 1) test matrices of the max rank TT-RSVD (Sec. 5 (2),
+    App. A Alg. 4) for a vector of length 2^d: one n_k x (rmax + p) block per
+    level k = 1..d-1 (n_k = 2^(d-k)), column-major, one after the other (the
+    layout qtt_decompose_rsvd reads).  Returns (flat, omega) with
+    omega(k, n, l) the FP64 block of level k."""
+    l = rmax + p
+    sizes = [2 ** (d - k) * l for k in range(1, d)]
+    flat = rng.standard_normal(int(sum(sizes))).astype(dtype)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+    def omega(k, n, ll):
+        assert ll == l and n == 2 ** (d - k)
+        return flat[offs[k - 1]:offs[k]].reshape((n, l), order="F").astype(np.float64)
+
+    return flat, omega
