@@ -97,6 +97,27 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
                          int interleave, const qtt_trunc* tr, void* stream,
                          qtt_tensor** out);
 
+/* Max rank TT-RSVD (Sec. 5 modification (2); App. A, Algs. 4-5) of a 1D
+ * vector: Alg. 1 with the SVD of every unfolding A^{k} (m_k x n_k) replaced by
+ * the randomized SVD with k = rmax and oversampling p -- Y = A Omega with a
+ * Gaussian n_k x (rmax + p) test matrix Omega, Q R = Y, B = Q^* A, the SVD of
+ * B (from its Gram by the relative-accuracy Jacobi solver), U = Q U~ -- each
+ * level keeping min(rmax, ...) triplets (no threshold: the cap alone); a
+ * level with min(m_k, n_k) <= rmax + p reverts to the max rank TT-SVD.
+ * x: device array of 2^log2_len elements (QTT_C64: complex64, QTT_F64:
+ * double), QTT order.  1 <= rmax <= 64, p >= 1, rmax + p <= 96.
+ * omega: NULL = the test matrices are drawn on the device (N(0, 1) by
+ * Philox4x32-10 with counter (index, level) and key seed, Box-Muller);
+ * otherwise a device array of the real type (float for QTT_C64, double for
+ * QTT_F64) holding, for k = 1 .. log2_len-1 in order, the n_k x (rmax + p)
+ * block of level k column-major, n_k = 2^(log2_len - k) (every level has a
+ * block; the levels that revert to the SVD ignore theirs).  Asynchronous;
+ * returns a library-owned handle in *out (free with qtt_free); errors:
+ * QTT_EINVAL (arguments), QTT_ENOMEM, QTT_ECUDA. */
+qtt_status qtt_decompose_rsvd(const void* x, qtt_dtype dt, int log2_len, int rmax, int p,
+                              const void* omega, unsigned long long seed, void* stream,
+                              qtt_tensor** out);
+
 /* qtt_conv_sinc -- Alg. 2 step 3 with the convolution done by the QTT
  * Toeplitz operator of the sinc kernel (Sec. 1 [KKT13]; kernel Eq. GAF with
  * Delta_x = 1/B on the midpoint grid of [0,1]^D, h = 2^-d per axis), then

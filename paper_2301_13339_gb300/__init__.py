@@ -22,7 +22,7 @@ __all__ = [
     "qtt_op_create",
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
-    "qtt_from_device_cores", "empty_cores", "core_tensors",
+    "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd",
 ]
 
 QTT_F64 = 0
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
-    "qtt_batch_free", "qtt_batch_conv_sinc",
+    "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd",
 ]
 
 
@@ -106,6 +106,7 @@ def load(path=None):
         "qtt_small_eigh": (i, [vp, i, i, vp, vp, vp]),
         "qtt_debug_set_eig_solver": (None, [i]),
         "qtt_debug_set_heev_cluster": (None, [d, i]),
+        "qtt_decompose_rsvd": (i, [vp, i, i, i, i, vp, ctypes.c_ulonglong, vp, pp]),
         "qtt_debug_set_refine_sweeps": (None, [i]),
         "qtt_last_error": (ctypes.c_char_p, []),
         "qtt_version": (ctypes.c_char_p, []),
@@ -262,6 +263,37 @@ def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None
     out = ctypes.c_void_p()
     _check(_lib.qtt_decompose(ctypes.c_void_p(x.data_ptr()), code, x.dim(), sh, int(interleave),
                               ctypes.byref(tr), _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_decompose_rsvd(x, rmax, p, omega=None, seed=20230131, stream=None):
+    """Max rank TT-RSVD (Sec. 5 modification (2), App. A Algs. 4-5) of a
+    contiguous 1D CUDA tensor of length 2^d.  omega: None (Gaussian test
+    matrices drawn on the device from seed) or a contiguous CUDA tensor of
+    the real dtype (float32 for complex64 x, float64 for float64 x) holding
+    the n_k x (rmax + p) block of every level k = 1..d-1 column-major, one
+    after the other (n_k = 2^(d-k))."""
+    load()
+    if not x.is_cuda or not x.is_contiguous() or x.dim() != 1:
+        raise ValueError("x must be a contiguous 1D CUDA tensor")
+    code = _dtype_code(x)
+    n = x.shape[0]
+    d = int(n).bit_length() - 1
+    if n < 4 or (1 << d) != n:
+        raise ValueError(f"length must be a power of two >= 4, got {n}")
+    optr = None
+    if omega is not None:
+        import torch
+        want = torch.float64 if code == QTT_F64 else torch.float32
+        need = sum((1 << (d - k)) * (rmax + p) for k in range(1, d))
+        if (not omega.is_cuda or not omega.is_contiguous() or omega.dtype != want
+                or omega.numel() < need):
+            raise ValueError(f"omega must be a contiguous CUDA {want} tensor of >= {need} elements")
+        optr = ctypes.c_void_p(omega.data_ptr())
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_decompose_rsvd(ctypes.c_void_p(x.data_ptr()), code, d, int(rmax), int(p), optr,
+                                   ctypes.c_ulonglong(int(seed)), _stream(stream),
+                                   ctypes.byref(out)))
     return QTTTensor(out)
 
 

@@ -274,6 +274,39 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
   return QTT_OK;
 }
 
+qtt_status qtt_decompose_rsvd(const void* x, qtt_dtype dt, int log2_len, int rmax, int p,
+                              const void* omega, unsigned long long seed, void* stream,
+                              qtt_tensor** out) {
+  g_err[0] = 0;
+  if (!x || !out) { set_error("qtt_decompose_rsvd: NULL argument"); return QTT_EINVAL; }
+  if (!valid_dtype(dt)) { set_error("qtt_decompose_rsvd: unsupported dtype %d", (int)dt); return QTT_EINVAL; }
+  if (log2_len < 2 || log2_len > 30) {
+    set_error("qtt_decompose_rsvd: log2 length %d outside [2, 30]", log2_len);
+    return QTT_EINVAL;
+  }
+  if (rmax < 1 || rmax > QTT_RANK_CAP || p < 1 || rmax + p > 96) {
+    set_error("qtt_decompose_rsvd: need 1 <= rmax <= %d, p >= 1, rmax + p <= 96", QTT_RANK_CAP);
+    return QTT_EINVAL;
+  }
+  TensorDesc desc;
+  desc.dt = dt;
+  desc.ndim = 1;
+  desc.interleave = 0;
+  desc.log2_shape[0] = log2_len;
+  desc.d = log2_len;
+  cudaStream_t s = (cudaStream_t)stream;
+  qtt_tensor* t = nullptr;
+  qtt_status st = tensor_alloc(desc, rank_caps(log2_len, rmax, QTT_RANK_CAP), s, &t);
+  if (st != QTT_OK) return st;
+  const qtt_trunc tr{0.0, rmax, 1, 0.0};
+  const RsvdOpt rs{p, omega, seed};
+  if (dt == QTT_F64) st = tt_svd<double>((const double*)x, log2_len, tr, t, s, &rs);
+  else st = tt_svd<float2>((const float2*)x, log2_len, tr, t, s, &rs);
+  if (st != QTT_OK) { tensor_free_async(t, s); return st; }
+  *out = t;
+  return QTT_OK;
+}
+
 qtt_status qtt_conv_sinc(const qtt_tensor* f, const double* B, int normalize, double eps_op,
                          const qtt_trunc* round_tr, int sketch, unsigned long long seed,
                          void* stream, qtt_tensor** out) {

@@ -63,6 +63,13 @@ __global__ void gauss_fill_kernel(R* out, long long n, unsigned long long seed, 
 
 #define GRID1(n) (unsigned)(((n) + 255) / 256), 256, 0, s
 
+void launch_gauss_fill(float* out, long long n, unsigned long long seed, uint32_t tag, cudaStream_t s) {
+  gauss_fill_kernel<float><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(out, n, seed, tag);
+}
+void launch_gauss_fill(double* out, long long n, unsigned long long seed, uint32_t tag, cudaStream_t s) {
+  gauss_fill_kernel<double><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(out, n, seed, tag);
+}
+
 // Orthonormal sketch cores.  Each Gaussian core Omega_k, read as the
 // (2 l_{k-1}) x l_k matrix Om[s' + l0 (j + 2 s)] (l_k <= 2 l_{k-1}), is
 // replaced by the Q factor of its Gram-Schmidt orthonormalisation (classical

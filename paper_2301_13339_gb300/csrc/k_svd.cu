@@ -1086,11 +1086,11 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
                       int write_norm2, int* status, cudaStream_t s, int relative,
-                      double delta) {
+                      double delta, int sweeps) {
   EigArgs<T> a{};
   a.relative = relative;
   a.delta = delta;
-  a.max_sweeps = (Sc<T>::cplx && relative) ? g_refine_sweeps : 0;
+  a.max_sweeps = (sweeps >= 0) ? sweeps : (Sc<T>::cplx && relative) ? g_refine_sweeps : 0;
   a.G = G; a.ldp = ldp; a.mg_ptr = mg_ptr; a.mg_mul = mg_mul; a.mg_const = mg_const;
   a.mode = mode; a.eps = eps; a.dmodes = dmodes; a.rmax = rmax; a.ncols_ptr = ncols_ptr;
   a.ncols_mul = ncols_mul; a.ncols_const = ncols_const; a.U1 = U1; a.Uout = Uout;
@@ -1105,19 +1105,118 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s, int relative, double delta) {
+                     int* status, cudaStream_t s, int relative, double delta, int sweeps) {
   double2* gfin = (double2*)scratch_alloc(sizeof(double2) * ldp * ldp, s);
   launch_reduce<T>(gram_part, nparts, ldp, gfin, s);
   launch_eig_dense<T>(gfin, ldp, mg_ptr, mg_mul, 0, mg_cap, mode, eps, dmodes, rmax, ncols_ptr,
                       ncols_mul, ncols_const, U1, Uout, core_out, rank_out, sig_out, norm2,
-                      write_norm2, status, s, relative, delta);
+                      write_norm2, status, s, relative, delta, sweeps);
   scratch_free(gfin, s);
 }
 
+// --------------------------------------------------------------------------
+// Max rank TT-RSVD (Sec. 5 modification (2), App. A Algs. 4-5) at one level:
+// Y = A Omega over the unfolding A (m x n, column-major) by column chunks,
+// per-CTA partials (128 x 128, ld 128) summed by gram_reduce_kernel; then
+// Q R = Y by Householder and U1 = [Q | 0] (m x m), which the refinement pass
+// of tt_svd turns into B = Q^* A, the SVD of B (its Gram and the Jacobi
+// solver) and U = Q U~.
+// --------------------------------------------------------------------------
+constexpr int SK_CC = 32;       // columns per chunk
+constexpr int SK_LMAX = 96;     // rmax + p
+
+__device__ __forceinline__ void macr(float2& acc, float2 a, float b) {
+  acc.x = fmaf(a.x, b, acc.x);
+  acc.y = fmaf(a.y, b, acc.y);
+}
+__device__ __forceinline__ void macr(double& acc, double a, double b) { acc = fma(a, b, acc); }
+
+template <typename T, typename R>
+static size_t sketch_smem_bytes() {
+  return sizeof(T) * 128 * SK_CC + sizeof(R) * SK_CC * SK_LMAX;
+}
+
+// thread (rb = tid & 31, cb = tid >> 5) owns rows 4 rb.., columns 12 cb.. of Y
+template <typename T, typename R>
+__global__ void __launch_bounds__(256)
+    sketch_kernel(const T* __restrict__ M, const int* m_ptr, int m_mul, long long n,
+                  const R* __restrict__ Om, int l, T* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sM = reinterpret_cast<T*>(smem_raw);                 // m x SK_CC, ld m
+  R* sO = reinterpret_cast<R*>(sM + 128 * SK_CC);          // SK_CC x l, ld SK_CC
+  const int tid = threadIdx.x;
+  const int m = m_mul * (*m_ptr);
+  const int rb = tid & 31, cb = tid >> 5;
+  T acc[4][12];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 12; ++y) acc[x][y] = szero<T>();
+  const long long nch = (n + SK_CC - 1) / SK_CC;
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long c0 = ch * SK_CC;
+    const int nc = (int)((n - c0) < SK_CC ? (n - c0) : SK_CC);
+    __syncthreads();
+    for (int e = tid; e < m * nc; e += 256) sM[e] = M[(size_t)c0 * m + e];
+    for (int e = tid; e < SK_CC * l; e += 256) {
+      const int cc = e % SK_CC, j = e / SK_CC;
+      sO[e] = (cc < nc) ? Om[(c0 + cc) + (size_t)n * j] : (R)0;
+    }
+    __syncthreads();
+    for (int cc = 0; cc < nc; ++cc) {
+      T a[4];
+      R b[12];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int i = 4 * rb + x;
+        a[x] = (i < m) ? sM[i + m * cc] : szero<T>();
+      }
+#pragma unroll
+      for (int y = 0; y < 12; ++y) {
+        const int j = 12 * cb + y;
+        b[y] = (j < l) ? sO[cc + SK_CC * j] : (R)0;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 12; ++y) macr(acc[x][y], a[x], b[y]);
+    }
+  }
+  T* pp = part + (size_t)blockIdx.x * 128 * 128;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 12; ++y) pp[(4 * rb + x) + 128 * (12 * cb + y)] = acc[x][y];
+}
+
+// U1 (m x m, ld m) = [Q | 0], Q R = Y (Y: m x l of the FP64 sums, ld 128)
 template <typename T>
-qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s) {
+__global__ void __launch_bounds__(QR_THREADS)
+    rsvd_qr_kernel(const double2* __restrict__ Yd, const int* m_ptr, int m_mul, int l,
+                   T* __restrict__ U1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T s_tau[128];
+  const int m = m_mul * (*m_ptr);
+  const int kk = min(m, l);
+  T* A = reinterpret_cast<T*>(smem_raw);     // m x l
+  T* E = A + (size_t)m * l;                  // m x kk
+  for (int e = threadIdx.x; e < m * l; e += QR_THREADS) from_d2(Yd[(e % m) + 128 * (e / m)], A[e]);
+  __syncthreads();
+  house_qr_factor(A, m, l, s_tau);
+  house_form_q(A, m, kk, kk, s_tau, E);
+  for (int e = threadIdx.x; e < m * m; e += QR_THREADS) {
+    const int j = e / m;
+    U1[e] = (j < kk) ? E[(e % m) + (size_t)m * j] : szero<T>();
+  }
+}
+
+template <typename T>
+qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s,
+                  const RsvdOpt* rs) {
+  using R = typename Sc<T>::R;
   const long long N = 1LL << d;
-  const bool refine = tr.refine || !Sc<T>::cplx;
+  const bool use_rs = rs && rs->p > 0;
+  const bool refine = tr.refine || !Sc<T>::cplx || use_rs;
   const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
   const int max_parts = 2 * 152;
   const int LDP = 128;
@@ -1177,18 +1276,66 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       continue;
     }
     if (refine) {
+      const int lrs = use_rs ? rmax_eff + rs->p : 0;
+      const bool rs_level = use_rs && std::min<long long>(mcap, n) > lrs;
+      if (rs_level) {
+        // pass 1 of the max rank TT-RSVD: U1 = [Q | 0] with Q R = A Omega
+        const R* Om = nullptr;
+        R* Omb = nullptr;
+        if (rs->omega) {
+          long long off = 0;
+          for (int kp = 1; kp < k; ++kp) off += (N >> kp) * lrs;
+          Om = (const R*)rs->omega + off;
+        } else {
+          Omb = (R*)scratch_alloc(sizeof(R) * (size_t)n * lrs, s);
+          if (!Omb) {
+            scratch_free(bufA, s); scratch_free(bufB, s); scratch_free(gp, s);
+            scratch_free(U1, s); scratch_free(U2, s);
+            set_error("tt_rsvd: scratch allocation failed");
+            return QTT_ENOMEM;
+          }
+          launch_gauss_fill(Omb, n * lrs, rs->seed, (uint32_t)k, s);
+          Om = Omb;
+        }
+        static bool sk_cfg = false;
+        if (!sk_cfg) {
+          cudaFuncSetAttribute(sketch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sketch_smem_bytes<T, R>());
+          cudaFuncSetAttribute(rsvd_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(T) * 2 * 128 * SK_LMAX));
+          sk_cfg = true;
+        }
+        const int nps = (int)std::min<long long>(max_parts, (n + SK_CC - 1) / SK_CC);
+        double2* Yd = (double2*)scratch_alloc(sizeof(double2) * 128 * 128, s);
+        {
+          QTT_PROF("rsvd_sketch", s);
+          sketch_kernel<T, R><<<nps, 256, sketch_smem_bytes<T, R>(), s>>>(M, rk + (k - 1), 2, n, Om,
+                                                                           lrs, gp);
+        }
+        launch_reduce<T>(gp, nps, 128, Yd, s);
+        {
+          QTT_PROF("rsvd_qr", s);
+          rsvd_qr_kernel<T><<<1, QR_THREADS, sizeof(T) * 2 * (size_t)mcap * lrs, s>>>(
+              Yd, rk + (k - 1), 2, lrs, U1);
+        }
+        scratch_free(Yd, s);
+        if (Omb) scratch_free(Omb, s);
+      } else {
       // pass 1: all eigenvectors of M M^H
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
                          nullptr, 0, n, nullptr, U1, nullptr, nullptr, nullptr, t->norm2,
                          k == skip + 1, t->status, s);
+      }
       // W1 = U1^H M, Gram of W1
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
                                    mcap, max_parts, s);
       // pass 2: decide the rank on the projected Gram, whose small
-      // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
+      // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r].
+      // After the TT-RSVD's range finder the projected Gram is dense (Q is
+      // any orthonormal basis of the range): run the Jacobi to convergence.
       launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
-                         t->status, s, 1, tr.delta);
+                         t->status, s, 1, tr.delta, rs_level ? 20 : -1);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
@@ -1210,22 +1357,26 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   return cuda_check(cudaGetLastError(), "tt_svd launch");
 }
 
-template qtt_status tt_svd<double>(const double*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t);
-template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t);
+template qtt_status tt_svd<double>(const double*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t,
+                                   const RsvdOpt*);
+template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_tensor*, cudaStream_t,
+                                   const RsvdOpt*);
 template void launch_eig_dense<double>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const double*,
                                        double*, double*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int, double);
+                                       cudaStream_t, int, double, int);
 template void launch_eig_dense<float2>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const float2*,
                                        float2*, float2*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int, double);
+                                       cudaStream_t, int, double, int);
 template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const double*, double*,
-                                      double*, int*, double*, double*, int, int*, cudaStream_t, int, double);
+                                      double*, int*, double*, double*, int, int*, cudaStream_t, int, double,
+                                      int);
 template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const float2*, float2*,
-                                      float2*, int*, double*, double*, int, int*, cudaStream_t, int, double);
+                                      float2*, int*, double*, double*, int, int*, cudaStream_t, int, double,
+                                      int);
 
 }  // namespace qtt
 

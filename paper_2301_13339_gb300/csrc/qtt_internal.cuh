@@ -207,8 +207,21 @@ qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap,
 // ------------------------------------------------------------- TT-SVD
 // Decompose the vector v (2^d elements, QTT order, device) into t (allocated
 // by the caller with caps from rank_caps).  eps/rmax/refine as qtt_trunc.
+// Max rank TT-RSVD (Sec. 5 modification (2)): p > 0 replaces the SVD of
+// every unfolding with min(m_k, n_k) > rmax + p by the randomized SVD with
+// oversampling p; omega = the Gaussian blocks (see qtt_decompose_rsvd) or
+// NULL to draw them on the device from seed.
+struct RsvdOpt {
+  int p;
+  const void* omega;
+  unsigned long long seed;
+};
 template <typename T>
-qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s);
+qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s,
+                  const RsvdOpt* rs = nullptr);
+// N(0, 1) draws, out[e] for e < n: Philox4x32-10 counter (e, tag), key seed, Box-Muller
+void launch_gauss_fill(float* out, long long n, unsigned long long seed, uint32_t tag, cudaStream_t s);
+void launch_gauss_fill(double* out, long long n, unsigned long long seed, uint32_t tag, cudaStream_t s);
 
 // ------------------------------------------------------------- small SVD
 // One-CTA SVD helper used by the rounding sweeps: see k_svd.cu.
@@ -217,7 +230,8 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s, int relative = 0, double delta = 0.0);
+                     int* status, cudaStream_t s, int relative = 0, double delta = 0.0,
+                     int sweeps = -1);
 
 // ------------------------------------------------------------- eigen
 enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
@@ -267,7 +281,7 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
                       int write_norm2, int* status, cudaStream_t s, int relative = 0,
-                      double delta = 0.0);
+                      double delta = 0.0, int sweeps = -1);
 
 // ------------------------------------------------------------- full
 template <typename T>
