@@ -54,6 +54,10 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "line_2p20_c64": dict(d=20, B=1024.0, rmax=64, eps=0.0, eps_op=1e-7, eps_round=1e-7,
                           nscat=50, nbumps=3, snr_db=20.0, tol=1e-5),
+    # the same line with the max rank TT-RSVD (Sec. 5 modification (2)), p = 8,
+    # on seeded Gaussian test matrices shared with the oracle
+    "line_2p20_c64_rsvd": dict(d=20, B=1024.0, rmax=64, eps=0.0, eps_op=1e-7, eps_round=1e-7,
+                               nscat=50, nbumps=3, snr_db=20.0, tol=1e-5, rsvd_p=8),
     "batch_256_c64": dict(kind="batch", nlines=256, dmin=14, dmax=18, snr_db=15.0, bmin=128.0,
                           bmax=1024.0, eps=0.0, eps_op=1e-7, eps_round=1e-7, tol=1e-5),
     "deconv_2048sq_c64": dict(kind="deconv", dy=11, dx=11, B=256.0, nscat=100, snr_db=20.0,
@@ -91,11 +95,26 @@ def make_input(wl, rank=0):
     return x.astype(np.complex64), clean
 
 
+def rsvd_omega(wl):
+    """The seeded test matrices of the TT-RSVD workload (float32, and the
+    oracle's FP64 view of the same values)."""
+    import synth
+    return synth.rsvd_omega_blocks(wl["d"], wl["rmax"], wl["rsvd_p"], synth.config_rng(7),
+                                   np.float32)
+
+
 def run_oracle(x, wl):
     from oracle import pipeline as P
     t0 = time.perf_counter()
-    out = P.conv_sinc_qtt(x.astype(np.complex128), wl["B"], wl["eps"], wl["rmax"],
-                          eps_op=wl["eps_op"], eps_round=wl["eps_round"])
+    if wl.get("rsvd_p"):
+        from oracle import rsvd as RS
+        _, omega = rsvd_omega(wl)
+        cores, _, _ = RS.tt_rsvd(x.astype(np.complex128), wl["d"], wl["rmax"], wl["rsvd_p"], omega)
+        ops = P.sinc_operators(x.shape, wl["B"], True, wl["eps_op"])
+        out = P.to_array(P.convolve_qtt(cores, ops, wl["eps_round"]), x.shape)
+    else:
+        out = P.conv_sinc_qtt(x.astype(np.complex128), wl["B"], wl["eps"], wl["rmax"],
+                              eps_op=wl["eps_op"], eps_round=wl["eps_round"])
     return out, time.perf_counter() - t0
 
 
@@ -179,9 +198,15 @@ def gpu_arm(args, wl):
     out = torch.empty(N, dtype=torch.complex64, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     refine = args.refine
+    om_dev = None
+    if wl.get("rsvd_p"):
+        om_dev = torch.from_numpy(rsvd_omega(wl)[0]).to(dev)
 
     def step(s, xin=xd, dst=out):
-        f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s)
+        if om_dev is not None:
+            f = q.qtt_decompose_rsvd(xin, wl["rmax"], wl["rsvd_p"], omega=om_dev, stream=s)
+        else:
+            f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s)
         y = q.qtt_conv_sinc(f, wl["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"],
                             refine=True, sketch=0, stream=s)
         q.qtt_to_full(y, out=dst, stream=s)
@@ -643,6 +668,8 @@ def main():
               "B": wl["B"], "rmax": wl["rmax"], "eps": wl["eps"], "eps_op": wl["eps_op"],
               "eps_round": wl["eps_round"], "snr_db": wl["snr_db"],
               "l2": "flushed (512 MiB write) before every timed step, outside the timed region"}
+    if wl.get("rsvd_p"):
+        config["decomposition"] = f"max rank TT-RSVD, p = {wl['rsvd_p']}"
 
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

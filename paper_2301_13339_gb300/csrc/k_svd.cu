@@ -1320,6 +1320,20 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
         }
         scratch_free(Yd, s);
         if (Omb) scratch_free(Omb, s);
+        // B = Q^* A and its Gram; U1 = Q U~ with U~ the eigenvectors of
+        // B B^* (absolute accuracy suffices: the refinement pass below
+        // projects again on U1 and gets the small eigenvalues to relative
+        // accuracy, as for the TT-SVD levels)
+        const int npb = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, nullptr,
+                                            0, gp, mcap, max_parts, s);
+        launch_gram_eig<T>(gp, npb, mcap, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
+                           nullptr, 0, n, nullptr, U2, nullptr, nullptr, nullptr, t->norm2, 0,
+                           t->status, s);
+        {
+          QTT_PROF("core_product", s);
+          core_product_kernel<T><<<mcap, 128, 0, s>>>(U1, U2, rk + (k - 1), 2, 0, nullptr, bufA);
+        }
+        cudaMemcpyAsync(U1, bufA, sizeof(T) * (size_t)mcap * mcap, cudaMemcpyDeviceToDevice, s);
       } else {
       // pass 1: all eigenvectors of M M^H
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
@@ -1330,12 +1344,10 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
                                    mcap, max_parts, s);
       // pass 2: decide the rank on the projected Gram, whose small
-      // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r].
-      // After the TT-RSVD's range finder the projected Gram is dense (Q is
-      // any orthonormal basis of the range): run the Jacobi to convergence.
+      // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
       launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
                          rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
-                         t->status, s, 1, tr.delta, rs_level ? 20 : -1);
+                         t->status, s, 1, tr.delta);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
