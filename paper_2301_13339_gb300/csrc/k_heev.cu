@@ -1,4 +1,4 @@
-// One-CTA Hermitian eigensolver for the FP32 path (complex float, n <= 128).
+// Hermitian eigensolver for the FP32 path (complex float, n <= 128).
 //
 // The Gram matrices of the TT-SVD steps (Alg. 1) and of the rounding sweep
 // are factored as G = U L U^H by
@@ -9,10 +9,14 @@
 //   3. eigenvectors of T for the wanted eigenvalues by the twisted
 //      factorisation T - lambda I = N_k D_k N_k^T (one thread per vector);
 //   4. modified Gram-Schmidt, twice, inside clusters of close eigenvalues;
-//   5. U = Q Z, each column transformed by its own group of 8 threads (no
-//      block-wide barrier per reflector).
-// About 10-20x fewer dependent steps than cyclic Jacobi (n-1 steps per sweep,
-// ~8 sweeps).  Same EigArgs contract as the Jacobi kernel in k_svd.cu.
+//   5. Newton-Schulz steps and U = Q Z.
+// Steps 1-4 run in one CTA (heev_tri_kernel).  For n <= 32 the same kernel
+// does step 5 too (8 threads per column of U); above, it hands Z and the
+// reflectors to heev_back_kernel, a cluster of 8 CTAs that splits the
+// columns (distributed shared memory for the Newton-Schulz exchange, 16
+// threads per column for the back-transformation).  About 10-20x fewer
+// dependent steps than cyclic Jacobi (n-1 steps per sweep, ~8 sweeps).  Same
+// EigArgs contract as the Jacobi kernels in k_svd.cu.
 #include "qtt_internal.cuh"
 #include <cooperative_groups.h>
 #include <algorithm>
