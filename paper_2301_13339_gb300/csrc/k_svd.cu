@@ -3,15 +3,20 @@
 // Each step of Alg. 1 factors the unfolding M_k (m_k x n_k, m_k = 2 r_{k-1},
 // n_k = 2^{d-k}, Lemma 5.1) and carries Sigma V^* to the next step.  The
 // factorisation is done through the Gram matrix M M^H (m_k <= 128):
-//   pass 1  G = M M^H, Jacobi eigen-decomposition G = U1 L U1^H;
-//   pass 2  (refinement) W1 = U1^H M, G2 = W1 W1^H, Jacobi again: G2 is
+//   pass 1  G = M M^H, eigen-decomposition G = U1 L U1^H (FP32: the
+//           tridiagonal solver of k_heev.cu; FP64: Jacobi);
+//   pass 2  (refinement) W1 = U1^H M, G2 = W1 W1^H, Jacobi: G2 is
 //           diagonally dominant up to scaling, so Jacobi resolves its small
 //           eigenvalues to relative accuracy (this is what makes the
-//           Gram route as accurate as an SVD of M);
+//           Gram route as accurate as an SVD of M); the FP32 Jacobi runs 2
+//           sweeps in three launches (jacobi_dm_kernel and its helpers);
 //   rank    r = min(rank_tau, R_max, m, n) from the eigenvalues sigma_i^2,
 //           tau = eps/sqrt(d-1) ||A||_F (Sec. 4 eps-rank);
 //   next    W = U_r^H M = Sigma_r V_r^*, whose reshape to (2 r) x (n/2) is the
 //           next unfolding; its Gram is accumulated by the same kernel.
+// Levels that keep every singular value are identities or one Householder QR
+// (qr_level_kernel); with the max rank TT-RSVD, pass 1 of the larger levels
+// is the randomized range finder (sketch_kernel, rsvd_qr_kernel).
 // Ranks live on the device: every kernel reads the ranks it needs, grids are
 // sized for the host-side capacities.
 #include "qtt_internal.cuh"
