@@ -22,5 +22,7 @@ Modules
                 dense adjoint and its core gradients.
 ``rsvd``     -- the range finder and randomized SVD (App. A, Algs. 4-5) and the
                 max rank TT-RSVD (Sec. 5 modification (2)).
+``qfft``     -- QTT-FFT / QTT-iFFT (Sec. 4, truncated as in Sec. 5), the
+                Hadamard product and the QTT convolution of Alg. 2 Step 3.
 """
-from . import qtt, conv, toeplitz, pipeline, rsvd  # noqa: F401
+from . import qtt, conv, toeplitz, pipeline, rsvd, qfft  # noqa: F401

@@ -1,0 +1,169 @@
+"""QTT-FFT, QTT-iFFT and the QTT convolution of Alg. 2 (test infrastructure:
+the oracle; only tests/, __graft_entry__.smoke() and bench.py's CPU legs
+use it).  complex128.
+
+Sec. 4 names the QTT-FFT approximation of [DKS12] without giving its steps;
+here it is the radix-2 decimation-in-frequency FFT written as one QTT
+operator per bit, each followed by TT-rounding (Sec. 5 puts the truncated
+SVD -- a rank cap R^_max, or a tolerance -- inside the QTT-FFT):
+
+* the stage on bit p of an axis whose K bits sit on modes lo..lo+K-1
+  (mode lo = the least significant bit) maps the pair (x_n, x_{n+2^(p-1)})
+  of each size-2^p sub-transform to (x_n + x_{n+2^(p-1)},
+  (x_n - x_{n+2^(p-1)}) w^n) with w = exp(-2 pi i / 2^p) (exp(+...) for
+  the inverse) and n the lower p-1 bits: the butterfly [[1, 1], [1, -1]] on
+  that mode and a diagonal twiddle w^(i_k 2^(k-1)) on each lower mode k,
+  switched on by the new bit -- a TT operator of rank 2 (the switch travels
+  down the bonds), the identity on every other mode;
+* after the K stages of an axis its mode lo+j holds output bit K-j (bit
+  reversal); reversing the whole chain of cores restores the bit order of
+  every axis and reverses the order of the axes' blocks, so a 2D transform
+  in the "x bits, then y bits" chain comes out in the "y bits, then x bits"
+  chain; the inverse transform of a product (same chain for both factors)
+  reverses it back.
+
+The Sec. 2 DFT convention: w_N = exp(-2 pi i / N), the inverse carries
+1/N^D (numpy's fft/ifft).
+
+``hadamard`` is the entrywise product (the core-wise Kronecker product; ranks
+multiply), ``qtt_conv`` is Step 3 of Alg. 2, I = QiFFT(QFFT(F) (.) QFFT(G)),
+the circular convolution of the two zero-padded arrays (Sec. 2), and
+``padded_kernel`` / ``linear_part`` are the Sec. 2 padding of the kernel
+samples and the extraction of the linear convolution from the circular one.
+"""
+import numpy as np
+
+from . import qtt as Q
+from . import toeplitz as T
+
+
+def stage_operator(d, lo, K, p, inverse=False):
+    """Operator cores O_k[left, out, in, right] (k = 1..d) of the DIF stage
+    on bit p (1..K) of the axis held by modes lo..lo+K-1."""
+    sgn = 1.0 if inverse else -1.0
+    H = np.array([[1.0, 1.0], [1.0, -1.0]], dtype=np.complex128)
+    ops = []
+    for k in range(1, d + 1):
+        kk = k - lo + 1                         # bit of the axis held by mode k
+        if kk < 1 or kk > p:
+            O = np.zeros((1, 2, 2, 1), dtype=np.complex128)
+            O[0, 0, 0, 0] = O[0, 1, 1, 0] = 1.0
+        elif kk == p:
+            if p == 1:
+                O = H.reshape((1, 2, 2, 1)).copy()
+            else:
+                # the new bit j picks the branch the lower bits see
+                O = np.zeros((2, 2, 2, 1), dtype=np.complex128)
+                for j in range(2):
+                    O[j, j, :, 0] = H[j, :]
+        else:
+            left = 1 if kk == 1 else 2
+            O = np.zeros((left, 2, 2, 2), dtype=np.complex128)
+            for c in range(2):
+                for i in range(2):
+                    t = np.exp(sgn * 2j * np.pi * i * 2.0 ** (kk - 1) / 2.0 ** p) if c else 1.0
+                    O[c if left == 2 else 0, i, i, c] = t
+        ops.append(O)
+    return ops
+
+
+def reverse_chain(cores):
+    """Mode k <- mode d+1-k (the two bonds of every core swap)."""
+    return [np.transpose(c, (2, 1, 0)).copy() for c in reversed(cores)]
+
+
+def qtt_fft(cores, sizes=None, rmax=None, eps=0.0, inverse=False):
+    """D-dimensional DFT (inverse=True: the IDFT with its 1/N^D) of a QTT
+    tensor whose chain holds the axes' bits block after block, sizes[a] bits
+    for block a (default: one axis of all modes).  With a cap rmax or a
+    tolerance eps the input and the result of every stage are TT-rounded
+    (without either the transform is exact up to rounding errors).  The
+    result's chain holds the blocks in reverse order (each in natural bit
+    order)."""
+    d = len(cores)
+    sizes = [d] if sizes is None else list(sizes)
+    assert sum(sizes) == d
+    trunc = rmax is not None or eps > 0.0
+    Y = [np.asarray(c, dtype=np.complex128) for c in cores]
+    if trunc:
+        Y = Q.tt_round(Y, eps, rmax)
+    lo = 1
+    for K in sizes:
+        for p in range(K, 0, -1):
+            Y = T.matvec(stage_operator(d, lo, K, p, inverse), Y)
+            if trunc:
+                Y = Q.tt_round(Y, eps, rmax)
+        lo += K
+    Y = reverse_chain(Y)
+    if inverse:
+        Y[0] = Y[0] / 2.0 ** d
+    return Y
+
+
+def hadamard(A, B):
+    """Entrywise product of two QTT tensors on the same chain:
+    Z_k[(a, a'), i, (b, b')] = A_k[a, i, b] B_k[a', i, b']."""
+    out = []
+    for a, b in zip(A, B):
+        z = np.einsum('aib,cid->acibd', a, b)
+        out.append(z.reshape((a.shape[0] * b.shape[0], 2, a.shape[2] * b.shape[2])))
+    return out
+
+
+def qtt_conv(F, G, sizes=None, rhat=None, eps_hat=0.0):
+    """Alg. 2, Step 3: QiFFT(QFFT(F) (.) QFFT(G)) with the cap rhat (or the
+    tolerance eps_hat) in all three transforms; the result is on the input
+    chain."""
+    d = len(F)
+    sizes = [d] if sizes is None else list(sizes)
+    Fh = qtt_fft(F, sizes, rhat, eps_hat)
+    Gh = qtt_fft(G, sizes, rhat, eps_hat)
+    return qtt_fft(hadamard(Fh, Gh), sizes[::-1], rhat, eps_hat, inverse=True)
+
+
+def padded_kernel(taps, N, n):
+    """Sec. 2 padding of the kernel: g^0_j = the kernel at grid point j of the
+    N-point grid (offset j - (N-1)/2 from its centre, N odd), zero for
+    N <= j < n.  taps[m + len(taps)//2] is the kernel (times the cell size)
+    at offset m."""
+    assert N % 2 == 1 and n >= 2 * N - 1
+    c = (len(taps) - 1) // 2
+    g = np.zeros(n, dtype=np.result_type(taps, np.float64))
+    h = (N - 1) // 2
+    for j in range(N):
+        g[j] = taps[c + j - h]
+    return g
+
+
+def linear_part(Ic, N):
+    """Sec. 2: the linear convolution I_j = I^c_{j + (N-1)/2}, j < N, per
+    axis of a circular convolution of padded arrays."""
+    h = (N - 1) // 2
+    Ic = np.asarray(Ic)
+    sl = tuple(slice(h, h + N) for _ in range(Ic.ndim))
+    return Ic[sl]
+
+
+def conv_qtt_fft_1d(f0, g0, rmax, rhat, eps_hat=0.0):
+    """Alg. 2 on padded vectors f0, g0 of 2^K entries: Steps 1-2 by the max
+    rank TT-SVD (Sec. 5 (1), cap rmax), Step 3 with the cap rhat, Step 4 by
+    Full (Alg. 3); returns the circular convolution I^c."""
+    n = len(f0)
+    d = n.bit_length() - 1
+    F, _, _ = Q.tt_svd(np.asarray(f0, dtype=np.complex128), d, 0.0, rmax)
+    G, _, _ = Q.tt_svd(np.asarray(g0, dtype=np.complex128), d, 0.0, rmax)
+    return Q.full(qtt_conv(F, G, [d], rhat, eps_hat))
+
+
+def conv_qtt_fft_2d(F0, G0, rmax, rhat, eps_hat=0.0):
+    """Alg. 2 on padded 2^K x 2^K images in the plain chain (the column
+    index' bits, then the row index' bits); returns the 2D circular
+    convolution."""
+    ny, nx = F0.shape
+    dx, dy = nx.bit_length() - 1, ny.bit_length() - 1
+    f = Q.image_to_qtt_vector(np.asarray(F0, dtype=np.complex128), interleave=False)
+    g = Q.image_to_qtt_vector(np.asarray(G0, dtype=np.complex128), interleave=False)
+    F, _, _ = Q.tt_svd(f, dx + dy, 0.0, rmax)
+    G, _, _ = Q.tt_svd(g, dx + dy, 0.0, rmax)
+    v = Q.full(qtt_conv(F, G, [dx, dy], rhat, eps_hat))
+    return Q.qtt_vector_to_image(v, ny, nx, interleave=False)

@@ -1,0 +1,205 @@
+"""Pins of the QTT-FFT / QTT-iFFT oracle and of the QTT convolution of
+Alg. 2 (Sec. 4 QTT-FFT, Sec. 5 truncated transforms, Sec. 2 padding).
+
+* untruncated, the QTT-FFT is the DFT of Sec. 2 (numpy's fft / fft2 on the
+  full array, forward and inverse), for 1D chains and for the 2D chain of
+  two axis blocks;
+* closed forms: the DFT of the rank-1 exponential exp(2 pi i k0 j / n) is
+  n delta_{k0}, reached with the cap R^_max = 1 in every stage;
+* the stage operators have TT ranks <= 2 and are sqrt(2) times unitary (a
+  wrong twiddle modulus or butterfly fails here);
+* Eq. tolerance: with the tolerance eps in each of the d + 1 roundings the
+  result is within (d + 1) eps ||DFT(v)|| of the DFT;
+* the Hadamard product is the entrywise product, with multiplied ranks;
+* Alg. 2 at full ranks is the brute-force circular convolution (two loops),
+  and the Sec. 2 extraction I_j = I^c_{j+(N-1)/2} is the linear convolution
+  with the kernel samples of the N-point grid;
+* Table 6.1 (tests/golden/table_6_1_errors.txt): with R_max = 10 and
+  R^_max = 15 (the values Sec. 7 states for all three examples) the QTT-FFT
+  route gives E2(I_QTT0) within 10 % of the printed value for Examples 1
+  and 2 and within 15 % for Example 3, and E2(I_xi) within 5 %.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import conv as C, qfft as QF, qtt as Q, toeplitz as T
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_qtt(rng, d, r):
+    ranks = [1] + [min(r, 2 ** k, 2 ** (d - k)) for k in range(1, d)] + [1]
+    return [rng.standard_normal((ranks[k], 2, ranks[k + 1]))
+            + 1j * rng.standard_normal((ranks[k], 2, ranks[k + 1])) for k in range(d)]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 6, 9])
+def test_fft_is_the_dft(d):
+    rng = np.random.default_rng(40 + d)
+    cores = _random_qtt(rng, d, 3)
+    x = Q.full(cores)
+    y = Q.full(QF.qtt_fft(cores))
+    ref = np.fft.fft(x)
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+    z = Q.full(QF.qtt_fft(cores, inverse=True))
+    ref = np.fft.ifft(x)
+    assert np.abs(z - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dx,dy", [(1, 1), (2, 3), (4, 4), (5, 2)])
+def test_fft_2d_is_fft2(dx, dy):
+    rng = np.random.default_rng(7 * dx + dy)
+    img = rng.standard_normal((2 ** dy, 2 ** dx)) + 1j * rng.standard_normal((2 ** dy, 2 ** dx))
+    v = Q.image_to_qtt_vector(img, interleave=False)
+    cores, _, _ = Q.tt_svd(v, dx + dy, 0.0)
+    Y = QF.qtt_fft(cores, [dx, dy])
+    # the output chain holds the row index' bits first: the transposed image
+    got = Q.qtt_vector_to_image(Q.full(Y), 2 ** dx, 2 ** dy, interleave=False).T
+    ref = np.fft.fft2(img)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    back = Q.full(QF.qtt_fft(Y, [dy, dx], inverse=True))
+    assert np.abs(back - v).max() <= 1e-13 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("k0", [0, 1, 37, 511, 1000])
+def test_exponential_to_delta_at_rank_one(k0):
+    d = 10
+    n = 2 ** d
+    # the rank-1 QTT of exp(2 pi i k0 j / n): core k holds exp(2 pi i k0 i_k 2^(k-1) / n)
+    cores = [np.array([1.0, np.exp(2j * np.pi * k0 * 2.0 ** k / n)]).reshape((1, 2, 1))
+             for k in range(d)]
+    assert np.allclose(Q.full(cores), np.exp(2j * np.pi * k0 * np.arange(n) / n))
+    Y = QF.qtt_fft(cores, rmax=1)
+    assert Q.ranks_of(Y) == [1] * (d + 1)
+    ref = np.zeros(n, dtype=complex)
+    ref[k0] = n
+    assert np.abs(Q.full(Y) - ref).max() <= 1e-11 * n
+
+
+@pytest.mark.parametrize("d,lo,K", [(6, 1, 6), (7, 3, 4), (5, 1, 2)])
+def test_stage_operators(d, lo, K):
+    for inverse in (False, True):
+        for p in range(1, K + 1):
+            ops = QF.stage_operator(d, lo, K, p, inverse)
+            assert max(max(o.shape[0], o.shape[3]) for o in ops) <= 2
+            M = T.operator_dense(ops)
+            assert np.allclose(M.conj().T @ M, 2.0 * np.eye(2 ** d), atol=1e-12)
+
+
+def test_tolerance_bound():
+    rng = np.random.default_rng(3)
+    d = 12
+    for eps in (1e-1, 1e-2, 1e-3):
+        # a smooth signal plus noise: the roundings do truncate
+        t = np.arange(2 ** d) / 2 ** d
+        x = np.exp(-30 * (t - 0.4) ** 2) * np.cos(90 * t) + 0.05 * rng.standard_normal(2 ** d)
+        cores, _, _ = Q.tt_svd(x.astype(complex), d, 0.0, 24)
+        xq = Q.full(cores)
+        ref = np.fft.fft(xq)
+        y = Q.full(QF.qtt_fft(cores, eps=eps))
+        err = np.linalg.norm(y - ref)
+        assert err <= (d + 1) * eps * np.linalg.norm(ref)
+
+
+def test_hadamard():
+    rng = np.random.default_rng(9)
+    d = 8
+    A = _random_qtt(rng, d, 3)
+    B = _random_qtt(rng, d, 2)
+    Z = QF.hadamard(A, B)
+    assert np.allclose(Q.full(Z), Q.full(A) * Q.full(B), rtol=0, atol=1e-12 * np.abs(Q.full(Z)).max())
+    ra, rb = Q.ranks_of(A), Q.ranks_of(B)
+    assert Q.ranks_of(Z) == [a * b for a, b in zip(ra, rb)]
+
+
+def _circ_loops(f, g):
+    n = len(f)
+    out = np.zeros(n, dtype=complex)
+    for j in range(n):
+        for i in range(n):
+            out[j] += f[i] * g[(j - i) % n]
+    return out
+
+
+@pytest.mark.parametrize("K", [3, 4, 5])
+def test_alg2_full_rank_is_circular_convolution(K):
+    rng = np.random.default_rng(K)
+    n = 2 ** K
+    N = 2 ** (K - 1) - 1
+    f0 = np.zeros(n)
+    f0[:N] = rng.standard_normal(N)
+    taps = C.sinc_taps(n, n / 4.0)
+    g0 = QF.padded_kernel(taps, N, n)
+    ic = QF.conv_qtt_fft_1d(f0, g0, rmax=2 ** K, rhat=None)
+    assert np.allclose(ic, _circ_loops(f0, g0), rtol=0, atol=1e-13)
+    # Sec. 2: the linear part is Eq. dconv with the kernel on the N-grid offsets
+    h, c = (N - 1) // 2, (len(taps) - 1) // 2
+    tw = np.where(np.abs(np.arange(len(taps)) - c) <= h, taps, 0.0)[c - (N - 1):c + N]
+    lin = C.conv_direct_loops(f0[:N], tw)
+    assert np.allclose(QF.linear_part(ic, N).real, lin, rtol=0, atol=1e-13)
+
+
+def test_alg2_2d_full_rank_is_circular_convolution():
+    rng = np.random.default_rng(11)
+    K = 3
+    n = 2 ** K
+    F0 = rng.standard_normal((n, n))
+    G0 = rng.standard_normal((n, n))
+    got = QF.conv_qtt_fft_2d(F0, G0, rmax=n * n, rhat=None)
+    ref = np.zeros((n, n))
+    for y in range(n):
+        for x in range(n):
+            for yy in range(n):
+                for xx in range(n):
+                    ref[y, x] += F0[yy, xx] * G0[(y - yy) % n, (x - xx) % n]
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def _table(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _grid_taps(taps, N):
+    """Kernel samples at the offsets of the N-point grid (|m| <= (N-1)/2),
+    laid out as Toeplitz taps for a length-N convolution."""
+    h, c = (N - 1) // 2, (len(taps) - 1) // 2
+    t = np.where(np.abs(np.arange(len(taps)) - c) <= h, taps, 0.0)
+    return t[c - (N - 1):c + N]
+
+
+@pytest.mark.parametrize("example", [1, 2, 3])
+def test_table_6_1_through_qtt_fft(example):
+    row = [r for r in _table("table_6_1_errors.txt") if int(r[0]) == example][0]
+    K, e_xi_p, e_q_p = int(row[1]), float(row[2]), float(row[3])
+    n = 2 ** K
+    if example < 3:
+        noisy, clean, N, B = synth.paper_example_1d(example, K, synth.config_rng(5, sub=example))
+        taps = C.sinc_taps(n, B)
+        tw = _grid_taps(taps, N)
+        itrue = C.conv_fft(clean[:N], tw)
+        ixi = C.conv_fft(noisy[:N], tw)
+        ic = QF.conv_qtt_fft_1d(noisy, QF.padded_kernel(taps, N, n), 10, 15)
+        tol = 0.10
+    else:
+        noisy, clean, N, B = synth.paper_example_2d(K, synth.config_rng(5, sub=example))
+        taps = C.sinc_taps(n, B)
+        tw = _grid_taps(taps, N)
+        itrue = C.conv2d_fft(clean[:N, :N], tw, tw)
+        ixi = C.conv2d_fft(noisy[:N, :N], tw, tw)
+        g = QF.padded_kernel(taps, N, n)
+        ic = QF.conv_qtt_fft_2d(noisy, np.outer(g, g), 10, 15)
+        tol = 0.15
+    iq = QF.linear_part(ic, N)
+    e_xi = np.linalg.norm(ixi - itrue) / np.linalg.norm(itrue)
+    e_q = np.linalg.norm(iq - itrue) / np.linalg.norm(itrue)
+    assert abs(e_xi - e_xi_p) <= 0.05 * e_xi_p, e_xi
+    assert abs(e_q - e_q_p) <= tol * e_q_p, e_q
