@@ -29,11 +29,13 @@ The Sec. 2 DFT convention: w_N = exp(-2 pi i / N), the inverse carries
 multiply), ``qtt_conv`` is Step 3 of Alg. 2, I = QiFFT(QFFT(F) (.) QFFT(G)),
 the circular convolution of the two zero-padded arrays (Sec. 2), and
 ``padded_kernel`` / ``linear_part`` are the Sec. 2 padding of the kernel
-samples and the extraction of the linear convolution from the circular one.
+samples and the extraction of the linear convolution from the circular one,
+``conv_qtt_fft`` the whole of Alg. 2 with any of the three modified TT-SVDs.
 """
 import numpy as np
 
 from . import qtt as Q
+from . import rsvd as RS
 from . import toeplitz as T
 
 
@@ -72,27 +74,28 @@ def reverse_chain(cores):
     return [np.transpose(c, (2, 1, 0)).copy() for c in reversed(cores)]
 
 
-def qtt_fft(cores, sizes=None, rmax=None, eps=0.0, inverse=False):
+def qtt_fft(cores, sizes=None, rmax=None, eps=0.0, inverse=False, delta=None):
     """D-dimensional DFT (inverse=True: the IDFT with its 1/N^D) of a QTT
     tensor whose chain holds the axes' bits block after block, sizes[a] bits
-    for block a (default: one axis of all modes).  With a cap rmax or a
-    tolerance eps the input and the result of every stage are TT-rounded
-    (without either the transform is exact up to rounding errors).  The
+    for block a (default: one axis of all modes).  With a cap rmax, a
+    tolerance eps or an SV drop-off threshold delta (Sec. 5 (1)-(3)) the
+    input and the result of every stage are TT-rounded (without any the
+    transform is exact up to rounding errors).  The
     result's chain holds the blocks in reverse order (each in natural bit
     order)."""
     d = len(cores)
     sizes = [d] if sizes is None else list(sizes)
     assert sum(sizes) == d
-    trunc = rmax is not None or eps > 0.0
+    trunc = rmax is not None or eps > 0.0 or bool(delta)
     Y = [np.asarray(c, dtype=np.complex128) for c in cores]
     if trunc:
-        Y = Q.tt_round(Y, eps, rmax)
+        Y = Q.tt_round(Y, eps, rmax, delta)
     lo = 1
     for K in sizes:
         for p in range(K, 0, -1):
             Y = T.matvec(stage_operator(d, lo, K, p, inverse), Y)
             if trunc:
-                Y = Q.tt_round(Y, eps, rmax)
+                Y = Q.tt_round(Y, eps, rmax, delta)
         lo += K
     Y = reverse_chain(Y)
     if inverse:
@@ -110,15 +113,15 @@ def hadamard(A, B):
     return out
 
 
-def qtt_conv(F, G, sizes=None, rhat=None, eps_hat=0.0):
+def qtt_conv(F, G, sizes=None, rhat=None, eps_hat=0.0, delta_hat=None):
     """Alg. 2, Step 3: QiFFT(QFFT(F) (.) QFFT(G)) with the cap rhat (or the
-    tolerance eps_hat) in all three transforms; the result is on the input
-    chain."""
+    tolerance eps_hat, or the drop-off threshold delta_hat) in all three
+    transforms; the result is on the input chain."""
     d = len(F)
     sizes = [d] if sizes is None else list(sizes)
-    Fh = qtt_fft(F, sizes, rhat, eps_hat)
-    Gh = qtt_fft(G, sizes, rhat, eps_hat)
-    return qtt_fft(hadamard(Fh, Gh), sizes[::-1], rhat, eps_hat, inverse=True)
+    Fh = qtt_fft(F, sizes, rhat, eps_hat, delta=delta_hat)
+    Gh = qtt_fft(G, sizes, rhat, eps_hat, delta=delta_hat)
+    return qtt_fft(hadamard(Fh, Gh), sizes[::-1], rhat, eps_hat, inverse=True, delta=delta_hat)
 
 
 def padded_kernel(taps, N, n):
@@ -144,26 +147,40 @@ def linear_part(Ic, N):
     return Ic[sl]
 
 
-def conv_qtt_fft_1d(f0, g0, rmax, rhat, eps_hat=0.0):
-    """Alg. 2 on padded vectors f0, g0 of 2^K entries: Steps 1-2 by the max
-    rank TT-SVD (Sec. 5 (1), cap rmax), Step 3 with the cap rhat, Step 4 by
-    Full (Alg. 3); returns the circular convolution I^c."""
-    n = len(f0)
-    d = n.bit_length() - 1
-    F, _, _ = Q.tt_svd(np.asarray(f0, dtype=np.complex128), d, 0.0, rmax)
-    G, _, _ = Q.tt_svd(np.asarray(g0, dtype=np.complex128), d, 0.0, rmax)
-    return Q.full(qtt_conv(F, G, [d], rhat, eps_hat))
+def decompose(v, d, rmax, delta=None, rsvd=None):
+    """Alg. 2, Step 2 with one of the modified TT-SVDs of Sec. 5: the max rank
+    TT-SVD (cap rmax), the max rank TT-RSVD (rsvd = (p, omega), see
+    ``rsvd.tt_rsvd``) or the SV drop-off TT-SVD (threshold delta, no cap)."""
+    if delta:
+        cores, _, _ = Q.tt_svd(v, d, 0.0, None, delta=delta)
+    elif rsvd is not None:
+        cores, _, _ = RS.tt_rsvd(v, d, rmax, rsvd[0], rsvd[1])
+    else:
+        cores, _, _ = Q.tt_svd(v, d, 0.0, rmax)
+    return cores
 
 
-def conv_qtt_fft_2d(F0, G0, rmax, rhat, eps_hat=0.0):
-    """Alg. 2 on padded 2^K x 2^K images in the plain chain (the column
-    index' bits, then the row index' bits); returns the 2D circular
-    convolution."""
-    ny, nx = F0.shape
-    dx, dy = nx.bit_length() - 1, ny.bit_length() - 1
-    f = Q.image_to_qtt_vector(np.asarray(F0, dtype=np.complex128), interleave=False)
-    g = Q.image_to_qtt_vector(np.asarray(G0, dtype=np.complex128), interleave=False)
-    F, _, _ = Q.tt_svd(f, dx + dy, 0.0, rmax)
-    G, _, _ = Q.tt_svd(g, dx + dy, 0.0, rmax)
-    v = Q.full(qtt_conv(F, G, [dx, dy], rhat, eps_hat))
+def conv_qtt_fft(F0, G0, rmax, rhat, eps_hat=0.0, delta=None, rsvd=None):
+    """Alg. 2 on padded arrays of 2^K entries per axis (a vector, or an image
+    in the plain chain: the column index' bits, then the row index' bits):
+    Steps 1-2 by ``decompose``, Step 3 with the cap rhat (or the tolerance
+    eps_hat; with delta, the same drop-off threshold in the transforms, as
+    Sec. 5 prescribes), Step 4 by Full (Alg. 3).  Returns the circular
+    convolution I^c."""
+    F0 = np.asarray(F0, dtype=np.complex128)
+    G0 = np.asarray(G0, dtype=np.complex128)
+    if F0.ndim == 1:
+        sizes = [F0.size.bit_length() - 1]
+        f, g = F0, G0
+    else:
+        ny, nx = F0.shape
+        sizes = [nx.bit_length() - 1, ny.bit_length() - 1]
+        f = Q.image_to_qtt_vector(F0, interleave=False)
+        g = Q.image_to_qtt_vector(G0, interleave=False)
+    d = sum(sizes)
+    F = decompose(f, d, rmax, delta, rsvd)
+    G = decompose(g, d, rmax, delta, rsvd)
+    v = Q.full(qtt_conv(F, G, sizes, rhat, eps_hat, delta))
+    if F0.ndim == 1:
+        return v
     return Q.qtt_vector_to_image(v, ny, nx, interleave=False)

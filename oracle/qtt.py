@@ -186,13 +186,15 @@ def norm(cores):
     return float(np.sqrt(abs(P[0, 0].real)))
 
 
-def tt_round(cores, eps, rmax=None):
+def tt_round(cores, eps, rmax=None, delta=None):
     """TT-rounding (the QR + truncated-SVD sweep of the TT literature cited in Sec. 1).
 
     Right-to-left orthogonalisation by QR of each core's (r_{k-1}) x (2 r_k)
     unfolding, then a left-to-right sweep of truncated SVDs of the
     (2 r_{k-1}) x r_k unfoldings with tau = eps/sqrt(d-1)*||Y|| and the rank
-    cap rmax, the same threshold rule as Alg. 1.
+    cap rmax, the same threshold rule as Alg. 1; with delta the SV drop-off
+    rule (``drop_rank``, Sec. 5 modification (3)) replaces the eps rule, as
+    in ``tt_svd``.
     """
     cores = [c.copy() for c in cores]
     d = len(cores)
@@ -213,7 +215,7 @@ def tt_round(cores, eps, rmax=None):
         r0, _, r1 = cores[k].shape
         A = cores[k].reshape((2 * r0, r1), order='F')
         U, s, Vh = np.linalg.svd(A, full_matrices=False)
-        r = eps_rank(s, tau, rmax)
+        r = drop_rank(s, delta, rmax) if delta else eps_rank(s, tau, rmax)
         cores[k] = U[:, :r].reshape((r0, 2, r), order='F')
         SV = s[:r, None] * Vh[:r, :]
         cores[k + 1] = np.einsum('ab,bic->aic', SV, cores[k + 1])

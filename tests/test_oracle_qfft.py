@@ -17,7 +17,11 @@ Alg. 2 (Sec. 4 QTT-FFT, Sec. 5 truncated transforms, Sec. 2 padding).
 * Table 6.1 (tests/golden/table_6_1_errors.txt): with R_max = 10 and
   R^_max = 15 (the values Sec. 7 states for all three examples) the QTT-FFT
   route gives E2(I_QTT0) within 10 % of the printed value for Examples 1
-  and 2 and within 15 % for Example 3, and E2(I_xi) within 5 %.
+  and 2 and within 15 % for Example 3, and E2(I_xi) within 5 %; the SV
+  drop-off column I_delta within 10 % for Examples 1 and 2 (Example 3's
+  0.1650 is not reproduced: this route gives 0.11); the TT-RSVD column
+  I_QTTr in the printed order between I_QTT0 and I_xi and within a factor
+  2 (its oversampling p is not printed).
 """
 import os
 
@@ -133,7 +137,7 @@ def test_alg2_full_rank_is_circular_convolution(K):
     f0[:N] = rng.standard_normal(N)
     taps = C.sinc_taps(n, n / 4.0)
     g0 = QF.padded_kernel(taps, N, n)
-    ic = QF.conv_qtt_fft_1d(f0, g0, rmax=2 ** K, rhat=None)
+    ic = QF.conv_qtt_fft(f0, g0, rmax=2 ** K, rhat=None)
     assert np.allclose(ic, _circ_loops(f0, g0), rtol=0, atol=1e-13)
     # Sec. 2: the linear part is Eq. dconv with the kernel on the N-grid offsets
     h, c = (N - 1) // 2, (len(taps) - 1) // 2
@@ -148,7 +152,7 @@ def test_alg2_2d_full_rank_is_circular_convolution():
     n = 2 ** K
     F0 = rng.standard_normal((n, n))
     G0 = rng.standard_normal((n, n))
-    got = QF.conv_qtt_fft_2d(F0, G0, rmax=n * n, rhat=None)
+    got = QF.conv_qtt_fft(F0, G0, rmax=n * n, rhat=None)
     ref = np.zeros((n, n))
     for y in range(n):
         for x in range(n):
@@ -176,10 +180,11 @@ def _grid_taps(taps, N):
     return t[c - (N - 1):c + N]
 
 
-@pytest.mark.parametrize("example", [1, 2, 3])
-def test_table_6_1_through_qtt_fft(example):
+def _example(example):
+    """(noisy, kernel array, N, true convolution, noisy convolution) of a
+    Sec. 7 example, the kernel sampled on the N-point grid (Sec. 2)."""
     row = [r for r in _table("table_6_1_errors.txt") if int(r[0]) == example][0]
-    K, e_xi_p, e_q_p = int(row[1]), float(row[2]), float(row[3])
+    K = int(row[1])
     n = 2 ** K
     if example < 3:
         noisy, clean, N, B = synth.paper_example_1d(example, K, synth.config_rng(5, sub=example))
@@ -187,8 +192,7 @@ def test_table_6_1_through_qtt_fft(example):
         tw = _grid_taps(taps, N)
         itrue = C.conv_fft(clean[:N], tw)
         ixi = C.conv_fft(noisy[:N], tw)
-        ic = QF.conv_qtt_fft_1d(noisy, QF.padded_kernel(taps, N, n), 10, 15)
-        tol = 0.10
+        g0 = QF.padded_kernel(taps, N, n)
     else:
         noisy, clean, N, B = synth.paper_example_2d(K, synth.config_rng(5, sub=example))
         taps = C.sinc_taps(n, B)
@@ -196,10 +200,46 @@ def test_table_6_1_through_qtt_fft(example):
         itrue = C.conv2d_fft(clean[:N, :N], tw, tw)
         ixi = C.conv2d_fft(noisy[:N, :N], tw, tw)
         g = QF.padded_kernel(taps, N, n)
-        ic = QF.conv_qtt_fft_2d(noisy, np.outer(g, g), 10, 15)
-        tol = 0.15
-    iq = QF.linear_part(ic, N)
-    e_xi = np.linalg.norm(ixi - itrue) / np.linalg.norm(itrue)
-    e_q = np.linalg.norm(iq - itrue) / np.linalg.norm(itrue)
+        g0 = np.outer(g, g)
+    return row, noisy, g0, N, itrue, ixi
+
+
+def _e2(a, ref):
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("example", [1, 2, 3])
+def test_table_6_1_through_qtt_fft(example):
+    row, noisy, g0, N, itrue, ixi = _example(example)
+    e_xi_p, e_q_p = float(row[2]), float(row[3])
+    e_q = _e2(QF.linear_part(QF.conv_qtt_fft(noisy, g0, 10, 15), N), itrue)
+    e_xi = _e2(ixi, itrue)
     assert abs(e_xi - e_xi_p) <= 0.05 * e_xi_p, e_xi
-    assert abs(e_q - e_q_p) <= tol * e_q_p, e_q
+    assert abs(e_q - e_q_p) <= (0.10 if example < 3 else 0.15) * e_q_p, e_q
+
+
+@pytest.mark.parametrize("example", [1, 2])
+def test_table_6_1_sv_dropoff(example):
+    """I_delta: the SV drop-off TT-SVD with the printed delta and the same
+    threshold in the QTT-FFT / QTT-iFFT roundings (Sec. 5)."""
+    row, noisy, g0, N, itrue, _ = _example(example)
+    e_p, delta = float(row[5]), float(row[6])
+    e = _e2(QF.linear_part(QF.conv_qtt_fft(noisy, g0, None, None, delta=delta), N), itrue)
+    assert abs(e - e_p) <= 0.10 * e_p, e
+
+
+@pytest.mark.parametrize("example", [1, 2, 3])
+def test_table_6_1_tt_rsvd(example):
+    """I_QTTr: the max rank TT-RSVD (R_max = 10) in place of the TT-SVD.  The
+    oversampling p is not printed; p = 5 keeps the randomized SVD on every
+    level with m_k = 2 R_max > R_max + p.  The printed ordering holds,
+    E2(I_QTT0) < E2(I_QTTr) < E2(I_xi), and the value is within a factor 2
+    of the printed one."""
+    row, noisy, g0, N, itrue, ixi = _example(example)
+    e_r_p = float(row[4])
+    d = int(row[1]) * (1 if example < 3 else 2)
+    _, omega = synth.rsvd_omega_blocks(d, 10, 5, np.random.default_rng(2300 + example))
+    e_r = _e2(QF.linear_part(QF.conv_qtt_fft(noisy, g0, 10, 15, rsvd=(5, omega)), N), itrue)
+    e_q = _e2(QF.linear_part(QF.conv_qtt_fft(noisy, g0, 10, 15), N), itrue)
+    assert e_q < e_r < _e2(ixi, itrue)
+    assert e_r_p / 2 <= e_r <= 2 * e_r_p, e_r
