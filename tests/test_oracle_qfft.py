@@ -7,7 +7,10 @@ Alg. 2 (Sec. 4 QTT-FFT, Sec. 5 truncated transforms, Sec. 2 padding).
 * closed forms: the DFT of the rank-1 exponential exp(2 pi i k0 j / n) is
   n delta_{k0}, reached with the cap R^_max = 1 in every stage;
 * the stage operators have TT ranks <= 2 and are sqrt(2) times unitary (a
-  wrong twiddle modulus or butterfly fails here);
+  wrong twiddle modulus or butterfly fails here), also for an axis whose
+  bits are interleaved with another's;
+* the interleaved 2D chain: numpy's fft2 read through the mirrored bit
+  positions, and Alg. 2 on it = the circular convolution by fft2;
 * Eq. tolerance: with the tolerance eps in each of the d + 1 roundings the
   result is within (d + 1) eps ||DFT(v)|| of the DFT;
 * the Hadamard product is the entrywise product, with multiplied ranks;
@@ -68,6 +71,47 @@ def test_fft_2d_is_fft2(dx, dy):
     assert np.abs(back - v).max() <= 1e-13 * np.abs(v).max()
 
 
+@pytest.mark.parametrize("dx,dy", [(1, 1), (2, 3), (4, 4), (4, 2)])
+def test_fft_2d_interleaved_is_fft2(dx, dy):
+    rng = np.random.default_rng(70 * dx + dy)
+    img = rng.standard_normal((2 ** dy, 2 ** dx)) + 1j * rng.standard_normal((2 ** dy, 2 ** dx))
+    v = Q.image_to_qtt_vector(img, interleave=True)
+    d = dx + dy
+    cores, _, _ = Q.tt_svd(v, d, 0.0)
+    modes = Q.mode_map_2d(dx, dy, True)
+    axes = [[m + 1 for m, (ax, _) in enumerate(modes) if ax == a] for a in (0, 1)]
+    Y = QF.qtt_fft(cores, axes)
+    # bit (axis, b) of the input chain's position m ends at position d+1-m' of
+    # the mirrored chain: read the output through the mirrored positions
+    out = Q.full(Y)
+    q = np.arange(2 ** d)
+    kx = np.zeros_like(q)
+    ky = np.zeros_like(q)
+    for a, pos in enumerate(QF.reversed_axes(axes, d)):
+        for b, m in enumerate(pos):
+            bit = (q >> (m - 1)) & 1
+            if a == 0:
+                kx |= bit << b
+            else:
+                ky |= bit << b
+    ref = np.fft.fft2(img)
+    assert np.abs(out - ref[ky, kx]).max() <= 1e-13 * np.abs(ref).max()
+    back = Q.full(QF.qtt_fft(Y, QF.reversed_axes(axes, d), inverse=True))
+    assert np.abs(back - v).max() <= 1e-13 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("interleave", [False, True])
+def test_alg2_2d_interleaved_chain(interleave):
+    rng = np.random.default_rng(12)
+    n = 8
+    F0 = rng.standard_normal((n, n))
+    G0 = rng.standard_normal((n, n))
+    # rounding at eps 1e-14 keeps the exact ranks (<= 8) between the stages
+    got = QF.conv_qtt_fft(F0, G0, rmax=n * n, rhat=None, eps_hat=1e-14, interleave=interleave)
+    ref = np.real(np.fft.ifft2(np.fft.fft2(F0) * np.fft.fft2(G0)))
+    assert np.allclose(got, ref, rtol=0, atol=1e-12)
+
+
 @pytest.mark.parametrize("k0", [0, 1, 37, 511, 1000])
 def test_exponential_to_delta_at_rank_one(k0):
     d = 10
@@ -83,11 +127,12 @@ def test_exponential_to_delta_at_rank_one(k0):
     assert np.abs(Q.full(Y) - ref).max() <= 1e-11 * n
 
 
-@pytest.mark.parametrize("d,lo,K", [(6, 1, 6), (7, 3, 4), (5, 1, 2)])
-def test_stage_operators(d, lo, K):
+@pytest.mark.parametrize("d,modes", [(6, [1, 2, 3, 4, 5, 6]), (7, [3, 4, 5, 6]), (5, [1, 2]),
+                                     (6, [1, 3, 5]), (7, [2, 3, 6, 7])])
+def test_stage_operators(d, modes):
     for inverse in (False, True):
-        for p in range(1, K + 1):
-            ops = QF.stage_operator(d, lo, K, p, inverse)
+        for p in range(1, len(modes) + 1):
+            ops = QF.stage_operator(d, modes, p, inverse)
             assert max(max(o.shape[0], o.shape[3]) for o in ops) <= 2
             M = T.operator_dense(ops)
             assert np.allclose(M.conj().T @ M, 2.0 * np.eye(2 ** d), atol=1e-12)
