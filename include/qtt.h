@@ -309,6 +309,36 @@ void qtt_op_free(qtt_op* op);
 #define QTT_PRODUCT_CAP 4096
 qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_tensor** out);
 
+/* qtt_fft -- QTT-FFT / QTT-iFFT (Sec. 4, the QTT-FFT of [DKS12]; truncated
+ * as Sec. 5 prescribes for the transforms of Alg. 2): the radix-2
+ * decimation-in-frequency FFT as one rank-2 QTT operator per bit, the input
+ * and every stage TT-rounded with tr, then the chain of cores reversed
+ * (bit reversal).
+ *   x        QTT_C64 handle (a real handle cannot hold a spectrum:
+ *            QTT_EUNSUPPORTED): 1D; 2D plain (interleave 0); or 2D
+ *            interleaved with dy == dx (else QTT_EUNSUPPORTED).  Not
+ *            modified.
+ *   inverse  0: X[k] = sum_n x[n] exp(-2 pi i k n / N) per axis (the Sec. 2
+ *            DFT); 1: the inverse DFT including 1/N^D.
+ *   tr       truncation of every rounding: rmax = R^_max, or eps, or the
+ *            SV drop-off delta (rmax <= 0 and eps = 0: cap QTT_RANK_CAP).
+ *   sketch, seed  as qtt_round (the seed advances by one per stage).
+ *   out      new handle.  1D: the transform in natural order.  2D: the
+ *            transform laid out as the TRANSPOSED image (log2 shape
+ *            {dx, dy}, same interleave flag), so that the inverse of a
+ *            product of two transforms returns the input layout.
+ * The axes are transformed in the order of their least significant bit's
+ * mode.  Asynchronous; device status flags of the roundings carry over. */
+qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sketch,
+                   unsigned long long seed, void* stream, qtt_tensor** out);
+
+/* qtt_hadamard -- new handle holding the entrywise product x .* y (the
+ * product of Alg. 2 Step 3) of two handles of the same layout: core k is
+ * Z[(a + ra a'), i, (b + rb b')] = X[a, i, b] Y[a', i, b'], ranks multiply
+ * (each at most QTT_PRODUCT_CAP, else QTT_EINVAL); no rounding.
+ * Asynchronous. */
+qtt_status qtt_hadamard(const qtt_tensor* x, const qtt_tensor* y, void* stream, qtt_tensor** out);
+
 /* Per-kernel timing.  When enabled, each kernel launch of the library is
  * bracketed by CUDA events on its stream (adds ~2 event records per launch).
  * qtt_profile_read synchronises the device and writes, for up to cap kernel

@@ -101,18 +101,21 @@ def reverse_chain(cores):
 
 
 def _axes(axes, d):
+    """The axes' mode positions, in the order the transform takes them: by
+    the position of each axis' least significant bit."""
     if axes is None:
         return [list(range(1, d + 1))]
     if all(np.isscalar(a) for a in axes):
-        return plain_axes(axes)
-    return [list(a) for a in axes]
+        axes = plain_axes(axes)
+    return sorted((list(a) for a in axes), key=lambda a: a[0])
 
 
 def qtt_fft(cores, axes=None, rmax=None, eps=0.0, inverse=False, delta=None):
     """D-dimensional DFT (inverse=True: the IDFT with its 1/N^D) of a QTT
     tensor.  axes: per axis the mode positions of its bits (LSB first), or a
     list of bit counts for a plain chain (block after block); default one
-    axis of all modes.  With a cap rmax, a tolerance eps or an SV drop-off
+    axis of all modes; the axes are transformed in the order of their least
+    significant bit's mode.  With a cap rmax, a tolerance eps or an SV drop-off
     threshold delta (Sec. 5 (1)-(3)) the input and the result of every stage
     are TT-rounded (without any the transform is exact up to rounding
     errors).  The result's chain is reversed: the axes' bits sit at

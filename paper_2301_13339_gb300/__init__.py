@@ -22,7 +22,8 @@ __all__ = [
     "qtt_op_create",
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
-    "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd",
+    "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd", "qtt_fft",
+    "qtt_hadamard", "qtt_conv_fft",
 ]
 
 QTT_F64 = 0
@@ -40,7 +41,7 @@ EXPORTED_SYMBOLS = [
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
-    "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd",
+    "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
 ]
 
 
@@ -102,6 +103,8 @@ def load(path=None):
         "qtt_op_get_cores": (i, [vp, vp]),
         "qtt_op_free": (None, [vp]),
         "qtt_matvec": (i, [vp, vp, vp, pp]),
+        "qtt_fft": (i, [vp, i, tp, i, ull, vp, pp]),
+        "qtt_hadamard": (i, [vp, vp, vp, pp]),
         "qtt_release_workspace": (None, []),
         "qtt_small_eigh": (i, [vp, i, i, vp, vp, vp]),
         "qtt_debug_set_eig_solver": (None, [i]),
@@ -457,6 +460,42 @@ def qtt_matvec(op, t, stream=None):
     out = ctypes.c_void_p()
     _check(_lib.qtt_matvec(op._h, t.handle, _stream(stream), ctypes.byref(out)))
     return QTTTensor(out)
+
+
+def qtt_fft(t, inverse=False, rmax=15, eps=0.0, delta=0.0, refine=True, sketch=0,
+            seed=20230131, stream=None):
+    """QTT-FFT (inverse=True: QTT-iFFT with its 1/N^D) of a complex64 handle
+    (Sec. 4, truncated as in Sec. 5): every stage rounded to the cap rmax
+    (R^_max), or with eps, or with the SV drop-off delta.  2D results are
+    laid out as the transposed image (see include/qtt.h)."""
+    load()
+    tr = _trunc(eps, rmax, refine, delta)
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_fft(t.handle, int(bool(inverse)), ctypes.byref(tr), int(sketch),
+                        ctypes.c_ulonglong(int(seed)), _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_hadamard(x, y, stream=None):
+    """Entrywise product x .* y as a new handle (ranks multiply; not rounded)."""
+    load()
+    out = ctypes.c_void_p()
+    _check(_lib.qtt_hadamard(x.handle, y.handle, _stream(stream), ctypes.byref(out)))
+    return QTTTensor(out)
+
+
+def qtt_conv_fft(F, G, rhat=15, eps=0.0, delta=0.0, refine=True, stream=None):
+    """Alg. 2, Step 3: QiFFT(QFFT(F) .* QFFT(G)) of two complex64 handles of
+    the same layout, the transforms truncated with rhat (R^_max), eps or
+    delta; the circular convolution of the two arrays, on F's layout."""
+    Fh = qtt_fft(F, False, rhat, eps, delta, refine, stream=stream)
+    Gh = qtt_fft(G, False, rhat, eps, delta, refine, stream=stream)
+    P = qtt_hadamard(Fh, Gh, stream=stream)
+    Fh.free(stream)
+    Gh.free(stream)
+    out = qtt_fft(P, True, rhat, eps, delta, refine, stream=stream)
+    P.free(stream)
+    return out
 
 
 def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):

@@ -510,6 +510,23 @@ qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_t
   return matvec(op, x, (cudaStream_t)stream, out);
 }
 
+qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sketch,
+                   unsigned long long seed, void* stream, qtt_tensor** out) {
+  g_err[0] = 0;
+  if (!x || !out) { set_error("qtt_fft: NULL argument"); return QTT_EINVAL; }
+  qtt_trunc t0 = {0.0, 0, 1, 0.0};
+  if (tr) {
+    qtt_status st = check_trunc(tr);
+    if (st != QTT_OK) return st;
+    t0 = *tr;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  qtt_op* id = nullptr;
+  qtt_status st = cached_identity(x->desc.d, x->desc.dt, s, &id);
+  if (st != QTT_OK) return st;
+  return fft_transform(x, inverse, t0, id, sketch, seed, s, out);
+}
+
 void qtt_release_workspace(void) {
   cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -608,6 +625,13 @@ qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_ten
   if (!x || !y || !out) { set_error("qtt_add: NULL argument"); return QTT_EINVAL; }
   if (!same_layout(x, y)) { set_error("qtt_add: tensors differ in shape or type"); return QTT_EINVAL; }
   return tt_add(alpha, x, beta, y, (cudaStream_t)stream, out);
+}
+
+qtt_status qtt_hadamard(const qtt_tensor* x, const qtt_tensor* y, void* stream, qtt_tensor** out) {
+  g_err[0] = 0;
+  if (!x || !y || !out) { set_error("qtt_hadamard: NULL argument"); return QTT_EINVAL; }
+  if (!same_layout(x, y)) { set_error("qtt_hadamard: tensors differ in shape or type"); return QTT_EINVAL; }
+  return hadamard(x, y, (cudaStream_t)stream, out);
 }
 
 qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int d, qtt_dtype dt,

@@ -267,6 +267,7 @@ qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_ten
   const int d = x->desc.d;
   if (op->d != d) { set_error("matvec: operator has %d modes, tensor %d", op->d, d); return QTT_EINVAL; }
   if (op->dt != x->desc.dt) { set_error("matvec: operator/tensor dtype mismatch"); return QTT_EINVAL; }
+  if (op->cplx && x->desc.dt != QTT_C64) { set_error("matvec: complex operator on a real tensor"); return QTT_EINVAL; }
   std::vector<int> cap(d + 1);
   for (int k = 0; k <= d; ++k) {
     cap[k] = op->P[k] * x->rcap[k];
@@ -286,6 +287,11 @@ qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_ten
           (const double*)op->cores + op->off[k - 1], op->P[k - 1], op->P[k],
           (const double*)x->cores + x->off[k - 1], x->ranks, k, y->ranks,
           (double*)y->cores + y->off[k - 1], capel);
+    else if (op->cplx)
+      matvec_core_kernel<float2, float2><<<blocks, 256, 0, s>>>(
+          (const float2*)op->cores + op->off[k - 1], op->P[k - 1], op->P[k],
+          (const float2*)x->cores + x->off[k - 1], x->ranks, k, y->ranks,
+          (float2*)y->cores + y->off[k - 1], capel);
     else
       matvec_core_kernel<float2, float><<<blocks, 256, 0, s>>>(
           (const float*)op->cores + op->off[k - 1], op->P[k - 1], op->P[k],

@@ -935,6 +935,7 @@ qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc&
                          unsigned long long seed, cudaStream_t s, qtt_tensor** out) {
   if (op->d != x->desc.d) { set_error("round: operator/tensor mode count mismatch"); return QTT_EINVAL; }
   if (op->dt != x->desc.dt) { set_error("round: operator/tensor dtype mismatch"); return QTT_EINVAL; }
+  if (op->cplx) { set_error("round: complex operators are applied by matvec"); return QTT_EUNSUPPORTED; }
   if (x->desc.dt == QTT_F64) return round_product_t<double>(op, x, tr, sketch, seed, s, out);
   return round_product_t<float2>(op, x, tr, sketch, seed, s, out);
 }

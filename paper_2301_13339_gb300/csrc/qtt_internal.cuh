@@ -89,6 +89,13 @@ __device__ __forceinline__ void rmac(float2& acc, float r, float2 b) {
   acc.x = fmaf(r, b.x, acc.x);
   acc.y = fmaf(r, b.y, acc.y);
 }
+// acc += r * b  (r complex)
+__device__ __forceinline__ void rmac(float2& acc, float2 r, float2 b) {
+  acc.x = fmaf(r.x, b.x, acc.x);
+  acc.x = fmaf(-r.y, b.y, acc.x);
+  acc.y = fmaf(r.x, b.y, acc.y);
+  acc.y = fmaf(r.y, b.x, acc.y);
+}
 
 // Warp-wide sum of a T value with float shuffles for the FP32 path.
 __device__ __forceinline__ double warp_sum(double v) {
@@ -185,6 +192,7 @@ struct qtt_tensor {
 struct qtt_op {
   int d = 0;                      // number of modes the operator acts on
   qtt_dtype dt = QTT_C64;         // data type it is applied to (cores are real R)
+  int cplx = 0;                   // 1: complex cores (float2, QTT_C64 only; the QTT-FFT stages)
   std::vector<int> P;             // ranks P_0..P_d (host)
   std::vector<size_t> off;        // offsets of the cores (elements of R)
   size_t total = 0;
@@ -300,6 +308,12 @@ void op_free(qtt_op* op);
 
 // ------------------------------------------------------------- conv / rounding
 qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_tensor** out);
+// QTT-FFT / QTT-iFFT of x (QTT_C64), every stage rounded by round_product
+// with the identity operator id (k_fft.cu)
+qtt_status fft_transform(const qtt_tensor* x, int inverse, const qtt_trunc& tr, const qtt_op* id,
+                         int sketch, unsigned long long seed, cudaStream_t s, qtt_tensor** out);
+// entrywise product, ranks multiply (k_fft.cu)
+qtt_status hadamard(const qtt_tensor* x, const qtt_tensor* y, cudaStream_t s, qtt_tensor** out);
 qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,
                          unsigned long long seed, cudaStream_t s, qtt_tensor** out);
 
