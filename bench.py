@@ -44,6 +44,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -121,10 +122,13 @@ def run_oracle(x, wl):
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
+    csv_path = None            # --clocks-csv: keep the samples there
+
     def __init__(self, dev):
         self.dev = dev
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = Clocks.csv_path or os.path.join(tempfile.gettempdir(),
+                                                    f"qtt_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -651,7 +655,10 @@ def main():
     ap.add_argument("--workload", default="line_2p20_c64", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="file for the nvidia-smi samples of the timed region (default: a temp file)")
     args = ap.parse_args()
+    Clocks.csv_path = args.clocks_csv
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     wl = WORKLOADS[args.workload]
     metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"

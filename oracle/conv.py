@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  float64/complex128.
 
-Readings of the paper used here (each listed in the design doc):
+Readings of the paper used here (where it is silent or garbled):
 * Grid: midpoint rule of Sec. 2 on [0, 1], x_j = (j + 1/2) h, h = 1/N.
 * Kernel: Eq. (GAF), g(x) = A sinc(pi x / Delta_x) with Delta_x = 1/B, i.e.
   g(x) = A sinc(pi B x), sinc(u) = sin(u)/u, sinc(0) = 1.  With

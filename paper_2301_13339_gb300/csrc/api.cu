@@ -1,6 +1,7 @@
 // C ABI of libqtt: argument checks, handle management, operator plan cache.
 // The numerical work is in k_svd.cu (TT-SVD), k_op.cu (operator plan and
-// matvec), k_round.cu (rounding of operator x vector) and k_full.cu (Full).
+// matvec), k_round.cu (rounding of operator x vector), k_full.cu (Full) and
+// k_fft.cu (QTT-FFT stages, Hadamard product).
 #include "qtt_internal.cuh"
 #include <cstdarg>
 #include <cstdio>
