@@ -112,3 +112,21 @@ def test_noisy_line_error_near_tt_svd():
     e_r = np.linalg.norm(Q.full(got) - x)
     e_s = np.linalg.norm(Q.full(ref) - x)
     assert e_r <= 1.5 * e_s
+
+
+def test_fallback_boundary_is_inclusive():
+    """Sec. 5: a level reverts to the SVD when min(m_k, n_k) <= R_max + p,
+    equality included.  d = 10, R_max = p = 8: the levels with m_k = 16 and
+    n_k >= 16 sit exactly on the boundary and revert; level k = 7 with
+    m_k = 16 and n_k = 8 reverts too; nothing here exceeds R_max + p."""
+    rng = np.random.default_rng(21)
+    d, rmax, p = 10, 8, 8
+    x = rng.standard_normal(2 ** d)
+    _, omega = synth.rsvd_omega_blocks(d, rmax, p, rng)
+    _, ranks, used = RS.tt_rsvd(x, d, rmax, p, omega)
+    assert ranks[4] == 8 and 2 * ranks[4] == rmax + p
+    assert not any(used)
+    # one less oversampling puts the m_k = 16 levels with n_k >= 16 above it
+    _, omega = synth.rsvd_omega_blocks(d, rmax, p - 1, rng)
+    _, _, used = RS.tt_rsvd(x, d, rmax, p - 1, omega)
+    assert used[3:6] == [True, True, True] and not any(used[:3])
