@@ -332,6 +332,20 @@ qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_t
 qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sketch,
                    unsigned long long seed, void* stream, qtt_tensor** out);
 
+/* qtt_sinc_padded -- the kernel array g of Alg. 2 for the sinc kernel, padded
+ * as in Sec. 2: g[j] = c(j - (N-1)/2) for j < N (the kernel at the N points
+ * of the grid, centred), 0 for N <= j < n = 2^log2_n, where c(m) = h A
+ * sinc(pi B m h) with h = 1/n and, for normalize = 1, h A = 1 / the sum of
+ * sinc(pi B m h) over m = -(n-1)..n-1 (the normalisation qtt_conv_sinc
+ * uses); normalize = 0: A = 1.
+ *   N      odd, 1 <= N and 2N - 1 <= n (room for the circular convolution
+ *          to equal the linear one), else QTT_EINVAL.
+ *   g_dev  caller-owned DEVICE array of n elements of dt (QTT_C64: real
+ *          part set, imaginary part 0).
+ * Asynchronous. */
+qtt_status qtt_sinc_padded(int log2_n, long long N, double B, int normalize, qtt_dtype dt,
+                           void* g_dev, void* stream);
+
 /* qtt_hadamard -- new handle holding the entrywise product x .* y (the
  * product of Alg. 2 Step 3) of two handles of the same layout: core k is
  * Z[(a + ra a'), i, (b + rb b')] = X[a, i, b] Y[a', i, b'], ranks multiply

@@ -23,7 +23,7 @@ __all__ = [
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
     "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd", "qtt_fft",
-    "qtt_hadamard", "qtt_conv_fft",
+    "qtt_hadamard", "qtt_conv_fft", "qtt_sinc_padded",
 ]
 
 QTT_F64 = 0
@@ -42,6 +42,7 @@ EXPORTED_SYMBOLS = [
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
+    "qtt_sinc_padded",
 ]
 
 
@@ -105,6 +106,7 @@ def load(path=None):
         "qtt_matvec": (i, [vp, vp, vp, pp]),
         "qtt_fft": (i, [vp, i, tp, i, ull, vp, pp]),
         "qtt_hadamard": (i, [vp, vp, vp, pp]),
+        "qtt_sinc_padded": (i, [i, ctypes.c_longlong, d, i, i, vp, vp]),
         "qtt_release_workspace": (None, []),
         "qtt_small_eigh": (i, [vp, i, i, vp, vp, vp]),
         "qtt_debug_set_eig_solver": (None, [i]),
@@ -474,6 +476,23 @@ def qtt_fft(t, inverse=False, rmax=15, eps=0.0, delta=0.0, refine=True, sketch=0
     _check(_lib.qtt_fft(t.handle, int(bool(inverse)), ctypes.byref(tr), int(sketch),
                         ctypes.c_ulonglong(int(seed)), _stream(stream), ctypes.byref(out)))
     return QTTTensor(out)
+
+
+def qtt_sinc_padded(log2_n, N, B, normalize=True, dtype=None, out=None, stream=None):
+    """The sinc kernel array g of Alg. 2, padded as in Sec. 2 (the kernel at
+    the N grid points, centred, then zeros up to 2^log2_n), as a new (or the
+    given) CUDA tensor of float64 or complex64."""
+    import torch
+    load()
+    dtype = dtype or torch.complex64
+    n = 1 << int(log2_n)
+    if out is None:
+        out = torch.empty(n, dtype=dtype, device="cuda")
+    if not out.is_cuda or not out.is_contiguous() or out.numel() != n:
+        raise ValueError(f"out must be a contiguous CUDA tensor of {n} elements")
+    _check(_lib.qtt_sinc_padded(int(log2_n), int(N), float(B), int(bool(normalize)),
+                                _dtype_code(out), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 def qtt_hadamard(x, y, stream=None):

@@ -511,6 +511,22 @@ qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_t
   return matvec(op, x, (cudaStream_t)stream, out);
 }
 
+qtt_status qtt_sinc_padded(int log2_n, long long N, double B, int normalize, qtt_dtype dt,
+                           void* g_dev, void* stream) {
+  g_err[0] = 0;
+  if (!g_dev) { set_error("qtt_sinc_padded: NULL output"); return QTT_EINVAL; }
+  if (!valid_dtype(dt) || log2_n < 1 || log2_n > 30) {
+    set_error("qtt_sinc_padded: bad dtype or log2_n");
+    return QTT_EINVAL;
+  }
+  const long long n = 1LL << log2_n;
+  if (N < 1 || N % 2 == 0 || 2 * N - 1 > n) {
+    set_error("qtt_sinc_padded: need N odd with 2N - 1 <= 2^log2_n (got N = %lld)", N);
+    return QTT_EINVAL;
+  }
+  return sinc_padded(log2_n, N, B, normalize, dt, g_dev, (cudaStream_t)stream);
+}
+
 qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sketch,
                    unsigned long long seed, void* stream, qtt_tensor** out) {
   g_err[0] = 0;

@@ -57,6 +57,46 @@ __global__ void chat_kernel(long long n, double B, int normalize, const double* 
   chat[t] = normalize ? s / (*sum) : s / (double)n;
 }
 
+// Sec. 2 padding of the kernel samples (the array g of Alg. 2): g[j] =
+// c(j - (N-1)/2) for j < N (the kernel at the N grid points, centred), 0 for
+// N <= j < n, with c(m) = h A sinc(pi B m h) normalised as in the operator
+// plan (h = 1/n, h A = 1 / the sum over the 2n-1 offsets of the n-grid).
+__device__ __forceinline__ void store_real(double& g, double v) { g = v; }
+__device__ __forceinline__ void store_real(float2& g, double v) { g = make_float2((float)v, 0.f); }
+
+template <typename T>
+__global__ void sinc_padded_kernel(long long n, long long N, double B, int normalize,
+                                   const double* __restrict__ sum, T* __restrict__ g) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double v = 0.0;
+  if (j < N) {
+    const long long m = j - (N - 1) / 2;
+    double sv = 1.0;
+    if (m != 0) {
+      const double x = B * (double)m / (double)n;
+      sv = sinpi(x) / (M_PI * x);
+    }
+    v = normalize ? sv / (*sum) : sv / (double)n;
+  }
+  store_real(g[j], v);
+}
+
+qtt_status sinc_padded(int log2_n, long long N, double B, int normalize, qtt_dtype dt, void* g,
+                       cudaStream_t s) {
+  const long long n = 1LL << log2_n;
+  double* sum = (double*)scratch_alloc(sizeof(double), s);
+  if (!sum) { set_error("qtt_sinc_padded: alloc"); return QTT_ENOMEM; }
+  cudaMemsetAsync(sum, 0, sizeof(double), s);
+  const int blocks = (int)std::min<long long>((2 * n + 255) / 256, 4096);
+  sinc_sum_kernel<<<blocks, 256, 0, s>>>(n, B, sum);
+  const int gb = (int)((n + 255) / 256);
+  if (dt == QTT_F64) sinc_padded_kernel<double><<<gb, 256, 0, s>>>(n, N, B, normalize, sum, (double*)g);
+  else sinc_padded_kernel<float2><<<gb, 256, 0, s>>>(n, N, B, normalize, sum, (float2*)g);
+  scratch_free(sum, s);
+  return cuda_check(cudaGetLastError(), "qtt_sinc_padded");
+}
+
 // One thread per operator core element; core k (1-based) of P_{k-1} x 2 x 2 x P_k,
 // element (p, j, i, q) at p + P_{k-1} (j + 2 (i + 2 q)).
 template <typename R>

@@ -312,6 +312,9 @@ qtt_status matvec(const qtt_op* op, const qtt_tensor* x, cudaStream_t s, qtt_ten
 // with the identity operator id (k_fft.cu)
 qtt_status fft_transform(const qtt_tensor* x, int inverse, const qtt_trunc& tr, const qtt_op* id,
                          int sketch, unsigned long long seed, cudaStream_t s, qtt_tensor** out);
+// Sec. 2 padded kernel samples of the sinc (k_op.cu)
+qtt_status sinc_padded(int log2_n, long long N, double B, int normalize, qtt_dtype dt, void* g,
+                       cudaStream_t s);
 // entrywise product, ranks multiply (k_fft.cu)
 qtt_status hadamard(const qtt_tensor* x, const qtt_tensor* y, cudaStream_t s, qtt_tensor** out);
 qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,

@@ -7,7 +7,9 @@
   2D interleaved; 2D results in the transposed image's layout);
 * QiFFT(QFFT(x)) = x; the Hadamard product = the entrywise product;
 * Alg. 2 (max rank TT-SVD with R_max = 10, transforms with R^_max = 15) on a
-  Sec. 7 example against the oracle's route on the same noisy input;
+  Sec. 7 example against the oracle's route on the same noisy input, each
+  side with its own kernel samples (qtt_sinc_padded on the device, checked
+  against the oracle's Sec. 2 padding);
 * argument errors: a real handle, an interleaved layout with unequal axes.
 
 These tests have not yet run on a GPU: they are opt-in
@@ -121,12 +123,27 @@ def test_alg2_example_parity(qlib, example, K):
     import torch
     noisy, clean, N, B = synth.paper_example_1d(example, K, synth.config_rng(5, sub=example))
     n = 2 ** K
-    g0 = QF.padded_kernel(C.sinc_taps(n, B), N, n)
-    ref = QF.conv_qtt_fft(noisy, g0, 10, 15)
+    ref = QF.conv_qtt_fft(noisy, QF.padded_kernel(C.sinc_taps(n, B), N, n), 10, 15)
+    g_dev = qlib.qtt_sinc_padded(K, N, B)               # the library's own kernel samples
     F = qlib.qtt_decompose(torch.from_numpy(noisy.astype(np.complex64)).cuda(), 0.0, 10, refine=True)
-    G = qlib.qtt_decompose(torch.from_numpy(g0.astype(np.complex64)).cuda(), 0.0, 10, refine=True)
+    G = qlib.qtt_decompose(g_dev, 0.0, 10, refine=True)
     got = _full(qlib, qlib.qtt_conv_fft(F, G, rhat=15))
     assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("K,B,normalize", [(8, 64.0, True), (12, 1024.0, True), (10, 37.5, False)])
+def test_sinc_padded(qlib, K, B, normalize):
+    import torch
+    n = 2 ** K
+    N = 2 ** (K - 1) - 1
+    ref = QF.padded_kernel(C.sinc_taps(n, B, normalize), N, n)
+    g64 = qlib.qtt_sinc_padded(K, N, B, normalize, dtype=torch.float64).cpu().numpy()
+    assert np.abs(g64 - ref).max() <= 1e-13 * np.abs(ref).max()
+    g32 = qlib.qtt_sinc_padded(K, N, B, normalize).cpu().numpy()
+    assert np.abs(g32.imag).max() == 0.0
+    assert np.abs(g32.real - ref).max() <= 1e-6 * np.abs(ref).max()
+    with pytest.raises(qlib.QTTError):
+        qlib.qtt_sinc_padded(K, N + 1, B)
 
 
 def test_argument_errors(qlib):
