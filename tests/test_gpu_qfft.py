@@ -1,5 +1,6 @@
 """QTT-FFT / QTT-iFFT and the QTT convolution of Alg. 2 through the C ABI
-(complex64) against the oracle (oracle/qfft.py) on the same input cores:
+(complex64) against the oracle (oracle/qfft.py) on the same seeded inputs
+(random cores, or arrays the library decomposes itself):
 
 * one transform, truncated to R^_max: the full spectrum within 1e-5
   (relative, FP32), ranks within the cap;
@@ -44,11 +45,6 @@ def _full(q, t):
     return q.qtt_to_full(t).cpu().numpy().astype(np.complex128)
 
 
-def _axes_2d(dy, dx, interleave):
-    modes = Q.mode_map_2d(dx, dy, interleave)
-    return [[m + 1 for m, (ax, _) in enumerate(modes) if ax == a] for a in (0, 1)]
-
-
 @pytest.mark.parametrize("d,rhat", [(10, 15), (14, 15), (12, 8)])
 def test_fft_truncated_parity(qlib, d, rhat):
     rng = np.random.default_rng(d + rhat)
@@ -73,11 +69,13 @@ def test_fft_exact_is_numpy_fft(qlib, d):
 
 @pytest.mark.parametrize("dy,dx,interleave", [(3, 4, False), (4, 4, True), (2, 5, False)])
 def test_fft_2d_is_fft2_transposed(qlib, dy, dx, interleave):
+    import torch
     rng = np.random.default_rng(7 * dx + dy)
     img = rng.standard_normal((2 ** dy, 2 ** dx)) + 1j * rng.standard_normal((2 ** dy, 2 ** dx))
-    v = Q.image_to_qtt_vector(img, interleave=interleave)
-    cores, _, _ = Q.tt_svd(v, dx + dy, 0.0)
-    t = qlib.qtt_fft(_handle(qlib, cores, [dy, dx], interleave), rmax=64)
+    # the library's own TT-SVD at full rank (exact) builds the input handle
+    x = qlib.qtt_decompose(torch.from_numpy(img.astype(np.complex64)).cuda(), 0.0, 0, refine=True,
+                           interleave=interleave)
+    t = qlib.qtt_fft(x, rmax=64)
     assert t.shape == (2 ** dx, 2 ** dy)
     got = _full(qlib, t)
     ref = np.fft.fft2(img).T
@@ -151,8 +149,7 @@ def test_argument_errors(qlib):
     real = qlib.qtt_from_cores([c.real.copy() for c in _random_qtt(rng, 6, 2)], [6])
     with pytest.raises(qlib.QTTError):
         qlib.qtt_fft(real)
-    cores, _, _ = Q.tt_svd(rng.standard_normal(2 ** 5).astype(complex), 5, 0.0)
-    inter = _handle(qlib, cores, [2, 3], interleave=True)
+    inter = _handle(qlib, _random_qtt(rng, 5, 2), [2, 3], interleave=True)
     with pytest.raises(qlib.QTTError):
         qlib.qtt_fft(inter)
     other = _handle(qlib, _random_qtt(rng, 5, 2), [5])
