@@ -171,7 +171,8 @@ def paper_example_1d(example, K, rng):
 def paper_example_2d(K, rng):
     """Example 3: f = exp(-((2x)^2 + (2y)^2)) (sin 2 pi x - cos 7 pi y
     + cos 4 pi x y - sin 3 pi x y) on [-1, 1]^2, noise 0.1, Delta_x = 2 dx;
-    rows are x, columns y."""
+    returned as F[y, x] (rows y, columns x: x is the fast index, so the plain
+    QTT chain -- column bits first -- takes the x bits first)."""
     x, dx, N = _paper_grid(-1.0, 1.0, K)
     X, Y = np.meshgrid(x, x, indexing="ij")
     f = np.exp(-((2 * X) ** 2 + (2 * Y) ** 2)) * (np.sin(2 * np.pi * X) - np.cos(7 * np.pi * Y)
@@ -182,7 +183,7 @@ def paper_example_2d(K, rng):
     clean[:N, :N] = f
     noisy = clean.copy()
     noisy[:N, :N] += rng.normal(0.0, 0.1, size=(N, N))
-    return noisy, clean, N, n / 2.0
+    return noisy.T.copy(), clean.T.copy(), N, n / 2.0
 
 
 # ---------------------------------------------------------------- TT-RSVD draws
