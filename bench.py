@@ -63,6 +63,9 @@ WORKLOADS = {
                           bmax=1024.0, eps=0.0, eps_op=1e-7, eps_round=1e-7, tol=1e-5),
     "deconv_2048sq_c64": dict(kind="deconv", dy=11, dx=11, B=256.0, nscat=100, snr_db=20.0,
                               rank_f=32, rank_g=64, eps_op=1e-7, eps_round=1e-7),
+    # Alg. 2 with the paper's QTT-FFT step on Example 1 of Sec. 7 at K = 20
+    # (R_max = 10, R^_max = 15)
+    "example1_2p20_qfft": dict(kind="qfft", example=1, K=20, rmax=10, rhat=15, tol=1e-5),
 }
 
 
@@ -646,6 +649,180 @@ def deconv_main(args, wl):
     print(json.dumps(line))
 
 
+def _grid_taps(taps, N):
+    """Kernel samples at the offsets of the N-point grid (|m| <= (N-1)/2) as
+    Toeplitz taps of a length-N convolution: the linear convolution that
+    Alg. 2's padded circular convolution equals on its first N outputs."""
+    h, c = (N - 1) // 2, (len(taps) - 1) // 2
+    t = np.where(np.abs(np.arange(len(taps)) - c) <= h, taps, 0.0)
+    return t[c - (N - 1):c + N]
+
+
+def qfft_main(args, wl):
+    """Alg. 2 with the QTT-FFT step on a Sec. 7 example: per step the max rank
+    TT-SVD of the padded noisy data, QFFT, the entrywise product with the
+    kernel's transform, QiFFT (R^_max in the transforms) and Full.  The
+    kernel's QTT and its transform are plan-time, like the Toeplitz route's
+    operator plan, on both arms."""
+    import synth
+    K = wl["K"]
+    n = 2 ** K
+    noisy, clean, N, B = synth.paper_example_1d(wl["example"], K,
+                                                synth.config_rng(5, sub=wl["example"]))
+    metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"
+    config = {"workload": args.workload, "samples_per_line": n, "dtype_in": "complex64",
+              "example": wl["example"], "N": N, "B": B, "rmax": wl["rmax"], "rhat": wl["rhat"],
+              "route": "QTT-FFT (Alg. 2 Step 3)",
+              "l2": "flushed (512 MiB write) before every timed step, outside the timed region"}
+
+    def oracle_plan():
+        from oracle import conv as C, qfft as QF
+        g0 = QF.padded_kernel(C.sinc_taps(n, B), N, n)
+        return QF.qtt_fft(QF.decompose(g0.astype(np.complex128), K, wl["rmax"]), None, wl["rhat"])
+
+    def oracle_step(x, Gh):
+        from oracle import qfft as QF, qtt as Q
+        t0 = time.perf_counter()
+        F = QF.decompose(x.astype(np.complex128), K, wl["rmax"])
+        Fh = QF.qtt_fft(F, None, wl["rhat"])
+        out = Q.full(QF.qtt_fft(QF.hadamard(Fh, Gh), None, wl["rhat"], inverse=True))
+        return out, time.perf_counter() - t0
+
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        Gh = oracle_plan()
+        x = noisy.astype(np.complex64)
+        for _ in range(args.warmup):
+            oracle_step(x, Gh)
+        tot = sum(oracle_step(x, Gh)[1] for _ in range(args.steps))
+        v = n * args.steps / tot / 1e6
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "Msamples/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": v, "unit": "Msamples/s",
+                                           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                           "sample": f"one full line (2^{K} samples) per step, numpy FP64"},
+                          "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import ctypes
+    import torch
+    import paper_2301_13339_gb300 as q
+    dev = torch.device("cuda", 0)
+    q.load()
+    L = q.lib()
+    stream = torch.cuda.Stream(device=dev)
+    x = noisy.astype(np.complex64)
+    xd = torch.from_numpy(x).to(dev)
+    out = torch.empty(n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    rmax, rhat = wl["rmax"], wl["rhat"]
+    torch.cuda.synchronize(dev)
+    t_plan = time.perf_counter()
+    with torch.cuda.stream(stream):
+        G = q.qtt_decompose(q.qtt_sinc_padded(K, N, B, stream=stream), eps=0.0, rmax=rmax,
+                            refine=True, stream=stream)
+        Gh = q.qtt_fft(G, rmax=rhat, stream=stream)
+    torch.cuda.synchronize(dev)
+    plan_ms = 1e3 * (time.perf_counter() - t_plan)
+
+    def step(s, xin=xd, dst=out):
+        F = q.qtt_decompose(xin, eps=0.0, rmax=rmax, refine=True, stream=s)
+        Fh = q.qtt_fft(F, rmax=rhat, stream=s)
+        P = q.qtt_hadamard(Fh, Gh, stream=s)
+        I = q.qtt_fft(P, inverse=True, rmax=rhat, stream=s)
+        q.qtt_to_full(I, out=dst, stream=s)
+        for t in (F, Fh, P, I):
+            t.free(stream=s)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step(stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(dev.index)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step(stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    # e2e: pinned host input in, the result back to the host, every step
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.empty(n, dtype=torch.complex64).pin_memory()
+    x2 = torch.empty_like(xd)
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            eve[i][0].record(stream)
+            x2.copy_(xh, non_blocking=True)
+            step(stream, xin=x2)
+            oh.copy_(out, non_blocking=True)
+            eve[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eve)
+    # per-kernel CUDA-event profile of the same steps
+    L.qtt_profile_enable.argtypes = [ctypes.c_int]
+    L.qtt_profile_read.restype = ctypes.c_int
+    L.qtt_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.qtt_profile_reset()
+    L.qtt_profile_enable(1)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            step(stream)
+    torch.cuda.synchronize(dev)
+    L.qtt_profile_enable(0)
+    cap, stride = 64, 64
+    names = ctypes.create_string_buffer(cap * stride)
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int * cap)()
+    nk = L.qtt_profile_read(names, stride, ms, cnt, cap)
+    kern = {}
+    for i in range(nk):
+        nm = names.raw[i * stride:(i + 1) * stride].split(b"\0")[0].decode()
+        kern[nm] = {"ms_per_step": ms[i] / args.steps, "launches_per_step": cnt[i] / args.steps}
+    L.qtt_profile_reset()
+    got = out.cpu().numpy().astype(np.complex128)
+    peaks, peak_kind = _peaks()
+    value = n * args.steps / (total_ms * 1e-3) / 1e6
+    line = {"metric": metric, "value": value, "unit": "Msamples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 arithmetic)", "data": "synthetic", "config": config,
+            "e2e": {"value": n * args.steps / (e2e_ms * 1e-3) / 1e6, "unit": "Msamples/s",
+                    "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": int(round(sum(k["launches_per_step"] for k in kern.values()) * args.steps)),
+            "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in kern.items()},
+            "roofline": roofline(kern, {"d": K, "rmax": rmax}, peaks, peak_kind),
+            "clocks": clk, "plan_ms": plan_ms}
+    if not args.no_cpu_baseline:
+        from oracle import conv as C, qfft as QF
+        ref, t = oracle_step(x, oracle_plan())
+        e2 = C.rel_l2(got, ref)
+        line["parity"] = {"e2_vs_oracle": e2, "tol": wl["tol"], "ok": bool(e2 <= wl["tol"])}
+        tw = _grid_taps(C.sinc_taps(n, B), N)
+        itrue = C.conv_fft(clean[:N], tw)
+        line["e2_vs_noise_free"] = C.rel_l2(QF.linear_part(got, N), itrue)
+        line["e2_noisy_input_vs_noise_free"] = C.rel_l2(C.conv_fft(noisy[:N], tw), itrue)
+        line["cpu_baseline"] = {"value": n / t / 1e6, "unit": "Msamples/s",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"one full line (2^{K} samples), numpy FP64"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -664,6 +841,9 @@ def main():
     metric = "QTT decompose+convolve+reconstruct Msamples/s at fixed rel. error vs FP64 oracle"
     if wl.get("kind") == "deconv":
         deconv_main(args, wl)
+        return
+    if wl.get("kind") == "qfft":
+        qfft_main(args, wl)
         return
     if wl.get("kind") == "batch":
         # more hardware work queues for the concurrent line chains (process-local)
