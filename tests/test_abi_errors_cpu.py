@@ -1,0 +1,126 @@
+"""Argument errors of the C ABI, without a GPU: every call below is rejected
+by the entry point's own checks before any CUDA call, returns QTT_EINVAL
+(-1) and leaves a message for qtt_last_error.  The buffers passed are host
+memory that the rejected calls never touch."""
+import ctypes
+
+import pytest
+
+QTT_EINVAL = -1
+QTT_F64, QTT_C64 = 0, 2
+
+
+class Trunc(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int),
+                ("delta", ctypes.c_double)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2301_13339_gb300 import _build
+    L = ctypes.CDLL(_build.build())
+    L.qtt_last_error.restype = ctypes.c_char_p
+    return L
+
+
+@pytest.fixture
+def buf():
+    return ctypes.create_string_buffer(4096)
+
+
+def _expect(lib, status, words):
+    assert status == QTT_EINVAL
+    msg = lib.qtt_last_error().decode()
+    for w in words:
+        assert w in msg, msg
+
+
+def test_decompose_arguments(lib, buf):
+    out = ctypes.c_void_p()
+    ok = Trunc(0.0, 64, 1, 0.0)
+    sh = (ctypes.c_int * 2)(10, 0)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    f = lib.qtt_decompose
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                  ctypes.c_int, ctypes.POINTER(Trunc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, f(None, QTT_C64, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["NULL"])
+    _expect(lib, f(p, 1, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["dtype"])
+    _expect(lib, f(p, QTT_C64, 3, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["ndim"])
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, None, None, ctypes.byref(out)), ["NULL"])
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(1.5, 0, 1, 0.0)), None,
+                   ctypes.byref(out)), ["eps"])
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 0, 1, 1.0)), None,
+                   ctypes.byref(out)), ["delta"])
+    _expect(lib, f(p, QTT_C64, 1, (ctypes.c_int * 2)(31, 0), 1, ctypes.byref(ok), None,
+                   ctypes.byref(out)), ["out of range"])
+    _expect(lib, f(p, QTT_C64, 1, (ctypes.c_int * 2)(1, 0), 1, ctypes.byref(ok), None,
+                   ctypes.byref(out)), ["d=1"])
+    assert not out.value
+
+
+def test_rsvd_arguments(lib, buf):
+    out = ctypes.c_void_p()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    f = lib.qtt_decompose_rsvd
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, f(p, QTT_C64, 10, 0, 4, None, 1, None, ctypes.byref(out)), ["rmax"])
+    _expect(lib, f(p, QTT_C64, 10, 64, 40, None, 1, None, ctypes.byref(out)), ["rmax + p"])
+    _expect(lib, f(p, QTT_C64, 10, 8, 0, None, 1, None, ctypes.byref(out)), ["p >= 1"])
+    _expect(lib, f(p, QTT_C64, 1, 8, 4, None, 1, None, ctypes.byref(out)), ["log2 length"])
+    assert not out.value
+
+
+def test_sinc_padded_arguments(lib, buf):
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    f = lib.qtt_sinc_padded
+    f.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    _expect(lib, f(10, 511, 64.0, 1, QTT_C64, None, None), ["NULL"])
+    _expect(lib, f(10, 510, 64.0, 1, QTT_C64, p, None), ["N odd"])      # even N
+    _expect(lib, f(10, 513, 64.0, 1, QTT_C64, p, None), ["N odd"])      # 2N - 1 > n
+    _expect(lib, f(10, 0, 64.0, 1, QTT_C64, p, None), ["N odd"])
+    _expect(lib, f(31, 511, 64.0, 1, QTT_C64, p, None), ["log2_n"])
+    _expect(lib, f(10, 511, 64.0, 1, 1, p, None), ["dtype"])
+
+
+def test_handle_entries_reject_null(lib, buf):
+    out = ctypes.c_void_p()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    lib.qtt_fft.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Trunc), ctypes.c_int,
+                            ctypes.c_ulonglong, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, lib.qtt_fft(None, 0, None, 0, 1, None, ctypes.byref(out)), ["qtt_fft", "NULL"])
+    lib.qtt_hadamard.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, lib.qtt_hadamard(None, None, None, ctypes.byref(out)), ["qtt_hadamard", "NULL"])
+    lib.qtt_to_full.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    _expect(lib, lib.qtt_to_full(None, p, None), ["qtt_to_full", "NULL"])
+    lib.qtt_conv_sinc.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                  ctypes.c_double, ctypes.POINTER(Trunc), ctypes.c_int,
+                                  ctypes.c_ulonglong, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, lib.qtt_conv_sinc(None, None, 1, 1e-7, None, 0, 1, None, ctypes.byref(out)),
+            ["qtt_conv_sinc", "NULL"])
+    assert not out.value
+
+
+def test_from_cores_and_operator_arguments(lib, buf):
+    out = ctypes.c_void_p()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    f = lib.qtt_from_cores
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                  ctypes.POINTER(ctypes.c_void_p)]
+    sh = (ctypes.c_int * 2)(4, 0)
+    _expect(lib, f(p, (ctypes.c_int * 5)(2, 2, 2, 2, 1), 4, QTT_C64, 1, sh, 1, None,
+                   ctypes.byref(out)), ["boundary ranks"])
+    _expect(lib, f(p, (ctypes.c_int * 5)(1, 2, 2, 2, 1), 4, QTT_C64, 1, (ctypes.c_int * 2)(5, 0), 1,
+                   None, ctypes.byref(out)), ["log2 shape"])
+    _expect(lib, f(p, (ctypes.c_int * 5)(1, 0, 2, 2, 1), 4, QTT_C64, 1, sh, 1, None,
+                   ctypes.byref(out)), ["rank"])
+    g = lib.qtt_op_create
+    g.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    _expect(lib, g(10, 0.0, 1, 1e-7, QTT_C64, None, ctypes.byref(out)), ["B > 0"])
+    _expect(lib, g(10, 64.0, 1, 0.0, QTT_C64, None, ctypes.byref(out)), ["eps_op"])
+    assert not out.value
