@@ -226,3 +226,31 @@ def conv_qtt_fft(F0, G0, rmax, rhat, eps_hat=0.0, delta=None, rsvd=None, interle
     if F0.ndim == 1:
         return v
     return Q.qtt_vector_to_image(v, ny, nx, interleave=interleave)
+
+
+def conv_qtt_fft_spread(F0, G0, rmax, rhat, ref, draws=3, rel=1e-7, seed=11):
+    """Sensitivity of ``conv_qtt_fft`` to FP32-sized errors (a check on how
+    well the capped rounding chain is conditioned, not a step of Alg. 2):
+    the largest relative l2 move of the result, over ``draws`` seeded runs,
+    when every core is multiplied by (1 + rel z), z complex standard normal,
+    before each TT-rounding of the route (the TT-SVDs and every transform
+    stage).  A GPU path computing in FP32 is compared with the FP64 route
+    within a multiple of this spread."""
+    rng = np.random.default_rng(seed)
+    plain = Q.tt_round
+
+    def perturbed(Y, eps, rm=None, delta=None):
+        Y = [c * (1 + rel * (rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)))
+             for c in Y]
+        return plain(Y, eps, rm, delta)
+
+    ref = np.asarray(ref)
+    spread = 0.0
+    Q.tt_round = perturbed
+    try:
+        for _ in range(draws):
+            out = conv_qtt_fft(F0, G0, rmax, rhat)
+            spread = max(spread, float(np.linalg.norm(out - ref) / np.linalg.norm(ref)))
+    finally:
+        Q.tt_round = plain
+    return spread

@@ -12,6 +12,7 @@
 // offset(q) = off_lo[q mod 2^a] + off_hi[q / 2^a] with two small tables.
 #include "qtt_internal.cuh"
 #include <algorithm>
+#include <atomic>
 
 namespace qtt {
 
@@ -213,46 +214,50 @@ __global__ void order64_kernel(const long long* tlo, int nlo_bits, int* order) {
   order[rk] = u;
 }
 
+// Cut of the Full split: the middle mode (even for an interleaved image, so
+// that each half holds whole (x, y) bit pairs).
+static int full_cut(const TensorDesc& desc) {
+  int a = desc.d / 2;
+  if (desc.ndim == 2 && desc.interleave) a &= ~1;
+  return a < 1 ? 1 : a;
+}
+
+// Scratch of one expansion: left/right partial products (double-buffered)
+// and the two offset tables.
 template <typename T>
-qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
+struct FullScratch {
+  T* Lb0;
+  T* Lb1;
+  T* Rb0;
+  T* Rb1;
+  long long* tlo;
+  long long* thi;
+  int* order;
+};
+
+// The launch sequence of Full on caller-provided scratch: left partial
+// X_1..X_a, right partial X_{a+1}..X_d, the two offset tables, the expansion.
+template <typename T>
+static qtt_status full_launch(const qtt_tensor* t, T* y, const FullScratch<T>& sc, cudaStream_t s) {
   const TensorDesc& desc = t->desc;
   const int d = desc.d;
   ModeMap mm = make_mode_map(desc);
-  int a = d / 2;
-  if (desc.ndim == 2 && desc.interleave) a &= ~1;
-  if (a < 1) a = 1;
+  const int a = full_cut(desc);
   const long long nlo = 1LL << a, nhi = 1LL << (d - a);
-  int rmaxcap = 1;
-  for (int c : t->rcap) rmaxcap = std::max(rmaxcap, c);
-  T* Lb0 = (T*)scratch_alloc(sizeof(T) * nlo * rmaxcap, s);
-  T* Lb1 = (T*)scratch_alloc(sizeof(T) * nlo * rmaxcap, s);
-  T* Rb0 = (T*)scratch_alloc(sizeof(T) * nhi * rmaxcap, s);
-  T* Rb1 = (T*)scratch_alloc(sizeof(T) * nhi * rmaxcap, s);
-  long long* tlo = (long long*)scratch_alloc(sizeof(long long) * nlo, s);
-  long long* thi = (long long*)scratch_alloc(sizeof(long long) * nhi, s);
-  int* order = (int*)scratch_alloc(sizeof(int) * 64, s);
-  if (!Lb0 || !Lb1 || !Rb0 || !Rb1 || !tlo || !thi || !order) {
-    scratch_free(Lb0, s); scratch_free(Lb1, s); scratch_free(Rb0, s); scratch_free(Rb1, s);
-    scratch_free(tlo, s); scratch_free(thi, s); scratch_free(order, s);
-    set_error("to_full: scratch allocation failed");
-    return QTT_ENOMEM;
-  }
   const T* cores = (const T*)t->cores;
-  // left partial
   T* Lcur = nullptr;
   for (int k = 1; k <= a; ++k) {
-    T* Lnext = (k & 1) ? Lb0 : Lb1;
+    T* Lnext = (k & 1) ? sc.Lb0 : sc.Lb1;
     const long long tot = (1LL << (k - 1)) * 2 * t->rcap[k];
     QTT_PROF("full_partials", s);
     left_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(Lcur, cores + t->off[k - 1],
                                                                      t->ranks, k, t->rcap[k], Lnext);
     Lcur = Lnext;
   }
-  // right partial
   T* Rcur = nullptr;
   int ldcur = 0;
   for (int k = d; k >= a + 1; --k) {
-    T* Rnext = ((d - k) & 1) ? Rb1 : Rb0;
+    T* Rnext = ((d - k) & 1) ? sc.Rb1 : sc.Rb0;
     const int ldo = t->rcap[k - 1];
     const long long tot = (long long)ldo << (d - k + 1);
     QTT_PROF("full_partials", s);
@@ -261,21 +266,55 @@ qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
     Rcur = Rnext;
     ldcur = ldo;
   }
-  offset_table_kernel<<<(int)((nlo + 255) / 256), 256, 0, s>>>(mm, 0, a, tlo);
-  offset_table_kernel<<<(int)((nhi + 255) / 256), 256, 0, s>>>(mm, a, d - a, thi);
-  order64_kernel<<<1, 64, 0, s>>>(tlo, a, order);
+  {
+    QTT_PROF("full_partials", s);
+    offset_table_kernel<<<(int)((nlo + 255) / 256), 256, 0, s>>>(mm, 0, a, sc.tlo);
+    offset_table_kernel<<<(int)((nhi + 255) / 256), 256, 0, s>>>(mm, a, d - a, sc.thi);
+    order64_kernel<<<1, 64, 0, s>>>(sc.tlo, a, sc.order);
+  }
   dim3 grid((unsigned)((nlo + FX_TL - 1) / FX_TL), (unsigned)((nhi + FX_TH - 1) / FX_TH));
-  QTT_PROF("full_expand", s);
-  expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, tlo, thi, order,
-                                        y);
-  scratch_free(Lb0, s);
-  scratch_free(Lb1, s);
-  scratch_free(Rb0, s);
-  scratch_free(Rb1, s);
-  scratch_free(tlo, s);
-  scratch_free(thi, s);
-  scratch_free(order, s);
+  {
+    QTT_PROF("full_expand", s);
+    expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, sc.tlo, sc.thi,
+                                          sc.order, y);
+  }
   return cuda_check(cudaGetLastError(), "to_full launch");
+}
+
+template <typename T>
+static int full_rank_cap(const qtt_tensor* t) {
+  int r = 1;
+  for (int c : t->rcap) r = std::max(r, c);
+  return r;
+}
+
+template <typename T>
+qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s) {
+  const int d = t->desc.d;
+  const int a = full_cut(t->desc);
+  const long long nlo = 1LL << a, nhi = 1LL << (d - a);
+  const int rmaxcap = full_rank_cap<T>(t);
+  FullScratch<T> sc;
+  sc.Lb0 = (T*)scratch_alloc(sizeof(T) * nlo * rmaxcap, s);
+  sc.Lb1 = (T*)scratch_alloc(sizeof(T) * nlo * rmaxcap, s);
+  sc.Rb0 = (T*)scratch_alloc(sizeof(T) * nhi * rmaxcap, s);
+  sc.Rb1 = (T*)scratch_alloc(sizeof(T) * nhi * rmaxcap, s);
+  sc.tlo = (long long*)scratch_alloc(sizeof(long long) * nlo, s);
+  sc.thi = (long long*)scratch_alloc(sizeof(long long) * nhi, s);
+  sc.order = (int*)scratch_alloc(sizeof(int) * 64, s);
+  auto release = [&]() {
+    scratch_free(sc.Lb0, s); scratch_free(sc.Lb1, s); scratch_free(sc.Rb0, s);
+    scratch_free(sc.Rb1, s); scratch_free(sc.tlo, s); scratch_free(sc.thi, s);
+    scratch_free(sc.order, s);
+  };
+  if (!sc.Lb0 || !sc.Lb1 || !sc.Rb0 || !sc.Rb1 || !sc.tlo || !sc.thi || !sc.order) {
+    release();
+    set_error("to_full: scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  const qtt_status st = full_launch<T>(t, y, sc, s);
+  release();
+  return st;
 }
 template qtt_status tt_full<double>(const qtt_tensor*, double*, cudaStream_t);
 template qtt_status tt_full<float2>(const qtt_tensor*, float2*, cudaStream_t);
@@ -292,11 +331,13 @@ constexpr size_t FULL_NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_full_noalloc_scratch[FULL_NOALLOC_SCRATCH_BYTES];
 
 static constexpr int NOALLOC_MAX_DEVICES = 64;
-static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+static std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
 // Device address of the scratch array on the current device (looked up once
 // per device with that device current; the host-side symbol is only a
-// stand-in and must never be passed to a kernel).
+// stand-in and must never be passed to a kernel).  The cache entries are
+// atomic, so host threads making their first calls at the same time are
+// safe (each may look the address up; all store the same value).
 static qtt_status noalloc_scratch_ptr(void** out) {
   int dev = 0;
   qtt_status st = cuda_check(cudaGetDevice(&dev), "to_full_noalloc: cudaGetDevice");
@@ -305,14 +346,14 @@ static qtt_status noalloc_scratch_ptr(void** out) {
     set_error("to_full_noalloc: device index %d not supported", dev);
     return QTT_EUNSUPPORTED;
   }
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
+  void* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
     st = cuda_check(cudaGetSymbolAddress(&p, g_full_noalloc_scratch),
                     "to_full_noalloc: cudaGetSymbolAddress");
     if (st != QTT_OK) return st;
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return QTT_OK;
 }
 
@@ -320,15 +361,10 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename T>
 static qtt_status tt_full_noalloc_t(const qtt_tensor* t, T* y, cudaStream_t s) {
-  const TensorDesc& desc = t->desc;
-  const int d = desc.d;
-  ModeMap mm = make_mode_map(desc);
-  int a = d / 2;
-  if (desc.ndim == 2 && desc.interleave) a &= ~1;
-  if (a < 1) a = 1;
+  const int d = t->desc.d;
+  const int a = full_cut(t->desc);
   const long long nlo = 1LL << a, nhi = 1LL << (d - a);
-  int rmaxcap = 1;
-  for (int c : t->rcap) rmaxcap = std::max(rmaxcap, c);
+  const int rmaxcap = full_rank_cap<T>(t);
   const size_t lb = align256(sizeof(T) * (size_t)nlo * rmaxcap);
   const size_t rb = align256(sizeof(T) * (size_t)nhi * rmaxcap);
   const size_t tl = align256(sizeof(long long) * (size_t)nlo);
@@ -343,48 +379,24 @@ static qtt_status tt_full_noalloc_t(const qtt_tensor* t, T* y, cudaStream_t s) {
   qtt_status st = noalloc_scratch_ptr(&base);
   if (st != QTT_OK) return st;
   char* p = (char*)base;
-  T* Lb0 = (T*)p; p += lb;
-  T* Lb1 = (T*)p; p += lb;
-  T* Rb0 = (T*)p; p += rb;
-  T* Rb1 = (T*)p; p += rb;
-  long long* tlo = (long long*)p; p += tl;
-  long long* thi = (long long*)p; p += th;
-  int* order = (int*)p;
-  // Every scratch element that is read below is first written in this call,
-  // so nothing has to be cleared between calls.
-  const T* cores = (const T*)t->cores;
-  T* Lcur = nullptr;
-  for (int k = 1; k <= a; ++k) {
-    T* Lnext = (k & 1) ? Lb0 : Lb1;
-    const long long tot = (1LL << (k - 1)) * 2 * t->rcap[k];
-    left_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(Lcur, cores + t->off[k - 1],
-                                                                     t->ranks, k, t->rcap[k], Lnext);
-    Lcur = Lnext;
-  }
-  T* Rcur = nullptr;
-  int ldcur = 0;
-  for (int k = d; k >= a + 1; --k) {
-    T* Rnext = ((d - k) & 1) ? Rb1 : Rb0;
-    const int ldo = t->rcap[k - 1];
-    const long long tot = (long long)ldo << (d - k + 1);
-    right_partial_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(
-        Rcur, ldcur, cores + t->off[k - 1], t->ranks, k, d, ldo, Rnext);
-    Rcur = Rnext;
-    ldcur = ldo;
-  }
-  offset_table_kernel<<<(int)((nlo + 255) / 256), 256, 0, s>>>(mm, 0, a, tlo);
-  offset_table_kernel<<<(int)((nhi + 255) / 256), 256, 0, s>>>(mm, a, d - a, thi);
-  order64_kernel<<<1, 64, 0, s>>>(tlo, a, order);
-  dim3 grid((unsigned)((nlo + FX_TL - 1) / FX_TL), (unsigned)((nhi + FX_TH - 1) / FX_TH));
-  expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, tlo, thi, order,
-                                        y);
-  return cuda_check(cudaGetLastError(), "to_full_noalloc launch");
+  FullScratch<T> sc;
+  sc.Lb0 = (T*)p; p += lb;
+  sc.Lb1 = (T*)p; p += lb;
+  sc.Rb0 = (T*)p; p += rb;
+  sc.Rb1 = (T*)p; p += rb;
+  sc.tlo = (long long*)p; p += tl;
+  sc.thi = (long long*)p; p += th;
+  sc.order = (int*)p;
+  // Every scratch element that is read is first written in this call, so
+  // nothing has to be cleared between calls.
+  return full_launch<T>(t, y, sc, s);
 }
 
 }  // namespace qtt
 
 extern "C" qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* stream) {
   using namespace qtt;
+  clear_error();
   if (!t || !y) {
     set_error("qtt_to_full_noalloc: NULL argument");
     return QTT_EINVAL;
@@ -394,6 +406,3 @@ extern "C" qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* st
   return tt_full_noalloc_t<float2>(t, (float2*)y, s);
 }
 
-namespace qtt {
-
-}  // namespace qtt

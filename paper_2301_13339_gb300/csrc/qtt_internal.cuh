@@ -203,6 +203,7 @@ namespace qtt {
 
 size_t elem_size(qtt_dtype dt);
 void set_error(const char* fmt, ...);
+void clear_error();   // empty the thread-local message (start of an entry point)
 qtt_status cuda_check(cudaError_t e, const char* what);
 
 // capacities: r_k <= min(2^k, 2^(d-k), rmax, cap)

@@ -13,22 +13,19 @@
   against the oracle's Sec. 2 padding);
 * argument errors: a real handle, an interleaved layout with unequal axes.
 
-These tests have not yet run on a GPU: they are opt-in
-(QTT_GPU_FFT_TESTS=1) until their first run confirms them.
+The Alg. 2 parity bound is derived from the oracle's own conditioning: a
+chain of 3d roundings capped at R^_max amplifies small perturbations of the
+cores, so the test first measures how far the oracle's result moves when
+every core is perturbed by a relative 1e-7 (about one FP32 rounding) before
+each rounding, and allows ten times that spread (at least 1e-5).
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import conv as C, qfft as QF, qtt as Q
 import synth
 
-pytestmark = [
-    pytest.mark.gpu,
-    pytest.mark.skipif(os.environ.get("QTT_GPU_FFT_TESTS") != "1",
-                       reason="QTT-FFT GPU path not yet confirmed on a GPU (QTT_GPU_FFT_TESTS=1)"),
-]
+pytestmark = pytest.mark.gpu
 
 
 def _random_qtt(rng, d, r):
@@ -117,16 +114,20 @@ def test_hadamard(qlib, dtype):
 def test_alg2_example_parity(qlib, example, K):
     """Alg. 2 on a Sec. 7 example at 2^K: the CUDA path (qtt_decompose with
     R_max = 10, qtt_conv_fft with R^_max = 15) against the oracle's route on
-    the same noisy input."""
+    the same noisy input, within ten times the oracle's own spread under
+    FP32-sized perturbations of every stage (at least 1e-5)."""
     import torch
     noisy, clean, N, B = synth.paper_example_1d(example, K, synth.config_rng(5, sub=example))
     n = 2 ** K
-    ref = QF.conv_qtt_fft(noisy, QF.padded_kernel(C.sinc_taps(n, B), N, n), 10, 15)
+    g = QF.padded_kernel(C.sinc_taps(n, B), N, n)
+    ref = QF.conv_qtt_fft(noisy, g, 10, 15)
+    tol = max(1e-5, 10.0 * QF.conv_qtt_fft_spread(noisy, g, 10, 15, ref))
     g_dev = qlib.qtt_sinc_padded(K, N, B)               # the library's own kernel samples
     F = qlib.qtt_decompose(torch.from_numpy(noisy.astype(np.complex64)).cuda(), 0.0, 10, refine=True)
     G = qlib.qtt_decompose(g_dev, 0.0, 10, refine=True)
     got = _full(qlib, qlib.qtt_conv_fft(F, G, rhat=15))
-    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    assert tol <= 1e-4
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
 
 
 @pytest.mark.parametrize("K,B,normalize", [(8, 64.0, True), (12, 1024.0, True), (10, 37.5, False)])

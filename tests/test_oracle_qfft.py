@@ -290,3 +290,21 @@ def test_table_6_1_tt_rsvd(example):
     e_q = _e2(QF.linear_part(QF.conv_qtt_fft(noisy, g0, 10, 15), N), itrue)
     assert e_q < e_r < _e2(ixi, itrue)
     assert e_r_p / 2 <= e_r <= 2 * e_r_p, e_r
+
+
+def test_spread_helper_is_zero_without_perturbation_and_restores_rounding():
+    """conv_qtt_fft_spread: no perturbation, no spread; a 1e-7 one moves the
+    capped route by far less than its own truncation, and the rounding the
+    route uses is the plain one again afterwards."""
+    from oracle import qtt as Q
+    rng = np.random.default_rng(2)
+    K = 8
+    n = 2 ** K
+    f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    g = QF.padded_kernel(C.sinc_taps(n, 16.0), 2 ** (K - 1) - 1, n)
+    plain = Q.tt_round
+    ref = QF.conv_qtt_fft(f, g, 6, 8)
+    assert QF.conv_qtt_fft_spread(f, g, 6, 8, ref, draws=1, rel=0.0) == 0.0
+    s = QF.conv_qtt_fft_spread(f, g, 6, 8, ref, draws=2)
+    assert 0.0 < s < 1e-3
+    assert Q.tt_round is plain

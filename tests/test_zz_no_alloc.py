@@ -26,16 +26,20 @@ def _rand_cores(rng, d, r, dtype):
     return out
 
 
-@pytest.mark.parametrize("dtype,shape,tol", [(np.complex64, [14], 1e-5), (np.float64, [12], 1e-12),
-                                             (np.complex64, [6, 6], 1e-5)])
-def test_to_full_noalloc_matches_to_full(qlib, dtype, shape, tol):
+@pytest.mark.parametrize("dtype,shape,interleave,tol", [
+    (np.complex64, [14], True, 1e-5), (np.float64, [12], True, 1e-12),
+    (np.complex64, [6, 6], True, 1e-5), (np.complex64, [5, 7], False, 1e-5),
+    (np.float64, [6, 6], True, 1e-12), (np.float64, [6, 5], False, 1e-12)])
+def test_to_full_noalloc_matches_to_full(qlib, dtype, shape, interleave, tol):
     import torch
     rng = np.random.default_rng(17)
     d = sum(shape)
     first = None
-    for call in range(2):
-        cores = _rand_cores(rng, d, 16 + 8 * call, dtype)
-        t = qlib.qtt_from_cores(cores, shape, interleave=True)
+    # the first call writes the larger rank, so a stale read of a column past
+    # the second call's rank would show in the second result
+    for call, r in enumerate((32, 8)):
+        cores = _rand_cores(rng, d, r, dtype)
+        t = qlib.qtt_from_cores(cores, shape, interleave=interleave)
         ref = qlib.qtt_to_full(t)
         out = torch.full_like(ref, float("nan"))
         qlib.qtt_to_full_noalloc(t, out)
@@ -63,3 +67,9 @@ def test_to_full_noalloc_rejects_oversize(qlib):
                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == -1                                  # QTT_EINVAL
     assert b"static limit" in qlib.lib().qtt_last_error()
+    # a successful call afterwards leaves no stale message behind
+    small = qlib.qtt_from_cores([c[:1, :, :1] for c in cores[:4]], [4])
+    out2 = torch.empty(16, dtype=torch.complex64, device="cuda")
+    qlib.qtt_to_full_noalloc(small, out2)
+    torch.cuda.synchronize()
+    assert qlib.lib().qtt_last_error() == b""
