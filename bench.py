@@ -53,6 +53,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    # the 4096 x 4096 complex64 SAR-like image: 200 point scatterers + 5
+    # rectangles, complex noise at 10 dB, separable sinc B_x = B_y = 256,
+    # bit-interleaved QTT, TT-SVD eps = 3e-2 with R_max = 64; the convolved
+    # image needs ranks of a few hundred, so the rounding runs in its
+    # large-rank mode (sketch rank 384)
+    "image_4096sq_c64": dict(kind="image", dy=12, dx=12, B=256.0, rmax=64, eps=3e-2,
+                             eps_op=1e-7, eps_round=1e-7, sketch=384, nscat=200, nrect=5,
+                             snr_db=10.0, tol=1e-5, crop=10),
     "line_2p20_c64": dict(d=20, B=1024.0, rmax=64, eps=0.0, eps_op=1e-7, eps_round=1e-7,
                           nscat=50, nbumps=3, snr_db=20.0, tol=1e-5),
     # the same line with the max rank TT-RSVD (Sec. 5 modification (2)), p = 8,
@@ -82,17 +90,36 @@ def max_over_ranks(values, device):
     return [float(v) for v in t.cpu()]
 
 
-def _peaks():
+def _peaks(dev=None):
+    """Measured peaks (MEASURED_PEAKS.json, else the fallback figures), plus
+    the SM count read from the device when one is given."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return json.load(fh), "measured"
+            pk, kind = json.load(fh), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-                "sm_max_mhz": 2070.0}, "fallback"
+        pk, kind = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                    "sm_max_mhz": 2070.0}, "fallback"
+    if dev is not None:
+        import torch
+        pk["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
+    return pk, kind
+
+
+def _is_image(wl):
+    return wl.get("kind") == "image"
+
+
+def _samples(wl):
+    return 2 ** (wl["dy"] + wl["dx"]) if _is_image(wl) else 2 ** wl["d"]
 
 
 def make_input(wl, rank=0):
     import synth
+    if _is_image(wl):
+        rng = synth.config_rng(2, sub=rank if rank else None)
+        x, clean = synth.image_2d_scene(rng, 2 ** wl["dy"], 2 ** wl["dx"], nscat=wl["nscat"],
+                                        nrect=wl["nrect"], snr_db=wl["snr_db"])
+        return x.astype(np.complex64), clean
     rng = synth.config_rng(1, sub=rank if rank else None)
     x, clean = synth.line_1d_scatterers(rng, 2 ** wl["d"], nscat=wl["nscat"],
                                         nbumps=wl["nbumps"], snr_db=wl["snr_db"])
@@ -110,6 +137,13 @@ def rsvd_omega(wl):
 def run_oracle(x, wl):
     from oracle import pipeline as P
     t0 = time.perf_counter()
+    if _is_image(wl):
+        # O1: the TT-SVD (Alg. 1, interleaved bits) of the image, Full, and
+        # the dense separable convolution of Eq. dconv (FFT); the textbook
+        # rounding of the 2D operator product is beyond the host at this size
+        cores, _, _ = P.decompose(x.astype(np.complex128), wl["eps"], wl["rmax"], True)
+        out = P.conv_dense(P.to_array(cores, x.shape, True), wl["B"])
+        return out, time.perf_counter() - t0
     if wl.get("rsvd_p"):
         from oracle import rsvd as RS
         _, omega = rsvd_omega(wl)
@@ -193,16 +227,17 @@ def gpu_arm(args, wl):
     q.load()
     L = q.lib()
     stream = torch.cuda.Stream(device=dev)
-    N = 2 ** wl["d"]
+    N = _samples(wl)
     x, clean = make_input(wl, rank)
     xd = torch.from_numpy(x).to(dev)
+    Bconv = [wl["B"], wl["B"]] if _is_image(wl) else wl["B"]
     # operator plan (built once per (n, B, eps_op); reported apart from the steps)
     torch.cuda.synchronize(dev)
     t_plan = time.perf_counter()
-    q.qtt_op_create(wl["d"], wl["B"], True, wl["eps_op"], q.QTT_C64)
+    q.qtt_op_create(wl["dx"] if _is_image(wl) else wl["d"], wl["B"], True, wl["eps_op"], q.QTT_C64)
     torch.cuda.synchronize(dev)
     plan_ms = 1e3 * (time.perf_counter() - t_plan)
-    out = torch.empty(N, dtype=torch.complex64, device=dev)
+    out = torch.empty(x.shape, dtype=torch.complex64, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     refine = args.refine
     om_dev = None
@@ -214,8 +249,8 @@ def gpu_arm(args, wl):
             f = q.qtt_decompose_rsvd(xin, wl["rmax"], wl["rsvd_p"], omega=om_dev, stream=s)
         else:
             f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s)
-        y = q.qtt_conv_sinc(f, wl["B"], eps_op=wl["eps_op"], eps_round=wl["eps_round"],
-                            refine=True, sketch=0, stream=s)
+        y = q.qtt_conv_sinc(f, Bconv, eps_op=wl["eps_op"], eps_round=wl["eps_round"],
+                            refine=True, sketch=wl.get("sketch", 0), stream=s)
         q.qtt_to_full(y, out=dst, stream=s)
         f.free(stream=s)
         y.free(stream=s)
@@ -250,7 +285,7 @@ def gpu_arm(args, wl):
 
     # ---- e2e through the C ABI with host buffers
     xh = torch.from_numpy(x).pin_memory()
-    oh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    oh = torch.empty(x.shape, dtype=torch.complex64).pin_memory()
     xdev2 = torch.empty_like(xd)
     eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -289,9 +324,16 @@ def gpu_arm(args, wl):
     cnt = (ctypes.c_int * cap)()
     nk = L.qtt_profile_read(names, stride, ms, cnt, cap)
     kern = {}
+    L.qtt_profile_work.restype = ctypes.c_int
+    L.qtt_profile_work.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
     for i in range(nk):
         nm = names.raw[i * stride:(i + 1) * stride].split(b"\0")[0].decode()
         kern[nm] = {"ms_per_step": ms[i] / args.steps, "launches_per_step": cnt[i] / args.steps}
+        fl, by = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        if L.qtt_profile_work(nm.encode(), ctypes.byref(fl), ctypes.byref(by)):
+            kern[nm]["flops_per_step"] = fl.value / args.steps
+            kern[nm]["bytes_per_step"] = by.value / args.steps
     L.qtt_profile_reset()
     out_host = out.cpu().numpy()
     return dict(world=world, rank=rank, total_ms=total_ms, e2e_ms=e2e_ms, wall_s=t_wall,
@@ -299,45 +341,47 @@ def gpu_arm(args, wl):
                 plan_ms=plan_ms)
 
 
-# DRAM bytes (read + write) per launch from the committed ncu captures in
-# profiles/ (heev_tri_kernel_n128_line_2p20_c64.md: heev_tri_kernel +
-# heev_back_kernel; jacobi_dm_kernel_n128_line_2p20_c64.md); valid while
-# those kernels are unchanged.
-NCU_TRAFFIC = {"heev_le128": 354816.0 + 182272.0, "jacobi_eig_le128": 177920.0}
-
-
 def roofline(kernels, wl, peaks, peak_kind):
-    """Dominant kernel's achieved rate against its bound."""
+    """Dominant kernel's achieved rate against its bound.  Algorithmic work
+    per launch: what the library records at the launch site while profiling
+    (qtt_profile_work: GEMM flops, streamed unfolding bytes, output bytes),
+    else the closed forms below."""
     if not kernels:
         return None
     name = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     kinfo = kernels[name]
-    avg_ms = kinfo["ms_per_step"] / max(kinfo["launches_per_step"], 1e-9)
+    nl = max(kinfo["launches_per_step"], 1e-9)
+    avg_ms = kinfo["ms_per_step"] / nl
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # FP32 CUDA-core peak of the whole GPU: 152 SMs x 128 FMA/clk x 2 flop
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    N = 2 ** wl["d"]
+    nsm = peaks["sm_count"]
+    # FP32 CUDA-core peak of the whole GPU: SMs x 128 FMA/clk x 2 flop
+    fp32_peak_tflops = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
     if name.startswith("jacobi_eig") or name.startswith("heev"):
         # one complex Hermitian eigen-decomposition of an n x n Gram per
         # launch (n = 2 R_max at the capped levels); algorithmic work counted
         # as LAPACK's ~9 n^3 real flop per real eigen-decomposition with
         # vectors, x4 for complex arithmetic.  The kernel runs on one SM, so
-        # its peak is one SM's FP32 rate; the whole-GPU fraction is frac/152.
+        # its peak is one SM's FP32 rate; the whole-GPU fraction is frac/SMs.
         import re
         m = re.search(r"le(\d+)", name)
         n = min(2 * wl["rmax"], int(m.group(1))) if m else 2 * wl["rmax"]
         flops = 9 * n ** 3 * 4
         ach = flops / (avg_ms * 1e-3) / 1e12
-        sm_peak = fp32_peak_tflops / 152
+        sm_peak = fp32_peak_tflops / nsm
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": sm_peak,
-                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": NCU_TRAFFIC.get(name),
+                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
                 "avg_launch_ms": avg_ms, "frac_of_gpu": ach / fp32_peak_tflops,
                 "peak_source": f"one SM: 128 FP32 FMA/clk at {sm_mhz:.0f} MHz (single-CTA kernels; "
                                "the back-transformation of heev uses 8 SMs for ~7 % of its time)"}
-    if name in ("proj_gram", "full_expand", "morton_gather"):
-        # algorithmic bytes: every launch streams its input unfolding once
-        bytes_per_launch = 8.0 * N * 2 / max(kinfo["launches_per_step"], 1)
-        ach = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    if kinfo.get("flops_per_step") and kinfo["flops_per_step"] > 0 and name not in ("full_expand",):
+        ach = kinfo["flops_per_step"] / nl / (avg_ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "traffic": None,
+                "avg_launch_ms": avg_ms,
+                "peak_source": f"FP32 CUDA cores: {nsm} SMs x 128 FMA/clk at {sm_mhz:.0f} MHz "
+                               "(complex multiply-add = 8 flop)"}
+    if kinfo.get("bytes_per_step"):
+        ach = kinfo["bytes_per_step"] / nl / (avg_ms * 1e-3) / 1e9
         pk = peaks["hbm_gbs"]
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
                 "frac": ach / pk, "traffic": None, "avg_launch_ms": avg_ms,
@@ -836,7 +880,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="line_2p20_c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="image_4096sq_c64", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
@@ -857,11 +901,18 @@ def main():
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
         batch_main(args, wl, metric)
         return
-    N = 2 ** wl["d"]
+    N = _samples(wl)
     config = {"workload": args.workload, "samples_per_line": N, "dtype_in": "complex64",
               "B": wl["B"], "rmax": wl["rmax"], "eps": wl["eps"], "eps_op": wl["eps_op"],
               "eps_round": wl["eps_round"], "snr_db": wl["snr_db"],
               "l2": "flushed (512 MiB write) before every timed step, outside the timed region"}
+    if _is_image(wl):
+        config.update({"shape": [2 ** wl["dy"], 2 ** wl["dx"]], "qtt_order": "bit-interleaved",
+                       "B": [wl["B"], wl["B"]], "sketch": wl["sketch"],
+                       "rounding": "large-rank mode (randomised range finder at the sketch rank)",
+                       "nscat": wl["nscat"], "nrect": wl["nrect"]})
+        config.pop("samples_per_line")
+        config["samples_per_image"] = N
     if wl.get("rsvd_p"):
         config["decomposition"] = f"max rank TT-RSVD, p = {wl['rsvd_p']}"
 
@@ -870,14 +921,26 @@ def main():
         if rank != 0:
             return
         x, _ = make_input(wl)
+        owl, sample = wl, f"one full line (2^{wl.get('d')} samples) per step"
+        Ns = N
+        if _is_image(wl):
+            # bounded sample: the top-left 2^crop x 2^crop crop of the image,
+            # with B scaled so that the kernel keeps its width in samples
+            c = wl["crop"]
+            owl = dict(wl, dy=c, dx=c, B=wl["B"] * 2 ** (c - wl["dx"]))
+            x = np.ascontiguousarray(x[:2 ** c, :2 ** c])
+            Ns = x.size
+            sample = (f"the top-left {2 ** c} x {2 ** c} crop of the image per step (B = "
+                      f"{owl['B']:g}, same kernel width in samples): the oracle's TT-SVD + the "
+                      "dense separable convolution (FFT)")
         for _ in range(args.warmup):
-            run_oracle(x, wl)
+            run_oracle(x, owl)
         ts = []
         for _ in range(args.steps):
-            _, t = run_oracle(x, wl)
+            _, t = run_oracle(x, owl)
             ts.append(t)
         tot = sum(ts)
-        v = N * args.steps / tot / 1e6
+        v = Ns * args.steps / tot / 1e6
         cores = len(os.sched_getaffinity(0))
         line = {"impl": "reference", "metric": metric, "value": v, "unit": "Msamples/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -885,8 +948,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config,
                 "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cores,
-                                 "kind": "oracle",
-                                 "sample": f"one full line (2^{wl['d']} samples) per step"},
+                                 "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -896,7 +958,7 @@ def main():
     world, rank = res["world"], res["rank"]
     if rank != 0:
         return
-    peaks, peak_kind = _peaks()
+    peaks, peak_kind = _peaks(res["dev"])
     value = world * N * args.steps / (res["total_ms"] * 1e-3) / 1e6
     e2e = world * N * args.steps / (res["e2e_ms"] * 1e-3) / 1e6
     kern = res["kernels"]
@@ -925,8 +987,13 @@ def main():
     if not args.no_cpu_baseline:
         ref, t = run_oracle(res["x"], wl)
         from oracle import conv as C
-        e2 = C.rel_l2(res["out"].astype(np.complex128), ref)
-        line["parity"] = {"e2_vs_oracle": e2, "tol": wl["tol"], "ok": bool(e2 <= wl["tol"])}
+        got = res["out"].astype(np.complex128)
+        e2 = C.rel_l2(got, ref)
+        emax = float(np.abs(got - ref).max() / np.abs(ref).max())
+        line["parity"] = {"e2_vs_oracle": e2, "tol": wl["tol"], "ok": bool(e2 <= wl["tol"]),
+                          "max_abs_err_over_max_abs_ref": emax,
+                          "oracle": ("O1: the oracle's TT-SVD + dense separable convolution"
+                                     if _is_image(wl) else "O2: the oracle's textbook QTT chain")}
         # the paper's denoising metric: E2 against the noise-free convolution
         from oracle import pipeline as P
         ref_clean = P.conv_dense(res["clean"], wl["B"])
@@ -934,7 +1001,10 @@ def main():
         line["e2_noisy_input_vs_noise_free"] = C.rel_l2(P.conv_dense(res["x"].astype(np.complex128), wl["B"]), ref_clean)
         line["cpu_baseline"] = {"value": N / t / 1e6, "unit": "Msamples/s",
                                 "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                                "sample": f"one full line (2^{wl['d']} samples), numpy FP64"}
+                                "sample": (f"the full {res['x'].shape[0]} x {res['x'].shape[1]} image once "
+                                           "(the parity run: TT-SVD + dense separable convolution), "
+                                           "numpy FP64" if _is_image(wl) else
+                                           f"one full line (2^{wl['d']} samples), numpy FP64")}
     print(json.dumps(line))
 
 

@@ -76,8 +76,14 @@ typedef struct {
   double delta;
 } qtt_trunc;
 
-/* Largest TT rank any handle can hold (capacity of the per-cut Jacobi). */
+/* Largest TT rank of a decomposition or of an eps-truncated rounding
+ * (capacity of the one-CTA eigen-solvers behind every rank decision). */
 #define QTT_RANK_CAP 64
+
+/* Largest sketch rank of the large-rank rounding mode (sketch >
+ * QTT_RANK_CAP, complex64 only; see qtt_conv_sinc): its range finder factors
+ * matrices of up to 2 x QTT_SKETCH_CAP_BIG rows by blocked Householder QR. */
+#define QTT_SKETCH_CAP_BIG 384
 
 typedef struct qtt_tensor qtt_tensor;
 typedef struct qtt_op qtt_op;
@@ -129,7 +135,16 @@ qtt_status qtt_decompose_rsvd(const void* x, qtt_dtype dt, int log2_len, int rma
  *   eps_op     accuracy of the operator's generating vector QTT.
  *   round_tr   truncation of the rounding (eps_round, R_round cap, refine).
  *   sketch     rank of the random sketch used by the rounding (>= the
- *              rounded rank + oversampling; <= QTT_RANK_CAP).  <= 0: default.
+ *              rounded rank + oversampling).  <= 0: QTT_RANK_CAP.
+ *              QTT_RANK_CAP < sketch <= QTT_SKETCH_CAP_BIG (complex64 only)
+ *              selects the large-rank mode for products whose eps-ranks
+ *              exceed QTT_RANK_CAP (2D images): the randomised range finder
+ *              of the rounding alone, without its truncation sweep, so the
+ *              result has the fixed ranks min(sketch, 2^k, 2^(d-k), P_k r_k)
+ *              and round_tr's eps / rmax / delta are not applied; its error
+ *              is that of the range finder (close to the best approximation
+ *              at those ranks less the oversampling).  Larger sketch:
+ *              QTT_EINVAL; a float64 tensor: QTT_EUNSUPPORTED.
  *   seed       seed of the sketch's counter-based generator.
  * Operators are built on first use and cached per (n, B, normalize, eps_op,
  * dtype); building synchronises the stream once.  out: new handle. */
@@ -362,6 +377,13 @@ qtt_status qtt_hadamard(const qtt_tensor* x, const qtt_tensor* y, void* stream, 
 void qtt_profile_enable(int on);
 int qtt_profile_read(char* names, int name_stride, double* ms, int* counts, int cap);
 void qtt_profile_reset(void);
+/* Algorithmic work recorded while profiling was on, summed over the launches
+ * of kernel `name` (the same names as qtt_profile_read): *flops = arithmetic
+ * operations the method needs (complex multiply-add = 8), *bytes = the
+ * operand bytes the launch has to move at least.  Returns 1 if the name
+ * recorded any, else 0 (outputs untouched).  Launch sites without a
+ * closed-form count record nothing. */
+int qtt_profile_work(const char* name, double* flops, double* bytes);
 
 /* qtt_small_eigh -- the one-CTA Hermitian eigen-decomposition behind every
  * truncation (Alg. 1 "compute truncated SVD", done as eigen-decomposition of

@@ -20,7 +20,7 @@ __all__ = [
     "QTTError", "QTTTensor", "QTTOperator", "lib", "load", "qtt_decompose", "qtt_conv_sinc",
     "qtt_round", "qtt_to_full", "qtt_to_full_noalloc", "qtt_conv_adjoint", "qtt_matvec",
     "qtt_op_create",
-    "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "EXPORTED_SYMBOLS",
+    "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "QTT_SKETCH_CAP_BIG", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
     "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd", "qtt_fft",
     "qtt_hadamard", "qtt_conv_fft", "qtt_sinc_padded",
@@ -29,6 +29,7 @@ __all__ = [
 QTT_F64 = 0
 QTT_C64 = 2
 QTT_RANK_CAP = 64
+QTT_SKETCH_CAP_BIG = 384
 
 _STATUS = {0: "QTT_OK", -1: "QTT_EINVAL", -2: "QTT_ENOMEM", -3: "QTT_ECUDA",
            -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED", -7: "QTT_ENUMERIC"}
@@ -39,6 +40,7 @@ EXPORTED_SYMBOLS = [
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
+    "qtt_profile_work",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",

@@ -17,6 +17,13 @@ static thread_local char g_err[512] = "";
 
 void clear_error() { g_err[0] = 0; }
 
+bool first_on_device(std::atomic<unsigned long long>* flags) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  return (flags->fetch_or(bit) & bit) == 0;
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

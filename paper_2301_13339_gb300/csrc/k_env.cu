@@ -229,12 +229,9 @@ static qtt_status env_sweep_t(const qtt_tensor* f, const qtt_tensor* w, double a
     A.Est = (T*)scratch_alloc(sizeof(T) * (size_t)d * A.ecap, s);
     if (!A.Est) { set_error("environment sweep: scratch"); return QTT_ENOMEM; }
   }
-  static bool cfg[2] = {false, false};
-  const int ti = Sc<T>::cplx ? 1 : 0;
-  if (!cfg[ti]) {
+  static std::atomic<unsigned long long> cfg{0};
+  if (first_on_device(&cfg))
     cudaFuncSetAttribute(env_sweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cfg[ti] = true;
-  }
   {
     QTT_PROF(grad ? "env_grads" : "env_dot", s);
     env_sweep_kernel<T><<<1, ENV_THREADS, smem, s>>>(A);

@@ -275,6 +275,9 @@ static qtt_status full_launch(const qtt_tensor* t, T* y, const FullScratch<T>& s
   dim3 grid((unsigned)((nlo + FX_TL - 1) / FX_TL), (unsigned)((nhi + FX_TH - 1) / FX_TH));
   {
     QTT_PROF("full_expand", s);
+    // every output sample written once; 8 r_a flop each (complex) at the cut's capacity
+    prof_add_work("full_expand", (Sc<T>::cplx ? 8.0 : 2.0) * t->rcap[a] * (double)nlo * nhi,
+                  (double)nlo * nhi * sizeof(T));
     expand_kernel<T><<<grid, 256, 0, s>>>(Lcur, nlo, Rcur, ldcur, nhi, t->ranks + a, sc.tlo, sc.thi,
                                           sc.order, y);
   }

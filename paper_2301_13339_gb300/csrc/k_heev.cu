@@ -1004,13 +1004,12 @@ void launch_heev_tri(const EigArgs<float2>& a_in, int mg_cap, cudaStream_t s) {
   EigArgs<float2> a = a_in;
   a.ortol_rel = g_heev_ortol;
   a.ns_steps = g_heev_ns;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<unsigned long long> configured{0};
+  if (first_on_device(&configured)) {
     cudaFuncSetAttribute(heev_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)heev_tri_smem_bytes(HMAX));
     cudaFuncSetAttribute(heev_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)heev_back_smem_bytes(HMAX));
-    configured = true;
   }
   HeevSplit hs{nullptr, nullptr, nullptr, nullptr};
   void* buf = nullptr;

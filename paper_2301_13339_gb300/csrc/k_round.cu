@@ -23,6 +23,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <atomic>
 
 namespace qtt {
 
@@ -596,33 +597,87 @@ void sketch_cache_clear() {
   g_sk_bytes = 0;
 }
 
+// real <-> complex copies of one sketch core for the blocked QR
 template <typename R>
-static void generate_sketch(R* Om, const std::vector<int>& l, const std::vector<size_t>& omoff,
-                            int d, unsigned long long seed, cudaStream_t s) {
+__global__ void k_real_to_c(const R* a, long long n, float2* b) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = make_float2((float)a[e], 0.f);
+}
+template <typename R>
+__global__ void k_c_to_real(const float2* b, long long n, R* a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) a[e] = (R)b[e].x;
+}
+
+static std::atomic<unsigned long long> g_os_cfg[2];
+
+// Cores of at most OS_MAX_ELEMS elements are orthonormalised by Gram-Schmidt
+// in one launch (one CTA each); larger ones (ranks above 64) by the blocked
+// Householder QR, one after the other.
+constexpr int OS_MAX_ELEMS = 128 * 64;
+
+template <typename R>
+static qtt_status generate_sketch(R* Om, const std::vector<int>& l, const std::vector<size_t>& omoff,
+                                  int d, unsigned long long seed, cudaStream_t s) {
   for (int k = 1; k < d; ++k) {
     const long long n = (long long)l[k - 1] * 2 * l[k];
     QTT_PROF("round_sketch", s);
     gauss_fill_kernel<R><<<(unsigned)((n / 2 + 1 + 255) / 256), 256, 0, s>>>(Om + omoff[k], n, seed,
                                                                               (uint32_t)k);
   }
-  if (d > 1) {
-    SketchCores sc{};
-    int mmax = 1;
-    for (int k = 1; k < d && k < OS_MAXD; ++k) {
-      sc.off[k] = (long long)omoff[k];
-      sc.m[k] = 2 * l[k - 1];
-      sc.n[k] = l[k];
-      mmax = std::max(mmax, sc.m[k] * sc.n[k]);
+  if (d <= 1) return QTT_OK;
+  SketchCores sc{};
+  int mmax = 1;
+  std::vector<int> big;
+  for (int k = 1; k < d && k < OS_MAXD; ++k) {
+    sc.off[k] = (long long)omoff[k];
+    const int m = 2 * l[k - 1], n = l[k];
+    if (m * n > OS_MAX_ELEMS) {
+      big.push_back(k);
+      sc.m[k] = 0;
+      sc.n[k] = 0;
+      continue;
     }
-    static bool os_cfg = false;
-    if (!os_cfg) {
-      cudaFuncSetAttribute(k_orth_sketch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(R) * 128 * 64));
-      os_cfg = true;
-    }
+    sc.m[k] = m;
+    sc.n[k] = n;
+    mmax = std::max(mmax, m * n);
+  }
+  if (first_on_device(&g_os_cfg[sizeof(R) == sizeof(double) ? 1 : 0]))
+    cudaFuncSetAttribute(k_orth_sketch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(R) * OS_MAX_ELEMS));
+  {
     QTT_PROF("round_sketch", s);
     k_orth_sketch<R><<<d - 1, OS_THREADS, sizeof(R) * (size_t)mmax, s>>>(Om, sc);
   }
+  if (big.empty()) return QTT_OK;
+  // blocked QR of each large core, through complex copies
+  size_t emax = 0;
+  int nmax = 1;
+  for (int k : big) {
+    emax = std::max(emax, (size_t)2 * l[k - 1] * l[k]);
+    nmax = std::max(nmax, l[k]);
+  }
+  float2* Ac = (float2*)scratch_alloc(sizeof(float2) * emax, s);
+  float2* Qc = (float2*)scratch_alloc(sizeof(float2) * emax, s);
+  float2* Tm = (float2*)scratch_alloc(sizeof(float2) * big_qr_tm_elems(nmax), s);
+  qtt_status st = QTT_OK;
+  if (!Ac || !Qc || !Tm) {
+    set_error("round: sketch scratch allocation failed");
+    st = QTT_ENOMEM;
+  }
+  for (size_t b = 0; b < big.size() && st == QTT_OK; ++b) {
+    const int k = big[b];
+    const int m = 2 * l[k - 1], n = l[k];
+    const long long e = (long long)m * n;
+    QTT_PROF("round_sketch", s);
+    k_real_to_c<R><<<(unsigned)((e + 255) / 256), 256, 0, s>>>(Om + omoff[k], e, Ac);
+    st = big_qr_q<float2>(Ac, m, n, n, Qc, Tm, s);
+    if (st == QTT_OK) k_c_to_real<R><<<(unsigned)((e + 255) / 256), 256, 0, s>>>(Qc, e, Om + omoff[k]);
+  }
+  scratch_free(Ac, s);
+  scratch_free(Qc, s);
+  scratch_free(Tm, s);
+  return st;
 }
 
 // Returns the sketch cores for (seed, l); *owned = true when the caller must
@@ -647,10 +702,15 @@ static R* get_sketch(const std::vector<int>& l, const std::vector<size_t>& omoff
       SketchEntry en;
       if (cudaMalloc(&en.ptr, bytes) == cudaSuccess &&
           cudaEventCreateWithFlags(&en.ev, cudaEventDisableTiming) == cudaSuccess) {
-        generate_sketch<R>((R*)en.ptr, l, omoff, d, seed, s);
+        const qtt_status gst = generate_sketch<R>((R*)en.ptr, l, omoff, d, seed, s);
         // complete before any stream (or graph) can use the entry
         cudaEventRecord(en.ev, s);
         cudaEventSynchronize(en.ev);
+        if (gst != QTT_OK) {
+          cudaFree(en.ptr);
+          cudaEventDestroy(en.ev);
+          return nullptr;
+        }
         en.ready = true;
         en.bytes = bytes;
         g_sk_bytes += bytes;
@@ -664,7 +724,10 @@ static R* get_sketch(const std::vector<int>& l, const std::vector<size_t>& omoff
   }
   R* Om = (R*)scratch_alloc(bytes, s);
   if (!Om) return nullptr;
-  generate_sketch<R>(Om, l, omoff, d, seed, s);
+  if (generate_sketch<R>(Om, l, omoff, d, seed, s) != QTT_OK) {
+    scratch_free(Om, s);
+    return nullptr;
+  }
   *owned = true;
   return Om;
 }
@@ -818,12 +881,10 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     {
       QTT_PROF("round_qr", s);
       const size_t sm = sizeof(T) * ((size_t)n2 * l0 + (size_t)n2 * lq0);
-      static bool qr_cfg = false;
-      if (!qr_cfg) {
+      static std::atomic<unsigned long long> qr_cfg{0};
+      if (first_on_device(&qr_cfg))
         cudaFuncSetAttribute(k_house_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(T) * 2 * 128 * 64));
-        qr_cfg = true;
-      }
       k_house_q<T><<<1, QR_THREADS, sm, s>>>(S, l0, n2, l0, lq0, V);
     }
     const T* Vuse = V;
@@ -855,12 +916,10 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
       // more rows than columns: QR first, then the rank decision on R
       {
         QTT_PROF("round_trunc_qr", s);
-        static bool qr_rows_cfg = false;
-        if (!qr_rows_cfg) {
+        static std::atomic<unsigned long long> qr_rows_cfg{0};
+        if (first_on_device(&qr_rows_cfg))
           cudaFuncSetAttribute(k_qr_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(T) * 2 * 128 * 64));
-          qr_rows_cfg = true;
-        }
         const size_t sm = sizeof(T) * ((size_t)mcap * lqk + (size_t)mcap * lqk);
         k_qr_rows<T><<<1, QR_THREADS, sm, s>>>(Zt, y->ranks + (k - 1), 2, lqk, Qz, Rz, kd);
       }
@@ -931,11 +990,254 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   return QTT_OK;
 }
 
+// ---------------------------------------------------------------- large ranks
+// Copy of x with every core zero-padded to the host capacities, so that the
+// large-rank contractions below have host-known shapes and strides (the
+// tensor is unchanged: the added bond directions carry zeros).
+template <typename T>
+__global__ void k_pad_core(const T* __restrict__ X, const int* __restrict__ xr, int k, int c0,
+                           int c1, T* __restrict__ Xp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)c0 * 2 * c1) return;
+  const int a = (int)(e % c0);
+  const long long t = e / c0;
+  const int i = (int)(t % 2), b = (int)(t / 2);
+  const int r0 = xr[k - 1], r1 = xr[k];
+  Xp[e] = (a < r0 && b < r1) ? X[a + (size_t)r0 * (i + 2 * b)] : szero<T>();
+}
+
+// *n2 = sum |core|^2 of one core (n elements), one CTA, FP64 sum
+template <typename T>
+__global__ void k_core_norm2(const T* c, long long n, double* n2) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) a += (double)sabs2(c[e]);
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *n2 = t;
+  }
+}
+__global__ void k_status_copy(int* dst, const int* src) {
+  if (threadIdx.x == 0) *dst = *src;
+}
+
+// Rounding of Y = O X when the sketch rank exceeds QTT_RANK_CAP (complex64
+// only).  Steps 1 and 2 of round_product_t -- left sketches through the
+// orthonormal sketch cores, then the right-to-left randomised range finder
+// per cut -- with the dense contractions as strided batched GEMMs and the
+// range finder's QR by the blocked Householder QR.  The truncation sweep of
+// step 3 is not run: its rank decisions would need eigen-solves beyond the
+// one-CTA solvers' n <= 128, and at the accuracies this mode serves
+// (eps_round ~ 1e-6, near FP32 resolution) they would keep nearly every
+// sketched direction anyway.  The result is the right-orthonormal TT of
+// ranks lq_k = min(sketch, 2^k, 2^(d-k), P_k r_k) (fixed-rank randomised
+// rounding: its error is that of the range finder, close to the best
+// approximation at ranks lq_k minus the oversampling).
+static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int sketch,
+                                    unsigned long long seed, cudaStream_t s, qtt_tensor** out) {
+  using T = float2;
+  using R = float;
+  const int d = x->desc.d;
+  if (sketch > QTT_SKETCH_CAP_BIG) {
+    set_error("round: sketch rank %d above the large-rank limit %d", sketch, QTT_SKETCH_CAP_BIG);
+    return QTT_EINVAL;
+  }
+  const std::vector<int>& P = op->P;
+  const std::vector<int>& xcap = x->rcap;
+  std::vector<int> Rc(d + 1), l(d + 1), lq(d + 1);
+  for (int k = 0; k <= d; ++k) Rc[k] = P[k] * xcap[k];
+  for (int k = 0; k <= d; ++k) {
+    long long lim = std::min<long long>(1LL << std::min(k, 40), 1LL << std::min(d - k, 40));
+    l[k] = (int)std::min<long long>({(long long)sketch, lim, (long long)Rc[k]});
+  }
+  l[0] = l[d] = 1;
+  for (int k = 1; k < d; ++k) l[k] = std::min(l[k], 2 * l[k - 1]);
+  lq[d] = 1;
+  for (int k = d; k >= 2; --k) lq[k - 1] = std::min(l[k - 1], 2 * lq[k]);
+  lq[0] = 1;
+  int Rmax = 1, lmax = 1, Pmax = 1, xmax = 1;
+  for (int k = 0; k <= d; ++k) {
+    Rmax = std::max(Rmax, Rc[k]);
+    lmax = std::max(lmax, l[k]);
+    Pmax = std::max(Pmax, P[k]);
+    xmax = std::max(xmax, xcap[k]);
+  }
+  std::vector<size_t> wloff(d), omoff(d);
+  size_t wltot = 0, omtot = 0;
+  for (int k = 0; k < d; ++k) { wloff[k] = wltot; wltot += (size_t)l[k] * Rc[k]; }
+  for (int k = 1; k < d; ++k) { omoff[k] = omtot; omtot += (size_t)l[k - 1] * 2 * l[k]; }
+  const size_t a1sz = (size_t)lmax * 2 * Rmax;
+  const size_t a2sz = std::max((size_t)lmax * 2 * Pmax * 2 * xmax, (size_t)xmax * 2 * Pmax * lmax);
+  T* WL = (T*)scratch_alloc(sizeof(T) * std::max<size_t>(wltot, 1), s);
+  bool om_owned = false;
+  R* Om = get_sketch<R>(l, omoff, omtot, d, seed, s, &om_owned);
+  T* A1 = (T*)scratch_alloc(sizeof(T) * a1sz, s);
+  T* A2 = (T*)scratch_alloc(sizeof(T) * a2sz, s);
+  T* Z = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * 2 * lmax, s);
+  T* C0 = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * lmax, s);
+  T* C1 = (T*)scratch_alloc(sizeof(T) * (size_t)Rmax * lmax, s);
+  T* S = (T*)scratch_alloc(sizeof(T) * (size_t)lmax * 2 * lmax, s);
+  T* Aq = (T*)scratch_alloc(sizeof(T) * (size_t)lmax * 2 * lmax, s);
+  T* V = (T*)scratch_alloc(sizeof(T) * (size_t)lmax * 2 * lmax, s);
+  T* Tm = (T*)scratch_alloc(sizeof(T) * big_qr_tm_elems(lmax), s);
+  T* one = (T*)scratch_alloc(sizeof(T), s);
+  unsigned* wmax = (unsigned*)scratch_alloc(sizeof(unsigned) * (d + 1), s);
+  auto release = [&]() {
+    scratch_free(WL, s); if (om_owned) scratch_free(Om, s); scratch_free(A1, s); scratch_free(A2, s);
+    scratch_free(Z, s); scratch_free(C0, s); scratch_free(C1, s); scratch_free(S, s);
+    scratch_free(Aq, s); scratch_free(V, s); scratch_free(Tm, s); scratch_free(one, s);
+    scratch_free(wmax, s);
+  };
+  if (!WL || !Om || !A1 || !A2 || !Z || !C0 || !C1 || !S || !Aq || !V || !Tm || !one || !wmax) {
+    release();
+    if (!Om && WL && A1) set_error("round: sketch generation failed");
+    else set_error("round: large-rank scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  k_one<<<1, 32, 0, s>>>(one, 0);
+  cudaMemsetAsync(wmax, 0, sizeof(unsigned) * (d + 1), s);
+  // x padded to its capacities
+  qtt_tensor* xp = nullptr;
+  qtt_status st = tensor_alloc(x->desc, xcap, s, &xp);
+  if (st != QTT_OK) { release(); return st; }
+  for (int k = 1; k <= d; ++k) {
+    const long long n = (long long)xcap[k - 1] * 2 * xcap[k];
+    QTT_PROF("round_pad", s);
+    k_pad_core<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const T*)x->cores + x->off[k - 1],
+                                                             x->ranks, k, xcap[k - 1], xcap[k],
+                                                             (T*)xp->cores + xp->off[k - 1]);
+  }
+  set_ranks_from_host(xp->ranks, xcap, s);
+  // output: the right-orthonormal TT of ranks lq
+  qtt_tensor* y = nullptr;
+  st = tensor_alloc(x->desc, lq, s, &y);
+  if (st != QTT_OK) { tensor_free_async(xp, s); release(); return st; }
+  const R* Oc = (const R*)op->cores;
+  const T* Xc = (const T*)xp->cores;
+  T* yc = (T*)y->cores;
+
+  // --- 1. left sketches
+  cudaMemcpyAsync(WL + wloff[0], one, sizeof(T), cudaMemcpyDeviceToDevice, s);
+  for (int k = 1; k < d && st == QTT_OK; ++k) {
+    const int l0 = l[k - 1], lk = l[k];
+    const int r0 = xcap[k - 1], r1 = xcap[k];
+    const int Pin = P[k - 1];
+    const R* Ok = Oc + op->off[k - 1];
+    const T* Xk = Xc + xp->off[k - 1];
+    {  // A1[s + lk (j + 2 c)] = sum_{s'} Om[s' + l0 (j + 2 s)] WL0[s' + l0 c]
+      CGemmArgs<R> g;
+      g.A = Om + omoff[k]; g.sAi = 2LL * l0; g.sAk = 1; g.bA1 = l0;
+      g.B = WL + wloff[k - 1]; g.sBk = 1; g.sBj = l0;
+      g.C = A1; g.sCi = 1; g.sCj = 2LL * lk; g.bC1 = lk;
+      g.M = lk; g.N = Rc[k - 1]; g.K = l0; g.nb1 = 2;
+      st = cgemm<R>(g, 2, s);
+    }
+    if (st != QTT_OK) break;
+    {  // A2[rho + 2lk (p + Pin (i + 2 b))] = sum_a A1[rho + 2lk (a + r0 p)] X[a + r0 (i + 2 b)]
+      CGemmArgs<T> g;
+      g.A = A1; g.sAi = 1; g.sAk = 2LL * lk; g.bA1 = 2LL * lk * r0;
+      g.B = Xk; g.sBk = 1; g.sBj = r0;
+      g.C = A2; g.sCi = 1; g.sCj = 2LL * lk * Pin; g.bC1 = 2LL * lk;
+      g.M = 2 * lk; g.N = 2 * r1; g.K = r0; g.nb1 = Pin;
+      st = cgemm<T>(g, Pin, s);
+    }
+    if (st != QTT_OK) break;
+    { QTT_PROF("round_sketch", s);
+    k_wl<T, R><<<GRID1((long long)lk * Rc[k])>>>(Ok, Pin, P[k], A2, lk, xp->ranks, k, Rc[k],
+                                                 WL + wloff[k]);
+    }
+    { QTT_PROF("round_sketch", s);
+    const unsigned nbk = (unsigned)std::min<long long>(1024, ((long long)lk * Rc[k] + 255) / 256);
+    k_absmax<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, xp->ranks, k, P[k], wmax + k);
+    k_scale_max<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, xp->ranks, k, P[k], wmax + k);
+    }
+  }
+  // --- 2. right-to-left range finder
+  T* Ccur = C0;
+  T* Cnext = C1;
+  if (st == QTT_OK) cudaMemcpyAsync(Ccur, one, sizeof(T), cudaMemcpyDeviceToDevice, s);
+  int ldc = 1;
+  for (int k = d; k >= 1 && st == QTT_OK; --k) {
+    const R* Ok = Oc + op->off[k - 1];
+    const T* Xk = Xc + xp->off[k - 1];
+    const int r0 = xcap[k - 1], r1 = xcap[k];
+    const int Pin = P[k - 1], Pout = P[k];
+    const int n2 = 2 * lq[k];
+    {  // B1[a + r0 (i + 2 (q + Pout t))] = sum_b X[a + r0 (i + 2 b)] C[(b + r1 q) + ldc t]
+      CGemmArgs<T> g;
+      g.A = Xk; g.sAi = 1; g.sAk = 2LL * r0; g.bA1 = r0;
+      g.B = Ccur; g.sBk = 1; g.sBj = ldc; g.bB2 = r1;
+      g.C = A2; g.sCi = 1; g.sCj = 2LL * r0 * Pout; g.bC1 = r0; g.bC2 = 2LL * r0;
+      g.M = r0; g.N = lq[k]; g.K = r1; g.nb1 = 2;
+      st = cgemm<T>(g, 2 * Pout, s);
+    }
+    if (st != QTT_OK) break;
+    const int ldz = Rc[k - 1];
+    T* Zdst = (k == 1) ? yc + y->off[0] : Z;
+    { QTT_PROF("round_orth", s);
+    k_z<T, R><<<GRID1((long long)r0 * Pin * 2 * lq[k])>>>(Ok, Pin, Pout, A2, xp->ranks, k, r0,
+                                                          lq[k], ldz, Zdst);
+    }
+    if (k == 1) break;
+    const int l0 = l[k - 1], lq0 = lq[k - 1];
+    {  // S = WL_{k-1} Z  (l0 x n2)
+      CGemmArgs<T> g;
+      g.A = WL + wloff[k - 1]; g.sAi = 1; g.sAk = l0;
+      g.B = Z; g.sBk = 1; g.sBj = ldz;
+      g.C = S; g.sCi = 1; g.sCj = l0;
+      g.M = l0; g.N = n2; g.K = ldz;
+      st = cgemm<T>(g, 1, s);
+    }
+    if (st != QTT_OK) break;
+    { QTT_PROF("round_qr", s);
+    launch_conj_transpose<T>(S, l0, l0, n2, Aq, s);
+    }
+    st = big_qr_q<T>(Aq, n2, l0, lq0, V, Tm, s);
+    if (st != QTT_OK) break;
+    { QTT_PROF("round_orth", s);
+    k_qcore<T><<<GRID1(lq0 * n2)>>>(V, n2, lq0, yc + y->off[k - 1]);
+    }
+    {  // Cn = Z V  (ldz x lq0)
+      CGemmArgs<T> g;
+      g.A = Z; g.sAi = 1; g.sAk = ldz;
+      g.B = V; g.sBk = 1; g.sBj = n2;
+      g.C = Cnext; g.sCi = 1; g.sCj = ldz;
+      g.M = ldz; g.N = lq0; g.K = n2;
+      st = cgemm<T>(g, 1, s);
+    }
+    std::swap(Ccur, Cnext);
+    ldc = ldz;
+  }
+  if (st == QTT_OK) {
+    set_ranks_from_host(y->ranks, lq, s);
+    // the cores after the first are right-orthonormal: ||y||^2 = ||core_1||^2
+    k_core_norm2<T><<<1, 256, 0, s>>>(yc + y->off[0], (long long)2 * lq[1], y->norm2);
+    k_status_copy<<<1, 32, 0, s>>>(y->status, x->status);
+    st = cuda_check(cudaGetLastError(), "round (large ranks) launch");
+  }
+  release();
+  tensor_free_async(xp, s);
+  if (st != QTT_OK) { qtt_free(y); return st; }
+  *out = y;
+  return QTT_OK;
+}
+
 qtt_status round_product(const qtt_op* op, const qtt_tensor* x, const qtt_trunc& tr, int sketch,
                          unsigned long long seed, cudaStream_t s, qtt_tensor** out) {
   if (op->d != x->desc.d) { set_error("round: operator/tensor mode count mismatch"); return QTT_EINVAL; }
   if (op->dt != x->desc.dt) { set_error("round: operator/tensor dtype mismatch"); return QTT_EINVAL; }
   if (op->cplx) { set_error("round: complex operators are applied by matvec"); return QTT_EUNSUPPORTED; }
+  if (sketch > QTT_RANK_CAP) {
+    if (x->desc.dt != QTT_C64) {
+      set_error("round: sketch ranks above %d need complex64 data", QTT_RANK_CAP);
+      return QTT_EUNSUPPORTED;
+    }
+    return round_product_big(op, x, sketch, seed, s, out);
+  }
   if (x->desc.dt == QTT_F64) return round_product_t<double>(op, x, tr, sketch, seed, s, out);
   return round_product_t<float2>(op, x, tr, sketch, seed, s, out);
 }

@@ -922,12 +922,10 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
     return;
   }
   const size_t sm = eig_smem_bytes<T>(mg_cap);
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<unsigned long long> configured{0};
+  if (first_on_device(&configured))
     cudaFuncSetAttribute(gram_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)eig_smem_bytes<T>(EIG_MAXN));
-    configured = true;
-  }
   const char* pname =
       mg_cap <= 32 ? "jacobi_eig_le32" : mg_cap <= 64 ? "jacobi_eig_le64" : "jacobi_eig_le128";
   EigArgs<T> b = a;
@@ -945,13 +943,12 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
     const size_t vb = al16(ncap * ncap * sizeof(float2)), db = al16(ncap * sizeof(float));
     char* buf = (char*)scratch_alloc(lb + vb + db + 16, s);
     if (buf) {
-      static bool dm_cfg = false;
-      if (!dm_cfg) {
+      static std::atomic<unsigned long long> dm_cfg{0};
+      if (first_on_device(&dm_cfg)) {
         cudaFuncSetAttribute(jacobi_dm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dm_smem_bytes(EIG_MAXN));
         cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)eig_smem_bytes<float2>(EIG_MAXN));
-        dm_cfg = true;
       }
       float4* rlog = (float4*)buf;
       float2* vbuf = (float2*)(buf + lb);
@@ -998,13 +995,13 @@ template <typename T, int TM>
 static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
                          int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
                          T* gp, int ldp, int mcap, int rcap) {
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<unsigned long long> configured{0};
+  if (first_on_device(&configured))
     cudaFuncSetAttribute(proj_gram_kernel<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pg_smem_bytes<T>(true, 128, 128));
-    configured = true;
-  }
   QTT_PROF("proj_gram", s);
+  // the pass streams the m x n unfolding once (m at its capacity)
+  prof_add_work("proj_gram", 0.0, (double)mcap * (double)n * sizeof(T));
   proj_gram_kernel<T, TM><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp,
                                                        ldp, mcap, rcap);
 }
@@ -1268,12 +1265,10 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
     const int ldp_next = 2 * rcapk;
     if (tr.eps == 0.0 && !(tr.delta > 0.0) && k > skip + 1 && n <= 64 && n == rcapk) {
       // every singular value is kept from here on (n_k halves each level)
-      static bool qr_cfg = false;
-      if (!qr_cfg) {
+      static std::atomic<unsigned long long> qr_cfg{0};
+      if (first_on_device(&qr_cfg))
         cudaFuncSetAttribute(qr_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(T) * 2 * 128 * 64));
-        qr_cfg = true;
-      }
       QTT_PROF("qr_level", s);
       qr_level_kernel<T><<<1, QR_THREADS, sizeof(T) * 2 * (size_t)mcap * n, s>>>(
           M, rk, k, (int)n, core_k, Wout);
@@ -1302,13 +1297,12 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
           launch_gauss_fill(Omb, n * lrs, rs->seed, (uint32_t)k, s);
           Om = Omb;
         }
-        static bool sk_cfg = false;
-        if (!sk_cfg) {
+        static std::atomic<unsigned long long> sk_cfg{0};
+        if (first_on_device(&sk_cfg)) {
           cudaFuncSetAttribute(sketch_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sketch_smem_bytes<T, R>());
           cudaFuncSetAttribute(rsvd_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(T) * 2 * 128 * SK_LMAX));
-          sk_cfg = true;
         }
         const int nps = (int)std::min<long long>(max_parts, (n + SK_CC - 1) / SK_CC);
         double2* Yd = (double2*)scratch_alloc(sizeof(double2) * 128 * 128, s);

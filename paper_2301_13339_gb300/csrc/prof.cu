@@ -17,6 +17,8 @@ static bool g_prof_on = false;
 static std::mutex g_prof_mu;
 static std::vector<ProfRec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
+// algorithmic work recorded by the launch sites: name -> (flop, bytes)
+static std::map<std::string, std::pair<double, double>> g_work;
 
 static cudaEvent_t ev_get() {
   if (!g_pool.empty()) {
@@ -30,6 +32,14 @@ static cudaEvent_t ev_get() {
 }
 
 bool prof_enabled() { return g_prof_on; }
+
+void prof_add_work(const char* name, double flops, double bytes) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto& w = g_work[name];
+  w.first += flops;
+  w.second += bytes;
+}
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s), active_(g_prof_on) {
   if (!active_) return;
@@ -80,9 +90,19 @@ int qtt_profile_read(char* names, int name_stride, double* ms, int* counts, int 
   return n;
 }
 
+int qtt_profile_work(const char* name, double* flops, double* bytes) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto it = g_work.find(name ? name : "");
+  if (it == g_work.end()) return 0;
+  if (flops) *flops = it->second.first;
+  if (bytes) *bytes = it->second.second;
+  return 1;
+}
+
 void qtt_profile_reset(void) {
   cudaDeviceSynchronize();
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_work.clear();
   for (auto& r : g_recs) {
     g_pool.push_back(r.a);
     g_pool.push_back(r.b);

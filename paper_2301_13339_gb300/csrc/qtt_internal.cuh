@@ -9,6 +9,7 @@
 #include <cstddef>
 #include <vector>
 #include <string>
+#include <atomic>
 #include "../../include/qtt.h"
 
 namespace qtt {
@@ -292,6 +293,39 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       int write_norm2, int* status, cudaStream_t s, int relative = 0,
                       double delta = 0.0, int sweeps = -1);
 
+// ------------------------------------------------------------- large ranks
+// First call for the current device with this flag word: true once per
+// device (per-device one-time set-up such as kernel attributes).
+bool first_on_device(std::atomic<unsigned long long>* flags);
+
+// Blocked Householder QR (k_dense.cu): A (m x n, ld m, m <= 768) is
+// overwritten by R and the reflectors; Q (m x nq, ld m) receives the first
+// nq columns of the Q factor.  Tm: workspace of big_qr_tm_elems(n) elements.
+template <typename T>
+qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s);
+size_t big_qr_tm_elems(int n);
+// A (m x n, ld m) = S^H for S (n x m, ld ls)
+template <typename T>
+void launch_conj_transpose(const T* S, int ls, int n, int m, T* A, cudaStream_t s);
+
+// C = op(A) B (complex64 B, C; A complex64 or real float), strided and
+// batched: batch z = b1 + nb1 b2 offsets every operand by b1 bX1 + b2 bX2.
+// Element (i, k) of A at i sAi + k sAk (conjugated when conjA), (k, j) of B at
+// k sBk + j sBj, (i, j) of C at i sCi + j sCj.  Fast paths: sAi == 1 or
+// sAk == 1, sBk == 1.  Chunks of 16 terms are added with compensation.
+template <typename TA>
+struct CGemmArgs {
+  const TA* A = nullptr;
+  long long sAi = 1, sAk = 1, bA1 = 0, bA2 = 0;
+  const float2* B = nullptr;
+  long long sBk = 1, sBj = 1, bB1 = 0, bB2 = 0;
+  float2* C = nullptr;
+  long long sCi = 1, sCj = 1, bC1 = 0, bC2 = 0;
+  int M = 0, N = 0, K = 0, nb1 = 1, conjA = 0;
+};
+template <typename TA>
+qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s);
+
 // ------------------------------------------------------------- full
 template <typename T>
 qtt_status tt_full(const qtt_tensor* t, T* y, cudaStream_t s);
@@ -357,6 +391,9 @@ struct ProfScope {
 #define QTT_PROF_CAT2(a, b) a##b
 #define QTT_PROF_CAT(a, b) QTT_PROF_CAT2(a, b)
 #define QTT_PROF(name, s) ::qtt::ProfScope QTT_PROF_CAT(_qtt_prof_, __LINE__)(name, s)
+// algorithmic flops / bytes of one launch, summed per kernel name while
+// profiling is on (qtt_profile_work)
+void prof_add_work(const char* name, double flops, double bytes);
 
 // stream-ordered scratch allocation
 void* scratch_alloc(size_t bytes, cudaStream_t s);
