@@ -54,7 +54,26 @@ typedef enum {
   QTT_ENUMERIC = -7       /* non-finite values (NaN / Inf) met in the data     */
 } qtt_status;
 
-typedef enum { QTT_F64 = 0, QTT_C64 = 2 } qtt_dtype;
+/* Element type of dense arrays and QTT cores.  This build computes with
+ * QTT_F64 (real double: FP64 arithmetic throughout) and QTT_C64 (complex
+ * float, interleaved re,im pairs: FP32 arithmetic with FP64 reductions for
+ * rank decisions).  QTT_F32 and QTT_C128 name the other two storage types of
+ * the problem statement; every entry point answers them with
+ * QTT_EUNSUPPORTED (real single-precision data takes the FP32 path as
+ * complex64 with zero imaginary part). */
+typedef enum { QTT_F64 = 0, QTT_F32 = 1, QTT_C64 = 2, QTT_C128 = 3 } qtt_dtype;
+
+/* Arithmetic of a TT-SVD or rounding.  QTT_PREC_AUTO: the element type's own
+ * (FP64 for QTT_F64, FP32 for QTT_C64); QTT_PREC_FP64 / QTT_PREC_FP32 must
+ * match it (else QTT_EINVAL).  The tensor-core modes (BF16 or TF32 products
+ * with an FP32 residual-correction pass) are not built: QTT_EUNSUPPORTED. */
+typedef enum {
+  QTT_PREC_AUTO = 0,
+  QTT_PREC_FP64 = 1,
+  QTT_PREC_FP32 = 2,
+  QTT_PREC_BF16_REFINED = 3,
+  QTT_PREC_TF32_REFINED = 4
+} qtt_prec;
 
 /* Truncation parameters of one TT-SVD or rounding sweep.
  *   eps    relative accuracy; per-cut threshold tau = eps/sqrt(d-1)*||A||_F,
@@ -68,12 +87,21 @@ typedef enum { QTT_F64 = 0, QTT_C64 = 2 } qtt_dtype;
  *   delta  0 < delta < 1: the SV drop-off rule (Sec. 5 modification (3))
  *          replaces the eps rule: rank = the first k with
  *          sigma_{k+1}/sigma_k < delta, all singular values if there is no
- *          such drop, then the cap rmax.  <= 0: off. */
+ *          such drop, then the cap rmax.  <= 0: off.
+ *   prec   qtt_prec (QTT_PREC_AUTO = 0 for the element type's arithmetic).
+ *   fixed_ranks  NULL, or d+1 host ints r_0..r_d (r_0 = r_d = 1, 1 <= r_k <=
+ *          min(2^k, 2^(d-k), QTT_RANK_CAP)): forced ranks, the parity mode
+ *          that takes another implementation's rank decisions -- cut k keeps
+ *          exactly r_k singular triplets (the dominant ones) and eps, delta
+ *          and rmax are not used.  In a rounding the sketch rank also bounds
+ *          r_k.  Read during the call only. */
 typedef struct {
   double eps;
   int rmax;
   int refine;
   double delta;
+  int prec;
+  const int* fixed_ranks;
 } qtt_trunc;
 
 /* Largest TT rank of a decomposition or of an eps-truncated rounding
@@ -286,6 +314,16 @@ qtt_status qtt_batch_conv_sinc(int nlines, const void* const* x, const int* log2
 /* Handle inspection and construction (tests, checkpoints). */
 /* ranks_host: d+1 ints r_0..r_d.  Synchronises; returns the device status. */
 qtt_status qtt_get_ranks(const qtt_tensor* t, int* ranks_host, void* stream);
+/* qtt_get_margins -- how close each rank decision of the call that made t
+ * came to its threshold (Alg. 1's eps-rank rule): margins_host[k], k = 0..d,
+ * receives min(|sqrt(tail(r_k)) - tau|, |sqrt(tail(r_k - 1)) - tau|) / tau
+ * for cut k, tail(r) = the sum of the eigenvalues sigma_i^2 beyond r that
+ * the decision saw, tau the cut's threshold; a margin near the working
+ * precision (1e-7 in FP32) says that another implementation may decide
+ * differently (rerun with fixed_ranks).  NaN where no eps rule decided
+ * (k = 0, d, a rank set by the cap, eps = 0, the drop-off rule, forced
+ * ranks, the large-rank rounding).  Synchronises. */
+qtt_status qtt_get_margins(const qtt_tensor* t, double* margins_host, void* stream);
 /* d, element type, ndim and log2 shape of a handle (host-side, no sync). */
 qtt_status qtt_get_info(const qtt_tensor* t, int* d, qtt_dtype* dt, int* ndim,
                         int* log2_shape, int* interleave);

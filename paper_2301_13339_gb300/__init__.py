@@ -23,7 +23,8 @@ __all__ = [
     "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "QTT_SKETCH_CAP_BIG", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
     "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd", "qtt_fft",
-    "qtt_hadamard", "qtt_conv_fft", "qtt_sinc_padded",
+    "qtt_hadamard", "qtt_conv_fft", "qtt_sinc_padded", "QTT_PREC_AUTO", "QTT_PREC_FP64",
+    "QTT_PREC_FP32", "QTT_PREC_BF16_REFINED", "QTT_PREC_TF32_REFINED",
 ]
 
 QTT_F64 = 0
@@ -40,7 +41,7 @@ EXPORTED_SYMBOLS = [
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
-    "qtt_profile_work",
+    "qtt_profile_work", "qtt_get_margins",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
@@ -56,7 +57,8 @@ class QTTError(RuntimeError):
 
 class _Trunc(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int),
-                ("delta", ctypes.c_double)]
+                ("delta", ctypes.c_double), ("prec", ctypes.c_int),
+                ("fixed_ranks", ctypes.POINTER(ctypes.c_int))]
 
 
 _lib = None
@@ -96,6 +98,7 @@ def load(path=None):
         "qtt_batch_free": (None, [vp]),
         "qtt_batch_conv_sinc": (i, [i, pp, ip, dp, ip, d, i, i, d, tp, pp, i, vp]),
         "qtt_get_ranks": (i, [vp, ip, vp]),
+        "qtt_get_margins": (i, [vp, dp, vp]),
         "qtt_get_info": (i, [vp, ip, ip, ip, ip, ip]),
         "qtt_get_cores": (i, [vp, vp, vp]),
         "qtt_from_cores": (i, [vp, ip, i, i, i, ip, i, vp, pp]),
@@ -186,6 +189,13 @@ class QTTTensor:
         _check(_lib.qtt_get_ranks(self._h, r, _stream(stream)))
         return [r[k] for k in range(self.d + 1)]
 
+    def margins(self, stream=None):
+        """Per-cut margin of the eps-rank decisions (qtt_get_margins; NaN
+        where no eps rule decided)."""
+        m = (ctypes.c_double * (self.d + 1))()
+        _check(_lib.qtt_get_margins(self._h, m, _stream(stream)))
+        return [m[k] for k in range(self.d + 1)]
+
     def cores(self, stream=None):
         """Cores as numpy arrays of shape (r_{k-1}, 2, r_k) (host copies)."""
         r = self.ranks(stream)
@@ -247,14 +257,26 @@ class QTTOperator:
             pass
 
 
-def _trunc(eps, rmax, refine, delta=0.0):
-    return _Trunc(float(eps), int(rmax or 0), int(bool(refine)), float(delta or 0.0))
+QTT_PREC_AUTO, QTT_PREC_FP64, QTT_PREC_FP32, QTT_PREC_BF16_REFINED, QTT_PREC_TF32_REFINED = range(5)
 
 
-def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None, delta=0.0):
+def _trunc(eps, rmax, refine, delta=0.0, prec=QTT_PREC_AUTO, fixed_ranks=None):
+    """qtt_trunc.  fixed_ranks: None or the d+1 ranks r_0..r_d to force (the
+    array is kept alive on the returned structure)."""
+    tr = _Trunc(float(eps), int(rmax or 0), int(bool(refine)), float(delta or 0.0), int(prec), None)
+    if fixed_ranks is not None:
+        arr = (ctypes.c_int * len(fixed_ranks))(*[int(r) for r in fixed_ranks])
+        tr.fixed_ranks = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int))
+        tr._keep = arr
+    return tr
+
+
+def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None, delta=0.0,
+                  prec=QTT_PREC_AUTO, fixed_ranks=None):
     """QTT reshape + TT-SVD (Alg. 1 with the max-rank cap of Sec. 5) of a
     contiguous CUDA tensor (1D length 2^d, or 2D 2^dy x 2^dx row-major).
-    delta > 0: the SV drop-off rule (Sec. 5 (3)) instead of eps."""
+    delta > 0: the SV drop-off rule (Sec. 5 (3)) instead of eps.
+    fixed_ranks: the d+1 ranks to keep (parity mode; eps/rmax/delta unused)."""
     load()
     if not x.is_cuda or not x.is_contiguous():
         raise ValueError("x must be a contiguous CUDA tensor")
@@ -266,7 +288,7 @@ def qtt_decompose(x, eps=0.0, rmax=0, refine=False, interleave=True, stream=None
             raise ValueError(f"sizes must be powers of two >= 2, got {tuple(x.shape)}")
         shape.append(ln)
     sh = (ctypes.c_int * 2)(*(shape + [0] * (2 - len(shape))))
-    tr = _trunc(eps, rmax, refine, delta)
+    tr = _trunc(eps, rmax, refine, delta, prec, fixed_ranks)
     out = ctypes.c_void_p()
     _check(_lib.qtt_decompose(ctypes.c_void_p(x.data_ptr()), code, x.dim(), sh, int(interleave),
                               ctypes.byref(tr), _stream(stream), ctypes.byref(out)))
@@ -305,12 +327,13 @@ def qtt_decompose_rsvd(x, rmax, p, omega=None, seed=20230131, stream=None):
 
 
 def qtt_conv_sinc(f, B, normalize=True, eps_op=1e-7, eps_round=1e-7, rround=0, refine=True,
-                  sketch=0, seed=20230131, stream=None):
-    """QTT Toeplitz convolution with the sinc kernel + TT-rounding."""
+                  sketch=0, seed=20230131, stream=None, prec=QTT_PREC_AUTO, fixed_ranks=None):
+    """QTT Toeplitz convolution with the sinc kernel + TT-rounding (sketch >
+    QTT_RANK_CAP: the large-rank mode, see include/qtt.h)."""
     load()
     Bs = [float(B)] * f.ndim if np.isscalar(B) else [float(b) for b in B]
     Barr = (ctypes.c_double * 2)(*(Bs + [0.0] * (2 - len(Bs))))
-    tr = _trunc(eps_round, rround, refine)
+    tr = _trunc(eps_round, rround, refine, 0.0, prec, fixed_ranks)
     out = ctypes.c_void_p()
     _check(_lib.qtt_conv_sinc(f.handle, Barr, int(bool(normalize)), float(eps_op),
                               ctypes.byref(tr), int(sketch), int(seed), _stream(stream),
@@ -318,9 +341,10 @@ def qtt_conv_sinc(f, B, normalize=True, eps_op=1e-7, eps_round=1e-7, rround=0, r
     return QTTTensor(out)
 
 
-def qtt_round(t, eps, rmax=0, refine=True, sketch=0, seed=20230131, stream=None):
+def qtt_round(t, eps, rmax=0, refine=True, sketch=0, seed=20230131, stream=None,
+              prec=QTT_PREC_AUTO, fixed_ranks=None):
     load()
-    tr = _trunc(eps, rmax, refine)
+    tr = _trunc(eps, rmax, refine, 0.0, prec, fixed_ranks)
     _check(_lib.qtt_round(t.handle, ctypes.byref(tr), int(sketch), int(seed), _stream(stream)))
     return t
 

@@ -106,7 +106,7 @@ qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap, cu
   t->total = tot;
   const size_t esz = elem_size(desc.dt);
   size_t core_bytes = (tot * esz + 255) & ~(size_t)255;
-  size_t meta = 256 + 64;  // ranks (<= 33 ints -> 256 B), status, norm2
+  size_t meta = 256 + 64 + 320;  // ranks (<= 33 ints -> 256 B), status, norm2, margins
   char* base = (char*)scratch_alloc(core_bytes + meta, s);
   if (!base) {
     delete t;
@@ -117,7 +117,9 @@ qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap, cu
   t->ranks = (int*)(base + core_bytes);
   t->status = (int*)(base + core_bytes + 256);
   t->norm2 = (double*)(base + core_bytes + 256 + 8);
-  cudaMemsetAsync(base + core_bytes, 0, meta, s);
+  t->margin = (double*)(base + core_bytes + 320);
+  cudaMemsetAsync(base + core_bytes, 0, 320, s);
+  cudaMemsetAsync(base + core_bytes + 320, 0xff, meta - 320, s);   // NaN: no decision yet
   *out = t;
   return QTT_OK;
 }
@@ -220,14 +222,53 @@ static qtt_status cached_identity(int d, qtt_dtype dt, cudaStream_t s, qtt_op** 
   return QTT_OK;
 }
 
-static qtt_status check_trunc(const qtt_trunc* tr) {
+// Truncation parameters of a call on data of type dt with d modes (d <= 0:
+// not known here, the forced ranks are checked later).
+static qtt_status check_trunc(const qtt_trunc* tr, qtt_dtype dt, int d) {
   if (!tr) { set_error("truncation parameters are NULL"); return QTT_EINVAL; }
   if (!(tr->eps >= 0.0) || tr->eps >= 1.0) { set_error("eps must be in [0, 1)"); return QTT_EINVAL; }
   if (tr->delta >= 1.0 || tr->delta != tr->delta) { set_error("delta must be < 1 (<= 0: off)"); return QTT_EINVAL; }
+  if (tr->prec < QTT_PREC_AUTO || tr->prec > QTT_PREC_TF32_REFINED) {
+    set_error("prec %d is not a qtt_prec value", tr->prec);
+    return QTT_EINVAL;
+  }
+  if (tr->prec == QTT_PREC_BF16_REFINED || tr->prec == QTT_PREC_TF32_REFINED) {
+    set_error("the BF16/TF32 tensor-core precision modes are not built");
+    return QTT_EUNSUPPORTED;
+  }
+  if ((tr->prec == QTT_PREC_FP64 && dt != QTT_F64) || (tr->prec == QTT_PREC_FP32 && dt != QTT_C64)) {
+    set_error("prec %d does not match the element type %d (FP64 arithmetic for QTT_F64, FP32 for "
+              "QTT_C64)", tr->prec, (int)dt);
+    return QTT_EINVAL;
+  }
+  if (tr->fixed_ranks && d > 0) {
+    const int* r = tr->fixed_ranks;
+    if (r[0] != 1 || r[d] != 1) { set_error("fixed_ranks: r_0 and r_d must be 1"); return QTT_EINVAL; }
+    for (int k = 1; k < d; ++k) {
+      const long long lim = std::min<long long>({1LL << std::min(k, 40), 1LL << std::min(d - k, 40),
+                                                 (long long)QTT_RANK_CAP});
+      if (r[k] < 1 || r[k] > lim) {
+        set_error("fixed_ranks: r_%d = %d outside [1, %lld]", k, r[k], lim);
+        return QTT_EINVAL;
+      }
+    }
+  }
   return QTT_OK;
 }
 
 static bool valid_dtype(qtt_dtype dt) { return dt == QTT_F64 || dt == QTT_C64; }
+
+// QTT_EUNSUPPORTED for the storage types this build does not compute with,
+// QTT_EINVAL for values outside qtt_dtype
+static qtt_status dtype_status(qtt_dtype dt, const char* who) {
+  if (valid_dtype(dt)) return QTT_OK;
+  if (dt == QTT_F32 || dt == QTT_C128) {
+    set_error("%s: element type %d is not built (QTT_F64 and QTT_C64 are)", who, (int)dt);
+    return QTT_EUNSUPPORTED;
+  }
+  set_error("%s: unsupported dtype %d", who, (int)dt);
+  return QTT_EINVAL;
+}
 
 }  // namespace qtt
 
@@ -242,9 +283,10 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
                          int interleave, const qtt_trunc* tr, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !log2_shape || !out) { set_error("qtt_decompose: NULL argument"); return QTT_EINVAL; }
-  if (!valid_dtype(dt)) { set_error("qtt_decompose: unsupported dtype %d", (int)dt); return QTT_EINVAL; }
+  qtt_status st = dtype_status(dt, "qtt_decompose");
+  if (st != QTT_OK) return st;
   if (ndim != 1 && ndim != 2) { set_error("qtt_decompose: ndim must be 1 or 2"); return QTT_EINVAL; }
-  qtt_status st = check_trunc(tr);
+  st = check_trunc(tr, dt, 0);
   if (st != QTT_OK) return st;
   TensorDesc desc;
   desc.dt = dt;
@@ -261,9 +303,13 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
   }
   if (d < 2 || d > 30) { set_error("qtt_decompose: total modes d=%d outside [2, 30]", d); return QTT_EINVAL; }
   desc.d = d;
+  st = check_trunc(tr, dt, d);
+  if (st != QTT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   qtt_tensor* t = nullptr;
-  st = tensor_alloc(desc, rank_caps(d, tr->rmax, QTT_RANK_CAP), s, &t);
+  std::vector<int> caps = rank_caps(d, tr->rmax, QTT_RANK_CAP);
+  if (tr->fixed_ranks) caps.assign(tr->fixed_ranks, tr->fixed_ranks + d + 1);
+  st = tensor_alloc(desc, caps, s, &t);
   if (st != QTT_OK) return st;
   const void* v = x;
   void* perm = nullptr;
@@ -289,7 +335,10 @@ qtt_status qtt_decompose_rsvd(const void* x, qtt_dtype dt, int log2_len, int rma
                               qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !out) { set_error("qtt_decompose_rsvd: NULL argument"); return QTT_EINVAL; }
-  if (!valid_dtype(dt)) { set_error("qtt_decompose_rsvd: unsupported dtype %d", (int)dt); return QTT_EINVAL; }
+  {
+    const qtt_status dst = dtype_status(dt, "qtt_decompose_rsvd");
+    if (dst != QTT_OK) return dst;
+  }
   if (log2_len < 2 || log2_len > 30) {
     set_error("qtt_decompose_rsvd: log2 length %d outside [2, 30]", log2_len);
     return QTT_EINVAL;
@@ -322,7 +371,7 @@ qtt_status qtt_conv_sinc(const qtt_tensor* f, const double* B, int normalize, do
                          void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!f || !B || !out) { set_error("qtt_conv_sinc: NULL argument"); return QTT_EINVAL; }
-  qtt_status st = check_trunc(round_tr);
+  qtt_status st = check_trunc(round_tr, f->desc.dt, f->desc.d);
   if (st != QTT_OK) return st;
   if (!(eps_op > 0.0) || eps_op >= 1.0) { set_error("qtt_conv_sinc: eps_op must be in (0, 1)"); return QTT_EINVAL; }
   for (int a = 0; a < f->desc.ndim; ++a)
@@ -352,7 +401,7 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
                      void* stream) {
   g_err[0] = 0;
   if (!t) { set_error("qtt_round: NULL tensor"); return QTT_EINVAL; }
-  qtt_status st = check_trunc(tr);
+  qtt_status st = check_trunc(tr, t->desc.dt, t->desc.d);
   if (st != QTT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   qtt_op* id = nullptr;
@@ -370,6 +419,7 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
   t->ranks = y->ranks;
   t->status = y->status;
   t->norm2 = y->norm2;
+  t->margin = y->margin;
   delete y;
   return QTT_OK;
 }
@@ -380,6 +430,17 @@ qtt_status qtt_to_full(const qtt_tensor* t, void* y, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (t->desc.dt == QTT_F64) return tt_full<double>(t, (double*)y, s);
   return tt_full<float2>(t, (float2*)y, s);
+}
+
+qtt_status qtt_get_margins(const qtt_tensor* t, double* margins_host, void* stream) {
+  g_err[0] = 0;
+  if (!t || !margins_host) { set_error("qtt_get_margins: NULL argument"); return QTT_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  qtt_status st = cuda_check(cudaMemcpyAsync(margins_host, t->margin,
+                                             sizeof(double) * (t->desc.d + 1),
+                                             cudaMemcpyDeviceToHost, s), "qtt_get_margins");
+  if (st != QTT_OK) return st;
+  return cuda_check(cudaStreamSynchronize(s), "qtt_get_margins sync");
 }
 
 qtt_status qtt_get_ranks(const qtt_tensor* t, int* ranks_host, void* stream) {
@@ -445,6 +506,7 @@ qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_d
                           const int* log2_shape, int interleave, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!host_cores || !ranks || !log2_shape || !out) { set_error("qtt_from_cores: NULL argument"); return QTT_EINVAL; }
+  if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_from_cores");
   if (!valid_dtype(dt) || d < 2 || d > 30 || (ndim != 1 && ndim != 2)) {
     set_error("qtt_from_cores: bad dtype/d/ndim");
     return QTT_EINVAL;
@@ -490,6 +552,7 @@ void qtt_free_async(qtt_tensor* t, void* stream) { tensor_free_async(t, (cudaStr
 qtt_status qtt_op_create(int d, double B, int normalize, double eps_op, qtt_dtype dt, void* stream,
                          qtt_op** out) {
   g_err[0] = 0;
+  if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_op_create");
   if (!out || !valid_dtype(dt)) { set_error("qtt_op_create: bad argument"); return QTT_EINVAL; }
   if (!(B > 0.0) || !(eps_op > 0.0) || eps_op >= 1.0) { set_error("qtt_op_create: B > 0 and eps_op in (0,1) required"); return QTT_EINVAL; }
   return op_sinc_create(d, B, normalize ? 1 : 0, eps_op, dt, (cudaStream_t)stream, out);
@@ -524,6 +587,7 @@ qtt_status qtt_sinc_padded(int log2_n, long long N, double B, int normalize, qtt
                            void* g_dev, void* stream) {
   g_err[0] = 0;
   if (!g_dev) { set_error("qtt_sinc_padded: NULL output"); return QTT_EINVAL; }
+  if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_sinc_padded");
   if (!valid_dtype(dt) || log2_n < 1 || log2_n > 30) {
     set_error("qtt_sinc_padded: bad dtype or log2_n");
     return QTT_EINVAL;
@@ -540,9 +604,9 @@ qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sk
                    unsigned long long seed, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !out) { set_error("qtt_fft: NULL argument"); return QTT_EINVAL; }
-  qtt_trunc t0 = {0.0, 0, 1, 0.0};
+  qtt_trunc t0 = {0.0, 0, 1, 0.0, QTT_PREC_AUTO, nullptr};
   if (tr) {
-    qtt_status st = check_trunc(tr);
+    qtt_status st = check_trunc(tr, x->desc.dt, x->desc.d);
     if (st != QTT_OK) return st;
     t0 = *tr;
   }
@@ -590,7 +654,7 @@ qtt_status qtt_conv_adjoint(const qtt_tensor* f, const qtt_tensor* r, const doub
   if (grad_cores)
     for (int k = 0; k < r->desc.d; ++k)
       if (!grad_cores[k]) { set_error("qtt_conv_adjoint: grad_cores[%d] is NULL", k); return QTT_EINVAL; }
-  qtt_status st = check_trunc(round_tr);
+  qtt_status st = check_trunc(round_tr, r->desc.dt, r->desc.d);
   if (st != QTT_OK) return st;
   if (!(eps_op > 0.0) || eps_op >= 1.0) { set_error("qtt_conv_adjoint: eps_op must be in (0, 1)"); return QTT_EINVAL; }
   for (int a = 0; a < r->desc.ndim; ++a)
@@ -665,6 +729,7 @@ qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int
                                  qtt_tensor** out) {
   g_err[0] = 0;
   if (!cores || !ranks || !log2_shape || !out) { set_error("qtt_from_device_cores: NULL argument"); return QTT_EINVAL; }
+  if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_from_device_cores");
   if (!valid_dtype(dt) || d < 2 || d > 30 || (ndim != 1 && ndim != 2)) {
     set_error("qtt_from_device_cores: bad dtype/d/ndim");
     return QTT_EINVAL;

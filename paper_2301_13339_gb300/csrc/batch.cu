@@ -99,6 +99,18 @@ qtt_status qtt_batch_create(int nlines, const int* log2_len, const double* B, co
     set_error("qtt_batch_create: bad argument");
     return QTT_EINVAL;
   }
+  if (round_tr->fixed_ranks) {
+    set_error("qtt_batch_create: fixed_ranks are not supported for batches (lines differ in length)");
+    return QTT_EINVAL;
+  }
+  if (round_tr->prec == QTT_PREC_BF16_REFINED || round_tr->prec == QTT_PREC_TF32_REFINED) {
+    set_error("qtt_batch_create: the BF16/TF32 tensor-core precision modes are not built");
+    return QTT_EUNSUPPORTED;
+  }
+  if (dt == QTT_F32 || dt == QTT_C128) {
+    set_error("qtt_batch_create: element type %d is not built (QTT_F64 and QTT_C64 are)", (int)dt);
+    return QTT_EUNSUPPORTED;
+  }
   if (dt != QTT_C64 && dt != QTT_F64) { set_error("qtt_batch_create: dtype"); return QTT_EINVAL; }
   if (!(eps >= 0.0) || eps >= 1.0 || !(eps_op > 0.0) || eps_op >= 1.0) {
     set_error("qtt_batch_create: eps in [0, 1) and eps_op in (0, 1) required");

@@ -396,17 +396,23 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a, HeevSpl
           const double lp = (double)s_lam[n - c], lc = (double)s_lam[n - 1 - c];
           if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
         }
-      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
+      }
+      double margin = __longlong_as_double(0x7ff8000000000000LL);   // NaN: not an eps decision
+      if (!(a.delta > 0.0) && a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
+        double kept = 0.0;
+        bool stopped = false;
         for (int c = kmax - 1; c >= 1; --c) {
           const double l = (double)s_lam[n - 1 - c] * s_trace;
           tail += (l > 0.0 ? l : 0.0);
-          if (tail <= tau2) r = c;
-          else break;
+          if (tail <= tau2) { r = c; kept = tail; }
+          else { stopped = true; break; }
         }
+        if (tau2 > 0.0) margin = rank_margin(tau2, kept, tail, stopped);
       }
-      if (a.rmax > 0 && r > a.rmax) r = a.rmax;
+      if (a.rmax > 0 && r > a.rmax) { r = a.rmax; margin = __longlong_as_double(0x7ff8000000000000LL); }
       if (r < 1) r = 1;
       if (a.rank_out) *a.rank_out = r;
+      if (a.margin_out) *a.margin_out = margin;
     }
     s_r = r;
     // clusters over the descending order: c joins c-1's cluster when close

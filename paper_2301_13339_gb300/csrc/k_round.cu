@@ -742,6 +742,11 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   if (sketch <= 0) sketch = QTT_RANK_CAP;
   sketch = std::min(sketch, QTT_RANK_CAP);
   const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
+  // forced ranks (parity mode): the cap-only rule with a per-cut cap
+  const int* fixed = tr.fixed_ranks;
+  auto cap_at = [&](int k) { return fixed ? std::min(fixed[k], QTT_RANK_CAP) : rmax_eff; };
+  const double eps_u = fixed ? 0.0 : tr.eps;
+  const double delta_u = fixed ? 0.0 : tr.delta;
   const std::vector<int>& P = op->P;
   const std::vector<int>& xcap = x->rcap;
   std::vector<int> Rc(d + 1), l(d + 1), lq(d + 1), ocap(d + 1);
@@ -757,7 +762,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
   for (int k = d; k >= 2; --k) lq[k - 1] = std::min(l[k - 1], 2 * lq[k]);
   lq[0] = 1;
   ocap[0] = 1;
-  for (int k = 1; k < d; ++k) ocap[k] = std::min({2 * ocap[k - 1], lq[k], rmax_eff});
+  for (int k = 1; k < d; ++k) ocap[k] = std::min({2 * ocap[k - 1], lq[k], cap_at(k)});
   ocap[d] = 1;
 
   const R* Oc = (const R*)op->cores;
@@ -927,7 +932,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
       k_gram_rows<T><<<GRID1(lqk * lqk)>>>(Rz, kd, 1, lqk, lqk, G, 128);
       }
       if (refine) {
-        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 0 /*ALL*/, tr.eps, d, rmax_eff, nullptr, 0, lqk,
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 0 /*ALL*/, eps_u, d, cap_at(k), nullptr, 0, lqk,
                             nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1, y->status, s);
         { QTT_PROF("round_trunc", s);
         k_proj_rows<T><<<GRID1(lqk * lqk)>>>(V1, Rz, kd, 1, nullptr, lqk, lqk, W1);
@@ -935,13 +940,13 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
         { QTT_PROF("round_trunc", s);
         k_gram_rows<T><<<GRID1(lqk * lqk)>>>(W1, kd, 1, lqk, lqk, G, 128);
         }
-        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1 /*DECIDE*/, tr.eps, d, rmax_eff, nullptr, 0,
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1 /*DECIDE*/, eps_u, d, cap_at(k), nullptr, 0,
                             lqk, V1, V, Ur, y->ranks + k, nullptr, y->norm2, 0, y->status, s, 1,
-                            tr.delta);
+                            delta_u, -1, y->margin + k);
       } else {
-        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1, tr.eps, d, rmax_eff, nullptr, 0, lqk,
+        launch_eig_dense<T>(G, 128, kd, 1, 0, lqk, 1, eps_u, d, cap_at(k), nullptr, 0, lqk,
                             nullptr, Ur, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,
-                            y->status, s, 0, tr.delta);
+                            y->status, s, 0, delta_u, -1, y->margin + k);
       }
       const int rcapk = ocap[k];
       { QTT_PROF("round_trunc", s);
@@ -958,7 +963,7 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
     k_gram_rows<T><<<GRID1(mcap * mcap)>>>(Zt, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
     }
     if (refine) {
-      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 0 /*ALL*/, tr.eps, d, rmax_eff,
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 0 /*ALL*/, eps_u, d, cap_at(k),
                           nullptr, 0, lqk, nullptr, V1, nullptr, nullptr, nullptr, y->norm2, k == 1,
                           y->status, s);
       { QTT_PROF("round_trunc", s);
@@ -968,13 +973,13 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
       k_gram_rows<T><<<GRID1(mcap * mcap)>>>(W1, y->ranks + (k - 1), 2, mcap, lqk, G, 128);
       }
       // rank decision at eps_round: small eigenvalues to relative accuracy
-      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, tr.eps, d, rmax_eff,
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1 /*DECIDE*/, eps_u, d, cap_at(k),
                           nullptr, 0, lqk, V1, V, corek, y->ranks + k, nullptr, y->norm2, 0,
-                          y->status, s, 1, tr.delta);
+                          y->status, s, 1, delta_u, -1, y->margin + k);
     } else {
-      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1, tr.eps, d, rmax_eff, nullptr, 0,
+      launch_eig_dense<T>(G, 128, y->ranks + (k - 1), 2, 0, mcap, 1, eps_u, d, cap_at(k), nullptr, 0,
                           lqk, nullptr, corek, nullptr, y->ranks + k, nullptr, y->norm2, k == 1,
-                          y->status, s, 0, tr.delta);
+                          y->status, s, 0, delta_u, -1, y->margin + k);
     }
     // Lc = core_k^H Zt  (t_k x lq_k)
     { QTT_PROF("round_trunc", s);

@@ -267,17 +267,23 @@ __device__ void eig_post(const EigArgs<T>& a, T* A, T* V, int n, int mg, int ldv
           const double lp = s_lam[s_perm[c - 1]], lc = s_lam[s_perm[c]];
           if (lp > 0.0 && (lc > 0.0 ? lc : 0.0) < d2 * lp) { r = c; break; }
         }
-      } else if (a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
+      }
+      double margin = __longlong_as_double(0x7ff8000000000000LL);   // NaN: not an eps decision
+      if (!(a.delta > 0.0) && a.eps > 0.0) {   // eps = 0: the cap alone (max rank TT-SVD)
+        double kept = 0.0;
+        bool stopped = false;
         for (int c = kmax - 1; c >= 1; --c) {
           const double l = s_lam[s_perm[c]];
           tail += (l > 0.0 ? l : 0.0);
-          if (tail <= tau2) r = c;
-          else break;
+          if (tail <= tau2) { r = c; kept = tail; }
+          else { stopped = true; break; }
         }
+        if (tau2 > 0.0) margin = rank_margin(tau2, kept, tail, stopped);
       }
-      if (a.rmax > 0 && r > a.rmax) r = a.rmax;
+      if (a.rmax > 0 && r > a.rmax) { r = a.rmax; margin = __longlong_as_double(0x7ff8000000000000LL); }
       if (r < 1) r = 1;
       if (a.rank_out) *a.rank_out = r;
+      if (a.margin_out) *a.margin_out = margin;
     }
     s_r = r;
   }
@@ -1088,8 +1094,9 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
                       int write_norm2, int* status, cudaStream_t s, int relative,
-                      double delta, int sweeps) {
+                      double delta, int sweeps, double* margin_out) {
   EigArgs<T> a{};
+  a.margin_out = margin_out;
   a.relative = relative;
   a.delta = delta;
   a.max_sweeps = (sweeps >= 0) ? sweeps : (Sc<T>::cplx && relative) ? g_refine_sweeps : 0;
@@ -1107,12 +1114,13 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int mg_cap, int mode, double eps, int dmodes, int rmax, const int* ncols_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
-                     int* status, cudaStream_t s, int relative, double delta, int sweeps) {
+                     int* status, cudaStream_t s, int relative, double delta, int sweeps,
+                     double* margin_out) {
   double2* gfin = (double2*)scratch_alloc(sizeof(double2) * ldp * ldp, s);
   launch_reduce<T>(gram_part, nparts, ldp, gfin, s);
   launch_eig_dense<T>(gfin, ldp, mg_ptr, mg_mul, 0, mg_cap, mode, eps, dmodes, rmax, ncols_ptr,
                       ncols_mul, ncols_const, U1, Uout, core_out, rank_out, sig_out, norm2,
-                      write_norm2, status, s, relative, delta, sweeps);
+                      write_norm2, status, s, relative, delta, sweeps, margin_out);
   scratch_free(gfin, s);
 }
 
@@ -1220,6 +1228,12 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   const bool use_rs = rs && rs->p > 0;
   const bool refine = tr.refine || !Sc<T>::cplx || use_rs;
   const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
+  // forced ranks (parity mode): cut k keeps exactly fixed[k] singular
+  // triplets -- the cap-only rule (eps = 0) with a per-cut cap
+  const int* fixed = tr.fixed_ranks;
+  auto cap_at = [&](int k) { return fixed ? std::min(fixed[k], QTT_RANK_CAP) : rmax_eff; };
+  const double eps_u = fixed ? 0.0 : tr.eps;
+  const double delta_u = fixed ? 0.0 : tr.delta;
   const int max_parts = 2 * 152;
   const int LDP = 128;
   T* bufA = (T*)scratch_alloc(sizeof(T) * N, s);
@@ -1241,8 +1255,9 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   // tau = 0 keeps min(m, n) of them), so U can be the identity and
   // Sigma V^* is the unfolding itself: no factorisation, no data pass.
   int skip = 0;
-  if (tr.eps == 0.0 && !(tr.delta > 0.0))
-    while (skip + 1 <= d - 2 && (1LL << (skip + 1)) <= std::min<long long>(rmax_eff, 1LL << (d - skip - 1)))
+  if (eps_u == 0.0 && !(delta_u > 0.0))
+    while (skip + 1 <= d - 2 &&
+           (1LL << (skip + 1)) <= std::min<long long>(cap_at(skip + 1), 1LL << (d - skip - 1)))
       ++skip;
   for (int k = 1; k <= skip; ++k) {
     const int rp = 1 << (k - 1);
@@ -1263,7 +1278,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
     T* Wout = (k == d - 1) ? cores + t->off[d - 1] : (refine ? bufB : (M == bufA ? bufB : bufA));
     const int fold_next = (k < d - 1) ? 1 : -1;
     const int ldp_next = 2 * rcapk;
-    if (tr.eps == 0.0 && !(tr.delta > 0.0) && k > skip + 1 && n <= 64 && n == rcapk) {
+    if (eps_u == 0.0 && !(delta_u > 0.0) && k > skip + 1 && n <= 64 && n == rcapk) {
       // every singular value is kept from here on (n_k halves each level)
       static std::atomic<unsigned long long> qr_cfg{0};
       if (first_on_device(&qr_cfg))
@@ -1325,7 +1340,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
         // accuracy, as for the TT-SVD levels)
         const int npb = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, nullptr,
                                             0, gp, mcap, max_parts, s);
-        launch_gram_eig<T>(gp, npb, mcap, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
+        launch_gram_eig<T>(gp, npb, mcap, rk + (k - 1), 2, mcap, EIG_MODE_ALL, eps_u, d, cap_at(k),
                            nullptr, 0, n, nullptr, U2, nullptr, nullptr, nullptr, t->norm2, 0,
                            t->status, s);
         {
@@ -1335,7 +1350,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
         cudaMemcpyAsync(U1, bufA, sizeof(T) * (size_t)mcap * mcap, cudaMemcpyDeviceToDevice, s);
       } else {
       // pass 1: all eigenvectors of M M^H
-      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, tr.eps, d, rmax_eff,
+      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_ALL, eps_u, d, cap_at(k),
                          nullptr, 0, n, nullptr, U1, nullptr, nullptr, nullptr, t->norm2,
                          k == skip + 1, t->status, s);
       }
@@ -1344,16 +1359,16 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
                                    mcap, max_parts, s);
       // pass 2: decide the rank on the projected Gram, whose small
       // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
-      launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
-                         rmax_eff, nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
-                         t->status, s, 1, tr.delta);
+      launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, eps_u, d,
+                         cap_at(k), nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
+                         t->status, s, 1, delta_u, -1, t->margin + k);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     } else {
-      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, tr.eps, d,
-                         rmax_eff, nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
-                         t->norm2, k == skip + 1, t->status, s, 0, tr.delta);
+      launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, eps_u, d,
+                         cap_at(k), nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
+                         t->norm2, k == skip + 1, t->status, s, 0, delta_u, -1, t->margin + k);
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, core_k, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     }
@@ -1375,19 +1390,19 @@ template qtt_status tt_svd<float2>(const float2*, int, const qtt_trunc&, qtt_ten
 template void launch_eig_dense<double>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const double*,
                                        double*, double*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int, double, int);
+                                       cudaStream_t, int, double, int, double*);
 template void launch_eig_dense<float2>(const double2*, int, const int*, int, int, int, int, double,
                                        int, int, const int*, int, long long, const float2*,
                                        float2*, float2*, int*, double*, double*, int, int*,
-                                       cudaStream_t, int, double, int);
+                                       cudaStream_t, int, double, int, double*);
 template void launch_gram_eig<double>(const double*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const double*, double*,
                                       double*, int*, double*, double*, int, int*, cudaStream_t, int, double,
-                                      int);
+                                      int, double*);
 template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, int, int, double,
                                       int, int, const int*, int, long long, const float2*, float2*,
                                       float2*, int*, double*, double*, int, int*, cudaStream_t, int, double,
-                                      int);
+                                      int, double*);
 
 }  // namespace qtt
 

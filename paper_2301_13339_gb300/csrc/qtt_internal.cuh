@@ -188,6 +188,7 @@ struct qtt_tensor {
   int* ranks = nullptr;           // device, d+1 ints
   int* status = nullptr;          // device, 1 int
   double* norm2 = nullptr;        // device, 1 double (squared norm at creation)
+  double* margin = nullptr;       // device, d+1 doubles: eps-rule decision margin per cut (NaN: none)
 };
 
 struct qtt_op {
@@ -241,7 +242,7 @@ void launch_gram_eig(const T* gram_part, int nparts, int ldp, const int* mg_ptr,
                      int ncols_mul, long long ncols_const, const T* U1, T* Uout, T* core_out,
                      int* rank_out, double* sig_out, double* norm2, int write_norm2,
                      int* status, cudaStream_t s, int relative = 0, double delta = 0.0,
-                     int sweeps = -1);
+                     int sweeps = -1, double* margin_out = nullptr);
 
 // ------------------------------------------------------------- eigen
 enum { EIG_MODE_ALL = 0, EIG_MODE_DECIDE = 1 };
@@ -274,7 +275,23 @@ struct EigArgs {
   long long* phase_clk; // optional: clock64() at phase boundaries (diagnostics)
   float ortol_rel;      // tridiagonal solver: cluster gap / ||T|| for Gram-Schmidt
   int ns_steps;         // tridiagonal solver: Newton-Schulz steps
+  double* margin_out;   // optional (MODE_DECIDE): margin of the eps-rule decision
 };
+
+// Margin of an eps-rule rank decision: min over the two tails around the
+// cut of |sqrt(tail) - tau| / tau, with tail(r) = sum_{i >= r} lambda_i the
+// kept tail and tail(r-1) the one that was too large; NaN when the rank
+// was not decided by the eps rule (eps = 0, the drop-off rule, or the cap).
+__host__ __device__ inline double rank_margin(double tau2, double tail_kept, double tail_next,
+                                              bool has_next) {
+  const double tau = sqrt(tau2);
+  double m = fabs(sqrt(tail_kept > 0.0 ? tail_kept : 0.0) - tau) / tau;
+  if (has_next) {
+    const double m2 = fabs(sqrt(tail_next > 0.0 ? tail_next : 0.0) - tau) / tau;
+    m = m2 < m ? m2 : m;
+  }
+  return m;
+}
 
 
 // one-CTA Hermitian eigensolvers (k_svd.cu: Jacobi; k_heev.cu: Householder
@@ -291,7 +308,7 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
                       const int* ncols_ptr, int ncols_mul, long long ncols_const, const T* U1,
                       T* Uout, T* core_out, int* rank_out, double* sig_out, double* norm2,
                       int write_norm2, int* status, cudaStream_t s, int relative = 0,
-                      double delta = 0.0, int sweeps = -1);
+                      double delta = 0.0, int sweeps = -1, double* margin_out = nullptr);
 
 // ------------------------------------------------------------- large ranks
 // First call for the current device with this flag word: true once per

@@ -7,12 +7,14 @@ import ctypes
 import pytest
 
 QTT_EINVAL = -1
-QTT_F64, QTT_C64 = 0, 2
+QTT_EUNSUPPORTED = -6
+QTT_F64, QTT_F32, QTT_C64, QTT_C128 = 0, 1, 2, 3
 
 
 class Trunc(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("rmax", ctypes.c_int), ("refine", ctypes.c_int),
-                ("delta", ctypes.c_double)]
+                ("delta", ctypes.c_double), ("prec", ctypes.c_int),
+                ("fixed_ranks", ctypes.POINTER(ctypes.c_int))]
 
 
 @pytest.fixture(scope="module")
@@ -28,8 +30,8 @@ def buf():
     return ctypes.create_string_buffer(4096)
 
 
-def _expect(lib, status, words):
-    assert status == QTT_EINVAL
+def _expect(lib, status, words, code=QTT_EINVAL):
+    assert status == code
     msg = lib.qtt_last_error().decode()
     for w in words:
         assert w in msg, msg
@@ -44,7 +46,26 @@ def test_decompose_arguments(lib, buf):
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                   ctypes.c_int, ctypes.POINTER(Trunc), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     _expect(lib, f(None, QTT_C64, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["NULL"])
-    _expect(lib, f(p, 1, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["dtype"])
+    _expect(lib, f(p, 7, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["dtype"])
+    for dt in (QTT_F32, QTT_C128):   # named by the ABI, not built
+        _expect(lib, f(p, dt, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)),
+                ["not built"], QTT_EUNSUPPORTED)
+    # precision selector: tensor-core modes not built, FP64 with complex64 data
+    for pr in (3, 4):
+        _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, pr, None)), None,
+                       ctypes.byref(out)), ["not built"], QTT_EUNSUPPORTED)
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 1, None)), None,
+                   ctypes.byref(out)), ["does not match"])
+    _expect(lib, f(p, QTT_F64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 2, None)), None,
+                   ctypes.byref(out)), ["does not match"])
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 9, None)), None,
+                   ctypes.byref(out)), ["qtt_prec"])
+    # forced ranks: ends not 1, a rank above min(2^k, 2^(d-k), 64)
+    bad_ends = (ctypes.c_int * 11)(*([2] + [1] * 9 + [1]))
+    too_big = (ctypes.c_int * 11)(1, 2, 4, 9, 16, 32, 16, 8, 4, 2, 1)
+    for fr, w in ((bad_ends, "r_0"), (too_big, "r_3")):
+        tr = Trunc(0.0, 0, 1, 0.0, 0, ctypes.cast(fr, ctypes.POINTER(ctypes.c_int)))
+        _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(tr), None, ctypes.byref(out)), [w])
     _expect(lib, f(p, QTT_C64, 3, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)), ["ndim"])
     _expect(lib, f(p, QTT_C64, 1, sh, 1, None, None, ctypes.byref(out)), ["NULL"])
     _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(1.5, 0, 1, 0.0)), None,
@@ -81,7 +102,8 @@ def test_sinc_padded_arguments(lib, buf):
     _expect(lib, f(10, 513, 64.0, 1, QTT_C64, p, None), ["N odd"])      # 2N - 1 > n
     _expect(lib, f(10, 0, 64.0, 1, QTT_C64, p, None), ["N odd"])
     _expect(lib, f(31, 511, 64.0, 1, QTT_C64, p, None), ["log2_n"])
-    _expect(lib, f(10, 511, 64.0, 1, 1, p, None), ["dtype"])
+    _expect(lib, f(10, 511, 64.0, 1, 7, p, None), ["dtype"])
+    _expect(lib, f(10, 511, 64.0, 1, QTT_C128, p, None), ["not built"], QTT_EUNSUPPORTED)
 
 
 def test_handle_entries_reject_null(lib, buf):

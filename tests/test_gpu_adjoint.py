@@ -133,7 +133,18 @@ def test_core_grads_match_oracle_dense_adjoint(qlib, shape, cplx):
     assert abs(L.item() - Lref) <= _tol(cplx, 1e-9, 1e-4) * max(Lref, 1e-30) + _tol(cplx, 0, 1e-6) * np.linalg.norm(gdense) ** 2
     num = np.sqrt(sum(np.linalg.norm(gk.cpu().numpy() - rk) ** 2 for gk, rk in zip(grads, ref)))
     den = np.sqrt(sum(np.linalg.norm(rk) ** 2 for rk in ref))
-    assert num <= _tol(cplx, 1e-8, 2e-3) * den
+    # The gradient is linear in the residual r = T f - g, which the GPU forms
+    # as a difference of two rounded QTT tensors: each rounding is accurate to
+    # u relative to its own norm (u = eps_round on the FP64 path; 2e-6 on the
+    # FP32 path, the accuracy its roundings reach against the FP64 oracle),
+    # so |dr| <= u (||T f|| + ||g||) and the adjoint's rounding adds u ||r||:
+    # |d grad| / |grad| <= u (1 + kappa), kappa = (||T f|| + ||g||) / ||r||.
+    Tf = P.conv_dense(_dense(cf, shape), B1)
+    kappa = (np.linalg.norm(Tf) + np.linalg.norm(gdense)) / np.sqrt(Lref)
+    u = _tol(cplx, 1e-12, 2e-6)
+    bound = 3.0 * u * (1.0 + kappa)
+    assert bound <= _tol(cplx, 1e-8, 2e-3)
+    assert num <= bound * den, f"gradient error {num / den:.2e} > {bound:.2e} (kappa {kappa:.1f})"
 
 
 @pytest.mark.parametrize("shape", [(1024,), (32, 32)])
