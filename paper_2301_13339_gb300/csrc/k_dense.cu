@@ -31,42 +31,49 @@ constexpr int BQ_THREADS = 512;  // panel CTA
 constexpr int BQ_CB = 8;         // columns per CTA in the block-reflector application
 constexpr int BQ_MAXM = 768;     // rows (panel in shared memory: 768 x 32 x 8 B)
 
-// A[k:, j] <- (I - t v v^H) A[k:, j] with v = [1; A[k+1:, k]] (rows of P, ld
-// mp); one warp.
-template <typename T>
-__device__ __forceinline__ void bq_apply_col(T* P, int mp, int k, T t, int j) {
-  const int lane = threadIdx.x & 31;
-  const T* vk = P + (size_t)mp * k;
-  T* x = P + (size_t)mp * j;
-  T w = szero<T>();
-  for (int i = k + lane; i < mp; i += 32) {
-    const T v = (i == k) ? sone(T()) : vk[i];
-    macc(w, v, x[i]);
-  }
-  w = warp_sum(w);
-  const T f = smul(t, w);
-  for (int i = k + lane; i < mp; i += 32) {
-    const T v = (i == k) ? sone(T()) : vk[i];
-    x[i] = ssub(x[i], smul(v, f));
-  }
+// Block-wide reductions of the panel kernel: every thread gets the result
+// (one barrier; the 16 warp partials are read back by every thread).
+template <typename R>
+__device__ __forceinline__ R bq_block_max(R v, R* red) {
+  for (int off = 16; off > 0; off >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R m = red[0];
+  for (int w = 1; w < BQ_THREADS / 32; ++w) m = rmax(m, red[w]);
+  return m;
+}
+template <typename R>
+__device__ __forceinline__ R bq_block_sum(R v, R* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R t = (R)0;
+  for (int w = 0; w < BQ_THREADS / 32; ++w) t += red[w];
+  return t;
 }
 
-// Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory, write it
-// back (R on and above the diagonal, the v_k below) and T (BQ_NB x BQ_NB,
-// column-major) to Tm.
+// Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory (ld mp|1,
+// so consecutive columns fall on different banks), write it back (R on and
+// above the diagonal, the v_k below), V^T (kb x mp, row a = v_a, unit
+// diagonal and zeros above it written out) to Vt, and T (BQ_NB x BQ_NB,
+// column-major) to Tm.  Per reflector: its norm by block reductions over all
+// threads, then one warp per trailing panel column (dot and update).
 template <typename T>
 __global__ void __launch_bounds__(BQ_THREADS)
-k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm) {
+k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __restrict__ Vt) {
+  using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char bq_smem[];
   T* P = reinterpret_cast<T*>(bq_smem);
   __shared__ T s_tau[BQ_NB];
   __shared__ T s_Y[BQ_NB * BQ_NB];
   __shared__ T s_T[BQ_NB * BQ_NB];
+  __shared__ R s_red[2][BQ_THREADS / 32];
   const int mp = m - p;
-  const int tid = threadIdx.x, warp = tid >> 5, nw = BQ_THREADS / 32;
+  const int ld = mp | 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < mp * kb; e += BQ_THREADS) {
     const int i = e % mp, j = e / mp;
-    P[e] = A[(size_t)(p + i) + (size_t)m * (p + j)];
+    P[i + (size_t)ld * j] = A[(size_t)(p + i) + (size_t)m * (p + j)];
   }
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQ_THREADS) {
     s_T[e] = szero<T>();
@@ -74,95 +81,157 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm) {
   }
   __syncthreads();
   const int kmax = min(mp, kb);
-  if (kmax > 0 && warp == 0) house_form_reflector(P, mp, 0, s_tau);
-  __syncthreads();
   for (int k = 0; k < kmax; ++k) {
-    const T ctau = conjg(s_tau[k]);
-    if (warp == 0) {
-      if (k + 1 < kb) {
-        bq_apply_col(P, mp, k, ctau, k + 1);
-        __syncwarp();
-        if (k + 1 < kmax) house_form_reflector(P, mp, k + 1, s_tau);
+    T* col = P + (size_t)ld * k;
+    // reflector k: scaled by the column's largest entry (no overflow or
+    // underflow of |alpha - beta|^2 at any data scale)
+    R amax = (R)0;
+    for (int i = k + tid; i < mp; i += BQ_THREADS)
+      amax = rmax(amax, rmax(rabs(sreal(col[i])), rabs(simag(col[i]))));
+    amax = bq_block_max(amax, s_red[0]);
+    T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
+    bool act = false;
+    if (amax > (R)0) {
+      const R inv = (R)1 / amax;
+      R part = (R)0;
+      for (int i = k + 1 + tid; i < mp; i += BQ_THREADS) part += sabs2(rscale(col[i], inv));
+      part = bq_block_sum(part, s_red[1]);
+      const T al = rscale(col[k], inv);
+      const R ax = sreal(al), ay = simag(al);
+      if (part > (R)0 || ay != (R)0) {
+        act = true;
+        const R nrm = sqrt(ax * ax + ay * ay + part);
+        const R beta = (ax >= (R)0) ? -nrm : nrm;
+        const R rb = (R)1 / beta;
+        tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
+        const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
+        scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
+        beta_s = make_scalar<T>(beta * amax, (R)0);
       }
-    } else {
-      for (int j = k + 2 + (warp - 1); j < kb; j += nw - 1) bq_apply_col(P, mp, k, ctau, j);
+    }
+    __syncthreads();   // every thread has read col[k] before it changes
+    if (act)
+      for (int i = k + 1 + tid; i < mp; i += BQ_THREADS) col[i] = smul(col[i], scal);
+    if (tid == 0) {
+      col[k] = beta_s;
+      s_tau[k] = tau;
+    }
+    __syncthreads();
+    // trailing panel columns: A <- (I - conj(tau) v v^H) A, 16 threads (half
+    // a warp) per column, rows strided by 16, two partial sums each
+    const T ctau = conjg(tau);
+    {
+      const int g = tid >> 4, l16 = tid & 15;
+      const int j = k + 1 + g;
+      const bool live = j < kb;          // both halves of a warp shuffle below
+      T* x = P + (size_t)ld * (live ? j : k);
+      T w0 = szero<T>(), w1 = szero<T>();
+      if (live) {
+        int i = k + l16;
+        if (i == k) { macc(w0, sone(T()), x[i]); i += 16; }
+        for (; i + 16 < mp; i += 32) {
+          macc(w0, col[i], x[i]);
+          macc(w1, col[i + 16], x[i + 16]);
+        }
+        if (i < mp) macc(w0, col[i], x[i]);
+      }
+      T w = sadd(w0, w1);
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) w = sadd(w, shfl_xor_s(w, off));
+      if (live) {
+        const T f = smul(ctau, w);
+        for (int i = k + l16; i < mp; i += 16) x[i] = ssub(x[i], smul((i == k) ? sone(T()) : col[i], f));
+      }
     }
     __syncthreads();
   }
-  // Y[a + NB b] = v_a^H v_b (a < b), one warp per pair
-  for (int pr = warp; pr < kmax * kmax; pr += nw) {
+  // Y[a + NB b] = v_a^H v_b (a < b): one thread per pair (rows i >= b)
+  for (int pr = tid; pr < kmax * kmax; pr += BQ_THREADS) {
     const int a = pr % kmax, b = pr / kmax;
     if (a >= b) continue;
-    const int lane = tid & 31;
-    T acc = szero<T>();
-    for (int i = b + lane; i < mp; i += 32) {
-      const T vb = (i == b) ? sone(T()) : P[i + (size_t)mp * b];
-      macc(acc, P[i + (size_t)mp * a], vb);   // i >= b > a: v_a[i] = P[i, a]
+    const T* va = P + (size_t)ld * a;
+    const T* vb = P + (size_t)ld * b;
+    T acc = conjg(va[b]), acc1 = szero<T>(), acc2 = szero<T>(), acc3 = szero<T>();   // row b: v_b = 1
+    int i = b + 1;
+    for (; i + 3 < mp; i += 4) {
+      macc(acc, va[i], vb[i]);
+      macc(acc1, va[i + 1], vb[i + 1]);
+      macc(acc2, va[i + 2], vb[i + 2]);
+      macc(acc3, va[i + 3], vb[i + 3]);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) s_Y[a + BQ_NB * b] = acc;
+    for (; i < mp; ++i) macc(acc, va[i], vb[i]);
+    s_Y[a + BQ_NB * b] = sadd(sadd(acc, acc1), sadd(acc2, acc3));
   }
   __syncthreads();
-  // T(b, b) = tau_b;  T(0:b, b) = -tau_b T(0:b, 0:b) Y(0:b, b)
-  if (warp == 0) {
-    const int lane = tid & 31;
-    for (int b = 0; b < kmax; ++b) {
-      T val = szero<T>();
-      if (lane < b) {
-        for (int c = lane; c < b; ++c) mac(val, s_T[lane + BQ_NB * c], s_Y[c + BQ_NB * b]);
-        val = smul(make_scalar<T>(-sreal(s_tau[b]), -simag(s_tau[b])), val);
-      }
-      __syncwarp();
-      if (lane < b) s_T[lane + BQ_NB * b] = val;
-      if (lane == b) s_T[b + BQ_NB * b] = s_tau[b];
-      __syncwarp();
+  // T(a, a) = tau_a, T(a, b) = -tau_b sum_{c=a}^{b-1} T(a, c) Y(c, b): each
+  // row a is its own recurrence over b, one lane per row
+  if (warp == 0 && lane < kmax) {
+    const int a = lane;
+    s_T[a + BQ_NB * a] = s_tau[a];
+    for (int b = a + 1; b < kmax; ++b) {
+      T acc = szero<T>();
+      for (int c = a; c < b; ++c) mac(acc, s_T[a + BQ_NB * c], s_Y[c + BQ_NB * b]);
+      s_T[a + BQ_NB * b] = smul(make_scalar<T>(-sreal(s_tau[b]), -simag(s_tau[b])), acc);
     }
   }
   __syncthreads();
   for (int e = tid; e < mp * kb; e += BQ_THREADS) {
     const int i = e % mp, j = e / mp;
-    A[(size_t)(p + i) + (size_t)m * (p + j)] = P[e];
+    A[(size_t)(p + i) + (size_t)m * (p + j)] = P[i + (size_t)ld * j];
+  }
+  // V^T rows with the implicit unit diagonal and the zeros above it
+  for (int e = tid; e < mp * kb; e += BQ_THREADS) {
+    const int i = e % mp, a = e / mp;
+    Vt[i + (size_t)mp * a] = (i == a) ? sone(T()) : (i > a && a < kmax) ? P[i + (size_t)ld * a] : szero<T>();
   }
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQ_THREADS) Tm[e] = s_T[e];
 }
 
 // X[p:m, c] <- (I - V op(T) V^H) X[p:m, c] for the columns c of this CTA
-// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols); V = the kb
-// reflectors stored in A[p:m, p:p+kb] (unit diagonal).  adj = 1: op(T) = T^H
-// (applies Q^H, the trailing update); adj = 0: op(T) = T (forms Q).
+// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols); V^T = Vt (kb
+// rows of mp, ld mp).  adj = 1: op(T) = T^H (applies Q^H, the trailing
+// update); adj = 0: op(T) = T (forms Q).  W = V^H X by warps (4 reflectors x
+// BQ_CB columns each, lanes over rows), then op(T) W, then one warp per
+// column for the update.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_bq_apply(T* X, int m, int col0, int ncols, const T* A, int p, int kb, const T* __restrict__ Tm,
-           int adj) {
-  __shared__ T Vs[32][BQ_NB + 1];
-  __shared__ T Xs[32][BQ_CB];
+__global__ void __launch_bounds__(32 * BQ_CB)
+k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ Vt, int p, int kb,
+           const T* __restrict__ Tm, int adj) {
   __shared__ T W[BQ_NB][BQ_CB];
   __shared__ T W2[BQ_NB][BQ_CB];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cbase = col0 + BQ_CB * blockIdx.x;
+  const int cend = col0 + ncols;
   const int mp = m - p;
-  const int a = tid % BQ_NB, c = tid / BQ_NB;   // 32 x 8
-  T acc = szero<T>();
-  for (int r0 = 0; r0 < mp; r0 += 32) {
-    __syncthreads();
-    for (int e = tid; e < 32 * BQ_NB; e += 256) {
-      const int ri = e % 32, aa = e / 32, i = r0 + ri;
-      T v = szero<T>();
-      if (i < mp && aa < kb) v = (i == aa) ? sone(T()) : (i > aa) ? A[(size_t)(p + i) + (size_t)m * (p + aa)] : szero<T>();
-      Vs[ri][aa] = v;
+  constexpr int AW = BQ_NB / BQ_CB;   // reflectors per warp (8 warps x 4 = 32)
+  T acc[AW][BQ_CB];
+#pragma unroll
+  for (int u = 0; u < AW; ++u)
+#pragma unroll
+    for (int c = 0; c < BQ_CB; ++c) acc[u][c] = szero<T>();
+  for (int i = lane; i < mp; i += 32) {
+    T x[BQ_CB];
+#pragma unroll
+    for (int c = 0; c < BQ_CB; ++c)
+      x[c] = (cbase + c < cend) ? X[(size_t)(p + i) + (size_t)m * (cbase + c)] : szero<T>();
+#pragma unroll
+    for (int u = 0; u < AW; ++u) {
+      const int a = warp * AW + u;
+      const T v = (a < kb) ? Vt[i + (size_t)mp * a] : szero<T>();
+#pragma unroll
+      for (int c = 0; c < BQ_CB; ++c) macc(acc[u][c], v, x[c]);
     }
-    {
-      const int ri = tid % 32, cc = tid / 32, i = r0 + ri;
-      const int col = cbase + cc;
-      Xs[ri][cc] = (i < mp && col < col0 + ncols) ? X[(size_t)(p + i) + (size_t)m * col] : szero<T>();
-    }
-    __syncthreads();
-    const int rn = min(32, mp - r0);
-    for (int ri = 0; ri < rn; ++ri) macc(acc, Vs[ri][a], Xs[ri][c]);
   }
-  W[a][c] = acc;
+#pragma unroll
+  for (int u = 0; u < AW; ++u)
+#pragma unroll
+    for (int c = 0; c < BQ_CB; ++c) {
+      const T w = warp_sum(acc[u][c]);
+      if (lane == 0) W[warp * AW + u][c] = w;
+    }
   __syncthreads();
   {
+    const int a = tid % BQ_NB, c = tid / BQ_NB;
     T w2 = szero<T>();
     if (a < kb) {
       if (adj) {
@@ -173,23 +242,14 @@ k_bq_apply(T* X, int m, int col0, int ncols, const T* A, int p, int kb, const T*
     }
     W2[a][c] = w2;
   }
-  for (int r0 = 0; r0 < mp; r0 += 32) {
-    __syncthreads();
-    for (int e = tid; e < 32 * BQ_NB; e += 256) {
-      const int ri = e % 32, aa = e / 32, i = r0 + ri;
-      T v = szero<T>();
-      if (i < mp && aa < kb) v = (i == aa) ? sone(T()) : (i > aa) ? A[(size_t)(p + i) + (size_t)m * (p + aa)] : szero<T>();
-      Vs[ri][aa] = v;
-    }
-    __syncthreads();
-    const int ri = tid % 32, cc = tid / 32, i = r0 + ri;
-    const int col = cbase + cc;
-    if (i < mp && col < col0 + ncols) {
-      T s = szero<T>();
-      for (int aa = 0; aa < kb; ++aa) mac(s, Vs[ri][aa], W2[aa][cc]);
-      T* xp = X + (size_t)(p + i) + (size_t)m * col;
-      *xp = ssub(*xp, s);
-    }
+  __syncthreads();
+  const int col = cbase + warp;
+  if (col >= cend) return;
+  T* xc = X + (size_t)m * col;
+  for (int i = lane; i < mp; i += 32) {
+    T sacc = szero<T>();
+    for (int a = 0; a < kb; ++a) mac(sacc, Vt[i + (size_t)mp * a], W2[a][warp]);
+    xc[p + i] = ssub(xc[p + i], sacc);
   }
 }
 
@@ -211,8 +271,11 @@ __global__ void k_conj_transpose(const T* S, int ls, int n, int m, T* A) {
   A[e] = conjg(S[j + (size_t)ls * i]);
 }
 
-size_t big_qr_panel_smem(int m) { return sizeof(float2) * (size_t)m * BQ_NB; }
-size_t big_qr_tm_elems(int n) { return (size_t)((n + BQ_NB - 1) / BQ_NB) * BQ_NB * BQ_NB; }
+// workspace of big_qr_q: T of every panel, then V^T of every panel
+size_t big_qr_tm_elems(int n) {
+  const size_t np = (size_t)((n + BQ_NB - 1) / BQ_NB);
+  return np * BQ_NB * BQ_NB + np * BQ_NB * BQ_MAXM;
+}
 
 static std::atomic<unsigned long long> g_bq_cfg[2];
 
@@ -220,7 +283,7 @@ template <typename T>
 static void bq_configure() {
   if (first_on_device(&g_bq_cfg[sizeof(T) == sizeof(double) ? 1 : 0]))
     cudaFuncSetAttribute(k_bq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * BQ_MAXM * BQ_NB));
+                         (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
 }
 
 template <typename T>
@@ -232,31 +295,34 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
   }
   bq_configure<T>();
   const int kmax = std::min(m, n);
+  const int np = (kmax + BQ_NB - 1) / BQ_NB;
+  T* Vall = Tm + (size_t)((n + BQ_NB - 1) / BQ_NB) * BQ_NB * BQ_NB;   // V^T of panel pi at pi NB MAXM
   for (int p = 0; p < kmax; p += BQ_NB) {
     const int kb = std::min(BQ_NB, kmax - p);
     T* Tp = Tm + (size_t)(p / BQ_NB) * BQ_NB * BQ_NB;
+    T* Vp = Vall + (size_t)(p / BQ_NB) * BQ_NB * BQ_MAXM;
     {
       QTT_PROF("bigqr_panel", s);
-      k_bq_panel<T><<<1, BQ_THREADS, sizeof(T) * (size_t)(m - p) * kb, s>>>(A, m, p, kb, Tp);
+      k_bq_panel<T><<<1, BQ_THREADS, sizeof(T) * (size_t)((m - p) | 1) * kb, s>>>(A, m, p, kb, Tp, Vp);
     }
     const int c0 = p + kb, nc = kmax - c0;
     if (nc > 0) {
       QTT_PROF("bigqr_update", s);
-      k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 256, 0, s>>>(A, m, c0, nc, A, p, kb, Tp, 1);
+      k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nc, Vp, p, kb, Tp, 1);
     }
   }
   {
     QTT_PROF("bigqr_formq", s);
     k_bq_eye<T><<<(unsigned)(((long long)m * nq + 255) / 256), 256, 0, s>>>(Q, m, nq);
   }
-  const int np = (kmax + BQ_NB - 1) / BQ_NB;
   for (int pi = np - 1; pi >= 0; --pi) {
     const int p = pi * BQ_NB;
     const int kb = std::min(BQ_NB, kmax - p);
     if (p >= nq) continue;
     QTT_PROF("bigqr_formq", s);
-    k_bq_apply<T><<<(nq - p + BQ_CB - 1) / BQ_CB, 256, 0, s>>>(
-        Q, m, p, nq - p, A, p, kb, Tm + (size_t)pi * BQ_NB * BQ_NB, 0);
+    k_bq_apply<T><<<(nq - p + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(
+        Q, m, p, nq - p, Vall + (size_t)pi * BQ_NB * BQ_MAXM, p, kb,
+        Tm + (size_t)pi * BQ_NB * BQ_NB, 0);
   }
   return cuda_check(cudaGetLastError(), "big_qr launch");
 }
@@ -298,18 +364,26 @@ __device__ __forceinline__ void cg_kadd(float2& s, float2& c, float2 v) {
   s.y = t;
 }
 
+// One 64 x 64 output tile of batch z % nbatch over the k range of split
+// z / nbatch (kchunk terms each).  The next k chunk's operands are loaded
+// into registers while the current one is multiplied from shared memory
+// (two buffers, one barrier per chunk).  With splits > 1 the tile's partial
+// sum goes to part + split * ldpart (ld M), summed by k_cgemm_reduce.
 template <typename TA>
-__global__ void __launch_bounds__(CG_THREADS) k_cgemm(CGemmArgs<TA> g) {
-  __shared__ TA As[CG_BK][CG_BM + 1];
-  __shared__ float2 Bs[CG_BK][CG_BN + 1];
+__global__ void __launch_bounds__(CG_THREADS, 2)
+k_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, long long ldpart) {
+  __shared__ TA As[2][CG_BK][CG_BM + 1];
+  __shared__ float2 Bs[2][CG_BK][CG_BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int bz = blockIdx.z;
+  const int bz = blockIdx.z % nbatch, split = blockIdx.z / nbatch;
   const int b1 = bz % g.nb1, b2 = bz / g.nb1;
   const TA* A = g.A + g.bA1 * b1 + g.bA2 * b2;
   const float2* B = g.B + g.bB1 * b1 + g.bB2 * b2;
-  float2* C = g.C + g.bC1 * b1 + g.bC2 * b2;
   const long long i0 = (long long)blockIdx.y * CG_BM, j0 = (long long)blockIdx.x * CG_BN;
+  const int kbeg = split * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const bool a_rows_unit = (g.sAi == 1);
   float2 sum[4][4], cmp[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -318,52 +392,78 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgemm(CGemmArgs<TA> g) {
       sum[u][v] = make_float2(0.f, 0.f);
       cmp[u][v] = make_float2(0.f, 0.f);
     }
-  const bool a_rows_unit = (g.sAi == 1);
-  for (int k0 = 0; k0 < g.K; k0 += CG_BK) {
-    __syncthreads();
-    for (int e = tid; e < CG_BM * CG_BK; e += CG_THREADS) {
+  constexpr int LA = CG_BM * CG_BK / CG_THREADS;   // 4 elements of A and of B per thread
+  TA ra[LA];
+  float2 rb[LA];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < LA; ++t) {
+      const int e = tid + CG_THREADS * t;
       int ii, kk;
       if (a_rows_unit) { ii = e % CG_BM; kk = e / CG_BM; }
       else { kk = e % CG_BK; ii = e / CG_BK; }
       const long long i = i0 + ii;
       const int k = k0 + kk;
       TA v = cg_zero(TA());
-      if (i < g.M && k < g.K) {
+      if (i < g.M && k < kend) {
         v = A[i * g.sAi + (long long)k * g.sAk];
         if (g.conjA) v = cg_conj(v);
       }
-      As[kk][ii] = v;
-    }
-    for (int e = tid; e < CG_BN * CG_BK; e += CG_THREADS) {
-      const int kk = e % CG_BK, jj = e / CG_BK;
+      ra[t] = v;
+      const int kb = e % CG_BK, jj = e / CG_BK;
       const long long j = j0 + jj;
-      const int k = k0 + kk;
-      Bs[kk][jj] = (j < g.N && k < g.K) ? B[(long long)k * g.sBk + j * g.sBj] : make_float2(0.f, 0.f);
+      const int k2 = k0 + kb;
+      rb[t] = (j < g.N && k2 < kend) ? B[(long long)k2 * g.sBk + j * g.sBj] : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    float2 part[4][4];
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < LA; ++t) {
+      const int e = tid + CG_THREADS * t;
+      int ii, kk;
+      if (a_rows_unit) { ii = e % CG_BM; kk = e / CG_BM; }
+      else { kk = e % CG_BK; ii = e / CG_BK; }
+      As[buf][kk][ii] = ra[t];
+      Bs[buf][e % CG_BK][e / CG_BK] = rb[t];
+    }
+  };
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kbeg; k0 < kend; k0 += CG_BK) {
+    const bool more = k0 + CG_BK < kend;
+    if (more) load(k0 + CG_BK);
+    float2 pt[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) part[u][v] = make_float2(0.f, 0.f);
+      for (int v = 0; v < 4; ++v) pt[u][v] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int kk = 0; kk < CG_BK; ++kk) {
       TA a[4];
       float2 b[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = As[buf][kk][ty + 16 * u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) b[v] = Bs[buf][kk][tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) cg_mac(part[u][v], a[u], b[v]);
+        for (int v = 0; v < 4; ++v) cg_mac(pt[u][v], a[u], b[v]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) cg_kadd(sum[u][v], cmp[u][v], part[u][v]);
+      for (int v = 0; v < 4; ++v) cg_kadd(sum[u][v], cmp[u][v], pt[u][v]);
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
   }
+  float2* C = part ? part + (long long)split * ldpart : g.C + g.bC1 * b1 + g.bC2 * b2;
+  const long long sCi = part ? 1 : g.sCi, sCj = part ? g.M : g.sCj;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const long long i = i0 + ty + 16 * u;
@@ -372,33 +472,72 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgemm(CGemmArgs<TA> g) {
     for (int v = 0; v < 4; ++v) {
       const long long j = j0 + tx + 16 * v;
       if (j >= g.N) continue;
-      C[i * g.sCi + j * g.sCj] = make_float2(sum[u][v].x - cmp[u][v].x, sum[u][v].y - cmp[u][v].y);
+      C[i * sCi + j * sCj] = make_float2(sum[u][v].x - cmp[u][v].x, sum[u][v].y - cmp[u][v].y);
     }
   }
 }
 
+// C[i, j] = sum over splits of part[s][i + M j], compensated, in split order
+__global__ void k_cgemm_reduce(const float2* __restrict__ part, int splits, long long ldpart, int M,
+                               int N, float2* __restrict__ C, long long sCi, long long sCj) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)M * N) return;
+  const long long i = e % M, j = e / M;
+  float2 sm = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  for (int s2 = 0; s2 < splits; ++s2) cg_kadd(sm, c, part[e + (long long)s2 * ldpart]);
+  C[i * sCi + j * sCj] = make_float2(sm.x - c.x, sm.y - c.y);
+}
+
 template <typename TA>
-qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s) {
+qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char* name) {
   if (g.M <= 0 || g.N <= 0 || nbatch <= 0) return QTT_OK;
   if (g.nb1 < 1 || nbatch > 65535) {
     set_error("cgemm: bad batch (%d, nb1 %d)", nbatch, g.nb1);
     return QTT_EINVAL;
   }
-  dim3 grid((unsigned)((g.N + CG_BN - 1) / CG_BN), (unsigned)((g.M + CG_BM - 1) / CG_BM),
-            (unsigned)nbatch);
-  if (grid.y > 65535) {
+  if ((g.M + CG_BM - 1) / CG_BM > 65535) {
     set_error("cgemm: M = %d too large", g.M);
     return QTT_EINVAL;
   }
-  QTT_PROF("round_gemm", s);
+  const long long tiles = (long long)((g.N + CG_BN - 1) / CG_BN) * ((g.M + CG_BM - 1) / CG_BM);
+  // split k when the tiles alone cannot fill the GPU (one batch, long k)
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int splits = 1;
+  if (nbatch == 1 && tiles < 2LL * sms && g.K >= 8 * CG_BK) {
+    splits = (int)std::min<long long>((2LL * sms + tiles - 1) / tiles, (long long)g.K / (4 * CG_BK));
+    splits = std::max(1, std::min(splits, 16));
+  }
+  const int kchunk = ((g.K + splits - 1) / splits + CG_BK - 1) / CG_BK * CG_BK;
+  dim3 grid((unsigned)((g.N + CG_BN - 1) / CG_BN), (unsigned)((g.M + CG_BM - 1) / CG_BM),
+            (unsigned)(nbatch * splits));
+  QTT_PROF(name, s);
   const double mnk = (double)g.M * g.N * g.K * nbatch;
-  prof_add_work("round_gemm", (sizeof(TA) == sizeof(float) ? 4.0 : 8.0) * mnk,
+  prof_add_work(name, (sizeof(TA) == sizeof(float) ? 4.0 : 8.0) * mnk,
                 ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * 8.0 + (double)g.M * g.N * 8.0) *
                     nbatch);
-  k_cgemm<TA><<<grid, CG_THREADS, 0, s>>>(g);
+  if (splits == 1) {
+    k_cgemm<TA><<<grid, CG_THREADS, 0, s>>>(g, nbatch, kchunk, nullptr, 0);
+    return QTT_OK;
+  }
+  const long long ldpart = (long long)g.M * g.N;
+  float2* part = (float2*)scratch_alloc(sizeof(float2) * (size_t)(ldpart * splits), s);
+  if (!part) {
+    set_error("cgemm: split-k scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  k_cgemm<TA><<<grid, CG_THREADS, 0, s>>>(g, 1, kchunk, part, ldpart);
+  k_cgemm_reduce<<<(unsigned)((ldpart + 255) / 256), 256, 0, s>>>(part, splits, ldpart, g.M, g.N,
+                                                                  g.C, g.sCi, g.sCj);
+  scratch_free(part, s);
   return QTT_OK;
 }
-template qtt_status cgemm<float>(const CGemmArgs<float>&, int, cudaStream_t);
-template qtt_status cgemm<float2>(const CGemmArgs<float2>&, int, cudaStream_t);
+
+template qtt_status cgemm<float>(const CGemmArgs<float>&, int, cudaStream_t, const char*);
+template qtt_status cgemm<float2>(const CGemmArgs<float2>&, int, cudaStream_t, const char*);
 
 }  // namespace qtt

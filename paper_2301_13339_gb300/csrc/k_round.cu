@@ -1139,7 +1139,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = WL + wloff[k - 1]; g.sBk = 1; g.sBj = l0;
       g.C = A1; g.sCi = 1; g.sCj = 2LL * lk; g.bC1 = lk;
       g.M = lk; g.N = Rc[k - 1]; g.K = l0; g.nb1 = 2;
-      st = cgemm<R>(g, 2, s);
+      st = cgemm<R>(g, 2, s, "gemm_sketch_a1");
     }
     if (st != QTT_OK) break;
     {  // A2[rho + 2lk (p + Pin (i + 2 b))] = sum_a A1[rho + 2lk (a + r0 p)] X[a + r0 (i + 2 b)]
@@ -1148,7 +1148,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Xk; g.sBk = 1; g.sBj = r0;
       g.C = A2; g.sCi = 1; g.sCj = 2LL * lk * Pin; g.bC1 = 2LL * lk;
       g.M = 2 * lk; g.N = 2 * r1; g.K = r0; g.nb1 = Pin;
-      st = cgemm<T>(g, Pin, s);
+      st = cgemm<T>(g, Pin, s, "gemm_sketch_a2");
     }
     if (st != QTT_OK) break;
     { QTT_PROF("round_sketch", s);
@@ -1178,7 +1178,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Ccur; g.sBk = 1; g.sBj = ldc; g.bB2 = r1;
       g.C = A2; g.sCi = 1; g.sCj = 2LL * r0 * Pout; g.bC1 = r0; g.bC2 = 2LL * r0;
       g.M = r0; g.N = lq[k]; g.K = r1; g.nb1 = 2;
-      st = cgemm<T>(g, 2 * Pout, s);
+      st = cgemm<T>(g, 2 * Pout, s, "gemm_orth_b1");
     }
     if (st != QTT_OK) break;
     const int ldz = Rc[k - 1];
@@ -1195,7 +1195,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Z; g.sBk = 1; g.sBj = ldz;
       g.C = S; g.sCi = 1; g.sCj = l0;
       g.M = l0; g.N = n2; g.K = ldz;
-      st = cgemm<T>(g, 1, s);
+      st = cgemm<T>(g, 1, s, "gemm_orth_s");
     }
     if (st != QTT_OK) break;
     { QTT_PROF("round_qr", s);
@@ -1212,7 +1212,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = V; g.sBk = 1; g.sBj = n2;
       g.C = Cnext; g.sCi = 1; g.sCj = ldz;
       g.M = ldz; g.N = lq0; g.K = n2;
-      st = cgemm<T>(g, 1, s);
+      st = cgemm<T>(g, 1, s, "gemm_orth_c");
     }
     std::swap(Ccur, Cnext);
     ldc = ldz;

@@ -23,6 +23,7 @@
 #include "house_qr.cuh"
 #include <cstdio>
 #include <algorithm>
+#include <type_traits>
 
 namespace qtt {
 
@@ -39,15 +40,23 @@ namespace qtt {
 constexpr int PG_THREADS = 256;
 constexpr int PG_CC = 32;  // columns per chunk (even)
 
+// plain running sum with the interface of the compensated accumulators
+template <typename T>
+struct PlainAcc {
+  T s = szero<T>();
+  __device__ __forceinline__ void add_mul(T a, T b) { mac(s, a, b); }
+  __device__ __forceinline__ T get() const { return s; }
+};
+
 template <typename T, int TM>
 __global__ void __launch_bounds__(PG_THREADS)
 proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_mul, long long n,
                  const T* __restrict__ U, const int* __restrict__ r_ptr, T* __restrict__ W,
-                 int fold, T* __restrict__ gram_part, int ldp, int mcap, int rcap) {
+                 int fold, T* __restrict__ gram_part, int ldp, int mcap, int rcap, int cc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sUt = reinterpret_cast<T*>(smem_raw);                  // rcap x mcap : sUt[c + rcap*i] = conj(U[i,c])
-  T* sM = sUt + (U ? (size_t)rcap * mcap : 0);              // mcap x CC
-  T* sW = U ? sM + (size_t)mcap * PG_CC : sM;               // rcap x CC (alias when U == null)
+  T* sM = sUt + (U ? (size_t)rcap * mcap : 0);              // mcap x cc
+  T* sW = U ? sM + (size_t)mcap * cc : sM;                  // rcap x cc (alias when U == null)
   const int tid = threadIdx.x;
   const int m = m_mul * (*m_ptr);
   const int r = U ? (r_ptr ? *r_ptr : m) : m;
@@ -60,18 +69,27 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
       sUt[c + rcap * i] = conjg(U[i + (size_t)m * c]);
     }
   }
-  // Gram accumulators: thread (ti, tj) of a 16 x 16 grid owns rows ti*TM.., cols tj*TM..
-  const int ti = tid % 16, tj = tid / 16;
-  T acc[TM][TM];
-#pragma unroll
-  for (int x = 0; x < TM; ++x)
-#pragma unroll
-    for (int y = 0; y < TM; ++y) acc[x][y] = szero<T>();
+  // Gram accumulators: a group of mgt x mgt threads covers the mg x mg Gram
+  // (thread (ti, tj) owns rows ti*TM.., cols tj*TM..); the block holds
+  // PG_THREADS / (mgt mgt) such groups, each summing every groups-th column
+  // (many groups for the narrow unfoldings of the first levels).  Each chunk
+  // is summed with plain FMAs and added to the running sum with
+  // compensation; the groups are combined in a fixed order at the end.
+  const int mgt = (mg + TM - 1) / TM;
+  const int nthr_g = mgt * mgt;
+  // several groups only with one output per thread (TM = 1); a wider tile
+  // keeps a single group, whatever the device rank makes mg
+  const int groups = (TM == 1) ? PG_THREADS / nthr_g : 1;
+  const int grp = tid / nthr_g;
+  const bool gact = grp < groups;
+  const int ti = (tid % nthr_g) % mgt, tj = (tid % nthr_g) / mgt;
+  using Acc = typename std::conditional<TM == 8, PlainAcc<T>, typename KAccOf<T>::type>::type;
+  Acc acc[TM][TM];
 
-  const long long nchunks = (n + PG_CC - 1) / PG_CC;
+  const long long nchunks = (n + cc - 1) / cc;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const long long c0 = ch * PG_CC;
-    const int ncol = (int)((n - c0) < PG_CC ? (n - c0) : PG_CC);
+    const long long c0 = ch * cc;
+    const int ncol = (int)((n - c0) < cc ? (n - c0) : cc);
     __syncthreads();
     // load M chunk: contiguous m*ncol elements
     const T* Mc = M + (size_t)c0 * m;
@@ -116,10 +134,21 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
         }
       }
     }
-    if (fold >= 0) {
-      // Gram of this chunk
+    if (fold >= 0 && gact) {
+      // Gram of this chunk (this group's columns)
       const int ncg = (fold == 1) ? ncol / 2 : ncol;
-      for (int j = 0; j < ncg; ++j) {
+      // TM = 8 (Grams above 64 x 64): 64 outputs per thread leave registers
+      // for neither a chunk sum nor a compensation term, so these add
+      // straight into a plain running sum
+      constexpr bool direct = (TM == 8);
+      T part[direct ? 1 : TM][direct ? 1 : TM];
+      if (!direct) {
+#pragma unroll
+        for (int x = 0; x < (direct ? 1 : TM); ++x)
+#pragma unroll
+          for (int y = 0; y < (direct ? 1 : TM); ++y) part[x][y] = szero<T>();
+      }
+      for (int j = grp; j < ncg; j += groups) {
         T a[TM], b[TM];
 #pragma unroll
         for (int x = 0; x < TM; ++x) {
@@ -132,22 +161,58 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
             b[x] = (rb2 < mg) ? sW[rb2 + ldw * j] : szero<T>();
           }
         }
+        if constexpr (direct) {
+#pragma unroll
+          for (int x = 0; x < TM; ++x)
+#pragma unroll
+            for (int y = 0; y < TM; ++y) acc[x][y].add_mul(a[x], conjg(b[y]));
+        } else {
+#pragma unroll
+          for (int x = 0; x < TM; ++x)
+#pragma unroll
+            for (int y = 0; y < TM; ++y) macb(part[x % (direct ? 1 : TM)][y % (direct ? 1 : TM)], a[x], b[y]);
+        }
+      }
+      if constexpr (!direct) {
 #pragma unroll
         for (int x = 0; x < TM; ++x)
 #pragma unroll
-          for (int y = 0; y < TM; ++y) macb(acc[x][y], a[x], b[y]);
+          for (int y = 0; y < TM; ++y) acc[x][y].add_mul(part[x][y], sone(T()));
       }
     }
   }
   if (fold >= 0) {
+    // combine the groups in group order through shared memory (the chunk
+    // buffers are free now), then write the CTA's partial Gram
+    __syncthreads();
+    T* red = sM;
     T* gp = gram_part + (size_t)blockIdx.x * ldp * ldp;
+    // entries outside the covered mgt TM x mgt TM block are zero
+    const int cov = mgt * TM;
+    for (int e = tid; e < ldp * ldp; e += PG_THREADS) {
+      const int ra = e % ldp, rb2 = e / ldp;
+      if (ra >= cov || rb2 >= cov) gp[e] = szero<T>();
+    }
+    if (groups == 1) {
+      if (gact) {
 #pragma unroll
-    for (int x = 0; x < TM; ++x)
+        for (int x = 0; x < TM; ++x)
 #pragma unroll
-      for (int y = 0; y < TM; ++y) {
-        const int ra = ti * TM + x, rb2 = tj * TM + y;
-        if (ra < ldp && rb2 < ldp) gp[ra + (size_t)ldp * rb2] = acc[x][y];
+          for (int y = 0; y < TM; ++y) {
+            const int ra = ti * TM + x, rb2 = tj * TM + y;
+            if (ra < ldp && rb2 < ldp) gp[ra + (size_t)ldp * rb2] = acc[x][y].get();
+          }
       }
+    } else {
+      // groups > 1 only when TM == 1: one value per thread
+      if (gact) red[tid] = acc[0][0].get();
+      __syncthreads();
+      if (grp == 0) {
+        typename KAccOf<T>::type t;
+        for (int g2 = 0; g2 < groups; ++g2) t.add_mul(red[tid + g2 * nthr_g], sone(T()));
+        if (ti < ldp && tj < ldp) gp[ti + (size_t)ldp * tj] = t.get();
+      }
+    }
   }
 }
 
@@ -990,26 +1055,35 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   }
 }
 
+// columns per chunk: about 4096 elements of the m x n unfolding (at least
+// PG_CC, even), so that the narrow unfoldings of the first levels stream in
+// wide chunks
+static int pg_chunk_cols(int mcap) {
+  int cc = 4096 / std::max(mcap, 1);
+  cc = std::max(PG_CC, std::min(cc, 2048));
+  return cc & ~1;
+}
+
 template <typename T>
-static size_t pg_smem_bytes(bool has_u, int mcap, int rcap) {
-  size_t e = (size_t)mcap * PG_CC;
-  if (has_u) e += (size_t)rcap * mcap + (size_t)rcap * PG_CC;
+static size_t pg_smem_bytes(bool has_u, int mcap, int rcap, int cc) {
+  size_t e = std::max((size_t)mcap * cc, (size_t)PG_THREADS);   // also the group reduction
+  if (has_u) e += (size_t)rcap * mcap + (size_t)rcap * cc;
   return e * sizeof(T);
 }
 
 template <typename T, int TM>
 static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
                          int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
-                         T* gp, int ldp, int mcap, int rcap) {
+                         T* gp, int ldp, int mcap, int rcap, int cc) {
   static std::atomic<unsigned long long> configured{0};
   if (first_on_device(&configured))
     cudaFuncSetAttribute(proj_gram_kernel<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)pg_smem_bytes<T>(true, 128, 128));
+                         (int)pg_smem_bytes<T>(true, 128, 128, PG_CC));
   QTT_PROF("proj_gram", s);
   // the pass streams the m x n unfolding once (m at its capacity)
   prof_add_work("proj_gram", 0.0, (double)mcap * (double)n * sizeof(T));
   proj_gram_kernel<T, TM><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp,
-                                                       ldp, mcap, rcap);
+                                                       ldp, mcap, rcap, cc);
 }
 
 // Launch the fused projection/Gram kernel.  Returns the number of partials.
@@ -1017,21 +1091,24 @@ template <typename T>
 static int launch_proj_gram(const T* M, const int* m_ptr, int m_mul, int mcap, long long n,
                             const T* U, const int* r_ptr, int rcap, T* W, int fold, T* gp,
                             int ldp, int max_parts, cudaStream_t s) {
-  const long long nchunks = (n + PG_CC - 1) / PG_CC;
+  const bool has_u = (U != nullptr);
+  // chunks of about 4096 elements of the wider of the m-row input and the
+  // r-row projection
+  const int cc = pg_chunk_cols(has_u ? std::max(mcap, rcap) : mcap);
+  const long long nchunks = (n + cc - 1) / cc;
   int grid = (int)std::min<long long>(nchunks, (long long)max_parts);
   if (grid < 1) grid = 1;
-  const bool has_u = (U != nullptr);
   const int rc = has_u ? rcap : mcap;
   const int mgcap = (fold == 1) ? 2 * rc : rc;
-  const size_t sm = pg_smem_bytes<T>(has_u, mcap, rcap);
+  const size_t sm = pg_smem_bytes<T>(has_u, mcap, rcap, cc);
   if (fold < 0 || mgcap <= 16)
-    launch_pg_tm<T, 1>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+    launch_pg_tm<T, 1>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
   else if (mgcap <= 32)
-    launch_pg_tm<T, 2>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+    launch_pg_tm<T, 2>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
   else if (mgcap <= 64)
-    launch_pg_tm<T, 4>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+    launch_pg_tm<T, 4>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
   else
-    launch_pg_tm<T, 8>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap);
+    launch_pg_tm<T, 8>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
   return grid;
 }
 

@@ -341,7 +341,7 @@ struct CGemmArgs {
   int M = 0, N = 0, K = 0, nb1 = 1, conjA = 0;
 };
 template <typename TA>
-qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s);
+qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char* name);
 
 // ------------------------------------------------------------- full
 template <typename T>
