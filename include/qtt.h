@@ -459,11 +459,28 @@ void qtt_debug_set_eig_solver(int which);
  * to the convergence test; negative = back to the default. */
 void qtt_debug_set_refine_sweeps(int sweeps);
 
+/* Diagnostics: per-CTA partial Grams of the TT-SVD passes per SM (1-16;
+ * default 2; anything else restores the default).  Each partial sums its
+ * columns in FP32 and the partials are added in FP64, so more partials
+ * shorten the FP32 sums. */
+void qtt_debug_set_gram_parts(int per_sm);
+
 /* Diagnostics: FP32 tridiagonal solver's orthogonalisation.  Eigenvalues
  * closer than ortol_rel * ||T|| chain into clusters orthogonalised by
  * Gram-Schmidt (default 1e-6); ns_steps Newton-Schulz steps follow
  * (default 3).  Non-positive values restore the defaults. */
 void qtt_debug_set_heev_cluster(double ortol_rel, int ns_steps);
+
+/* Diagnostics: the tensor-core (tcgen05) MMA path checked on its own --
+ * C (128 x N, row-major, FP32) = A (128 x K, row-major) B^T, B (N x K,
+ * row-major), with TF32 operands staged in shared memory and FP32
+ * accumulators in tensor memory, one CTA, one 8-deep K step per MMA.
+ * A, B, C, err_dev: DEVICE pointers; *err_dev is set to 1 if a wait on the
+ * MMA completion ran out (the kernel then frees its tensor memory and
+ * returns).  N in {32, 64, 128, 256}, K a positive multiple of 8, else
+ * QTT_EINVAL.  Asynchronous. */
+qtt_status qtt_debug_tc_selftest(const float* A, const float* B, float* C, int N, int K,
+                                 int* err_dev, void* stream);
 
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);

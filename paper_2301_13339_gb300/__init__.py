@@ -543,6 +543,23 @@ def qtt_conv_fft(F, G, rhat=15, eps=0.0, delta=0.0, refine=True, stream=None):
     return out
 
 
+def tc_selftest(A, B, stream=None):
+    """The tensor-core (tcgen05, TF32) MMA path on its own: returns
+    (A @ B.T as computed on the tensor cores, wait-limit flag) for float32 CUDA
+    tensors A (128 x K) and B (N x K)."""
+    import torch
+    load()
+    N, K = int(B.shape[0]), int(B.shape[1])
+    C = torch.empty((128, N), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    f = _lib.qtt_debug_tc_selftest
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    _check(f(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+             N, K, ctypes.c_void_p(err.data_ptr()), _stream(stream)))
+    return C, int(err.item())
+
+
 def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):
     """Handle from host cores (numpy arrays (r_{k-1}, 2, r_k))."""
     load()

@@ -501,12 +501,7 @@ qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char*
   }
   const long long tiles = (long long)((g.N + CG_BN - 1) / CG_BN) * ((g.M + CG_BM - 1) / CG_BM);
   // split k when the tiles alone cannot fill the GPU (one batch, long k)
-  int sms = 152;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  const int sms = device_sm_count();
   int splits = 1;
   if (nbatch == 1 && tiles < 2LL * sms && g.K >= 8 * CG_BK) {
     splits = (int)std::min<long long>((2LL * sms + tiles - 1) / tiles, (long long)g.K / (4 * CG_BK));

@@ -852,7 +852,8 @@ static qtt_status round_product_t(const qtt_op* op, const qtt_tensor* x, const q
                                                  WL + wloff[k]);
     }
     { QTT_PROF("round_sketch", s);
-    const unsigned nbk = (unsigned)std::min<long long>(152, ((long long)lk * Rc[k] + 255) / 256);
+    const unsigned nbk =
+        (unsigned)std::min<long long>(device_sm_count(), ((long long)lk * Rc[k] + 255) / 256);
     k_absmax<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k], wmax + k);
     k_scale_max<T><<<nbk, 256, 0, s>>>(WL + wloff[k], lk, x->ranks, k, P[k], wmax + k);
     }
@@ -1198,11 +1199,22 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       st = cgemm<T>(g, 1, s, "gemm_orth_s");
     }
     if (st != QTT_OK) break;
-    { QTT_PROF("round_qr", s);
-    launch_conj_transpose<T>(S, l0, l0, n2, Aq, s);
+    if (n2 <= QR_MAXM && l0 <= 64 && lq0 <= 64) {
+      // small cut: the one-CTA Householder QR of the rank-64 path (one launch)
+      QTT_PROF("round_qr", s);
+      static std::atomic<unsigned long long> qr_cfg_big{0};
+      if (first_on_device(&qr_cfg_big))
+        cudaFuncSetAttribute(k_house_q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 2 * 128 * 64));
+      const size_t sm = sizeof(T) * ((size_t)n2 * l0 + (size_t)n2 * lq0);
+      k_house_q<T><<<1, QR_THREADS, sm, s>>>(S, l0, n2, l0, lq0, V);
+    } else {
+      { QTT_PROF("round_qr", s);
+      launch_conj_transpose<T>(S, l0, l0, n2, Aq, s);
+      }
+      st = big_qr_q<T>(Aq, n2, l0, lq0, V, Tm, s);
+      if (st != QTT_OK) break;
     }
-    st = big_qr_q<T>(Aq, n2, l0, lq0, V, Tm, s);
-    if (st != QTT_OK) break;
     { QTT_PROF("round_orth", s);
     k_qcore<T><<<GRID1(lq0 * n2)>>>(V, n2, lq0, yc + y->off[k - 1]);
     }

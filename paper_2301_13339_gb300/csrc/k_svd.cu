@@ -103,11 +103,11 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
       const int rb = (r + 3) / 4, jb = (ncol + 3) / 4;
       for (int tb = tid; tb < rb * jb; tb += PG_THREADS) {
         const int cb = (tb % rb) * 4, jb0 = (tb / rb) * 4;
-        T o[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) o[x][y] = szero<T>();
+        // the projection feeds the rank decisions: nearly orthogonal
+        // directions cancel the large components of M, so the m-term sums
+        // are Dot2 sums (exact products, compensated additions) and a small
+        // row of W keeps accuracy relative to its own size
+        typename Dot2Of<T>::type o[4][4];
         for (int i = 0; i < m; ++i) {
           T u[4], v[4];
 #pragma unroll
@@ -117,13 +117,13 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) mac(o[x][y], u[x], v[y]);
+            for (int y = 0; y < 4; ++y) o[x][y].add_mul(u[x], v[y]);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
           for (int y = 0; y < 4; ++y)
-            if (cb + x < r && jb0 + y < ncol) sW[(cb + x) + rcap * (jb0 + y)] = o[x][y];
+            if (cb + x < r && jb0 + y < ncol) sW[(cb + x) + rcap * (jb0 + y)] = o[x][y].get();
       }
       __syncthreads();
       if (W) {
@@ -977,6 +977,9 @@ static long long* g_small_eigh_clk = nullptr;
 // 1, 2 and 3 sweeps after the first pass's orthogonalisation changed); 2 keep
 // one squaring of the rotation angles as margin.
 static int g_refine_sweeps = 2;
+// per-CTA partial Grams of a TT-SVD pass: this many per SM (each CTA sums
+// its columns in FP32; the partials are added in FP64)
+static int g_gram_parts_per_sm = 2;
 
 template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
@@ -1311,7 +1314,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   auto cap_at = [&](int k) { return fixed ? std::min(fixed[k], QTT_RANK_CAP) : rmax_eff; };
   const double eps_u = fixed ? 0.0 : tr.eps;
   const double delta_u = fixed ? 0.0 : tr.delta;
-  const int max_parts = 2 * 152;
+  const int max_parts = g_gram_parts_per_sm * device_sm_count();
   const int LDP = 128;
   T* bufA = (T*)scratch_alloc(sizeof(T) * N, s);
   T* bufB = (T*)scratch_alloc(sizeof(T) * N, s);
@@ -1487,6 +1490,9 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 // 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
 extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps = sweeps >= 0 ? sweeps : 2; }
+extern "C" void qtt_debug_set_gram_parts(int per_sm) {
+  qtt::g_gram_parts_per_sm = (per_sm >= 1 && per_sm <= 16) ? per_sm : 2;
+}
 
 // Hermitian eigen-decomposition of one n x n matrix (n <= 128) with the
 // one-CTA solvers used by the TT-SVD: G (device, double2, ld n) in; U

@@ -150,6 +150,41 @@ struct KAcc32 {
   __device__ __forceinline__ void add_rmul(float r, float2 b) { add(make_float2(r * b.x, r * b.y)); }
   __device__ __forceinline__ float2 get() const { return make_float2(s.x - c.x, s.y - c.y); }
 };
+// Dot2 accumulation (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005): each product is split exactly into p + e by an FMA and
+// the running sum is carried by TwoSum with the rounding errors collected in
+// c, so the result is as accurate as a sum in twice the working precision:
+// its error is about eps |result| + eps^2 sum |a b|.  Used where FP32 sums
+// cancel strongly (projections onto nearly orthogonal directions).
+struct Dot2Acc32 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+  }
+  __device__ __forceinline__ void add_term(float& sm, float& cm, float p, float e) {
+    float q;
+    two_sum(sm, p, sm, q);
+    cm += q + e;
+  }
+  // acc += a * b (complex)
+  __device__ __forceinline__ void add_mul(float2 a, float2 b) {
+    const float p1 = a.x * b.x, e1 = fmaf(a.x, b.x, -p1);
+    const float p2 = -a.y * b.y, e2 = fmaf(-a.y, b.y, -p2);
+    const float p3 = a.x * b.y, e3 = fmaf(a.x, b.y, -p3);
+    const float p4 = a.y * b.x, e4 = fmaf(a.y, b.x, -p4);
+    add_term(s.x, c.x, p1, e1);
+    add_term(s.x, c.x, p2, e2);
+    add_term(s.y, c.y, p3, e3);
+    add_term(s.y, c.y, p4, e4);
+  }
+  __device__ __forceinline__ float2 get() const { return make_float2(s.x + c.x, s.y + c.y); }
+};
+template <typename T> struct Dot2Of;
+template <> struct Dot2Of<double> { using type = KAcc64; };
+template <> struct Dot2Of<float2> { using type = Dot2Acc32; };
+
 template <typename T> struct KAccOf;
 template <> struct KAccOf<double> { using type = KAcc64; };
 template <> struct KAccOf<float2> { using type = KAcc32; };
@@ -314,6 +349,8 @@ void launch_eig_dense(const double2* G, int ldp, const int* mg_ptr, int mg_mul, 
 // First call for the current device with this flag word: true once per
 // device (per-device one-time set-up such as kernel attributes).
 bool first_on_device(std::atomic<unsigned long long>* flags);
+// multiprocessors of the current device (grid sizing)
+int device_sm_count();
 
 // Blocked Householder QR (k_dense.cu): A (m x n, ld m, m <= 768) is
 // overwritten by R and the reflectors; Q (m x nq, ld m) receives the first
