@@ -240,6 +240,7 @@ def gpu_arm(args, wl):
     out = torch.empty(x.shape, dtype=torch.complex64, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     refine = args.refine
+    prec = q.QTT_PREC_TF32_REFINED if args.prec == "tf32" else q.QTT_PREC_AUTO
     om_dev = None
     if wl.get("rsvd_p"):
         om_dev = torch.from_numpy(rsvd_omega(wl)[0]).to(dev)
@@ -248,7 +249,8 @@ def gpu_arm(args, wl):
         if om_dev is not None:
             f = q.qtt_decompose_rsvd(xin, wl["rmax"], wl["rsvd_p"], omega=om_dev, stream=s)
         else:
-            f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s)
+            f = q.qtt_decompose(xin, eps=wl["eps"], rmax=wl["rmax"], refine=refine, stream=s,
+                                prec=prec)
         y = q.qtt_conv_sinc(f, Bconv, eps_op=wl["eps_op"], eps_round=wl["eps_round"],
                             refine=True, sketch=wl.get("sketch", 0), stream=s)
         q.qtt_to_full(y, out=dst, stream=s)
@@ -882,6 +884,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="image_4096sq_c64", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32"],
+                    help="TT-SVD arithmetic: fp32 (CUDA cores) or tf32 (first Gram pass on the "
+                         "tensor cores, FP32 refinement)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="file for the nvidia-smi samples of the timed region (default: a temp file)")
@@ -987,7 +992,7 @@ def main():
                           "two_pass_bytes_per_sample": 24,
                           "two_pass_frac": 24.0 * N * args.steps / (res["total_ms"] * 1e-3) / 1e9
                           / peaks["hbm_gbs"]},
-            "clocks": res["clocks"], "refine": args.refine,
+            "clocks": res["clocks"], "refine": args.refine, "prec": args.prec,
             "plan_ms": res["plan_ms"]}
     if not args.no_cpu_baseline:
         ref, t = run_oracle(res["x"], wl)

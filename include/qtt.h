@@ -65,8 +65,15 @@ typedef enum { QTT_F64 = 0, QTT_F32 = 1, QTT_C64 = 2, QTT_C128 = 3 } qtt_dtype;
 
 /* Arithmetic of a TT-SVD or rounding.  QTT_PREC_AUTO: the element type's own
  * (FP64 for QTT_F64, FP32 for QTT_C64); QTT_PREC_FP64 / QTT_PREC_FP32 must
- * match it (else QTT_EINVAL).  The tensor-core modes (BF16 or TF32 products
- * with an FP32 residual-correction pass) are not built: QTT_EUNSUPPORTED. */
+ * match it (else QTT_EINVAL).  QTT_PREC_TF32_REFINED (complex64 TT-SVD,
+ * qtt_decompose only): the first Gram pass of every factored unfolding with
+ * at least 32 rows runs on the tensor cores (tcgen05 MMAs on TF32 operands,
+ * FP32 accumulation, FP64 sum of the per-CTA partials); its eigenvectors
+ * only seed the second, FP32 pass (the projected Gram and the
+ * relative-accuracy Jacobi, which decides the ranks), so the result keeps
+ * the FP32 path's accuracy (Alg. 1; the refinement is what makes the Gram
+ * route as accurate as an SVD).  Other calls answer it, and every call
+ * answers QTT_PREC_BF16_REFINED, with QTT_EUNSUPPORTED. */
 typedef enum {
   QTT_PREC_AUTO = 0,
   QTT_PREC_FP64 = 1,
@@ -481,6 +488,41 @@ void qtt_debug_set_heev_cluster(double ortol_rel, int ns_steps);
  * QTT_EINVAL.  Asynchronous. */
 qtt_status qtt_debug_tc_selftest(const float* A, const float* B, float* C, int N, int K,
                                  int* err_dev, void* stream);
+
+/* Diagnostics: the complex tensor-core GEMM of the large-rank rounding on
+ * its own -- C (M x N) = op(A) B with A (M x K), B (K x N), C all complex64
+ * column-major DEVICE arrays (interleaved re, im), op(A) = conj(A) when
+ * conjA != 0.  The complex product runs as one real product over the
+ * stacking [[Re A, -Im A], [Im A, Re A]] [Re B; Im B] on tcgen05 MMAs
+ * (kind::tf32) with each operand split into a TF32 head and its FP32
+ * remainder (three products: FP32-level accuracy) and FP32 accumulators in
+ * tensor memory; runs of k above 256 are split and the partials added with
+ * compensation.  *status_dev (a device int, QTT_OK on entry) receives
+ * QTT_ETIMEOUT if a wait on the MMA completion ran out.  Negative sizes, a
+ * NULL status_dev or a NULL array of nonzero size: QTT_EINVAL; K = 0 gives
+ * C = 0.  Asynchronous. */
+qtt_status qtt_debug_tc_cgemm(const void* A, const void* B, void* C, int M, int N, int K,
+                              int conjA, int* status_dev, void* stream);
+
+/* Diagnostics: the tensor-core Gram pass on its own -- per-CTA partial
+ * Grams X X^H of X (m x n complex64, column-major DEVICE array, 1 <= m <=
+ * 128) written to gram_part (DEVICE, max_parts x ldp x ldp complex64,
+ * element (a, b) of a partial at a + ldp b, zero outside m x m; m <= ldp <=
+ * 128), as the TF32-refined TT-SVD's first pass computes them: split 1 feeds
+ * TF32-rounded operands, split 3 a TF32 head and remainder (3xTF32).
+ * Returns the number of partials written (<= max_parts; their sum is the
+ * Gram), or a negative qtt_status (QTT_EINVAL for bad arguments).
+ * *status_dev receives QTT_ETIMEOUT if a wait ran out.  Asynchronous. */
+int qtt_debug_tc_gram(const void* X, int m, long long n, int split, void* gram_part, int ldp,
+                      int max_parts, int* status_dev, void* stream);
+
+/* Diagnostics: 1 routes the large-rank rounding's products (sketch ranks
+ * above 64) to the tensor-core GEMM, 0 (default) to the CUDA-core GEMM with
+ * compensated chunk sums.  The tensor cores' FP32 accumulator rounds
+ * one-signed, and along the range finder's chain of products that bias
+ * reaches the result (E2 ~3e-5 where the compensated GEMM stays below
+ * 1e-5), so the default keeps the compensated sums. */
+void qtt_debug_set_tc_gemm(int on);
 
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);

@@ -41,7 +41,8 @@ EXPORTED_SYMBOLS = [
     "qtt_free_async", "qtt_op_create", "qtt_op_get_ranks", "qtt_op_get_cores", "qtt_op_free",
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
-    "qtt_profile_work", "qtt_get_margins",
+    "qtt_profile_work", "qtt_get_margins", "qtt_debug_tc_selftest", "qtt_debug_tc_cgemm",
+    "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
@@ -558,6 +559,60 @@ def tc_selftest(A, B, stream=None):
     _check(f(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
              N, K, ctypes.c_void_p(err.data_ptr()), _stream(stream)))
     return C, int(err.item())
+
+
+def tc_cgemm(A, B, conj_a=False, stream=None):
+    """C = op(A) @ B (complex64 CUDA tensors, A (M x K), B (K x N)) through the
+    tensor-core complex GEMM (tcgen05, 3xTF32, FP32 accumulators) of the
+    large-rank rounding; returns (C, device status word)."""
+    import torch
+    load()
+    M, K = int(A.shape[0]), int(A.shape[1])
+    N = int(B.shape[1])
+    if int(B.shape[0]) != K:
+        raise ValueError("tc_cgemm: inner sizes differ")
+    # column-major operands: the transposes of contiguous row-major copies
+    Ac = A.t().contiguous()
+    Bc = B.t().contiguous()
+    Cc = torch.empty((N, M), dtype=torch.complex64, device=A.device)
+    st = torch.zeros(1, dtype=torch.int32, device=A.device)
+    f = _lib.qtt_debug_tc_cgemm
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4 + [ctypes.c_void_p, ctypes.c_void_p]
+    _check(f(ctypes.c_void_p(Ac.data_ptr()), ctypes.c_void_p(Bc.data_ptr()),
+             ctypes.c_void_p(Cc.data_ptr()), M, N, K, int(bool(conj_a)),
+             ctypes.c_void_p(st.data_ptr()), _stream(stream)))
+    return Cc.t(), int(st.item())
+
+
+def tc_gram(X, split=1, max_parts=8, stream=None):
+    """Per-CTA partial Grams X X^H of X (m x n complex64 CUDA tensor, m <= 128)
+    on the tensor cores, as the TF32-refined TT-SVD's first pass computes
+    them (split 1: TF32 operands; 3: 3xTF32).  Returns (partials as an
+    (nparts, m, m) complex64 tensor, device status word)."""
+    import torch
+    load()
+    m, n = int(X.shape[0]), int(X.shape[1])
+    Xc = X.t().contiguous()                     # column-major m x n
+    gp = torch.empty((max_parts, m, m), dtype=torch.complex64, device=X.device)
+    st = torch.zeros(1, dtype=torch.int32, device=X.device)
+    f = _lib.qtt_debug_tc_gram
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    npart = f(ctypes.c_void_p(Xc.data_ptr()), m, n, int(split), ctypes.c_void_p(gp.data_ptr()), m,
+              int(max_parts), ctypes.c_void_p(st.data_ptr()), _stream(stream))
+    if npart < 0:
+        _check(npart)
+    # element (a, b) of a partial is at a + m b: the transpose of the row-major view
+    return gp[:npart].transpose(1, 2), int(st.item())
+
+
+def qtt_debug_set_tc_gemm(on):
+    """Select the large-rank rounding's product kernel: tensor cores (True)
+    or the CUDA-core compensated GEMM (False, the default)."""
+    load()
+    _lib.qtt_debug_set_tc_gemm(int(bool(on)))
 
 
 def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):

@@ -233,8 +233,9 @@ static qtt_status cached_identity(int d, qtt_dtype dt, cudaStream_t s, qtt_op** 
 }
 
 // Truncation parameters of a call on data of type dt with d modes (d <= 0:
-// not known here, the forced ranks are checked later).
-static qtt_status check_trunc(const qtt_trunc* tr, qtt_dtype dt, int d) {
+// not known here, the forced ranks are checked later); tt_svd: the call is
+// a TT-SVD (the TF32-refined mode exists there, for complex64).
+static qtt_status check_trunc(const qtt_trunc* tr, qtt_dtype dt, int d, bool tt_svd = false) {
   if (!tr) { set_error("truncation parameters are NULL"); return QTT_EINVAL; }
   if (!(tr->eps >= 0.0) || tr->eps >= 1.0) { set_error("eps must be in [0, 1)"); return QTT_EINVAL; }
   if (tr->delta >= 1.0 || tr->delta != tr->delta) { set_error("delta must be < 1 (<= 0: off)"); return QTT_EINVAL; }
@@ -242,8 +243,12 @@ static qtt_status check_trunc(const qtt_trunc* tr, qtt_dtype dt, int d) {
     set_error("prec %d is not a qtt_prec value", tr->prec);
     return QTT_EINVAL;
   }
-  if (tr->prec == QTT_PREC_BF16_REFINED || tr->prec == QTT_PREC_TF32_REFINED) {
-    set_error("the BF16/TF32 tensor-core precision modes are not built");
+  if (tr->prec == QTT_PREC_TF32_REFINED && !(tt_svd && dt == QTT_C64)) {
+    set_error("the TF32-refined mode is built for the complex64 TT-SVD (qtt_decompose) only");
+    return QTT_EUNSUPPORTED;
+  }
+  if (tr->prec == QTT_PREC_BF16_REFINED) {
+    set_error("the BF16-refined tensor-core mode is not built");
     return QTT_EUNSUPPORTED;
   }
   if ((tr->prec == QTT_PREC_FP64 && dt != QTT_F64) || (tr->prec == QTT_PREC_FP32 && dt != QTT_C64)) {
@@ -296,7 +301,7 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
   qtt_status st = dtype_status(dt, "qtt_decompose");
   if (st != QTT_OK) return st;
   if (ndim != 1 && ndim != 2) { set_error("qtt_decompose: ndim must be 1 or 2"); return QTT_EINVAL; }
-  st = check_trunc(tr, dt, 0);
+  st = check_trunc(tr, dt, 0, true);
   if (st != QTT_OK) return st;
   TensorDesc desc;
   desc.dt = dt;
@@ -313,7 +318,7 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
   }
   if (d < 2 || d > 30) { set_error("qtt_decompose: total modes d=%d outside [2, 30]", d); return QTT_EINVAL; }
   desc.d = d;
-  st = check_trunc(tr, dt, d);
+  st = check_trunc(tr, dt, d, true);
   if (st != QTT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   qtt_tensor* t = nullptr;

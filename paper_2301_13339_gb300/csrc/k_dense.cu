@@ -488,6 +488,12 @@ __global__ void k_cgemm_reduce(const float2* __restrict__ part, int splits, long
   C[i * sCi + j * sCj] = make_float2(sm.x - c.x, sm.y - c.y);
 }
 
+void cgemm_reduce(const float2* part, int splits, long long ldpart, int M, int N, float2* C,
+                  long long sCi, long long sCj, cudaStream_t s) {
+  k_cgemm_reduce<<<(unsigned)((ldpart + 255) / 256), 256, 0, s>>>(part, splits, ldpart, M, N, C, sCi,
+                                                                  sCj);
+}
+
 template <typename TA>
 qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char* name) {
   if (g.M <= 0 || g.N <= 0 || nbatch <= 0) return QTT_OK;
@@ -526,8 +532,7 @@ qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char*
     return QTT_ENOMEM;
   }
   k_cgemm<TA><<<grid, CG_THREADS, 0, s>>>(g, 1, kchunk, part, ldpart);
-  k_cgemm_reduce<<<(unsigned)((ldpart + 255) / 256), 256, 0, s>>>(part, splits, ldpart, g.M, g.N,
-                                                                  g.C, g.sCi, g.sCj);
+  cgemm_reduce(part, splits, ldpart, g.M, g.N, g.C, g.sCi, g.sCj, s);
   scratch_free(part, s);
   return QTT_OK;
 }

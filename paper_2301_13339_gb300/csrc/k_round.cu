@@ -1027,8 +1027,16 @@ __global__ void k_core_norm2(const T* c, long long n, double* n2) {
     *n2 = t;
   }
 }
-__global__ void k_status_copy(int* dst, const int* src) {
-  if (threadIdx.x == 0) *dst = *src;
+// dst keeps its own error if it has one, else takes src's
+__global__ void k_status_merge(int* dst, const int* src) {
+  if (threadIdx.x == 0 && *dst == 0) *dst = *src;
+}
+
+// the products of the large-rank rounding: tensor cores unless switched off
+template <typename TA>
+static qtt_status big_gemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
+                           const char* name) {
+  return tc_gemm_enabled() ? tc_cgemm<TA>(g, nbatch, status, s, name) : cgemm<TA>(g, nbatch, s, name);
 }
 
 // Rounding of Y = O X when the sketch rank exceeds QTT_RANK_CAP (complex64
@@ -1140,7 +1148,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = WL + wloff[k - 1]; g.sBk = 1; g.sBj = l0;
       g.C = A1; g.sCi = 1; g.sCj = 2LL * lk; g.bC1 = lk;
       g.M = lk; g.N = Rc[k - 1]; g.K = l0; g.nb1 = 2;
-      st = cgemm<R>(g, 2, s, "gemm_sketch_a1");
+      st = big_gemm<R>(g, 2, y->status, s, "gemm_sketch_a1");
     }
     if (st != QTT_OK) break;
     {  // A2[rho + 2lk (p + Pin (i + 2 b))] = sum_a A1[rho + 2lk (a + r0 p)] X[a + r0 (i + 2 b)]
@@ -1149,7 +1157,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Xk; g.sBk = 1; g.sBj = r0;
       g.C = A2; g.sCi = 1; g.sCj = 2LL * lk * Pin; g.bC1 = 2LL * lk;
       g.M = 2 * lk; g.N = 2 * r1; g.K = r0; g.nb1 = Pin;
-      st = cgemm<T>(g, Pin, s, "gemm_sketch_a2");
+      st = big_gemm<T>(g, Pin, y->status, s, "gemm_sketch_a2");
     }
     if (st != QTT_OK) break;
     { QTT_PROF("round_sketch", s);
@@ -1179,7 +1187,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Ccur; g.sBk = 1; g.sBj = ldc; g.bB2 = r1;
       g.C = A2; g.sCi = 1; g.sCj = 2LL * r0 * Pout; g.bC1 = r0; g.bC2 = 2LL * r0;
       g.M = r0; g.N = lq[k]; g.K = r1; g.nb1 = 2;
-      st = cgemm<T>(g, 2 * Pout, s, "gemm_orth_b1");
+      st = big_gemm<T>(g, 2 * Pout, y->status, s, "gemm_orth_b1");
     }
     if (st != QTT_OK) break;
     const int ldz = Rc[k - 1];
@@ -1196,7 +1204,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = Z; g.sBk = 1; g.sBj = ldz;
       g.C = S; g.sCi = 1; g.sCj = l0;
       g.M = l0; g.N = n2; g.K = ldz;
-      st = cgemm<T>(g, 1, s, "gemm_orth_s");
+      st = big_gemm<T>(g, 1, y->status, s, "gemm_orth_s");
     }
     if (st != QTT_OK) break;
     if (n2 <= QR_MAXM && l0 <= 64 && lq0 <= 64) {
@@ -1224,7 +1232,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
       g.B = V; g.sBk = 1; g.sBj = n2;
       g.C = Cnext; g.sCi = 1; g.sCj = ldz;
       g.M = ldz; g.N = lq0; g.K = n2;
-      st = cgemm<T>(g, 1, s, "gemm_orth_c");
+      st = big_gemm<T>(g, 1, y->status, s, "gemm_orth_c");
     }
     std::swap(Ccur, Cnext);
     ldc = ldz;
@@ -1233,7 +1241,7 @@ static qtt_status round_product_big(const qtt_op* op, const qtt_tensor* x, int s
     set_ranks_from_host(y->ranks, lq, s);
     // the cores after the first are right-orthonormal: ||y||^2 = ||core_1||^2
     k_core_norm2<T><<<1, 256, 0, s>>>(yc + y->off[0], (long long)2 * lq[1], y->norm2);
-    k_status_copy<<<1, 32, 0, s>>>(y->status, x->status);
+    k_status_merge<<<1, 32, 0, s>>>(y->status, x->status);
     st = cuda_check(cudaGetLastError(), "round (large ranks) launch");
   }
   release();

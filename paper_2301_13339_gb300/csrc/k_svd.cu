@@ -1306,7 +1306,10 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   using R = typename Sc<T>::R;
   const long long N = 1LL << d;
   const bool use_rs = rs && rs->p > 0;
-  const bool refine = tr.refine || !Sc<T>::cplx || use_rs;
+  // TF32-refined: the first Gram pass of the wider unfoldings on the tensor
+  // cores; the FP32 second pass (always run in this mode) decides the ranks
+  const bool tc_pass1 = Sc<T>::cplx && tr.prec == QTT_PREC_TF32_REFINED;
+  const bool refine = tr.refine || !Sc<T>::cplx || use_rs || tc_pass1;
   const int rmax_eff = std::min(tr.rmax > 0 ? tr.rmax : QTT_RANK_CAP, QTT_RANK_CAP);
   // forced ranks (parity mode): cut k keeps exactly fixed[k] singular
   // triplets -- the cap-only rule (eps = 0) with a per-cut cap
@@ -1328,6 +1331,13 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
     return QTT_ENOMEM;
   }
   set_boundary_ranks_kernel<<<1, 32, 0, s>>>(t->ranks, d);
+  constexpr int TC_GRAM_MIN_ROWS = 32;   // below: the CUDA-core pass (many column groups)
+  auto gram_pass1 = [&](const T* X, const int* m_ptr, int mcap_g, long long ncols, int ldp_g) {
+    if constexpr (std::is_same<T, float2>::value)
+      return tc_gram(X, m_ptr, 2, mcap_g, ncols, 1, gp, ldp_g, max_parts, t->status, s);
+    else
+      return 0;
+  };
   T* cores = (T*)t->cores;
   int* rk = t->ranks;
   // Cap-only truncation (eps = 0): a level whose unfolding has
@@ -1346,8 +1356,10 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   }
   // Gram of the first factored unfolding (2^{skip+1} x 2^{d-skip-1})
   const int m0cap = 2 * t->rcap[skip];
-  int nparts = launch_proj_gram<T>(v, rk + skip, 2, m0cap, N >> (skip + 1), nullptr, nullptr, 0,
-                                   nullptr, 0, gp, m0cap, max_parts, s);
+  int nparts = (tc_pass1 && m0cap >= TC_GRAM_MIN_ROWS)
+                   ? gram_pass1(v, rk + skip, m0cap, N >> (skip + 1), m0cap)
+                   : launch_proj_gram<T>(v, rk + skip, 2, m0cap, N >> (skip + 1), nullptr, nullptr,
+                                         0, nullptr, 0, gp, m0cap, max_parts, s);
   int ldp = m0cap;
   const T* M = v;
   for (int k = skip + 1; k <= d - 1; ++k) {
@@ -1443,8 +1455,16 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
                          cap_at(k), nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
                          t->status, s, 1, delta_u, -1, t->margin + k);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
-      nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
-                                   fold_next, gp, ldp_next, max_parts, s);
+      if (tc_pass1 && fold_next == 1 && ldp_next >= TC_GRAM_MIN_ROWS) {
+        // W alone, then the Gram of its fold (W is r x n with ld r, so the
+        // next unfolding is the same memory read as 2r x n/2 with ld 2r)
+        launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout, -1, nullptr,
+                            0, max_parts, s);
+        nparts = gram_pass1(Wout, rk + k, ldp_next, n / 2, ldp_next);
+      } else {
+        nparts = launch_proj_gram<T>(bufA, rk + (k - 1), 2, mcap, n, U2, rk + k, rcapk, Wout,
+                                     fold_next, gp, ldp_next, max_parts, s);
+      }
     } else {
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, eps_u, d,
                          cap_at(k), nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,

@@ -194,3 +194,578 @@ extern "C" qtt_status qtt_debug_tc_selftest(const float* A, const float* B, floa
   k_tc_selftest<<<1, 128, sm, s>>>(A, B, C, N, K, err_dev);
   return cuda_check(cudaGetLastError(), "qtt_debug_tc_selftest launch");
 }
+
+namespace qtt {
+
+// ---------------------------------------------------------------------------
+// Complex GEMM on the tensor cores, FP32-accurate (3xTF32): C = op(A) B with
+// the strides and batching of CGemmArgs (A complex or real).
+//
+// The complex product is one real product over the stacking
+//   A' = [[Re A, -Im A], [Im A, Re A]]   (2M x 2K; real k 2k = Re, 2k+1 = Im)
+//   B' = [Re B; Im B]                    (2K x N)
+// whose rows 0..M-1 are Re C and rows M..2M-1 Im C.  A CTA owns 64 complex
+// rows (one M = 128 MMA) and TN_TC complex columns.  Each operand is split
+// x ~ hi + lo with hi = x and lo = x - hi both rounded to nearest TF32, and
+// C' += hi hi + hi lo + lo hi in one tensor-memory accumulator (the products
+// of 11-bit values are exact in FP32; the dropped lo lo term and the
+// rounding of lo are near 2^-22 relative, without a sign bias).  k advances 8 complex values (16 real: two MMA k-steps) per
+// chunk: the global loads of chunk c + 1 are in flight in registers while
+// the MMAs of chunk c run, and the two shared-memory buffers are released by
+// an mbarrier that the MMAs' commit arrives on.  With split-K the partial of
+// the tile goes to part (element (i, j) at i + M j) for a compensated sum.
+constexpr int TN_TC = 256;             // complex columns per CTA (MMA N)
+constexpr int TC_KC = 8;               // complex k per chunk
+constexpr int TC_THREADS = 256;
+constexpr int TC_A_TILE = 128 * 8 * 4;         // bytes of one A k-step tile (128 x 8 TF32)
+constexpr int TC_B_TILE = TN_TC * 8 * 4;       // bytes of one B k-step tile
+constexpr int TC_BUF = 4 * TC_A_TILE + 4 * TC_B_TILE;   // {hi, lo} x two k-steps
+constexpr size_t TC_SMEM = 2 * (size_t)TC_BUF + 1024;
+constexpr int TC_AE = 64 * TC_KC / TC_THREADS;      // A elements per thread and chunk (2)
+constexpr int TC_BE = TN_TC * TC_KC / TC_THREADS;   // B elements per thread and chunk (8)
+// longest k run summed in one FP32 tensor accumulator (single-batch products
+// split k beyond it and add the partials with compensation)
+constexpr int TC_KMAX = 256;
+
+// x rounded to the nearest TF32 value (ties away from zero): the result
+// has 11 significant bits, so the tensor core consumes it exactly
+__device__ __forceinline__ float tc_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float2 tc_load_a(const float* p, int) { return make_float2(__ldg(p), 0.f); }
+__device__ __forceinline__ float2 tc_load_a(const float2* p, int conj) {
+  const float2 v = __ldg(p);
+  return make_float2(v.x, conj ? -v.y : v.y);
+}
+
+// hi and lo parts of v at (row, real k) of the chunk's {hi, lo} x step
+// tiles: hi = tf32(v), lo = tf32(v - hi) (v - hi is exact in FP32), so both
+// are exact TF32 operands and v - hi - lo is below 2^-22 |v|, unbiased
+__device__ __forceinline__ void tc_put(unsigned char* tiles, int tile_bytes, int row, int kr, float v) {
+  const int step = kr >> 3;
+  const uint32_t off = tc_tile_off(row, kr & 7);
+  const float hi = tc_tf32(v);
+  *reinterpret_cast<float*>(tiles + (size_t)step * tile_bytes + off) = hi;
+  *reinterpret_cast<float*>(tiles + (size_t)(2 + step) * tile_bytes + off) = tc_tf32(v - hi);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, long long ldpart,
+           int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_dyn[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int bz = blockIdx.z % nbatch, split = blockIdx.z / nbatch;
+  const int b1 = bz % g.nb1, b2 = bz / g.nb1;
+  const TA* A = g.A + g.bA1 * b1 + g.bA2 * b2;
+  const float2* B = g.B + g.bB1 * b1 + g.bB2 * b2;
+  const long long i0 = (long long)blockIdx.y * 64, j0 = (long long)blockIdx.x * TN_TC;
+  const int kbeg = split * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const int nch = (kend > kbeg) ? (kend - kbeg + TC_KC - 1) / TC_KC : 0;
+  unsigned char* base = tc_dyn + ((1024u - (tc_smem_u32(tc_dyn) & 1023u)) & 1023u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem_u32(&tmem_slot)),
+                 "r"((uint32_t)TN_TC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    tc_mbar_init(tc_smem_u32(&mbar[0]), 1);
+    tc_mbar_init(tc_smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc_idesc_tf32(128, TN_TC);
+
+  // this thread's elements of a chunk: A (ii, kk) and B (kk, jj)
+  int a_ii[TC_AE], a_kk[TC_AE], b_kk[TC_BE], b_jj[TC_BE];
+#pragma unroll
+  for (int t = 0; t < TC_AE; ++t) {
+    const int e = tid + t * TC_THREADS;
+    if (g.sAi == 1) { a_ii[t] = e % 64; a_kk[t] = e / 64; }
+    else { a_kk[t] = e % TC_KC; a_ii[t] = e / TC_KC; }
+  }
+#pragma unroll
+  for (int t = 0; t < TC_BE; ++t) {
+    const int e = tid + t * TC_THREADS;
+    b_kk[t] = e % TC_KC;
+    b_jj[t] = e / TC_KC;
+  }
+  float2 ra[TC_AE], rb[TC_BE];
+  auto load_chunk = [&](int c) {
+    const int k0 = kbeg + c * TC_KC;
+#pragma unroll
+    for (int t = 0; t < TC_AE; ++t) {
+      const long long i = i0 + a_ii[t];
+      const int k = k0 + a_kk[t];
+      ra[t] = (i < g.M && k < kend) ? tc_load_a(A + i * g.sAi + (long long)k * g.sAk, g.conjA)
+                                    : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < TC_BE; ++t) {
+      const long long j = j0 + b_jj[t];
+      const int k = k0 + b_kk[t];
+      rb[t] = (j < g.N && k < kend) ? __ldg(B + (long long)k * g.sBk + j * g.sBj)
+                                    : make_float2(0.f, 0.f);
+    }
+  };
+
+  uint32_t phase[2] = {0u, 0u};
+  int used[2] = {0, 0};
+  bool ok = true;
+  if (nch > 0) load_chunk(0);
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    unsigned char* sa = base + (size_t)buf * TC_BUF;
+    unsigned char* sb = sa + 4 * TC_A_TILE;
+    if (used[buf]) {   // the MMAs of chunk c - 2 have read this buffer
+      ok = __syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[buf]), phase[buf])) != 0;
+      if (!ok) break;  // block-uniform; the buffer stays marked for the drain below
+      phase[buf] ^= 1u;
+      used[buf] = 0;
+    }
+    // row ii (Re C) takes [Re a, -Im a], row 64 + ii (Im C) takes [Im a, Re a]
+#pragma unroll
+    for (int t = 0; t < TC_AE; ++t) {
+      const float2 a = ra[t];
+      const int ii = a_ii[t], kr = 2 * a_kk[t];
+      tc_put(sa, TC_A_TILE, ii, kr, a.x);
+      tc_put(sa, TC_A_TILE, ii, kr + 1, -a.y);
+      tc_put(sa, TC_A_TILE, 64 + ii, kr, a.y);
+      tc_put(sa, TC_A_TILE, 64 + ii, kr + 1, a.x);
+    }
+#pragma unroll
+    for (int t = 0; t < TC_BE; ++t) {
+      tc_put(sb, TC_B_TILE, b_jj[t], 2 * b_kk[t], rb[t].x);
+      tc_put(sb, TC_B_TILE, b_jj[t], 2 * b_kk[t] + 1, rb[t].y);
+    }
+    tc_fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int step = 0; step < 2; ++step) {
+        const uint64_t dah = tc_sdesc(tc_smem_u32(sa + (size_t)step * TC_A_TILE), TC_LBO, TC_SBO);
+        const uint64_t dal = tc_sdesc(tc_smem_u32(sa + (size_t)(2 + step) * TC_A_TILE), TC_LBO, TC_SBO);
+        const uint64_t dbh = tc_sdesc(tc_smem_u32(sb + (size_t)step * TC_B_TILE), TC_LBO, TC_SBO);
+        const uint64_t dbl = tc_sdesc(tc_smem_u32(sb + (size_t)(2 + step) * TC_B_TILE), TC_LBO, TC_SBO);
+        tc_mma_tf32(tmem, dah, dbh, idesc, (c > 0 || step > 0) ? 1u : 0u);
+        tc_mma_tf32(tmem, dah, dbl, idesc, 1u);
+        tc_mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      tc_commit(tc_smem_u32(&mbar[buf]));
+    }
+    used[buf] = 1;
+    if (c + 1 < nch) load_chunk(c + 1);
+  }
+  // the last commit of each buffer (after a failed wait, still drain the
+  // other buffer's MMAs before the tensor memory is released)
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+    if (used[b]) {   // block-uniform
+      if (!__syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[b]), phase[b]))) ok = false;
+      phase[b] ^= 1u;
+    }
+  tc_fence_after();
+  __syncthreads();
+  if (!ok) {
+    if (tid == 0) atomicCAS(status, 0, (int)QTT_ETIMEOUT);
+  } else {
+    // warp w reads TMEM lanes 32 (w % 4) ..: lane r < 64 holds Re of row
+    // i0 + r, lane r >= 64 Im of row i0 + r - 64; warps 0-3 take columns
+    // 0..127, warps 4-7 columns 128..255
+    const int lane_r = 32 * (warp & 3) + (tid & 31);
+    const int cbase = (warp >> 2) * (TN_TC / 2);
+    const long long i = i0 + (lane_r & 63);
+    const int comp = lane_r >> 6;
+    float* Cf;
+    long long sCi, sCj;
+    if (part) {
+      Cf = reinterpret_cast<float*>(part + (long long)split * ldpart);
+      sCi = 1;
+      sCj = g.M;
+    } else {
+      Cf = reinterpret_cast<float*>(g.C + g.bC1 * b1 + g.bC2 * b2);
+      sCi = g.sCi;
+      sCj = g.sCj;
+    }
+    for (int c0 = 0; c0 < TN_TC / 2; c0 += 16) {
+      if (j0 + cbase + c0 >= g.N) break;   // warp-uniform
+      float v[16];
+      if (nch > 0) {
+        tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + c0), v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      }
+      if (i < g.M) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const long long j = j0 + cbase + c0 + q;
+          if (j < g.N) Cf[2 * (i * sCi + j * sCj) + comp] = v[q];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)TN_TC)
+                 : "memory");
+}
+
+static std::atomic<unsigned long long> g_tc_cfg[2];
+
+template <typename TA>
+qtt_status tc_cgemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
+                    const char* name) {
+  if (g.M <= 0 || g.N <= 0 || nbatch <= 0) return QTT_OK;
+  if (!status || g.nb1 < 1 || nbatch > 65535 || (g.M + 63) / 64 > 65535) {
+    set_error("tc_cgemm: bad shape, batch or status word");
+    return QTT_EINVAL;
+  }
+  if (first_on_device(&g_tc_cfg[sizeof(TA) == sizeof(float) ? 0 : 1]))
+    cudaFuncSetAttribute(k_tc_cgemm<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  const long long tiles = (long long)((g.N + TN_TC - 1) / TN_TC) * ((g.M + 63) / 64);
+  const int sms = device_sm_count();
+  int splits = 1;
+  if (nbatch == 1) {
+    // split k beyond TC_KMAX terms per accumulator, and further while the
+    // tiles alone cannot fill the GPU (chunks of at least 4 k-steps)
+    splits = (g.K + TC_KMAX - 1) / TC_KMAX;
+    if (tiles * splits < 2LL * sms)
+      splits = (int)std::max<long long>(
+          splits, std::min<long long>((2LL * sms + tiles - 1) / tiles, (long long)g.K / (4 * TC_KC)));
+    splits = std::max(1, std::min(splits, 64));
+  }
+  const int kchunk = std::max(TC_KC, ((g.K + splits - 1) / splits + TC_KC - 1) / TC_KC * TC_KC);
+  splits = std::max(1, (g.K + kchunk - 1) / kchunk);   // no empty split
+  dim3 grid((unsigned)((g.N + TN_TC - 1) / TN_TC), (unsigned)((g.M + 63) / 64),
+            (unsigned)(nbatch * splits));
+  QTT_PROF(name, s);
+  const double mnk = (double)g.M * g.N * g.K * nbatch;
+  prof_add_work(name, (sizeof(TA) == sizeof(float) ? 4.0 : 8.0) * mnk,
+                ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * 8.0 + (double)g.M * g.N * 8.0) *
+                    nbatch);
+  if (splits == 1) {
+    k_tc_cgemm<TA><<<grid, TC_THREADS, TC_SMEM, s>>>(g, nbatch, kchunk, nullptr, 0, status);
+    return QTT_OK;
+  }
+  const long long ldpart = (long long)g.M * g.N;
+  float2* part = (float2*)scratch_alloc(sizeof(float2) * (size_t)(ldpart * splits), s);
+  if (!part) {
+    set_error("tc_cgemm: split-k scratch allocation failed");
+    return QTT_ENOMEM;
+  }
+  k_tc_cgemm<TA><<<grid, TC_THREADS, TC_SMEM, s>>>(g, 1, kchunk, part, ldpart, status);
+  cgemm_reduce(part, splits, ldpart, g.M, g.N, g.C, g.sCi, g.sCj, s);
+  scratch_free(part, s);
+  return QTT_OK;
+}
+template qtt_status tc_cgemm<float>(const CGemmArgs<float>&, int, int*, cudaStream_t, const char*);
+template qtt_status tc_cgemm<float2>(const CGemmArgs<float2>&, int, int*, cudaStream_t, const char*);
+
+// which kernel the large-rank rounding's products use.  0 (default): the
+// CUDA-core GEMM with compensated chunk sums.  The tensor cores' FP32
+// accumulator rounds one-signed, and along the range finder's chain of
+// products that bias reaches the result (measured on the exact-regime
+// 256 x 256 case: E2 3e-5 against < 1e-5); 1 selects them anyway.
+static int g_tc_gemm = 0;
+int tc_gemm_enabled() { return g_tc_gemm; }
+
+}  // namespace qtt
+
+extern "C" void qtt_debug_set_tc_gemm(int on) { qtt::g_tc_gemm = (on != 0); }
+
+// C (M x N, column-major, complex64) = op(A) B through the tensor-core GEMM:
+// A (M x K, column-major, complex64; conjugated when conjA), B (K x N,
+// column-major).  *status_dev receives QTT_ETIMEOUT if a wait ran out.
+extern "C" qtt_status qtt_debug_tc_cgemm(const void* A, const void* B, void* C, int M, int N, int K,
+                                         int conjA, int* status_dev, void* stream) {
+  clear_error();
+  if (M < 0 || N < 0 || K < 0 || !status_dev || (!A && M > 0 && K > 0) ||
+      (!B && K > 0 && N > 0) || (!C && M > 0 && N > 0)) {
+    set_error("qtt_debug_tc_cgemm: NULL argument or negative size");
+    return QTT_EINVAL;
+  }
+  if (M == 0 || N == 0) return QTT_OK;
+  qtt::CGemmArgs<float2> g;
+  g.A = (const float2*)A; g.sAi = 1; g.sAk = M;
+  g.B = (const float2*)B; g.sBk = 1; g.sBj = K;
+  g.C = (float2*)C; g.sCi = 1; g.sCj = M;
+  g.M = M; g.N = N; g.K = K; g.conjA = conjA;
+  if (K == 0) {
+    const qtt_status st = qtt::cuda_check(
+        cudaMemsetAsync(C, 0, sizeof(float2) * (size_t)M * N, (cudaStream_t)stream), "tc_cgemm");
+    return st;
+  }
+  const qtt_status st = qtt::tc_cgemm<float2>(g, 1, status_dev, (cudaStream_t)stream, "tc_cgemm");
+  if (st != QTT_OK) return st;
+  return qtt::cuda_check(cudaGetLastError(), "tc_cgemm launch");
+}
+
+namespace qtt {
+
+// ---------------------------------------------------------------------------
+// Gram partials on the tensor cores: for X (m x n complex64, column-major,
+// ld m, m = m_mul * *m_ptr <= mp) every CTA sums G = X X^H over its columns
+// and writes it to gram_part[blockIdx.x] (ldp x ldp, element (a, b) at
+// a + ldp b, zero outside m x m) -- the partial format of the CUDA-core
+// Gram pass, reduced in FP64 by the same reduction.
+//
+// Real form: with Y = [Re X | Im X] and Z = [Im X | -Re X] (real k 2j, 2j+1
+// = column j), Y Y^T = Re G and Z Y^T = Im G, since
+// Im(x conj(y)) = Im x Re y - Re x Im y.  A chunk is 8 complex columns (two
+// TF32 k-steps of 8).  When 2 mp <= 128 one M = 128 MMA takes the stacked
+// [Y; Z] as A and Y (its first mp rows) as B (N = mp); above, two MMAs put
+// Re G in tensor-memory columns 0.. and Im G in 128.. .  SPLIT = 1 feeds
+// each value rounded to TF32 (one product per k-step: the first pass of the
+// TF32-refined TT-SVD, whose second pass recomputes the Gram in FP32);
+// SPLIT = 3 feeds hi + lo (3xTF32).
+constexpr int TG_THREADS = 256;
+constexpr int TG_KC = 8;                       // complex columns per chunk
+constexpr int TG_TILE = 128 * 8 * 4;           // one 128-row TF32 k-step tile
+constexpr int TG_BUF = 8 * TG_TILE;            // {Y, Z} x {hi, lo} x two k-steps
+// requested dynamic shared memory: two buffers, and at least 80 KB so that
+// at most two CTAs share an SM (each holds 256 tensor-memory columns)
+constexpr size_t TG_SMEM = (2 * (size_t)TG_BUF + 1024) > 80 * 1024 ? (2 * (size_t)TG_BUF + 1024)
+                                                                   : 80 * 1024;
+
+__device__ __forceinline__ unsigned char* tg_tile(unsigned char* buf, int op, int part, int step) {
+  return buf + (size_t)(((op * 2 + part) * 2 + step)) * TG_TILE;
+}
+
+__device__ __forceinline__ void tg_put4(unsigned char* buf, int op, int step, int row, int kq,
+                                        float4 v, bool split) {
+  const uint32_t off = tc_tile_off(row, 4 * kq);
+  float4 hi = make_float4(tc_tf32(v.x), tc_tf32(v.y), tc_tf32(v.z), tc_tf32(v.w));
+  *reinterpret_cast<float4*>(tg_tile(buf, op, 0, step) + off) = hi;
+  if (split) {
+    float4 lo = make_float4(tc_tf32(v.x - hi.x), tc_tf32(v.y - hi.y), tc_tf32(v.z - hi.z),
+                            tc_tf32(v.w - hi.w));
+    *reinterpret_cast<float4*>(tg_tile(buf, op, 1, step) + off) = lo;
+  }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(TG_THREADS, 1)
+k_tc_gram(const float2* __restrict__ X, const int* __restrict__ m_ptr, int m_mul, long long n,
+          int mp, float2* __restrict__ gram_part, int ldp, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tg_dyn[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  constexpr bool split = (SPLIT == 3);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = min(m_mul * (*m_ptr), mp);
+  const bool single = (2 * mp <= 128);
+  unsigned char* base = tg_dyn + ((1024u - (tc_smem_u32(tg_dyn) & 1023u)) & 1023u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem_u32(&tmem_slot)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    tc_mbar_init(tc_smem_u32(&mbar[0]), 1);
+    tc_mbar_init(tc_smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc_idesc_tf32(128, mp);
+
+  // this thread's (row, column pair) slots of a chunk: mp rows x 4 pairs
+  const int nslot = mp * 4;
+  constexpr int TG_MAXS = 128 * 4 / TG_THREADS;   // 2
+  const long long nchunk = (n + TG_KC - 1) / TG_KC;
+  const int my = (blockIdx.x < nchunk) ? (int)((nchunk - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  float2 r0[TG_MAXS], r1[TG_MAXS];
+  auto load_chunk = [&](int c) {
+    const long long j0 = (blockIdx.x + (long long)c * gridDim.x) * TG_KC;
+#pragma unroll
+    for (int t = 0; t < TG_MAXS; ++t) {
+      const int e = tid + t * TG_THREADS;
+      const int a = e % mp, g = e / mp;
+      const long long j = j0 + 2 * g;
+      const bool ok = (e < nslot) && (a < m);
+      r0[t] = (ok && j < n) ? __ldg(X + a + (long long)m * j) : make_float2(0.f, 0.f);
+      r1[t] = (ok && j + 1 < n) ? __ldg(X + a + (long long)m * (j + 1)) : make_float2(0.f, 0.f);
+    }
+  };
+  uint32_t phase[2] = {0u, 0u};
+  int used[2] = {0, 0};
+  bool ok = true;
+  if (my > 0) load_chunk(0);
+  for (int c = 0; c < my; ++c) {
+    const int buf = c & 1;
+    unsigned char* sb = base + (size_t)buf * TG_BUF;
+    if (used[buf]) {
+      ok = __syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[buf]), phase[buf])) != 0;
+      if (!ok) break;
+      phase[buf] ^= 1u;
+      used[buf] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < TG_MAXS; ++t) {
+      const int e = tid + t * TG_THREADS;
+      if (e < nslot) {
+        const int a = e % mp, g = e / mp;
+        const int step = g >> 1, kq = g & 1;
+        const float2 x0 = r0[t], x1 = r1[t];
+        tg_put4(sb, 0, step, a, kq, make_float4(x0.x, x0.y, x1.x, x1.y), split);
+        if (single)
+          tg_put4(sb, 0, step, mp + a, kq, make_float4(x0.y, -x0.x, x1.y, -x1.x), split);
+        else
+          tg_put4(sb, 1, step, a, kq, make_float4(x0.y, -x0.x, x1.y, -x1.x), split);
+      }
+    }
+    tc_fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int step = 0; step < 2; ++step) {
+        const uint32_t acc0 = (c > 0 || step > 0) ? 1u : 0u;
+        const uint64_t yh = tc_sdesc(tc_smem_u32(tg_tile(sb, 0, 0, step)), TC_LBO, TC_SBO);
+        const uint64_t yl = tc_sdesc(tc_smem_u32(tg_tile(sb, 0, 1, step)), TC_LBO, TC_SBO);
+        if (single) {
+          tc_mma_tf32(tmem, yh, yh, idesc, acc0);
+          if (split) {
+            tc_mma_tf32(tmem, yh, yl, idesc, 1u);
+            tc_mma_tf32(tmem, yl, yh, idesc, 1u);
+          }
+        } else {
+          const uint64_t zh = tc_sdesc(tc_smem_u32(tg_tile(sb, 1, 0, step)), TC_LBO, TC_SBO);
+          const uint64_t zl = tc_sdesc(tc_smem_u32(tg_tile(sb, 1, 1, step)), TC_LBO, TC_SBO);
+          tc_mma_tf32(tmem, yh, yh, idesc, acc0);
+          tc_mma_tf32(tmem + 128, zh, yh, idesc, acc0);
+          if (split) {
+            tc_mma_tf32(tmem, yh, yl, idesc, 1u);
+            tc_mma_tf32(tmem, yl, yh, idesc, 1u);
+            tc_mma_tf32(tmem + 128, zh, yl, idesc, 1u);
+            tc_mma_tf32(tmem + 128, zl, yh, idesc, 1u);
+          }
+        }
+      }
+      tc_commit(tc_smem_u32(&mbar[buf]));
+    }
+    used[buf] = 1;
+    if (c + 1 < my) load_chunk(c + 1);
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+    if (used[b]) {
+      if (!__syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[b]), phase[b]))) ok = false;
+      phase[b] ^= 1u;
+    }
+  tc_fence_after();
+  __syncthreads();
+  float2* gp = gram_part + (size_t)blockIdx.x * ldp * ldp;
+  float* gpf = reinterpret_cast<float*>(gp);
+  // entries outside the mp x mp block covered by the MMAs
+  for (int e = tid; e < ldp * ldp; e += TG_THREADS) {
+    const int a = e % ldp, b = e / ldp;
+    if (a >= mp || b >= mp) gp[e] = make_float2(0.f, 0.f);
+  }
+  if (!ok) {
+    if (tid == 0) atomicCAS(status, 0, (int)QTT_ETIMEOUT);
+  } else {
+    const int lane = 32 * (warp & 3) + (tid & 31);
+    const int half = warp >> 2;
+    const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+    // single: lanes < mp hold Re G rows, lanes mp.. 2 mp Im G rows;
+    // double: lanes are rows, columns 0.. Re, 128.. Im
+    const int nrep = single ? 1 : 2;
+    for (int rep = 0; rep < nrep; ++rep) {
+      int a, comp;
+      if (single) { a = lane < mp ? lane : lane - mp; comp = lane < mp ? 0 : 1; }
+      else { a = lane; comp = rep; }
+      const bool live = single ? (lane < 2 * mp) : (lane < mp);
+      for (int p = half; p < mp / 16; p += 2) {
+        float v[16];
+        if (my > 0) {
+          tc_ld16(tmem + lane_addr + (uint32_t)(128 * rep + 16 * p), v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] = 0.f;
+        }
+        if (live && a < ldp) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int b = 16 * p + q;
+            if (b < ldp) gpf[2 * (a + (size_t)ldp * b) + comp] = v[q];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                 : "memory");
+}
+
+static std::atomic<unsigned long long> g_tg_cfg[2];
+
+int tc_gram(const float2* X, const int* m_ptr, int m_mul, int mcap, long long n, int split,
+            float2* gram_part, int ldp, int max_parts, int* status, cudaStream_t s) {
+  const int mp = std::max(16, (mcap + 15) / 16 * 16);
+  const long long nchunk = (n + TG_KC - 1) / TG_KC;
+  int grid = (int)std::min<long long>(std::max<long long>(nchunk, 1), (long long)max_parts);
+  if (grid < 1) grid = 1;
+  QTT_PROF(split == 3 ? "tc_gram_3xtf32" : "tc_gram_tf32", s);
+  // algorithmic work: the m x n complex operand once; m^2 n complex MACs
+  prof_add_work(split == 3 ? "tc_gram_3xtf32" : "tc_gram_tf32", 8.0 * mcap * (double)mcap * n,
+                8.0 * mcap * (double)n);
+  if (split == 3) {
+    if (first_on_device(&g_tg_cfg[1]))
+      cudaFuncSetAttribute(k_tc_gram<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
+    k_tc_gram<3><<<grid, TG_THREADS, TG_SMEM, s>>>(X, m_ptr, m_mul, n, mp, gram_part, ldp, status);
+  } else {
+    if (first_on_device(&g_tg_cfg[0]))
+      cudaFuncSetAttribute(k_tc_gram<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
+    k_tc_gram<1><<<grid, TG_THREADS, TG_SMEM, s>>>(X, m_ptr, m_mul, n, mp, gram_part, ldp, status);
+  }
+  return grid;
+}
+
+}  // namespace qtt
+
+// Gram partials of X (m x n complex64, column-major) on the tensor cores:
+// gram_part (nparts x ldp x ldp complex64) as the TT-SVD's first pass
+// computes them; returns nparts (<= max_parts), or a negative status.
+extern "C" int qtt_debug_tc_gram(const void* X, int m, long long n, int split, void* gram_part,
+                                 int ldp, int max_parts, int* status_dev, void* stream) {
+  clear_error();
+  if (!X || !gram_part || !status_dev || m < 1 || m > 128 || n < 0 || ldp < m || ldp > 128 ||
+      max_parts < 1 || (split != 1 && split != 3)) {
+    set_error("qtt_debug_tc_gram: bad argument");
+    return QTT_EINVAL;
+  }
+  int* mdev = nullptr;
+  if (cudaMallocAsync(&mdev, sizeof(int), (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("qtt_debug_tc_gram: allocation failed");
+    return QTT_ENOMEM;
+  }
+  cudaMemcpyAsync(mdev, &m, sizeof(int), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  const int np = qtt::tc_gram((const float2*)X, mdev, 1, m, n, split, (float2*)gram_part, ldp,
+                              max_parts, status_dev, (cudaStream_t)stream);
+  cudaFreeAsync(mdev, (cudaStream_t)stream);
+  const qtt_status st = qtt::cuda_check(cudaGetLastError(), "tc_gram launch");
+  return st == QTT_OK ? np : (int)st;
+}

@@ -379,6 +379,21 @@ struct CGemmArgs {
 };
 template <typename TA>
 qtt_status cgemm(const CGemmArgs<TA>& g, int nbatch, cudaStream_t s, const char* name);
+// C[i + M j] (then to C at sCi, sCj) = compensated sum over s of part[s ldpart + i + M j]
+void cgemm_reduce(const float2* part, int splits, long long ldpart, int M, int N, float2* C,
+                  long long sCi, long long sCj, cudaStream_t s);
+// the same product on the tensor cores (tcgen05, 3xTF32, FP32 accumulators);
+// a wait that runs out writes QTT_ETIMEOUT to *status (a device word) if it
+// holds QTT_OK
+template <typename TA>
+qtt_status tc_cgemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
+                    const char* name);
+int tc_gemm_enabled();
+// per-CTA partial Grams X X^H of X (m x n, ld m, m = m_mul * *m_ptr <= mcap
+// <= 128) on the tensor cores (split 1: TF32 operands; 3: 3xTF32), in the
+// partial format of the CUDA-core Gram pass; returns the number of partials
+int tc_gram(const float2* X, const int* m_ptr, int m_mul, int mcap, long long n, int split,
+            float2* gram_part, int ldp, int max_parts, int* status, cudaStream_t s);
 
 // ------------------------------------------------------------- full
 template <typename T>

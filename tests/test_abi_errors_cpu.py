@@ -50,10 +50,12 @@ def test_decompose_arguments(lib, buf):
     for dt in (QTT_F32, QTT_C128):   # named by the ABI, not built
         _expect(lib, f(p, dt, 1, sh, 1, ctypes.byref(ok), None, ctypes.byref(out)),
                 ["not built"], QTT_EUNSUPPORTED)
-    # precision selector: tensor-core modes not built, FP64 with complex64 data
-    for pr in (3, 4):
-        _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, pr, None)), None,
-                       ctypes.byref(out)), ["not built"], QTT_EUNSUPPORTED)
+    # precision selector: the BF16-refined mode is not built, the TF32-refined
+    # one only for complex64; FP64 with complex64 data
+    _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 3, None)), None,
+                   ctypes.byref(out)), ["not built"], QTT_EUNSUPPORTED)
+    _expect(lib, f(p, QTT_F64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 4, None)), None,
+                   ctypes.byref(out)), ["complex64"], QTT_EUNSUPPORTED)
     _expect(lib, f(p, QTT_C64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 1, None)), None,
                    ctypes.byref(out)), ["does not match"])
     _expect(lib, f(p, QTT_F64, 1, sh, 1, ctypes.byref(Trunc(0.0, 64, 1, 0.0, 2, None)), None,

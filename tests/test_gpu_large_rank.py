@@ -89,3 +89,23 @@ def test_large_rank_arguments(qlib):
     cplx = qlib.qtt_from_cores([c.astype(np.complex64) for c in _rand_cores(rng, 8, 8)], [4, 4])
     with pytest.raises(qlib.QTTError):
         qlib.qtt_conv_sinc(cplx, 8.0, sketch=385)          # above QTT_SKETCH_CAP_BIG
+
+
+def test_large_rank_tensor_core_products(qlib):
+    """The exact regime with the range finder's products on the tensor-core
+    GEMM (qtt_debug_set_tc_gemm(1)): the same result at the accuracy that
+    GEMM's one-signed accumulator rounding allows along the chain of
+    products (measured E2 ~3e-5; bound 1e-4), against < 1e-5 on the
+    compensated CUDA-core GEMM that the library uses by default."""
+    rng = np.random.default_rng(240)
+    d2 = 8
+    cores = _rand_cores(rng, 2 * d2, 64)
+    t = qlib.qtt_from_cores([c.astype(np.complex64) for c in cores], [d2, d2], True)
+    qlib.qtt_debug_set_tc_gemm(True)
+    try:
+        y = qlib.qtt_conv_sinc(t, 16.0, eps_op=1e-7, eps_round=1e-7, sketch=384)
+        got = qlib.qtt_to_full(y).cpu().numpy().astype(np.complex128)
+    finally:
+        qlib.qtt_debug_set_tc_gemm(False)
+    img = Q.qtt_vector_to_image(Q.full(cores), 2 ** d2, 2 ** d2, True)
+    _check(got, _dense_conv(img, 16.0), 1e-4)
