@@ -884,9 +884,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="image_4096sq_c64", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32"],
-                    help="TT-SVD arithmetic: fp32 (CUDA cores) or tf32 (first Gram pass on the "
-                         "tensor cores, FP32 refinement)")
+    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32"],
+                    help="TT-SVD arithmetic: tf32 = the TF32-refined mode (first Gram pass on the "
+                         "tensor cores with 3xTF32 products, FP32 second pass and rank decisions), "
+                         "fp32 = every pass on the CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="file for the nvidia-smi samples of the timed region (default: a temp file)")
@@ -971,7 +972,9 @@ def main():
     line = {"metric": metric, "value": value, "unit": "Msamples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("c64 (fp32 arithmetic; TT-SVD first Gram pass as 3xTF32 tensor-core products)"
+                      if args.prec == "tf32" else "c64 (fp32 arithmetic)"),
             "data": "synthetic", "config": config,
             "e2e": {"value": e2e, "unit": "Msamples/s", "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},

@@ -67,8 +67,9 @@ typedef enum { QTT_F64 = 0, QTT_F32 = 1, QTT_C64 = 2, QTT_C128 = 3 } qtt_dtype;
  * (FP64 for QTT_F64, FP32 for QTT_C64); QTT_PREC_FP64 / QTT_PREC_FP32 must
  * match it (else QTT_EINVAL).  QTT_PREC_TF32_REFINED (complex64 TT-SVD,
  * qtt_decompose only): the first Gram pass of every factored unfolding with
- * at least 32 rows runs on the tensor cores (tcgen05 MMAs on TF32 operands,
- * FP32 accumulation, FP64 sum of the per-CTA partials); its eigenvectors
+ * at least 32 rows runs on the tensor cores (tcgen05 MMAs of kind tf32 on
+ * each operand's TF32 head and remainder -- three products, FP32-level
+ * products -- FP32 accumulation, FP64 sum of the per-CTA partials); its eigenvectors
  * only seed the second, FP32 pass (the projected Gram and the
  * relative-accuracy Jacobi, which decides the ranks), so the result keeps
  * the FP32 path's accuracy (Alg. 1; the refinement is what makes the Gram
@@ -504,6 +505,19 @@ qtt_status qtt_debug_tc_selftest(const float* A, const float* B, float* C, int N
 qtt_status qtt_debug_tc_cgemm(const void* A, const void* B, void* C, int M, int N, int K,
                               int conjA, int* status_dev, void* stream);
 
+/* Diagnostics: 1 (default) re-orthonormalises every complex64 TT-SVD core
+ * after its eigen-solves (C <- C (I - E/2), E = C^H C - I with compensated
+ * sums, the projection basis of the next unfolding corrected alike); 0
+ * keeps the cores as the FP32 eigen-solves give them. */
+void qtt_debug_set_orth_fix(int on);
+
+/* Diagnostics of QTT_PREC_TF32_REFINED: split = 3 (default) feeds the first
+ * pass's tensor-core Gram a TF32 head and remainder of every operand
+ * (3xTF32), 1 plain TF32 operands; pass2 != 0 also moves the second pass's
+ * Gram to the tensor cores (3xTF32; default 0: the FP32 CUDA-core pass,
+ * which decides the ranks). */
+void qtt_debug_set_tc_gram(int split, int pass2);
+
 /* Diagnostics: the tensor-core Gram pass on its own -- per-CTA partial
  * Grams X X^H of X (m x n complex64, column-major DEVICE array, 1 <= m <=
  * 128) written to gram_part (DEVICE, max_parts x ldp x ldp complex64,
@@ -517,8 +531,8 @@ int qtt_debug_tc_gram(const void* X, int m, long long n, int split, void* gram_p
                       int max_parts, int* status_dev, void* stream);
 
 /* Diagnostics: 1 routes the large-rank rounding's products (sketch ranks
- * above 64) to the tensor-core GEMM, 0 (default) to the CUDA-core GEMM with
- * compensated chunk sums.  The tensor cores' FP32 accumulator rounds
+ * above 64) to the tensor-core GEMM, 2 only those with k <= 64, 0 (default)
+ * all to the CUDA-core GEMM with compensated chunk sums.  The tensor cores' FP32 accumulator rounds
  * one-signed, and along the range finder's chain of products that bias
  * reaches the result (E2 ~3e-5 where the compensated GEMM stays below
  * 1e-5), so the default keeps the compensated sums. */

@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "qtt_matvec", "qtt_release_workspace", "qtt_last_error", "qtt_version", "qtt_small_eigh",
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
     "qtt_profile_work", "qtt_get_margins", "qtt_debug_tc_selftest", "qtt_debug_tc_cgemm",
-    "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram",
+    "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram", "qtt_debug_set_orth_fix", "qtt_debug_set_tc_gram",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
@@ -612,7 +612,7 @@ def qtt_debug_set_tc_gemm(on):
     """Select the large-rank rounding's product kernel: tensor cores (True)
     or the CUDA-core compensated GEMM (False, the default)."""
     load()
-    _lib.qtt_debug_set_tc_gemm(int(bool(on)))
+    _lib.qtt_debug_set_tc_gemm(int(on) if on in (0, 1, 2) else int(bool(on)))
 
 
 def qtt_from_cores(cores, shape_log2, interleave=True, stream=None):

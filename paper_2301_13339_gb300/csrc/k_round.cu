@@ -1036,7 +1036,9 @@ __global__ void k_status_merge(int* dst, const int* src) {
 template <typename TA>
 static qtt_status big_gemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
                            const char* name) {
-  return tc_gemm_enabled() ? tc_cgemm<TA>(g, nbatch, status, s, name) : cgemm<TA>(g, nbatch, s, name);
+  const int mode = tc_gemm_enabled();
+  const bool tc = (mode == 1) || (mode == 2 && g.K <= 64);
+  return tc ? tc_cgemm<TA>(g, nbatch, status, s, name) : cgemm<TA>(g, nbatch, s, name);
 }
 
 // Rounding of Y = O X when the sketch rank exceeds QTT_RANK_CAP (complex64

@@ -1300,6 +1300,85 @@ __global__ void __launch_bounds__(QR_THREADS)
   }
 }
 
+// --------------------------------------------------------------------------
+// Re-orthonormalisation of a TT-SVD core after the FP32 eigen-solves.  The
+// core C = U1 U2_r (m x r, ld m) is orthonormal only to the accuracy of the
+// FP32 eigenvectors (measured max |C^H C - I| up to ~2e-6 on the 128 x 64
+// cores of a 4096 x 4096 image, against ~2e-8 for an orthonormal matrix
+// rounded to FP32), and each cut's deviation enters the reconstruction,
+// since C C^H is then not a projector (Alg. 1 takes U with orthonormal
+// columns).  With E = C^H C - I, summed with Dot2 (the identity subtracted
+// inside the compensated sum, so E keeps its own relative accuracy),
+// S = I - E/2 gives (C S)^H (C S) = I + O(E^2).  V (the second pass's
+// eigenvectors U2_r, on which the next unfolding is projected, or null)
+// takes the same S, so that W = (V S)^H W1 = (C S)^H M stays the
+// projection on the corrected core.  One CTA: r <= 64, m <= 128.
+// --------------------------------------------------------------------------
+constexpr int OF_THREADS = 256;
+__global__ void __launch_bounds__(OF_THREADS)
+orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __restrict__ m_ptr,
+                int m_mul, const int* __restrict__ r_ptr, int mcap, int rcap) {
+  extern __shared__ __align__(16) unsigned char of_smem[];
+  const int m = min(m_mul * (*m_ptr), mcap), r = min(*r_ptr, rcap);
+  float2* E = reinterpret_cast<float2*>(of_smem);   // r x r, ld rcap
+  float2* X = E + (size_t)rcap * rcap;              // m x r staging, ld m
+  const int tid = threadIdx.x;
+  const int npair = r * (r + 1) / 2;
+  for (int p = tid; p < npair; p += OF_THREADS) {
+    // p -> (a, b), a <= b, column-packed upper triangle
+    int b = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    while (b > 0 && b * (b + 1) / 2 > p) --b;
+    while ((b + 1) * (b + 2) / 2 <= p) ++b;
+    const int a = p - b * (b + 1) / 2;
+    Dot2Acc32 acc;
+    if (a == b) acc.s.x = -1.f;
+    for (int i = 0; i < m; ++i) acc.add_mul(conjg(C[i + (size_t)m * a]), C[i + (size_t)m * b]);
+    const float2 e = acc.get();
+    E[a + rcap * b] = e;
+    E[b + rcap * a] = conjg(e);
+  }
+  __syncthreads();
+  for (int which = 0; which < 2; ++which) {
+    float2* Y = (which == 0) ? C : V;
+    if (!Y) continue;   // block-uniform
+    for (int e = tid; e < m * r; e += OF_THREADS) X[e] = Y[e];
+    __syncthreads();
+    for (int e = tid; e < m * r; e += OF_THREADS) {
+      const int i = e % m, b = e / m;
+      float2 sacc = make_float2(0.f, 0.f);
+      for (int a = 0; a < r; ++a) mac(sacc, X[i + (size_t)m * a], E[a + rcap * b]);
+      Y[e] = make_float2(X[e].x - 0.5f * sacc.x, X[e].y - 0.5f * sacc.y);
+    }
+    __syncthreads();
+  }
+}
+
+static int g_orth_fix = 1;   // diagnostics: 0 leaves the cores as the eigen-solves give them
+// TF32-refined mode: operand split of the first pass's tensor-core Gram.
+// 3xTF32 (TF32 head and remainder) by default: on the 4096 x 4096 image
+// (rank cap 64) it gives the oracle's ranks and E2 8.1e-6 after the
+// convolution, against 1.3e-5 with plain TF32 operands and 8.8e-6 on the
+// CUDA-core pass, at the same speed as plain TF32.  The second pass's Gram
+// on the tensor cores (diagnostic) is worse (1.8e-5): the accumulator's
+// one-signed rounding over long column runs reaches the rank decisions.
+static int g_tc_gram_split = 3;
+static int g_tc_pass2 = 0;
+
+template <typename T>
+static void launch_orth_fix(T* C, T* V, const int* m_ptr, int m_mul, const int* r_ptr, int mcap,
+                            int rcap, cudaStream_t s) {
+  if constexpr (std::is_same<T, float2>::value) {
+    if (!g_orth_fix) return;
+    static std::atomic<unsigned long long> cfg{0};
+    const size_t sm = sizeof(float2) * ((size_t)rcap * rcap + (size_t)mcap * rcap);
+    if (first_on_device(&cfg))
+      cudaFuncSetAttribute(orth_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float2) * (64 * 64 + 128 * 64)));
+    QTT_PROF("orth_fix", s);
+    orth_fix_kernel<<<1, OF_THREADS, sm, s>>>(C, V, m_ptr, m_mul, r_ptr, mcap, rcap);
+  }
+}
+
 template <typename T>
 qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStream_t s,
                   const RsvdOpt* rs) {
@@ -1334,7 +1413,8 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   constexpr int TC_GRAM_MIN_ROWS = 32;   // below: the CUDA-core pass (many column groups)
   auto gram_pass1 = [&](const T* X, const int* m_ptr, int mcap_g, long long ncols, int ldp_g) {
     if constexpr (std::is_same<T, float2>::value)
-      return tc_gram(X, m_ptr, 2, mcap_g, ncols, 1, gp, ldp_g, max_parts, t->status, s);
+      return tc_gram(X, m_ptr, 2, mcap_g, ncols, g_tc_gram_split, gp, ldp_g, max_parts, t->status,
+                     s);
     else
       return 0;
   };
@@ -1447,13 +1527,25 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
                          k == skip + 1, t->status, s);
       }
       // W1 = U1^H M, Gram of W1
-      nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
-                                   mcap, max_parts, s);
+      if constexpr (std::is_same<T, float2>::value) {
+        if (tc_pass1 && g_tc_pass2 && mcap >= TC_GRAM_MIN_ROWS) {
+          launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, -1, nullptr, 0,
+                              max_parts, s);
+          nparts = tc_gram(bufA, rk + (k - 1), 2, mcap, n, 3, gp, mcap, max_parts, t->status, s);
+        } else {
+          nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
+                                       mcap, max_parts, s);
+        }
+      } else {
+        nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, U1, nullptr, mcap, bufA, 0, gp,
+                                     mcap, max_parts, s);
+      }
       // pass 2: decide the rank on the projected Gram, whose small
       // eigenvalues the Jacobi solver gets to relative accuracy; core = U1 U2[:, :r]
       launch_gram_eig<T>(gp, nparts, mcap, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, eps_u, d,
                          cap_at(k), nullptr, 0, n, U1, U2, core_k, rk + k, nullptr, t->norm2, 0,
                          t->status, s, 1, delta_u, -1, t->margin + k);
+      launch_orth_fix<T>(core_k, U2, rk + (k - 1), 2, rk + k, mcap, rcapk, s);
       // W = U2_r^H W1 (rows = Sigma V^*), Gram of the next unfolding
       if (tc_pass1 && fold_next == 1 && ldp_next >= TC_GRAM_MIN_ROWS) {
         // W alone, then the Gram of its fold (W is r x n with ld r, so the
@@ -1469,6 +1561,7 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
       launch_gram_eig<T>(gp, nparts, ldp, rk + (k - 1), 2, mcap, EIG_MODE_DECIDE, eps_u, d,
                          cap_at(k), nullptr, 0, n, nullptr, core_k, nullptr, rk + k, nullptr,
                          t->norm2, k == skip + 1, t->status, s, 0, delta_u, -1, t->margin + k);
+      launch_orth_fix<T>(core_k, (T*)nullptr, rk + (k - 1), 2, rk + k, mcap, rcapk, s);
       nparts = launch_proj_gram<T>(M, rk + (k - 1), 2, mcap, n, core_k, rk + k, rcapk, Wout,
                                    fold_next, gp, ldp_next, max_parts, s);
     }
@@ -1509,6 +1602,11 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 // Diagnostics: choose the FP32 eigen-solver (0 = tridiagonal, 1 = Jacobi,
 // 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
+extern "C" void qtt_debug_set_orth_fix(int on) { qtt::g_orth_fix = (on != 0); }
+extern "C" void qtt_debug_set_tc_gram(int split, int pass2) {
+  qtt::g_tc_gram_split = (split == 1) ? 1 : 3;
+  qtt::g_tc_pass2 = (pass2 != 0);
+}
 extern "C" void qtt_debug_set_refine_sweeps(int sweeps) { qtt::g_refine_sweeps = sweeps >= 0 ? sweeps : 2; }
 extern "C" void qtt_debug_set_gram_parts(int per_sm) {
   qtt::g_gram_parts_per_sm = (per_sm >= 1 && per_sm <= 16) ? per_sm : 2;

@@ -485,7 +485,7 @@ int tc_gemm_enabled() { return g_tc_gemm; }
 
 }  // namespace qtt
 
-extern "C" void qtt_debug_set_tc_gemm(int on) { qtt::g_tc_gemm = (on != 0); }
+extern "C" void qtt_debug_set_tc_gemm(int on) { qtt::g_tc_gemm = (on == 1 || on == 2) ? on : 0; }
 
 // C (M x N, column-major, complex64) = op(A) B through the tensor-core GEMM:
 // A (M x K, column-major, complex64; conjugated when conjA), B (K x N,
