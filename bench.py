@@ -375,6 +375,17 @@ def roofline(kernels, wl, peaks, peak_kind):
                 "avg_launch_ms": avg_ms, "frac_of_gpu": ach / fp32_peak_tflops,
                 "peak_source": f"one SM: 128 FP32 FMA/clk at {sm_mhz:.0f} MHz (single-CTA kernels; "
                                "the back-transformation of heev uses 8 SMs for ~7 % of its time)"}
+    if name == "bigqr_panel" and kinfo.get("flops_per_step"):
+        # the Householder panel factorisation runs in one CTA (a sequential
+        # chain of reflectors): its peak is one SM's FP32 rate; the
+        # whole-GPU fraction is frac / SMs
+        ach = kinfo["flops_per_step"] / nl / (avg_ms * 1e-3) / 1e12
+        sm_peak = fp32_peak_tflops / nsm
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": sm_peak,
+                "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
+                "avg_launch_ms": avg_ms, "frac_of_gpu": ach / fp32_peak_tflops,
+                "peak_source": f"one SM: 128 FP32 FMA/clk at {sm_mhz:.0f} MHz (one-CTA kernel; "
+                               "algorithmic work 8 kb^2 (M - kb/3) flop per M x kb complex panel)"}
     if kinfo.get("flops_per_step") and kinfo["flops_per_step"] > 0 and name not in ("full_expand",):
         ach = kinfo["flops_per_step"] / nl / (avg_ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
@@ -985,6 +996,13 @@ def main():
             "kernel_shares": {k: round(v["ms_per_step"] / max(sum(x["ms_per_step"] for x in kern.values()), 1e-12), 4)
                               for k, v in kern.items()},
             "profiled_ms_per_step": round(sum(x["ms_per_step"] for x in kern.values()), 3),
+            # achieved rates of the kernels that record their algorithmic work
+            # (flop and streamed bytes per step over their profiled time)
+            "kernel_rates": {k: {"tflops": round(v["flops_per_step"] / (v["ms_per_step"] * 1e-3) / 1e12, 4)
+                                 if v.get("flops_per_step") else None,
+                                 "gbs": round(v["bytes_per_step"] / (v["ms_per_step"] * 1e-3) / 1e9, 1)
+                                 if v.get("bytes_per_step") else None}
+                             for k, v in kern.items() if v.get("flops_per_step") or v.get("bytes_per_step")},
             "roofline": roofline(kern, wl, peaks, peak_kind),
             # the end-to-end floor: each input sample read and each output
             # sample written once (16 B per complex64 sample); a two-pass

@@ -26,80 +26,89 @@
 namespace qtt {
 
 // ---------------------------------------------------------------- QR
-constexpr int BQ_NB = 32;        // panel width
-constexpr int BQ_THREADS = 512;  // panel CTA
+// panel width: the one-CTA panel factorisation issues ~kb^2 M instructions
+// per panel, so the panel chain of a QR costs ~kb n M and a narrower panel
+// moves work to the many-CTA block-reflector updates
+constexpr int BQ_NB = 16;
 constexpr int BQ_CB = 8;         // columns per CTA in the block-reflector application
 constexpr int BQ_MAXM = 768;     // rows (panel in shared memory: 768 x 32 x 8 B)
-
-// Block-wide reductions of the panel kernel: every thread gets the result
-// (one barrier; the 16 warp partials are read back by every thread).
-template <typename R>
-__device__ __forceinline__ R bq_block_max(R v, R* red) {
-  for (int off = 16; off > 0; off >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  R m = red[0];
-  for (int w = 1; w < BQ_THREADS / 32; ++w) m = rmax(m, red[w]);
-  return m;
-}
-template <typename R>
-__device__ __forceinline__ R bq_block_sum(R v, R* red) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  R t = (R)0;
-  for (int w = 0; w < BQ_THREADS / 32; ++w) t += red[w];
-  return t;
-}
 
 // Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory (ld mp|1,
 // so consecutive columns fall on different banks), write it back (R on and
 // above the diagonal, the v_k below), V^T (kb x mp, row a = v_a, unit
 // diagonal and zeros above it written out) to Vt, and T (BQ_NB x BQ_NB,
-// column-major) to Tm.  Per reflector: its norm by block reductions over all
-// threads, then one warp per trailing panel column (dot and update).
+// column-major) to Tm.
+//
+// One warp per trailing column (BQP_THREADS = 32 warps >= kb) and one
+// barrier per reflector: every thread derives reflector k (tau, the scale
+// 1/(alpha - beta) of v, beta) itself from the column's largest entry and
+// scaled sum of squares, which the warp that updated column k in the
+// previous step measured right after its update (look-ahead); the trailing
+// update takes v_i = col_i * scal on the fly (v^H x = x_k + conj(scal)
+// sum_{i>k} conj(col_i) x_i), so column k is scaled into v only in the next
+// step, by the warp that no trailing column needs (kb <= 32 leaves one).
+constexpr int BQP_THREADS = 1024;
+
+// largest |re|, |im| of x over rows i >= i0, and sum over i > i0 of
+// |x_i / amax|^2 (all lanes of the warp get both)
 template <typename T>
-__global__ void __launch_bounds__(BQ_THREADS)
+__device__ __forceinline__ void bq_col_norm(const T* x, int i0, int mp, int lane,
+                                            typename Sc<T>::R& amax, typename Sc<T>::R& ssq) {
+  using R = typename Sc<T>::R;
+  R a = (R)0;
+  for (int i = i0 + lane; i < mp; i += 32) a = rmax(a, rmax(rabs(sreal(x[i])), rabs(simag(x[i]))));
+  for (int off = 16; off > 0; off >>= 1) a = rmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+  R q = (R)0;
+  if (a > (R)0) {
+    const R inv = (R)1 / a;
+    for (int i = i0 + 1 + lane; i < mp; i += 32) q += sabs2(rscale(x[i], inv));
+  }
+  for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+  amax = a;
+  ssq = q;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BQP_THREADS)
 k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __restrict__ Vt) {
   using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char bq_smem[];
   T* P = reinterpret_cast<T*>(bq_smem);
-  __shared__ T s_tau[BQ_NB];
+  __shared__ T s_tau[BQ_NB], s_scal[BQ_NB], s_beta[BQ_NB];
+  __shared__ R s_amax[BQ_NB], s_ssq[BQ_NB];
   __shared__ T s_Y[BQ_NB * BQ_NB];
   __shared__ T s_T[BQ_NB * BQ_NB];
-  __shared__ R s_red[2][BQ_THREADS / 32];
   const int mp = m - p;
   const int ld = mp | 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < mp * kb; e += BQ_THREADS) {
+  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
     const int i = e % mp, j = e / mp;
     P[i + (size_t)ld * j] = A[(size_t)(p + i) + (size_t)m * (p + j)];
   }
-  for (int e = tid; e < BQ_NB * BQ_NB; e += BQ_THREADS) {
+  for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) {
     s_T[e] = szero<T>();
     s_Y[e] = szero<T>();
   }
   __syncthreads();
   const int kmax = min(mp, kb);
+  if (warp == 0) {
+    R a, q;
+    bq_col_norm(P, 0, mp, lane, a, q);
+    if (lane == 0) { s_amax[0] = a; s_ssq[0] = q; }
+  }
+  __syncthreads();
   for (int k = 0; k < kmax; ++k) {
-    T* col = P + (size_t)ld * k;
-    // reflector k: scaled by the column's largest entry (no overflow or
+    const T* col = P + (size_t)ld * k;
+    // reflector k, scaled by the column's largest entry (no overflow or
     // underflow of |alpha - beta|^2 at any data scale)
-    R amax = (R)0;
-    for (int i = k + tid; i < mp; i += BQ_THREADS)
-      amax = rmax(amax, rmax(rabs(sreal(col[i])), rabs(simag(col[i]))));
-    amax = bq_block_max(amax, s_red[0]);
+    const R amax = s_amax[k];
     T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
-    bool act = false;
     if (amax > (R)0) {
       const R inv = (R)1 / amax;
-      R part = (R)0;
-      for (int i = k + 1 + tid; i < mp; i += BQ_THREADS) part += sabs2(rscale(col[i], inv));
-      part = bq_block_sum(part, s_red[1]);
+      const R part = s_ssq[k];
       const T al = rscale(col[k], inv);
       const R ax = sreal(al), ay = simag(al);
       if (part > (R)0 || ay != (R)0) {
-        act = true;
         const R nrm = sqrt(ax * ax + ay * ay + part);
         const R beta = (ax >= (R)0) ? -nrm : nrm;
         const R rb = (R)1 / beta;
@@ -109,58 +118,106 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
         beta_s = make_scalar<T>(beta * amax, (R)0);
       }
     }
-    __syncthreads();   // every thread has read col[k] before it changes
-    if (act)
-      for (int i = k + 1 + tid; i < mp; i += BQ_THREADS) col[i] = smul(col[i], scal);
-    if (tid == 0) {
-      col[k] = beta_s;
-      s_tau[k] = tau;
-    }
-    __syncthreads();
-    // trailing panel columns: A <- (I - conj(tau) v v^H) A, 16 threads (half
-    // a warp) per column, rows strided by 16, two partial sums each
-    const T ctau = conjg(tau);
-    {
-      const int g = tid >> 4, l16 = tid & 15;
-      const int j = k + 1 + g;
-      const bool live = j < kb;          // both halves of a warp shuffle below
-      T* x = P + (size_t)ld * (live ? j : k);
-      T w0 = szero<T>(), w1 = szero<T>();
-      if (live) {
-        int i = k + l16;
-        if (i == k) { macc(w0, sone(T()), x[i]); i += 16; }
-        for (; i + 16 < mp; i += 32) {
-          macc(w0, col[i], x[i]);
-          macc(w1, col[i + 16], x[i + 16]);
-        }
-        if (i < mp) macc(w0, col[i], x[i]);
+    const int nt = kb - 1 - k;   // trailing columns of the panel (<= 31)
+    if (warp < nt) {
+      // x <- (I - conj(tau) v v^H) x for trailing column j; four rows per
+      // lane in flight in the dot and in the update
+      const int j = k + 1 + warp;
+      T* x = P + (size_t)ld * j;
+      T a0 = szero<T>(), a1 = szero<T>(), a2 = szero<T>(), a3 = szero<T>();
+      int i = k + 1 + lane;
+      for (; i + 96 < mp; i += 128) {
+        const T c0 = col[i], c1 = col[i + 32], c2 = col[i + 64], c3 = col[i + 96];
+        const T x0 = x[i], x1 = x[i + 32], x2 = x[i + 64], x3 = x[i + 96];
+        macc(a0, c0, x0);
+        macc(a1, c1, x1);
+        macc(a2, c2, x2);
+        macc(a3, c3, x3);
       }
-      T w = sadd(w0, w1);
+      for (; i < mp; i += 32) macc(a0, col[i], x[i]);
+      const T sdot = warp_sum(sadd(sadd(a0, a1), sadd(a2, a3)));
+      const T wdot = sadd(x[k], smul(conjg(scal), sdot));
+      const T f = smul(conjg(tau), wdot);
+      const T fs = smul(scal, f);
+      __syncwarp();                  // every lane has read x[k]
+      if (lane == 0) x[k] = ssub(x[k], f);
+      // column k + 1 (the next reflector's) also measures itself while it is
+      // updated: largest |re|, |im| over rows >= k + 1 and the plain sum of
+      // squares below row k + 1
+      const bool look = (j == k + 1 && j < kmax);
+      R am = (R)0, sq = (R)0;
+      int r = k + 1 + lane;
+      for (; r + 96 < mp; r += 128) {
+        T y[4];
 #pragma unroll
-      for (int off = 8; off > 0; off >>= 1) w = sadd(w, shfl_xor_s(w, off));
-      if (live) {
-        const T f = smul(ctau, w);
-        for (int i = k + l16; i < mp; i += 16) x[i] = ssub(x[i], smul((i == k) ? sone(T()) : col[i], f));
+        for (int u = 0; u < 4; ++u) y[u] = ssub(x[r + 32 * u], smul(col[r + 32 * u], fs));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[r + 32 * u] = y[u];
+          if (look) {
+            am = rmax(am, rmax(rabs(sreal(y[u])), rabs(simag(y[u]))));
+            if (r + 32 * u > j) sq += sabs2(y[u]);
+          }
+        }
       }
+      for (; r < mp; r += 32) {
+        const T y = ssub(x[r], smul(col[r], fs));
+        x[r] = y;
+        if (look) {
+          am = rmax(am, rmax(rabs(sreal(y)), rabs(simag(y))));
+          if (r > j) sq += sabs2(y);
+        }
+      }
+      if (look) {
+        for (int off = 16; off > 0; off >>= 1) {
+          am = rmax(am, __shfl_xor_sync(0xffffffffu, am, off));
+          sq += __shfl_xor_sync(0xffffffffu, sq, off);
+        }
+        // the unscaled sum is exact enough wherever amax^2 neither overflows
+        // nor underflows; outside that range the column is measured again
+        // with the scaled two-pass sum
+        const R lo = sizeof(R) == 4 ? (R)1e-15 : (R)1e-140, hi = sizeof(R) == 4 ? (R)1e15 : (R)1e140;
+        if (am == (R)0 || (am > lo && am < hi)) {
+          if (lane == 0) { s_amax[j] = am; s_ssq[j] = (am > (R)0) ? sq / (am * am) : (R)0; }
+        } else {
+          __syncwarp();
+          R a, q;
+          bq_col_norm(x, j, mp, lane, a, q);
+          if (lane == 0) { s_amax[j] = a; s_ssq[j] = q; }
+        }
+      }
+    } else if (warp == BQP_THREADS / 32 - 1 && k > 0) {
+      // column k - 1 is final: v_{k-1} = col * scal below the diagonal, beta on it
+      T* c1 = P + (size_t)ld * (k - 1);
+      const T sc = s_scal[k - 1];
+      for (int r = k + lane; r < mp; r += 32) c1[r] = smul(c1[r], sc);
+      if (lane == 0) c1[k - 1] = s_beta[k - 1];
+    }
+    if (tid == 0) {
+      s_tau[k] = tau;
+      s_scal[k] = scal;
+      s_beta[k] = beta_s;
     }
     __syncthreads();
   }
-  // Y[a + NB b] = v_a^H v_b (a < b): one thread per pair (rows i >= b)
-  for (int pr = tid; pr < kmax * kmax; pr += BQ_THREADS) {
+  if (warp == 0 && kmax > 0) {
+    T* c1 = P + (size_t)ld * (kmax - 1);
+    const T sc = s_scal[kmax - 1];
+    for (int r = kmax + lane; r < mp; r += 32) c1[r] = smul(c1[r], sc);
+    if (lane == 0) c1[kmax - 1] = s_beta[kmax - 1];
+  }
+  __syncthreads();
+  // Y[a + NB b] = v_a^H v_b (a < b), one warp per pair, lanes over the rows
+  // i > b (row b: v_b = 1)
+  for (int pr = warp; pr < kmax * kmax; pr += BQP_THREADS / 32) {
     const int a = pr % kmax, b = pr / kmax;
-    if (a >= b) continue;
+    if (a >= b) continue;   // warp-uniform
     const T* va = P + (size_t)ld * a;
     const T* vb = P + (size_t)ld * b;
-    T acc = conjg(va[b]), acc1 = szero<T>(), acc2 = szero<T>(), acc3 = szero<T>();   // row b: v_b = 1
-    int i = b + 1;
-    for (; i + 3 < mp; i += 4) {
-      macc(acc, va[i], vb[i]);
-      macc(acc1, va[i + 1], vb[i + 1]);
-      macc(acc2, va[i + 2], vb[i + 2]);
-      macc(acc3, va[i + 3], vb[i + 3]);
-    }
-    for (; i < mp; ++i) macc(acc, va[i], vb[i]);
-    s_Y[a + BQ_NB * b] = sadd(sadd(acc, acc1), sadd(acc2, acc3));
+    T acc = szero<T>();
+    for (int i = b + 1 + lane; i < mp; i += 32) macc(acc, va[i], vb[i]);
+    acc = warp_sum(acc);
+    if (lane == 0) s_Y[a + BQ_NB * b] = sadd(acc, conjg(va[b]));
   }
   __syncthreads();
   // T(a, a) = tau_a, T(a, b) = -tau_b sum_{c=a}^{b-1} T(a, c) Y(c, b): each
@@ -175,16 +232,16 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
     }
   }
   __syncthreads();
-  for (int e = tid; e < mp * kb; e += BQ_THREADS) {
+  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
     const int i = e % mp, j = e / mp;
     A[(size_t)(p + i) + (size_t)m * (p + j)] = P[i + (size_t)ld * j];
   }
   // V^T rows with the implicit unit diagonal and the zeros above it
-  for (int e = tid; e < mp * kb; e += BQ_THREADS) {
+  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
     const int i = e % mp, a = e / mp;
     Vt[i + (size_t)mp * a] = (i == a) ? sone(T()) : (i > a && a < kmax) ? P[i + (size_t)ld * a] : szero<T>();
   }
-  for (int e = tid; e < BQ_NB * BQ_NB; e += BQ_THREADS) Tm[e] = s_T[e];
+  for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) Tm[e] = s_T[e];
 }
 
 // X[p:m, c] <- (I - V op(T) V^H) X[p:m, c] for the columns c of this CTA
@@ -203,7 +260,7 @@ k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ 
   const int cbase = col0 + BQ_CB * blockIdx.x;
   const int cend = col0 + ncols;
   const int mp = m - p;
-  constexpr int AW = BQ_NB / BQ_CB;   // reflectors per warp (8 warps x 4 = 32)
+  constexpr int AW = BQ_NB / BQ_CB;   // reflectors per warp (BQ_CB warps x AW = BQ_NB)
   T acc[AW][BQ_CB];
 #pragma unroll
   for (int u = 0; u < AW; ++u)
@@ -230,8 +287,8 @@ k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ 
       if (lane == 0) W[warp * AW + u][c] = w;
     }
   __syncthreads();
-  {
-    const int a = tid % BQ_NB, c = tid / BQ_NB;
+  for (int e = tid; e < BQ_NB * BQ_CB; e += 32 * BQ_CB) {
+    const int a = e % BQ_NB, c = e / BQ_NB;
     T w2 = szero<T>();
     if (a < kb) {
       if (adj) {
@@ -301,13 +358,20 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
     const int kb = std::min(BQ_NB, kmax - p);
     T* Tp = Tm + (size_t)(p / BQ_NB) * BQ_NB * BQ_NB;
     T* Vp = Vall + (size_t)(p / BQ_NB) * BQ_NB * BQ_MAXM;
+    // algorithmic work (complex flop = 4 real multiplies + 4 adds): the
+    // Householder factorisation of the (m - p) x kb panel, 8 kb^2 (M - kb/3),
+    // and a block-reflector application to nc columns, 16 M kb nc
+    const double M = (double)(m - p);
+    const double cplx = Sc<T>::cplx ? 1.0 : 0.25;
     {
       QTT_PROF("bigqr_panel", s);
-      k_bq_panel<T><<<1, BQ_THREADS, sizeof(T) * (size_t)((m - p) | 1) * kb, s>>>(A, m, p, kb, Tp, Vp);
+      prof_add_work("bigqr_panel", cplx * 8.0 * kb * kb * (M - kb / 3.0), 2.0 * M * kb * sizeof(T));
+      k_bq_panel<T><<<1, BQP_THREADS, sizeof(T) * (size_t)((m - p) | 1) * kb, s>>>(A, m, p, kb, Tp, Vp);
     }
     const int c0 = p + kb, nc = kmax - c0;
     if (nc > 0) {
       QTT_PROF("bigqr_update", s);
+      prof_add_work("bigqr_update", cplx * 16.0 * M * kb * nc, 2.0 * M * nc * sizeof(T));
       k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nc, Vp, p, kb, Tp, 1);
     }
   }
@@ -320,6 +384,8 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
     const int kb = std::min(BQ_NB, kmax - p);
     if (p >= nq) continue;
     QTT_PROF("bigqr_formq", s);
+    prof_add_work("bigqr_formq", (Sc<T>::cplx ? 1.0 : 0.25) * 16.0 * (m - p) * kb * (double)(nq - p),
+                  2.0 * (m - p) * (double)(nq - p) * sizeof(T));
     k_bq_apply<T><<<(nq - p + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(
         Q, m, p, nq - p, Vall + (size_t)pi * BQ_NB * BQ_MAXM, p, kb,
         Tm + (size_t)pi * BQ_NB * BQ_NB, 0);

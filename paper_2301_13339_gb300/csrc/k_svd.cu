@@ -1314,7 +1314,7 @@ __global__ void __launch_bounds__(QR_THREADS)
 // takes the same S, so that W = (V S)^H W1 = (C S)^H M stays the
 // projection on the corrected core.  One CTA: r <= 64, m <= 128.
 // --------------------------------------------------------------------------
-constexpr int OF_THREADS = 256;
+constexpr int OF_THREADS = 1024;
 __global__ void __launch_bounds__(OF_THREADS)
 orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __restrict__ m_ptr,
                 int m_mul, const int* __restrict__ r_ptr, int mcap, int rcap) {
@@ -1323,6 +1323,8 @@ orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __res
   float2* E = reinterpret_cast<float2*>(of_smem);   // r x r, ld rcap
   float2* X = E + (size_t)rcap * rcap;              // m x r staging, ld m
   const int tid = threadIdx.x;
+  for (int e = tid; e < m * r; e += OF_THREADS) X[e] = C[e];
+  __syncthreads();
   const int npair = r * (r + 1) / 2;
   for (int p = tid; p < npair; p += OF_THREADS) {
     // p -> (a, b), a <= b, column-packed upper triangle
@@ -1332,7 +1334,7 @@ orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __res
     const int a = p - b * (b + 1) / 2;
     Dot2Acc32 acc;
     if (a == b) acc.s.x = -1.f;
-    for (int i = 0; i < m; ++i) acc.add_mul(conjg(C[i + (size_t)m * a]), C[i + (size_t)m * b]);
+    for (int i = 0; i < m; ++i) acc.add_mul(conjg(X[i + (size_t)m * a]), X[i + (size_t)m * b]);
     const float2 e = acc.get();
     E[a + rcap * b] = e;
     E[b + rcap * a] = conjg(e);
@@ -1341,8 +1343,10 @@ orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __res
   for (int which = 0; which < 2; ++which) {
     float2* Y = (which == 0) ? C : V;
     if (!Y) continue;   // block-uniform
-    for (int e = tid; e < m * r; e += OF_THREADS) X[e] = Y[e];
-    __syncthreads();
+    if (which == 1) {   // C is staged already
+      for (int e = tid; e < m * r; e += OF_THREADS) X[e] = Y[e];
+      __syncthreads();
+    }
     for (int e = tid; e < m * r; e += OF_THREADS) {
       const int i = e % m, b = e / m;
       float2 sacc = make_float2(0.f, 0.f);
