@@ -895,7 +895,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="image_4096sq_c64", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=1, help="second Gram pass in the TT-SVD")
-    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32"],
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32"],
                     help="TT-SVD arithmetic: tf32 = the TF32-refined mode (first Gram pass on the "
                          "tensor cores with 3xTF32 products, FP32 second pass and rank decisions), "
                          "fp32 = every pass on the CUDA cores")

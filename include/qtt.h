@@ -344,9 +344,13 @@ qtt_status qtt_get_cores(const qtt_tensor* t, void* host_buf, void* stream);
 qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_dtype dt,
                           int ndim, const int* log2_shape, int interleave, void* stream,
                           qtt_tensor** out);
-/* Release a handle.  qtt_free synchronises the device; qtt_free_async
- * releases the storage in stream order (the stream must be the one the
- * handle was last used on). */
+/* Release a handle without synchronising.  Every call that uses a handle
+ * records the handle's last-use event on its stream when it returns;
+ * qtt_free releases the storage on a library stream after that event (so
+ * after the last call's work, on whatever stream it ran; work that a caller
+ * enqueued on other streams after that call is the caller's to order, as for
+ * any stream-ordered free).  qtt_free_async releases it in the order of the
+ * given stream (the stream the handle was last used on). */
 void qtt_free(qtt_tensor* t);
 void qtt_free_async(qtt_tensor* t, void* stream);
 

@@ -130,14 +130,54 @@ qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap, cu
   t->margin = (double*)(base + core_bytes + 320);
   cudaMemsetAsync(base + core_bytes, 0, 320, s);
   cudaMemsetAsync(base + core_bytes + 320, 0xff, meta - 320, s);   // NaN: no decision yet
+  if (cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    t->used = nullptr;
+  }
+  tensor_stamp(t, s);
   *out = t;
   return QTT_OK;
+}
+
+void tensor_stamp(const qtt_tensor* t, cudaStream_t s) {
+  if (t && t->used) cudaEventRecord(t->used, s);
 }
 
 void tensor_free_async(qtt_tensor* t, cudaStream_t s) {
   if (!t) return;
   scratch_free(t->cores, s);
+  if (t->used) cudaEventDestroy(t->used);
   delete t;
+}
+
+// The handles a C-ABI call uses, stamped on its stream when the call returns
+// (after everything it enqueued), so that qtt_free can order the release
+// after the last use without synchronising the device.
+struct Touch {
+  cudaStream_t s;
+  const qtt_tensor* a;
+  const qtt_tensor* b;
+  qtt_tensor** out;
+  ~Touch() {
+    tensor_stamp(a, s);
+    tensor_stamp(b, s);
+    if (out) tensor_stamp(*out, s);
+  }
+};
+
+// per-device stream on which qtt_free releases storage after the handle's
+// last-use event
+static cudaStream_t free_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
 }
 
 // ---------------------------------------------------------------- op cache
@@ -298,6 +338,7 @@ qtt_status qtt_decompose(const void* x, qtt_dtype dt, int ndim, const int* log2_
                          int interleave, const qtt_trunc* tr, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !log2_shape || !out) { set_error("qtt_decompose: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, nullptr, nullptr, out};
   qtt_status st = dtype_status(dt, "qtt_decompose");
   if (st != QTT_OK) return st;
   if (ndim != 1 && ndim != 2) { set_error("qtt_decompose: ndim must be 1 or 2"); return QTT_EINVAL; }
@@ -350,6 +391,7 @@ qtt_status qtt_decompose_rsvd(const void* x, qtt_dtype dt, int log2_len, int rma
                               qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !out) { set_error("qtt_decompose_rsvd: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, nullptr, nullptr, out};
   {
     const qtt_status dst = dtype_status(dt, "qtt_decompose_rsvd");
     if (dst != QTT_OK) return dst;
@@ -386,6 +428,7 @@ qtt_status qtt_conv_sinc(const qtt_tensor* f, const double* B, int normalize, do
                          void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!f || !B || !out) { set_error("qtt_conv_sinc: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, f, nullptr, out};
   qtt_status st = check_trunc(round_tr, f->desc.dt, f->desc.d);
   if (st != QTT_OK) return st;
   if (!(eps_op > 0.0) || eps_op >= 1.0) { set_error("qtt_conv_sinc: eps_op must be in (0, 1)"); return QTT_EINVAL; }
@@ -416,6 +459,7 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
                      void* stream) {
   g_err[0] = 0;
   if (!t) { set_error("qtt_round: NULL tensor"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, t, nullptr, nullptr};
   qtt_status st = check_trunc(tr, t->desc.dt, t->desc.d);
   if (st != QTT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -435,6 +479,7 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
   t->status = y->status;
   t->norm2 = y->norm2;
   t->margin = y->margin;
+  if (y->used) cudaEventDestroy(y->used);
   delete y;
   return QTT_OK;
 }
@@ -442,6 +487,7 @@ qtt_status qtt_round(qtt_tensor* t, const qtt_trunc* tr, int sketch, unsigned lo
 qtt_status qtt_to_full(const qtt_tensor* t, void* y, void* stream) {
   g_err[0] = 0;
   if (!t || !y) { set_error("qtt_to_full: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, t, nullptr, nullptr};
   cudaStream_t s = (cudaStream_t)stream;
   if (t->desc.dt == QTT_F64) return tt_full<double>(t, (double*)y, s);
   return tt_full<float2>(t, (float2*)y, s);
@@ -521,6 +567,7 @@ qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_d
                           const int* log2_shape, int interleave, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!host_cores || !ranks || !log2_shape || !out) { set_error("qtt_from_cores: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, nullptr, nullptr, out};
   if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_from_cores");
   if (!valid_dtype(dt) || d < 2 || d > 30 || (ndim != 1 && ndim != 2)) {
     set_error("qtt_from_cores: bad dtype/d/ndim");
@@ -555,10 +602,18 @@ qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_d
 
 void qtt_free(qtt_tensor* t) {
   if (!t) return;
+  cudaStream_t fs = t->used ? free_stream() : nullptr;
+  if (fs) {
+    // released in stream order after the last call that used the handle
+    cudaStreamWaitEvent(fs, t->used, 0);
+    tensor_free_async(t, fs);
+    return;
+  }
   if (t->cores) {
     cudaDeviceSynchronize();
     cudaFree(t->cores);
   }
+  if (t->used) cudaEventDestroy(t->used);
   delete t;
 }
 
@@ -595,6 +650,7 @@ void qtt_op_free(qtt_op* op) {
 qtt_status qtt_matvec(const qtt_op* op, const qtt_tensor* x, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!op || !x || !out) { set_error("qtt_matvec: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, x, nullptr, out};
   return matvec(op, x, (cudaStream_t)stream, out);
 }
 
@@ -619,6 +675,7 @@ qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sk
                    unsigned long long seed, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !out) { set_error("qtt_fft: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, x, nullptr, out};
   qtt_trunc t0 = {0.0, 0, 1, 0.0, QTT_PREC_AUTO, nullptr};
   if (tr) {
     qtt_status st = check_trunc(tr, x->desc.dt, x->desc.d);
@@ -664,6 +721,7 @@ qtt_status qtt_conv_adjoint(const qtt_tensor* f, const qtt_tensor* r, const doub
                             qtt_tensor** adj_out, void* stream) {
   g_err[0] = 0;
   if (!r || !B) { set_error("qtt_conv_adjoint: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, f, r, adj_out};
   if (grad_cores && !f) { set_error("qtt_conv_adjoint: gradients need f"); return QTT_EINVAL; }
   if (f && !same_layout(f, r)) { set_error("qtt_conv_adjoint: f and r differ in shape or type"); return QTT_EINVAL; }
   if (grad_cores)
@@ -711,6 +769,7 @@ qtt_status qtt_core_grads(const qtt_tensor* f, const qtt_tensor* w, double alpha
                           void* const* grad_cores, void* stream) {
   g_err[0] = 0;
   if (!f || !w || !grad_cores) { set_error("qtt_core_grads: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, f, w, nullptr};
   if (!same_layout(f, w)) { set_error("qtt_core_grads: f and w differ in shape or type"); return QTT_EINVAL; }
   for (int k = 0; k < f->desc.d; ++k)
     if (!grad_cores[k]) { set_error("qtt_core_grads: grad_cores[%d] is NULL", k); return QTT_EINVAL; }
@@ -720,6 +779,7 @@ qtt_status qtt_core_grads(const qtt_tensor* f, const qtt_tensor* w, double alpha
 qtt_status qtt_dot(const qtt_tensor* x, const qtt_tensor* y, double* out_dev, void* stream) {
   g_err[0] = 0;
   if (!x || !y || !out_dev) { set_error("qtt_dot: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, x, y, nullptr};
   if (!same_layout(x, y)) { set_error("qtt_dot: tensors differ in shape or type"); return QTT_EINVAL; }
   return env_sweep(x, y, 0.0, 0.0, nullptr, (double2*)out_dev, (cudaStream_t)stream);
 }
@@ -728,6 +788,7 @@ qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_ten
                    void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !y || !out) { set_error("qtt_add: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, x, y, out};
   if (!same_layout(x, y)) { set_error("qtt_add: tensors differ in shape or type"); return QTT_EINVAL; }
   return tt_add(alpha, x, beta, y, (cudaStream_t)stream, out);
 }
@@ -735,6 +796,7 @@ qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_ten
 qtt_status qtt_hadamard(const qtt_tensor* x, const qtt_tensor* y, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !y || !out) { set_error("qtt_hadamard: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, x, y, out};
   if (!same_layout(x, y)) { set_error("qtt_hadamard: tensors differ in shape or type"); return QTT_EINVAL; }
   return hadamard(x, y, (cudaStream_t)stream, out);
 }
@@ -744,6 +806,7 @@ qtt_status qtt_from_device_cores(const void* const* cores, const int* ranks, int
                                  qtt_tensor** out) {
   g_err[0] = 0;
   if (!cores || !ranks || !log2_shape || !out) { set_error("qtt_from_device_cores: NULL argument"); return QTT_EINVAL; }
+  Touch tg{(cudaStream_t)stream, nullptr, nullptr, out};
   if (dt == QTT_F32 || dt == QTT_C128) return dtype_status(dt, "qtt_from_device_cores");
   if (!valid_dtype(dt) || d < 2 || d > 30 || (ndim != 1 && ndim != 2)) {
     set_error("qtt_from_device_cores: bad dtype/d/ndim");

@@ -405,7 +405,9 @@ extern "C" qtt_status qtt_to_full_noalloc(const qtt_tensor* t, void* y, void* st
     return QTT_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (t->desc.dt == QTT_F64) return tt_full_noalloc_t<double>(t, (double*)y, s);
-  return tt_full_noalloc_t<float2>(t, (float2*)y, s);
+  const qtt_status st = (t->desc.dt == QTT_F64) ? tt_full_noalloc_t<double>(t, (double*)y, s)
+                                                : tt_full_noalloc_t<float2>(t, (float2*)y, s);
+  tensor_stamp(t, s);   // records the handle's existing last-use event: no allocation
+  return st;
 }
 

@@ -1312,48 +1312,55 @@ __global__ void __launch_bounds__(QR_THREADS)
 // S = I - E/2 gives (C S)^H (C S) = I + O(E^2).  V (the second pass's
 // eigenvectors U2_r, on which the next unfolding is projected, or null)
 // takes the same S, so that W = (V S)^H W1 = (C S)^H M stays the
-// projection on the corrected core.  One CTA: r <= 64, m <= 128.
+// projection on the corrected core.  r <= 64, m <= 128.
 // --------------------------------------------------------------------------
-constexpr int OF_THREADS = 1024;
-__global__ void __launch_bounds__(OF_THREADS)
-orth_fix_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __restrict__ m_ptr,
-                int m_mul, const int* __restrict__ r_ptr, int mcap, int rcap) {
-  extern __shared__ __align__(16) unsigned char of_smem[];
+// E over r CTAs (CTA b: column b of E, one thread per row a, column b of C
+// staged in shared memory), then the corrections over many CTAs (four rows
+// of C or V per CTA, E staged in shared memory): no single-SM stage.
+constexpr int OF_ROWS = 4;
+__global__ void __launch_bounds__(64)
+orth_e_kernel(const float2* __restrict__ C, const int* __restrict__ m_ptr, int m_mul,
+              const int* __restrict__ r_ptr, int mcap, int rcap, float2* __restrict__ E) {
+  __shared__ float2 cb[128];
   const int m = min(m_mul * (*m_ptr), mcap), r = min(*r_ptr, rcap);
-  float2* E = reinterpret_cast<float2*>(of_smem);   // r x r, ld rcap
-  float2* X = E + (size_t)rcap * rcap;              // m x r staging, ld m
-  const int tid = threadIdx.x;
-  for (int e = tid; e < m * r; e += OF_THREADS) X[e] = C[e];
+  const int b = blockIdx.x, a = threadIdx.x;
+  if (b >= r) return;   // block-uniform
+  for (int i = a; i < m; i += 64) cb[i] = C[i + (size_t)m * b];
   __syncthreads();
-  const int npair = r * (r + 1) / 2;
-  for (int p = tid; p < npair; p += OF_THREADS) {
-    // p -> (a, b), a <= b, column-packed upper triangle
-    int b = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
-    while (b > 0 && b * (b + 1) / 2 > p) --b;
-    while ((b + 1) * (b + 2) / 2 <= p) ++b;
-    const int a = p - b * (b + 1) / 2;
-    Dot2Acc32 acc;
-    if (a == b) acc.s.x = -1.f;
-    for (int i = 0; i < m; ++i) acc.add_mul(conjg(X[i + (size_t)m * a]), X[i + (size_t)m * b]);
-    const float2 e = acc.get();
-    E[a + rcap * b] = e;
-    E[b + rcap * a] = conjg(e);
+  if (a >= r) return;
+  Dot2Acc32 acc;
+  if (a == b) acc.s.x = -1.f;
+  const float2* ca = C + (size_t)m * a;
+  for (int i = 0; i < m; ++i) acc.add_mul(conjg(ca[i]), cb[i]);
+  E[a + (size_t)rcap * b] = acc.get();
+}
+
+__global__ void __launch_bounds__(256)
+orth_apply_kernel(float2* __restrict__ C, float2* __restrict__ V, const int* __restrict__ m_ptr,
+                  int m_mul, const int* __restrict__ r_ptr, int mcap, int rcap,
+                  const float2* __restrict__ E) {
+  extern __shared__ __align__(16) unsigned char oa_smem[];
+  float2* sE = reinterpret_cast<float2*>(oa_smem);        // r x r, ld rcap
+  float2* sX = sE + (size_t)rcap * rcap;                   // OF_ROWS x r
+  const int m = min(m_mul * (*m_ptr), mcap), r = min(*r_ptr, rcap);
+  const int nblk = (m + OF_ROWS - 1) / OF_ROWS;
+  const int which = blockIdx.x / nblk, i0 = (blockIdx.x % nblk) * OF_ROWS;
+  float2* Y = (which == 0) ? C : V;
+  if (blockIdx.x >= 2 * nblk || !Y) return;   // block-uniform
+  const int tid = threadIdx.x;
+  for (int e = tid; e < r * r; e += 256) sE[(e % r) + (size_t)rcap * (e / r)] = E[(e % r) + (size_t)rcap * (e / r)];
+  for (int e = tid; e < OF_ROWS * r; e += 256) {
+    const int ii = e % OF_ROWS, c = e / OF_ROWS;
+    sX[ii + OF_ROWS * c] = (i0 + ii < m) ? Y[(i0 + ii) + (size_t)m * c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int which = 0; which < 2; ++which) {
-    float2* Y = (which == 0) ? C : V;
-    if (!Y) continue;   // block-uniform
-    if (which == 1) {   // C is staged already
-      for (int e = tid; e < m * r; e += OF_THREADS) X[e] = Y[e];
-      __syncthreads();
-    }
-    for (int e = tid; e < m * r; e += OF_THREADS) {
-      const int i = e % m, b = e / m;
-      float2 sacc = make_float2(0.f, 0.f);
-      for (int a = 0; a < r; ++a) mac(sacc, X[i + (size_t)m * a], E[a + rcap * b]);
-      Y[e] = make_float2(X[e].x - 0.5f * sacc.x, X[e].y - 0.5f * sacc.y);
-    }
-    __syncthreads();
+  for (int e = tid; e < OF_ROWS * r; e += 256) {
+    const int ii = e % OF_ROWS, b = e / OF_ROWS;
+    if (i0 + ii >= m) continue;
+    float2 sacc = make_float2(0.f, 0.f);
+    for (int a = 0; a < r; ++a) mac(sacc, sX[ii + OF_ROWS * a], sE[a + (size_t)rcap * b]);
+    const float2 x = sX[ii + OF_ROWS * b];
+    Y[(i0 + ii) + (size_t)m * b] = make_float2(x.x - 0.5f * sacc.x, x.y - 0.5f * sacc.y);
   }
 }
 
@@ -1373,13 +1380,14 @@ static void launch_orth_fix(T* C, T* V, const int* m_ptr, int m_mul, const int* 
                             int rcap, cudaStream_t s) {
   if constexpr (std::is_same<T, float2>::value) {
     if (!g_orth_fix) return;
-    static std::atomic<unsigned long long> cfg{0};
-    const size_t sm = sizeof(float2) * ((size_t)rcap * rcap + (size_t)mcap * rcap);
-    if (first_on_device(&cfg))
-      cudaFuncSetAttribute(orth_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float2) * (64 * 64 + 128 * 64)));
+    float2* E = (float2*)scratch_alloc(sizeof(float2) * (size_t)rcap * rcap, s);
+    if (!E) return;   // the correction is an accuracy refinement; without scratch it is skipped
     QTT_PROF("orth_fix", s);
-    orth_fix_kernel<<<1, OF_THREADS, sm, s>>>(C, V, m_ptr, m_mul, r_ptr, mcap, rcap);
+    orth_e_kernel<<<rcap, 64, 0, s>>>(C, m_ptr, m_mul, r_ptr, mcap, rcap, E);
+    const int nblk = (mcap + OF_ROWS - 1) / OF_ROWS;
+    const size_t sm = sizeof(float2) * ((size_t)rcap * rcap + (size_t)OF_ROWS * rcap);
+    orth_apply_kernel<<<2 * nblk, 256, sm, s>>>(C, V, m_ptr, m_mul, r_ptr, mcap, rcap, E);
+    scratch_free(E, s);
   }
 }
 

@@ -224,6 +224,7 @@ struct qtt_tensor {
   int* status = nullptr;          // device, 1 int
   double* norm2 = nullptr;        // device, 1 double (squared norm at creation)
   double* margin = nullptr;       // device, d+1 doubles: eps-rule decision margin per cut (NaN: none)
+  cudaEvent_t used = nullptr;     // recorded on the stream of every call that used the handle
 };
 
 struct qtt_op {
@@ -466,6 +467,9 @@ void prof_add_work(const char* name, double flops, double bytes);
 
 // stream-ordered scratch allocation
 void* scratch_alloc(size_t bytes, cudaStream_t s);
+// record the handle's last-use event on s (no allocation: the event exists
+// from tensor_alloc on)
+void tensor_stamp(const qtt_tensor* t, cudaStream_t s);
 void scratch_free(void* p, cudaStream_t s);
 
 }  // namespace qtt
