@@ -731,6 +731,20 @@ __global__ void __launch_bounds__(HT) heev_tri_kernel(EigArgs<float2> a, HeevSpl
     }
   }
   HEEV_STAMP(7);
+  if (a.orth_flag) {
+    // orthonormality after Newton-Schulz: a spectrum degenerate at FP32
+    // resolution can leave a cluster that neither the Gram-Schmidt nor the
+    // Newton-Schulz steps repair; such a solve is redone by the Jacobi
+    // solver that the host queues behind this kernel, gated by the flag
+    for (int e = tid; e < ncopy * ncopy; e += HT) {
+      const int i = e % ncopy, j = e / ncopy;
+      if (j < i) continue;
+      float g = 0.f;
+      for (int l = 0; l < n; ++l) g = fmaf(Z[l + (size_t)ldz * i], Z[l + (size_t)ldz * j], g);
+      if (i == j) g -= 1.f;
+      if (!(fabsf(g) <= 1e-4f)) atomicExch(a.orth_flag, 1);   // NaN included
+    }
+  }
   float2* Vp = A;                                  // packed reflectors
   float2* Uc = A + npack;                          // column chunk after them
   // columns per chunk: what fits in the rest of the n x n region, at most 64

@@ -455,6 +455,7 @@ __device__ void eig_post(const EigArgs<T>& a, T* A, T* V, int n, int mg, int ldv
 
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
+  if (a.only_if && *a.only_if == 0) return;   // a repair solve that is not needed
   using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_pp[EIG_MAXN / 2], s_pq[EIG_MAXN / 2];
@@ -936,7 +937,9 @@ __global__ void __launch_bounds__(EIG_THREADS)
 template <typename T>
 __global__ void __launch_bounds__(128)
     core_product_kernel(const T* __restrict__ U1, const T* __restrict__ U, const int* mg_ptr,
-                        int mg_mul, int mg_const, const int* r_ptr, T* __restrict__ core) {
+                        int mg_mul, int mg_const, const int* r_ptr, T* __restrict__ core,
+                        const int* only_if = nullptr) {
+  if (only_if && *only_if == 0) return;
   __shared__ T s_u[EIG_MAXN];
   const int mg = mg_ptr ? mg_mul * (*mg_ptr) : mg_const;
   const int r = r_ptr ? *r_ptr : mg;
@@ -982,19 +985,37 @@ static int g_refine_sweeps = 2;
 static int g_gram_parts_per_sm = 2;
 
 template <typename T>
+static void launch_eig_jacobi(const EigArgs<T>& a, int mg_cap, cudaStream_t s);
+
+template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   if (Sc<T>::cplx && g_eig_solver == 0 && !a.relative) {
-    if (g_small_eigh_clk && !a.phase_clk) {
-      EigArgs<T> b = a;
-      b.phase_clk = g_small_eigh_clk;
+    EigArgs<T> b = a;
+    if (g_small_eigh_clk && !a.phase_clk) b.phase_clk = g_small_eigh_clk;
+    // n <= 32: the solve checks its eigenvectors' orthonormality and a
+    // Jacobi solve of the same Gram follows, gated by that check
+    int* flag = (mg_cap <= 32) ? (int*)scratch_alloc(sizeof(int), s) : nullptr;
+    if (flag) {
+      cudaMemsetAsync(flag, 0, sizeof(int), s);
+      b.orth_flag = flag;
+    }
+    {
       QTT_PROF(mg_cap <= 32 ? "heev_le32" : mg_cap <= 64 ? "heev_le64" : "heev_le128", s);
       launch_heev_tri(reinterpret_cast<const EigArgs<float2>&>(b), mg_cap, s);
-      return;
     }
-    QTT_PROF(mg_cap <= 32 ? "heev_le32" : mg_cap <= 64 ? "heev_le64" : "heev_le128", s);
-    launch_heev_tri(reinterpret_cast<const EigArgs<float2>&>(a), mg_cap, s);
+    if (flag) {
+      EigArgs<T> c = a;
+      c.only_if = flag;
+      launch_eig_jacobi<T>(c, mg_cap, s);
+      scratch_free(flag, s);
+    }
     return;
   }
+  launch_eig_jacobi<T>(a, mg_cap, s);
+}
+
+template <typename T>
+static void launch_eig_jacobi(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
   const size_t sm = eig_smem_bytes<T>(mg_cap);
   static std::atomic<unsigned long long> configured{0};
   if (first_on_device(&configured))
@@ -1054,7 +1075,7 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
     QTT_PROF("core_product", s);
     core_product_kernel<T><<<mg_cap, 128, 0, s>>>(a.U1, a.Uout, a.mg_ptr, a.mg_mul, a.mg_const,
                                                   a.mode == EIG_MODE_ALL ? nullptr : a.rank_out,
-                                                  a.core_out);
+                                                  a.core_out, a.only_if);
   }
 }
 

@@ -312,6 +312,9 @@ struct EigArgs {
   float ortol_rel;      // tridiagonal solver: cluster gap / ||T|| for Gram-Schmidt
   int ns_steps;         // tridiagonal solver: Newton-Schulz steps
   double* margin_out;   // optional (MODE_DECIDE): margin of the eps-rule decision
+  int* orth_flag;       // optional (tridiagonal solver, n <= 32): set to 1 when its
+                        // eigenvectors leave max |Z^T Z - I| above 1e-4
+  const int* only_if;   // optional (Jacobi solver): run only when *only_if != 0
 };
 
 // Margin of an eps-rule rank decision: min over the two tails around the
