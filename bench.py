@@ -92,15 +92,17 @@ def max_over_ranks(values, device):
 
 def _peaks(dev=None):
     """Measured peaks (MEASURED_PEAKS.json, else the fallback figures), plus
-    the SM count read from the device when one is given."""
+    the SM count read from the given device (the current one by default)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             pk, kind = json.load(fh), "measured"
     except Exception:
         pk, kind = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                     "sm_max_mhz": 2070.0}, "fallback"
+    import torch
+    if dev is None and torch.cuda.is_available():
+        dev = torch.cuda.current_device()
     if dev is not None:
-        import torch
         pk["sm_count"] = torch.cuda.get_device_properties(dev).multi_processor_count
     return pk, kind
 
