@@ -350,7 +350,10 @@ qtt_status qtt_from_cores(const void* host_cores, const int* ranks, int d, qtt_d
  * after the last call's work, on whatever stream it ran; work that a caller
  * enqueued on other streams after that call is the caller's to order, as for
  * any stream-ordered free).  qtt_free_async releases it in the order of the
- * given stream (the stream the handle was last used on). */
+ * given stream (the stream the handle was last used on).  Calls made while
+ * their stream is being captured into a CUDA graph record no last-use
+ * event: a handle created or used inside a capture is released with
+ * qtt_free_async on the capturing stream. */
 void qtt_free(qtt_tensor* t);
 void qtt_free_async(qtt_tensor* t, void* stream);
 
@@ -514,6 +517,17 @@ qtt_status qtt_debug_tc_cgemm(const void* A, const void* B, void* C, int M, int 
  * sums, the projection basis of the next unfolding corrected alike); 0
  * keeps the cores as the FP32 eigen-solves give them. */
 void qtt_debug_set_orth_fix(int on);
+
+/* Diagnostics: allocates `bytes` from the library's stream-ordered memory
+ * pool, fills them with the byte `value` and returns them to the pool, so
+ * that the next scratch allocations start from known contents (a check that
+ * no kernel reads scratch it did not write).  Synchronises the stream. */
+qtt_status qtt_debug_fill_pool(size_t bytes, int value, void* stream);
+
+/* Diagnostics: accumulator of the complex64 TT-SVD's projections W = U^H M
+ * (the m-term sums): 0 (default) Dot2 (exact products, compensated sums),
+ * 1 Kahan-compensated sums of rounded products, 2 plain FMA. */
+void qtt_debug_set_proj_acc(int which);
 
 /* Diagnostics of QTT_PREC_TF32_REFINED: split = 3 (default) feeds the first
  * pass's tensor-core Gram a TF32 head and remainder of every operand

@@ -140,7 +140,16 @@ qtt_status tensor_alloc(const TensorDesc& desc, const std::vector<int>& rcap, cu
 }
 
 void tensor_stamp(const qtt_tensor* t, cudaStream_t s) {
-  if (t && t->used) cudaEventRecord(t->used, s);
+  if (!t || !t->used) return;
+  // no stamp while s is being captured into a CUDA graph: the event would
+  // become a node of the graph and must not be destroyed with the handle;
+  // inside a graph the release is ordered by the graph itself
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cs == cudaStreamCaptureStatusNone) cudaEventRecord(t->used, s);
 }
 
 void tensor_free_async(qtt_tensor* t, cudaStream_t s) {
@@ -687,6 +696,18 @@ qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sk
   qtt_status st = cached_identity(x->desc.d, x->desc.dt, s, &id);
   if (st != QTT_OK) return st;
   return fft_transform(x, inverse, t0, id, sketch, seed, s, out);
+}
+
+// diagnostics: hand the memory pool a block filled with one byte value, so
+// that the library's next scratch allocations start from known contents
+qtt_status qtt_debug_fill_pool(size_t bytes, int value, void* stream) {
+  g_err[0] = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* p = scratch_alloc(bytes, s);
+  if (!p) { set_error("qtt_debug_fill_pool: allocation of %zu bytes failed", bytes); return QTT_ENOMEM; }
+  cudaMemsetAsync(p, value & 0xff, bytes, s);
+  scratch_free(p, s);
+  return cuda_check(cudaStreamSynchronize(s), "qtt_debug_fill_pool");
 }
 
 void qtt_release_workspace(void) {

@@ -18,7 +18,7 @@
 
 namespace qtt {
 
-__global__ void sinc_sum_kernel(long long n, double B, double* sum) {
+__global__ void sinc_sum_kernel(long long n, double B, double* __restrict__ part) {
   __shared__ double red[32];
   double acc = 0.0;
   const long long tot = 2 * n - 1;
@@ -37,8 +37,29 @@ __global__ void sinc_sum_kernel(long long n, double B, double* sum) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    atomicAdd(sum, t);
+    part[blockIdx.x] = t;
   }
+}
+
+// *sum = the block partials added in a fixed order (lane l takes every 32nd
+// partial from l, then a fixed shuffle tree): the same sum on every run,
+// where an atomic accumulation would depend on the blocks' finishing order
+__global__ void sinc_sum_finish(const double* __restrict__ part, int nparts, double* sum) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) t += part[i];
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if (threadIdx.x == 0) *sum = t;
+}
+
+// sum over m = -(n-1)..n-1 of sinc(pi B m / n) into *sum (device)
+static qtt_status sinc_sum(long long n, double B, double* sum, cudaStream_t s) {
+  const int blocks = (int)std::min<long long>((2 * n + 255) / 256, 4096);
+  double* part = (double*)scratch_alloc(sizeof(double) * blocks, s);
+  if (!part) return QTT_ENOMEM;
+  sinc_sum_kernel<<<blocks, 256, 0, s>>>(n, B, part);
+  sinc_sum_finish<<<1, 32, 0, s>>>(part, blocks, sum);
+  scratch_free(part, s);
+  return QTT_OK;
 }
 
 __global__ void chat_kernel(long long n, double B, int normalize, const double* sum,
@@ -87,9 +108,11 @@ qtt_status sinc_padded(int log2_n, long long N, double B, int normalize, qtt_dty
   const long long n = 1LL << log2_n;
   double* sum = (double*)scratch_alloc(sizeof(double), s);
   if (!sum) { set_error("qtt_sinc_padded: alloc"); return QTT_ENOMEM; }
-  cudaMemsetAsync(sum, 0, sizeof(double), s);
-  const int blocks = (int)std::min<long long>((2 * n + 255) / 256, 4096);
-  sinc_sum_kernel<<<blocks, 256, 0, s>>>(n, B, sum);
+  if (sinc_sum(n, B, sum, s) != QTT_OK) {
+    scratch_free(sum, s);
+    set_error("qtt_sinc_padded: alloc");
+    return QTT_ENOMEM;
+  }
   const int gb = (int)((n + 255) / 256);
   if (dt == QTT_F64) sinc_padded_kernel<double><<<gb, 256, 0, s>>>(n, N, B, normalize, sum, (double*)g);
   else sinc_padded_kernel<float2><<<gb, 256, 0, s>>>(n, N, B, normalize, sum, (float2*)g);
@@ -146,9 +169,12 @@ qtt_status op_sinc_create(int d, double B, int normalize, double eps_op, qtt_dty
     set_error("op_sinc_create: alloc");
     return QTT_ENOMEM;
   }
-  cudaMemsetAsync(sum, 0, sizeof(double), s);
-  int blocks = (int)std::min<long long>((2 * n + 255) / 256, 4096);
-  sinc_sum_kernel<<<blocks, 256, 0, s>>>(n, B, sum);
+  if (sinc_sum(n, B, sum, s) != QTT_OK) {
+    scratch_free(sum, s);
+    scratch_free(chat, s);
+    set_error("op_sinc_create: alloc");
+    return QTT_ENOMEM;
+  }
   chat_kernel<<<(int)((2 * n + 255) / 256), 256, 0, s>>>(n, B, normalize, sum, chat);
   // TT-SVD of chat (d+1 modes), FP64 with refinement
   TensorDesc gd;

@@ -48,7 +48,14 @@ struct PlainAcc {
   __device__ __forceinline__ T get() const { return s; }
 };
 
-template <typename T, int TM>
+// projection accumulator: 0 Dot2 (exact products, compensated sums), 1 Kahan
+// (compensated sums of rounded products), 2 plain FMA
+template <typename T, int PA>
+using ProjAcc = typename std::conditional<
+    PA == 0, typename Dot2Of<T>::type,
+    typename std::conditional<PA == 1, typename KAccOf<T>::type, PlainAcc<T>>::type>::type;
+
+template <typename T, int TM, int PA = 0>
 __global__ void __launch_bounds__(PG_THREADS)
 proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_mul, long long n,
                  const T* __restrict__ U, const int* __restrict__ r_ptr, T* __restrict__ W,
@@ -107,7 +114,7 @@ proj_gram_kernel(const T* __restrict__ M, const int* __restrict__ m_ptr, int m_m
         // directions cancel the large components of M, so the m-term sums
         // are Dot2 sums (exact products, compensated additions) and a small
         // row of W keeps accuracy relative to its own size
-        typename Dot2Of<T>::type o[4][4];
+        ProjAcc<T, PA> o[4][4];
         for (int i = 0; i < m; ++i) {
           T u[4], v[4];
 #pragma unroll
@@ -1095,19 +1102,38 @@ static size_t pg_smem_bytes(bool has_u, int mcap, int rcap, int cc) {
   return e * sizeof(T);
 }
 
-template <typename T, int TM>
-static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
+static int g_proj_acc = 0;   // diagnostics: the complex64 projection's accumulator (ProjAcc)
+
+template <typename T, int TM, int PA>
+static void launch_pg_pa(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
                          int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
                          T* gp, int ldp, int mcap, int rcap, int cc) {
   static std::atomic<unsigned long long> configured{0};
   if (first_on_device(&configured))
-    cudaFuncSetAttribute(proj_gram_kernel<T, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(proj_gram_kernel<T, TM, PA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pg_smem_bytes<T>(true, 128, 128, PG_CC));
+  proj_gram_kernel<T, TM, PA><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold,
+                                                           gp, ldp, mcap, rcap, cc);
+}
+
+template <typename T, int TM>
+static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const int* m_ptr,
+                         int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
+                         T* gp, int ldp, int mcap, int rcap, int cc) {
   QTT_PROF("proj_gram", s);
   // the pass streams the m x n unfolding once (m at its capacity)
   prof_add_work("proj_gram", 0.0, (double)mcap * (double)n * sizeof(T));
-  proj_gram_kernel<T, TM><<<grid, PG_THREADS, sm, s>>>(M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp,
-                                                       ldp, mcap, rcap, cc);
+  if constexpr (std::is_same<T, float2>::value) {
+    if (U && g_proj_acc == 1) {
+      launch_pg_pa<T, TM, 1>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
+      return;
+    }
+    if (U && g_proj_acc == 2) {
+      launch_pg_pa<T, TM, 2>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
+      return;
+    }
+  }
+  launch_pg_pa<T, TM, 0>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
 }
 
 // Launch the fused projection/Gram kernel.  Returns the number of partials.
@@ -1636,6 +1662,7 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 // 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
 extern "C" void qtt_debug_set_orth_fix(int on) { qtt::g_orth_fix = (on != 0); }
+extern "C" void qtt_debug_set_proj_acc(int which) { qtt::g_proj_acc = (which == 1 || which == 2) ? which : 0; }
 extern "C" void qtt_debug_set_tc_gram(int split, int pass2) {
   qtt::g_tc_gram_split = (split == 1) ? 1 : 3;
   qtt::g_tc_pass2 = (pass2 != 0);
