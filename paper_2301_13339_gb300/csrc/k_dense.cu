@@ -250,15 +250,18 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
 // update); adj = 0: op(T) = T (forms Q).  W = V^H X by warps (4 reflectors x
 // BQ_CB columns each, lanes over rows), then op(T) W, then one warp per
 // column for the update.
+// The columns cbase + [0, BQ_CB) of X that lie in [clo, chi) <- (I - V op(T)
+// V^H) X[p:m, c] (V^T = Vt: kb rows of mp = m - p, ld mp).  adj = 1: op(T)
+// = T^H (applies Q^H, the trailing update); adj = 0: op(T) = T (forms Q).
+// W = V^H X by warps (AW reflectors x BQ_CB columns each, lanes over rows),
+// then op(T) W, then one warp per column for the update.  A column's
+// arithmetic does not depend on which other columns share the CTA.
 template <typename T>
-__global__ void __launch_bounds__(32 * BQ_CB)
-k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ Vt, int p, int kb,
-           const T* __restrict__ Tm, int adj) {
-  __shared__ T W[BQ_NB][BQ_CB];
-  __shared__ T W2[BQ_NB][BQ_CB];
+__device__ __forceinline__ void bq_apply_cols(T* __restrict__ X, int m, int cbase, int clo, int chi,
+                                              const T* __restrict__ Vt, int p, int kb,
+                                              const T* __restrict__ Tm, int adj,
+                                              T (&W)[BQ_NB][BQ_CB], T (&W2)[BQ_NB][BQ_CB]) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int cbase = col0 + BQ_CB * blockIdx.x;
-  const int cend = col0 + ncols;
   const int mp = m - p;
   constexpr int AW = BQ_NB / BQ_CB;   // reflectors per warp (BQ_CB warps x AW = BQ_NB)
   T acc[AW][BQ_CB];
@@ -269,8 +272,10 @@ k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ 
   for (int i = lane; i < mp; i += 32) {
     T x[BQ_CB];
 #pragma unroll
-    for (int c = 0; c < BQ_CB; ++c)
-      x[c] = (cbase + c < cend) ? X[(size_t)(p + i) + (size_t)m * (cbase + c)] : szero<T>();
+    for (int c = 0; c < BQ_CB; ++c) {
+      const int col = cbase + c;
+      x[c] = (col >= clo && col < chi) ? X[(size_t)(p + i) + (size_t)m * col] : szero<T>();
+    }
 #pragma unroll
     for (int u = 0; u < AW; ++u) {
       const int a = warp * AW + u;
@@ -301,12 +306,47 @@ k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ 
   }
   __syncthreads();
   const int col = cbase + warp;
-  if (col >= cend) return;
-  T* xc = X + (size_t)m * col;
-  for (int i = lane; i < mp; i += 32) {
-    T sacc = szero<T>();
-    for (int a = 0; a < kb; ++a) mac(sacc, Vt[i + (size_t)mp * a], W2[a][warp]);
-    xc[p + i] = ssub(xc[p + i], sacc);
+  if (col >= clo && col < chi) {
+    T* xc = X + (size_t)m * col;
+    for (int i = lane; i < mp; i += 32) {
+      T sacc = szero<T>();
+      for (int a = 0; a < kb; ++a) mac(sacc, Vt[i + (size_t)mp * a], W2[a][warp]);
+      xc[p + i] = ssub(xc[p + i], sacc);
+    }
+  }
+}
+
+// X[p:m, c] <- (I - V op(T) V^H) X[p:m, c] for the columns c of this CTA
+// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols)
+template <typename T>
+__global__ void __launch_bounds__(32 * BQ_CB)
+k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ Vt, int p, int kb,
+           const T* __restrict__ Tm, int adj) {
+  __shared__ T W[BQ_NB][BQ_CB];
+  __shared__ T W2[BQ_NB][BQ_CB];
+  bq_apply_cols(X, m, col0 + BQ_CB * (int)blockIdx.x, col0, col0 + ncols, Vt, p, kb, Tm, adj, W, W2);
+}
+
+// Q formation in one launch: the CTA's columns cbase + [0, BQ_CB) of Q pass
+// through the panels' block reflectors from the last panel to the first
+// (panel pi touches the columns in [p, nq)), the same arithmetic per column
+// as one k_bq_apply launch per panel, without a grid-wide step between
+// panels (the columns are independent).
+template <typename T>
+__global__ void __launch_bounds__(32 * BQ_CB)
+k_bq_formq(T* __restrict__ Q, int m, int nq, int kmax, const T* __restrict__ Vall,
+           const T* __restrict__ Tm) {
+  __shared__ T W[BQ_NB][BQ_CB];
+  __shared__ T W2[BQ_NB][BQ_CB];
+  const int cbase = BQ_CB * (int)blockIdx.x;
+  const int np = (kmax + BQ_NB - 1) / BQ_NB;
+  for (int pi = np - 1; pi >= 0; --pi) {
+    const int p = pi * BQ_NB;
+    if (p >= nq || cbase + BQ_CB <= p) continue;   // block-uniform: no column of this CTA
+    const int kb = min(BQ_NB, kmax - p);
+    bq_apply_cols(Q, m, cbase, p, nq, Vall + (size_t)pi * BQ_NB * BQ_MAXM, p, kb,
+                  Tm + (size_t)pi * BQ_NB * BQ_NB, 0, W, W2);
+    __syncthreads();   // the updated columns are read by every warp for the next panel
   }
 }
 
@@ -343,6 +383,32 @@ static void bq_configure() {
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
 }
 
+// per host thread and device: the side stream of the QR look-ahead and the
+// two events that fork it from and join it to the caller's stream
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream* side_stream() {
+  thread_local SideStream tab[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  SideStream& e = tab[dev];
+  if (!e.s) {
+    if (cudaStreamCreateWithFlags(&e.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      e = SideStream();
+      return nullptr;
+    }
+  }
+  return &e;
+}
+
 template <typename T>
 qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
   if (m < 1 || n < 1 || nq < 1 || m > BQ_MAXM || nq > m) {
@@ -354,6 +420,18 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
   const int kmax = std::min(m, n);
   const int np = (kmax + BQ_NB - 1) / BQ_NB;
   T* Vall = Tm + (size_t)((n + BQ_NB - 1) / BQ_NB) * BQ_NB * BQ_NB;   // V^T of panel pi at pi NB MAXM
+  // look-ahead: after panel p, its reflectors update the next panel's
+  // columns on s, the next panel is factored on s, and the rest of the
+  // trailing columns are updated concurrently on a side stream.  Every
+  // column receives the same updates in the same order as without the
+  // split.  The side stream forks from s and joins it by events, so the
+  // sequence is also valid inside a stream capture.
+  SideStream* ss = side_stream();
+  const bool ahead = ss && np > 2;
+  if (ahead) {
+    cudaEventRecord(ss->fork, s);
+    cudaStreamWaitEvent(ss->s, ss->fork, 0);
+  }
   for (int p = 0; p < kmax; p += BQ_NB) {
     const int kb = std::min(BQ_NB, kmax - p);
     T* Tp = Tm + (size_t)(p / BQ_NB) * BQ_NB * BQ_NB;
@@ -369,26 +447,48 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
       k_bq_panel<T><<<1, BQP_THREADS, sizeof(T) * (size_t)((m - p) | 1) * kb, s>>>(A, m, p, kb, Tp, Vp);
     }
     const int c0 = p + kb, nc = kmax - c0;
-    if (nc > 0) {
+    if (nc > 0 && ahead) {
+      // the next panel's columns (they also need the side stream's update
+      // from the panel before: wait for it), then the rest on the side
+      const int nn = std::min(BQ_NB, nc);
+      if (p > 0) cudaStreamWaitEvent(s, ss->join, 0);
+      {
+        QTT_PROF("bigqr_update", s);
+        prof_add_work("bigqr_update", cplx * 16.0 * M * kb * nn, 2.0 * M * nn * sizeof(T));
+        k_bq_apply<T><<<(nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nn, Vp, p, kb, Tp, 1);
+      }
+      if (nc > nn) {
+        cudaEventRecord(ss->fork, s);                 // panel p (and the update above) done
+        cudaStreamWaitEvent(ss->s, ss->fork, 0);
+        prof_add_work("bigqr_update", cplx * 16.0 * M * kb * (nc - nn), 2.0 * M * (nc - nn) * sizeof(T));
+        k_bq_apply<T><<<(nc - nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, ss->s>>>(A, m, c0 + nn, nc - nn,
+                                                                           Vp, p, kb, Tp, 1);
+        cudaEventRecord(ss->join, ss->s);
+      }
+    } else if (nc > 0) {
       QTT_PROF("bigqr_update", s);
       prof_add_work("bigqr_update", cplx * 16.0 * M * kb * nc, 2.0 * M * nc * sizeof(T));
       k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nc, Vp, p, kb, Tp, 1);
     }
   }
+  if (ahead) {
+    cudaEventRecord(ss->join, ss->s);   // the side stream's last work joins s
+    cudaStreamWaitEvent(s, ss->join, 0);
+  }
   {
     QTT_PROF("bigqr_formq", s);
     k_bq_eye<T><<<(unsigned)(((long long)m * nq + 255) / 256), 256, 0, s>>>(Q, m, nq);
   }
-  for (int pi = np - 1; pi >= 0; --pi) {
-    const int p = pi * BQ_NB;
-    const int kb = std::min(BQ_NB, kmax - p);
-    if (p >= nq) continue;
+  {
     QTT_PROF("bigqr_formq", s);
-    prof_add_work("bigqr_formq", (Sc<T>::cplx ? 1.0 : 0.25) * 16.0 * (m - p) * kb * (double)(nq - p),
-                  2.0 * (m - p) * (double)(nq - p) * sizeof(T));
-    k_bq_apply<T><<<(nq - p + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(
-        Q, m, p, nq - p, Vall + (size_t)pi * BQ_NB * BQ_MAXM, p, kb,
-        Tm + (size_t)pi * BQ_NB * BQ_NB, 0);
+    for (int pi = np - 1; pi >= 0; --pi) {
+      const int p = pi * BQ_NB;
+      const int kb = std::min(BQ_NB, kmax - p);
+      if (p >= nq) continue;
+      prof_add_work("bigqr_formq", (Sc<T>::cplx ? 1.0 : 0.25) * 16.0 * (m - p) * kb * (double)(nq - p),
+                    2.0 * (m - p) * (double)(nq - p) * sizeof(T));
+    }
+    k_bq_formq<T><<<(nq + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(Q, m, nq, kmax, Vall, Tm);
   }
   return cuda_check(cudaGetLastError(), "big_qr launch");
 }

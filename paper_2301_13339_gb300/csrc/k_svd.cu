@@ -1121,8 +1121,19 @@ static void launch_pg_tm(int grid, size_t sm, cudaStream_t s, const T* M, const 
                          int m_mul, long long n, const T* U, const int* r_ptr, T* W, int fold,
                          T* gp, int ldp, int mcap, int rcap, int cc) {
   QTT_PROF("proj_gram", s);
-  // the pass streams the m x n unfolding once (m at its capacity)
-  prof_add_work("proj_gram", 0.0, (double)mcap * (double)n * sizeof(T));
+  // algorithmic work at the capacities: the m x n unfolding streamed once;
+  // the projection W = U^H M (r m n multiply-adds) and the Gram of W or of
+  // its fold (mg^2 n_g, the whole square: the kernel forms every entry);
+  // complex multiply-add = 8 flop
+  {
+    const double cm = Sc<T>::cplx ? 8.0 : 2.0;
+    const double rr = U ? (double)rcap : 0.0;
+    const double mg = (fold == 1) ? 2.0 * (U ? rcap : mcap) : (U ? rcap : mcap);
+    const double ng = (fold == 1) ? (double)n / 2 : (double)n;
+    const double gram = (fold >= 0) ? mg * mg * ng : 0.0;
+    prof_add_work("proj_gram", cm * (rr * mcap * (double)n + gram),
+                  (double)mcap * (double)n * sizeof(T));
+  }
   if constexpr (std::is_same<T, float2>::value) {
     if (U && g_proj_acc == 1) {
       launch_pg_pa<T, TM, 1>(grid, sm, s, M, m_ptr, m_mul, n, U, r_ptr, W, fold, gp, ldp, mcap, rcap, cc);
