@@ -539,9 +539,28 @@ def batch_main(args, wl, metric):
     plain_ms = e0.elapsed_time(e1)
     plain_out = [y.clone() for y in ys]
 
-    # autotuned concurrency, captured as one graph
+    # untuned: the library's default stream count and tiles, captured as one graph
+    unt = q.QTTBatch([int(x.shape[0]).bit_length() - 1 for x in xs], Bs, rms, stream=stream, **kw)
+    unt.capture(xs, ys, stream)
+    with torch.cuda.stream(stream):
+        unt.launch(stream)
+        torch.cuda.synchronize(dev)
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(2.0)
+        u0.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            unt.launch(stream)
+        u1.record(stream)
+    torch.cuda.synchronize(dev)
+    untuned_ms = u0.elapsed_time(u1) / max(1, args.steps // 2)
+    untuned_cfg = {"nstreams": unt.info()["nstreams"], "gram_parts_per_sm": 0, "chunk_div": 0}
+    unt.free()
+
+    # autotuned concurrency and Gram tiles, captured as one graph
     best, tune = q.autotune_batch(xs, ys, Bs, rms, candidates=(8, 16, 32, 64), reps=1,
-                                  stream=stream, **kw)
+                                  stream=stream,
+                                  tiles=((0, 0), (1, 0), (4, 0), (8, 0), (0, 2), (1, 2), (2, 2),
+                                         (0, 4)), **kw)
     info = best.info()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -617,9 +636,15 @@ def batch_main(args, wl, metric):
                     "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
             "gpu_launches": int(info["graph_nodes"]) * args.steps,
             "graph": {"nodes": info["graph_nodes"], "nstreams": info["nstreams"],
-                      "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()}},
+                      "gram_parts_per_sm": best.tiles[0], "chunk_div": best.tiles[1],
+                      "autotune_ms": {"streams=%d parts=%d div=%d" % k: round(v, 3)
+                                      for k, v in tune.items()}},
+            "untuned": {"config": untuned_cfg, "ms": untuned_ms,
+                        "value": world * N / (untuned_ms * 1e-3) / 1e6, "unit": "Msamples/s"},
             "plain_single_stream": {"ms": plain_ms, "value": N / (plain_ms * 1e-3) / 1e6,
-                                    "unit": "Msamples/s", "bit_identical_to_graph": bool(same)},
+                                    "unit": "Msamples/s",
+                                    # equal bits are expected with the default tiles only
+                                    "bit_identical_to_graph": bool(same)},
             "kernels_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in kern.items()},
             "roofline": roofline(kern, {"d": 18, "rmax": 64}, peaks, peak_kind),
             "clocks": clk}

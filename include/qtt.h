@@ -312,6 +312,14 @@ qtt_status qtt_batch_create(int nlines, const int* log2_len, const double* B, co
 qtt_status qtt_batch_run(qtt_batch* b, const void* const* x, void* const* y, void* stream);
 qtt_status qtt_batch_capture(qtt_batch* b, const void* const* x, void* const* y, void* stream);
 qtt_status qtt_batch_launch(qtt_batch* b, void* stream);
+/* Tile settings of the lines' TT-SVD Gram passes (the autotuner's knobs):
+ * gram_parts_per_sm partial-Gram CTAs per SM (the passes' grid; 0: the
+ * library default of 2) and chunk_div, a divisor of the column-chunk width
+ * each CTA stages (its tile; 0 or 1: the default, 2 or 4: narrower).  They
+ * change the order of the FP32 sums, not the method.  They take effect at
+ * the next run or capture; a captured graph is dropped.  Out-of-range
+ * values: QTT_EINVAL. */
+qtt_status qtt_batch_set_tiles(qtt_batch* b, int gram_parts_per_sm, int chunk_div);
 qtt_status qtt_batch_info(const qtt_batch* b, int* nstreams, int* graph_nodes);
 void qtt_batch_free(qtt_batch* b);
 qtt_status qtt_batch_conv_sinc(int nlines, const void* const* x, const int* log2_len,

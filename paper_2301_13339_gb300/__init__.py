@@ -47,7 +47,7 @@ EXPORTED_SYMBOLS = [
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
-    "qtt_sinc_padded",
+    "qtt_sinc_padded", "qtt_batch_set_tiles",
 ]
 
 
@@ -674,6 +674,7 @@ class QTTBatch:
                                      _stream(stream), ctypes.byref(out)))
         self._h = out
         self._bufs = None
+        self.tiles = (0, 0)
 
     def run(self, xs, ys, stream=None):
         _, lg, xp, yp = _line_arrays(xs, ys)
@@ -691,6 +692,15 @@ class QTTBatch:
 
     def launch(self, stream=None):
         _check(_lib.qtt_batch_launch(self._h, _stream(stream)))
+
+    def set_tiles(self, gram_parts_per_sm=0, chunk_div=0):
+        """Tile settings of the lines' Gram passes (0: defaults); drops a
+        captured graph."""
+        f = _lib.qtt_batch_set_tiles
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        _check(f(self._h, int(gram_parts_per_sm), int(chunk_div)))
+        self.tiles = (int(gram_parts_per_sm), int(chunk_div))
 
     def info(self):
         ns, nn = ctypes.c_int(), ctypes.c_int()
@@ -728,18 +738,24 @@ def qtt_batch_conv_sinc(xs, B, rmax, ys=None, eps=0.0, refine=True, normalize=Tr
     return ys
 
 
-def autotune_batch(xs, ys, B, rmax, candidates=(8, 16, 32, 64), reps=2, stream=None, **kw):
-    """Pick the internal stream count of a captured batch by timing graph
-    launches (CUDA events on ``stream``); returns (best QTTBatch, {S: ms})."""
+def autotune_batch(xs, ys, B, rmax, candidates=(8, 16, 32, 64), reps=2, stream=None,
+                   tiles=((0, 0),), **kw):
+    """Pick the internal stream count and the Gram passes' tile settings
+    (``tiles``: (gram_parts_per_sm, chunk_div) pairs, (0, 0) = the defaults)
+    of a captured batch by timing graph launches (CUDA events on ``stream``).
+    Streams are searched first with the default tiles, then the tiles with
+    the best stream count.  Returns (best QTTBatch, {(S, parts, div): ms})."""
     import torch
     if stream is None:
         stream = torch.cuda.Stream()
     lg = [int(x.shape[0]).bit_length() - 1 for x in xs]
-    best, best_ms, times = None, None, {}
-    for S in candidates:
-        if S > len(xs) and times:
-            continue
+    state = {"best": None, "ms": None}
+    times = {}
+
+    def trial(S, t):
         b = QTTBatch(lg, B, rmax, nstreams=S, stream=stream, **kw)
+        if t != (0, 0):
+            b.set_tiles(*t)
         b.capture(xs, ys, stream)
         b.launch(stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -749,14 +765,23 @@ def autotune_batch(xs, ys, B, rmax, candidates=(8, 16, 32, 64), reps=2, stream=N
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        times[b.info()["nstreams"]] = ms
-        if best is None or ms < best_ms:
-            if best is not None:
-                best.free()
-            best, best_ms = b, ms
+        times[(b.info()["nstreams"],) + tuple(t)] = ms
+        if state["best"] is None or ms < state["ms"]:
+            if state["best"] is not None:
+                state["best"].free()
+            state["best"], state["ms"] = b, ms
         else:
             b.free()
-    return best, times
+
+    for S in candidates:
+        if S > len(xs) and times:
+            continue
+        trial(S, (0, 0))
+    S_best = state["best"].info()["nstreams"]
+    for t in tiles:
+        if tuple(t) != (0, 0):
+            trial(S_best, tuple(t))
+    return state["best"], times
 
 
 def qtt_small_eigh(G, dtype_code=QTT_C64, stream=None):

@@ -27,6 +27,8 @@ struct qtt_batch {
   qtt_trunc round_tr{};
   qtt_dtype dt = QTT_C64;
   int nstreams = 0;
+  int gram_parts = 0;   // tile settings of the lines' Gram passes (0: defaults)
+  int chunk_div = 0;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
@@ -54,7 +56,18 @@ static qtt_status run_line(qtt_batch* b, int i, const void* x, void* y, cudaStre
   return st;
 }
 
+static qtt_status run_all_body(qtt_batch* b, const void* const* x, void* const* y, cudaStream_t s);
+
+// the batch's tile settings hold while its lines are submitted (a captured
+// graph keeps the launch shapes it was captured with)
 static qtt_status run_all(qtt_batch* b, const void* const* x, void* const* y, cudaStream_t s) {
+  set_gram_tiles(b->gram_parts, b->chunk_div);
+  const qtt_status st = run_all_body(b, x, y, s);
+  set_gram_tiles(0, 0);
+  return st;
+}
+
+static qtt_status run_all_body(qtt_batch* b, const void* const* x, void* const* y, cudaStream_t s) {
   qtt_status st = cuda_check(cudaEventRecord(b->fork, s), "batch fork");
   if (st != QTT_OK) return st;
   for (int j = 0; j < b->nstreams; ++j) {
@@ -198,6 +211,21 @@ qtt_status qtt_batch_capture(qtt_batch* b, const void* const* x, void* const* y,
   b->graph = g;
   st = cuda_check(cudaGraphInstantiate(&b->exec, g, 0), "batch instantiate");
   return st;
+}
+
+qtt_status qtt_batch_set_tiles(qtt_batch* b, int gram_parts_per_sm, int chunk_div) {
+  if (!b) { set_error("qtt_batch_set_tiles: NULL batch"); return QTT_EINVAL; }
+  if (gram_parts_per_sm < 0 || gram_parts_per_sm > 16 ||
+      !(chunk_div == 0 || chunk_div == 1 || chunk_div == 2 || chunk_div == 4)) {
+    set_error("qtt_batch_set_tiles: gram_parts_per_sm in [0, 16], chunk_div in {0, 1, 2, 4}");
+    return QTT_EINVAL;
+  }
+  b->gram_parts = gram_parts_per_sm;
+  b->chunk_div = chunk_div > 1 ? chunk_div : 0;
+  // a captured graph holds the old shapes: it is dropped (capture again)
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  return QTT_OK;
 }
 
 qtt_status qtt_batch_launch(qtt_batch* b, void* stream) {

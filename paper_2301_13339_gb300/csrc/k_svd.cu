@@ -1089,9 +1089,20 @@ static void launch_eig_jacobi(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
 // columns per chunk: about 4096 elements of the m x n unfolding (at least
 // PG_CC, even), so that the narrow unfoldings of the first levels stream in
 // wide chunks
+// per-thread tile settings of the Gram passes, set by a batch while it
+// submits or captures its lines (0: the defaults): partial-Gram CTAs per SM
+// (the passes' grid) and a divisor of the column-chunk width (their tile)
+static thread_local int t_gram_parts_per_sm = 0;
+static thread_local int t_chunk_div = 0;
+void set_gram_tiles(int parts_per_sm, int chunk_div) {
+  t_gram_parts_per_sm = (parts_per_sm >= 1 && parts_per_sm <= 16) ? parts_per_sm : 0;
+  t_chunk_div = (chunk_div == 2 || chunk_div == 4) ? chunk_div : 0;
+}
+
 static int pg_chunk_cols(int mcap) {
   int cc = 4096 / std::max(mcap, 1);
   cc = std::max(PG_CC, std::min(cc, 2048));
+  if (t_chunk_div > 1) cc = std::max(PG_CC, cc / t_chunk_div);
   return cc & ~1;
 }
 
@@ -1466,7 +1477,8 @@ qtt_status tt_svd(const T* v, int d, const qtt_trunc& tr, qtt_tensor* t, cudaStr
   auto cap_at = [&](int k) { return fixed ? std::min(fixed[k], QTT_RANK_CAP) : rmax_eff; };
   const double eps_u = fixed ? 0.0 : tr.eps;
   const double delta_u = fixed ? 0.0 : tr.delta;
-  const int max_parts = g_gram_parts_per_sm * device_sm_count();
+  const int max_parts =
+      (t_gram_parts_per_sm > 0 ? t_gram_parts_per_sm : g_gram_parts_per_sm) * device_sm_count();
   const int LDP = 128;
   T* bufA = (T*)scratch_alloc(sizeof(T) * N, s);
   T* bufB = (T*)scratch_alloc(sizeof(T) * N, s);

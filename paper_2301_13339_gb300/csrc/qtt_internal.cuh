@@ -393,6 +393,8 @@ template <typename TA>
 qtt_status tc_cgemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
                     const char* name);
 int tc_gemm_enabled();
+// tile settings of this host thread's Gram passes (0, 0: the defaults)
+void set_gram_tiles(int parts_per_sm, int chunk_div);
 // per-CTA partial Grams X X^H of X (m x n, ld m, m = m_mul * *m_ptr <= mcap
 // <= 128) on the tensor cores (split 1: TF32 operands; 3: 3xTF32), in the
 // partial format of the CUDA-core Gram pass; returns the number of partials

@@ -84,6 +84,44 @@ def test_autotune_picks_a_candidate(qlib):
     xs = [torch.from_numpy(ln["x"]).cuda() for ln in lines]
     ys = [torch.empty_like(x) for x in xs]
     best, times = q.autotune_batch(xs, ys, [ln["B"] for ln in lines],
-                                   [ln["rmax"] for ln in lines], candidates=(2, 4, 8), reps=1)
-    assert best.info()["nstreams"] in times and len(times) >= 2
+                                   [ln["rmax"] for ln in lines], candidates=(2, 4, 8), reps=1,
+                                   tiles=((0, 0), (1, 0), (0, 2)))
+    key = (best.info()["nstreams"],) + tuple(best.tiles)
+    assert key in times and len(times) >= 4
+    assert times[key] == min(times.values())
     best.free()
+
+
+@pytest.mark.parametrize("tiles", [(1, 2), (8, 4)])
+def test_batch_tiles_match_oracle_and_replay(qlib, tiles):
+    """Non-default Gram tiles (partial-Gram CTAs per SM, narrower column
+    chunks) change the order of the FP32 sums only: sampled lines still match
+    the oracle at 1e-5, and the captured graph replays the eager run's bits."""
+    import torch
+    q = qlib
+    lines = _lines(n=6, dmin=10, dmax=12, seed=44)
+    s = torch.cuda.Stream()
+    xs = [torch.from_numpy(ln["x"]).cuda() for ln in lines]
+    ys = [torch.zeros_like(x) for x in xs]
+    b = q.QTTBatch([ln["d"] for ln in lines], [ln["B"] for ln in lines],
+                   [ln["rmax"] for ln in lines], nstreams=3, stream=s)
+    b.set_tiles(*tiles)
+    b.run(xs, ys, stream=s)
+    s.synchronize()
+    eager = [y.cpu().numpy() for y in ys]
+    for ln, y in list(zip(lines, eager))[:3]:
+        ref = P.conv_sinc_qtt(ln["x"].astype(np.complex128), ln["B"], 0.0, ln["rmax"],
+                              eps_op=1e-7, eps_round=1e-7)
+        assert C.rel_l2(y.astype(np.complex128), ref) <= 1e-5
+    b.capture(xs, ys, s)
+    for y in ys:
+        y.zero_()
+    b.launch(s)
+    s.synchronize()
+    for e, y in zip(eager, ys):
+        assert np.array_equal(e, y.cpu().numpy())
+    with pytest.raises(q.QTTError):
+        b.set_tiles(17, 0)
+    with pytest.raises(q.QTTError):
+        b.set_tiles(0, 3)
+    b.free()
