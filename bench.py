@@ -873,7 +873,7 @@ def qfft_main(args, wl):
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
-            run_step()
+            step(stream)
             ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()

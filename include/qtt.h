@@ -532,6 +532,13 @@ void qtt_debug_set_orth_fix(int on);
  * no kernel reads scratch it did not write).  Synchronises the stream. */
 qtt_status qtt_debug_fill_pool(size_t bytes, int value, void* stream);
 
+/* Diagnostics: in the QTT-FFT route's calls (qtt_fft, qtt_hadamard) the FP32
+ * tridiagonal solver (n <= 32) checks its eigenvectors' orthonormality and a
+ * Jacobi solve of the same Gram is queued behind it, run only when the
+ * check fails (spectra degenerate at FP32 resolution occur in the roundings
+ * of Hadamard products); 1 (default) allows that, 0 turns it off. */
+void qtt_debug_set_heev_repair(int on);
+
 /* Diagnostics: accumulator of the complex64 TT-SVD's projections W = U^H M
  * (the m-term sums): 0 (default) Dot2 (exact products, compensated sums),
  * 1 Kahan-compensated sums of rounded products, 2 plain FMA. */

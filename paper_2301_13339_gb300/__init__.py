@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "qtt_debug_set_eig_solver", "qtt_profile_enable", "qtt_profile_read", "qtt_profile_reset",
     "qtt_profile_work", "qtt_get_margins", "qtt_debug_tc_selftest", "qtt_debug_tc_cgemm",
     "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram", "qtt_debug_set_orth_fix", "qtt_debug_set_tc_gram",
-    "qtt_debug_set_proj_acc", "qtt_debug_fill_pool",
+    "qtt_debug_set_proj_acc", "qtt_debug_fill_pool", "qtt_debug_set_heev_repair",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",

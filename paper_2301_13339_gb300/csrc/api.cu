@@ -159,6 +159,12 @@ void tensor_free_async(qtt_tensor* t, cudaStream_t s) {
   delete t;
 }
 
+// the QTT-FFT route's calls: small eigen-solves check and repair themselves
+struct RepairScope {
+  RepairScope() { set_heev_repair(1); }
+  ~RepairScope() { set_heev_repair(0); }
+};
+
 // The handles a C-ABI call uses, stamped on its stream when the call returns
 // (after everything it enqueued), so that qtt_free can order the release
 // after the last use without synchronising the device.
@@ -684,6 +690,7 @@ qtt_status qtt_fft(const qtt_tensor* x, int inverse, const qtt_trunc* tr, int sk
                    unsigned long long seed, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !out) { set_error("qtt_fft: NULL argument"); return QTT_EINVAL; }
+  RepairScope rs;
   Touch tg{(cudaStream_t)stream, x, nullptr, out};
   qtt_trunc t0 = {0.0, 0, 1, 0.0, QTT_PREC_AUTO, nullptr};
   if (tr) {
@@ -817,6 +824,7 @@ qtt_status qtt_add(double alpha, const qtt_tensor* x, double beta, const qtt_ten
 qtt_status qtt_hadamard(const qtt_tensor* x, const qtt_tensor* y, void* stream, qtt_tensor** out) {
   g_err[0] = 0;
   if (!x || !y || !out) { set_error("qtt_hadamard: NULL argument"); return QTT_EINVAL; }
+  RepairScope rs;
   Touch tg{(cudaStream_t)stream, x, y, out};
   if (!same_layout(x, y)) { set_error("qtt_hadamard: tensors differ in shape or type"); return QTT_EINVAL; }
   return hadamard(x, y, (cudaStream_t)stream, out);

@@ -975,6 +975,14 @@ static size_t eig_smem_bytes(int mg_cap) {
   return sizeof(T) * ((size_t)n * (n + 1) / 2 + (size_t)n * (n + 1));
 }
 
+// The tridiagonal solver's orthonormality check and the gated Jacobi repair
+// behind it (n <= 32) run where spectra degenerate at FP32 resolution occur:
+// the roundings of the QTT-FFT route (Kronecker-structured Hadamard
+// products), enabled per host thread by its entry points.  g_heev_repair is
+// the diagnostics switch over all of them.
+static int g_heev_repair = 1;
+static thread_local int t_heev_repair = 0;
+void set_heev_repair(int on) { t_heev_repair = (on != 0); }
 static int g_eig_solver = 0;   // 0: tridiagonal solver for FP32, Jacobi for FP64; 1: Jacobi
 // diagnostics: phase clocks of every following FP32 tridiagonal solve (the
 // last one leaves its clocks), set by qtt_debug_small_eigh_clocks
@@ -1001,7 +1009,8 @@ static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
     if (g_small_eigh_clk && !a.phase_clk) b.phase_clk = g_small_eigh_clk;
     // n <= 32: the solve checks its eigenvectors' orthonormality and a
     // Jacobi solve of the same Gram follows, gated by that check
-    int* flag = (mg_cap <= 32) ? (int*)scratch_alloc(sizeof(int), s) : nullptr;
+    int* flag = (mg_cap <= 32 && g_heev_repair && t_heev_repair)
+                    ? (int*)scratch_alloc(sizeof(int), s) : nullptr;
     if (flag) {
       cudaMemsetAsync(flag, 0, sizeof(int), s);
       b.orth_flag = flag;
@@ -1685,6 +1694,7 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 // 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
 extern "C" void qtt_debug_set_orth_fix(int on) { qtt::g_orth_fix = (on != 0); }
+extern "C" void qtt_debug_set_heev_repair(int on) { qtt::g_heev_repair = (on != 0); }
 extern "C" void qtt_debug_set_proj_acc(int which) { qtt::g_proj_acc = (which == 1 || which == 2) ? which : 0; }
 extern "C" void qtt_debug_set_tc_gram(int split, int pass2) {
   qtt::g_tc_gram_split = (split == 1) ? 1 : 3;

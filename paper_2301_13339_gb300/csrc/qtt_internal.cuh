@@ -393,6 +393,9 @@ template <typename TA>
 qtt_status tc_cgemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_t s,
                     const char* name);
 int tc_gemm_enabled();
+// this host thread's small FP32 eigen-solves check their orthonormality and
+// repair failed solves (set by the QTT-FFT route's entry points)
+void set_heev_repair(int on);
 // tile settings of this host thread's Gram passes (0, 0: the defaults)
 void set_gram_tiles(int parts_per_sm, int chunk_div);
 // per-CTA partial Grams X X^H of X (m x n, ld m, m = m_mul * *m_ptr <= mcap
