@@ -119,7 +119,7 @@ typedef struct {
 /* Largest sketch rank of the large-rank rounding mode (sketch >
  * QTT_RANK_CAP, complex64 only; see qtt_conv_sinc): its range finder factors
  * matrices of up to 2 x QTT_SKETCH_CAP_BIG rows by blocked Householder QR. */
-#define QTT_SKETCH_CAP_BIG 384
+#define QTT_SKETCH_CAP_BIG 512
 
 typedef struct qtt_tensor qtt_tensor;
 typedef struct qtt_op qtt_op;
@@ -538,6 +538,12 @@ qtt_status qtt_debug_fill_pool(size_t bytes, int value, void* stream);
  * check fails (spectra degenerate at FP32 resolution occur in the roundings
  * of Hadamard products); 1 (default) allows that, 0 turns it off. */
 void qtt_debug_set_heev_repair(int on);
+
+/* Diagnostics: 1 runs every complex64 environment sweep (qtt_dot, core
+ * gradients) through its strided-GEMM form, which otherwise serves only rank
+ * capacities whose environments exceed one CTA's shared memory; 0 (default)
+ * restores that choice. */
+void qtt_debug_set_env_big(int on);
 
 /* Diagnostics: accumulator of the complex64 TT-SVD's projections W = U^H M
  * (the m-term sums): 0 (default) Dot2 (exact products, compensated sums),

@@ -30,7 +30,7 @@ __all__ = [
 QTT_F64 = 0
 QTT_C64 = 2
 QTT_RANK_CAP = 64
-QTT_SKETCH_CAP_BIG = 384
+QTT_SKETCH_CAP_BIG = 512
 
 _STATUS = {0: "QTT_OK", -1: "QTT_EINVAL", -2: "QTT_ENOMEM", -3: "QTT_ECUDA",
            -4: "QTT_ETIMEOUT", -5: "QTT_ERANK", -6: "QTT_EUNSUPPORTED", -7: "QTT_ENUMERIC"}
@@ -44,6 +44,7 @@ EXPORTED_SYMBOLS = [
     "qtt_profile_work", "qtt_get_margins", "qtt_debug_tc_selftest", "qtt_debug_tc_cgemm",
     "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram", "qtt_debug_set_orth_fix", "qtt_debug_set_tc_gram",
     "qtt_debug_set_proj_acc", "qtt_debug_fill_pool", "qtt_debug_set_heev_repair",
+    "qtt_debug_set_env_big",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",

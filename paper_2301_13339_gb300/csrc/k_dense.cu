@@ -31,7 +31,7 @@ namespace qtt {
 // moves work to the many-CTA block-reflector updates
 constexpr int BQ_NB = 16;
 constexpr int BQ_CB = 8;         // columns per CTA in the block-reflector application
-constexpr int BQ_MAXM = 768;     // rows (panel in shared memory: 768 x 32 x 8 B)
+constexpr int BQ_MAXM = 1024;    // rows (panel in shared memory: 1024 x 16 x 8 B)
 
 // Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory (ld mp|1,
 // so consecutive columns fall on different banks), write it back (R on and

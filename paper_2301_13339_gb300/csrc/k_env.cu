@@ -20,6 +20,7 @@
 // contractions held in shared memory.
 #include "qtt_internal.cuh"
 #include <algorithm>
+#include <type_traits>
 
 namespace qtt {
 
@@ -187,7 +188,162 @@ __global__ void op_transpose_kernel(const R* __restrict__ in, R* __restrict__ ou
   out[e] = in[p + P0 * (i + 2 * (j + 2 * q))];
 }
 
+// core k of t copied to its capacities c0 x 2 x c1 (zeros beyond the device ranks)
+__global__ void k_env_pad(const float2* __restrict__ X, const int* __restrict__ xr, int k, int c0,
+                          int c1, float2* __restrict__ Xp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)c0 * 2 * c1) return;
+  const int a = (int)(e % c0);
+  const long long t = e / c0;
+  const int i = (int)(t % 2), b = (int)(t / 2);
+  const int r0 = xr[k - 1], r1 = xr[k];
+  Xp[e] = (a < r0 && b < r1) ? X[a + (size_t)r0 * (i + 2 * b)] : make_float2(0.f, 0.f);
+}
+
+// grad_k (f's layout at its device ranks) = alpha Gp + beta grad_k, Gp at the capacities
+__global__ void k_env_grad_out(const float2* __restrict__ Gp, const int* __restrict__ fr, int k,
+                               int c0, int c1, double alpha, double beta, float2* __restrict__ G) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = fr[k - 1], r1 = fr[k];
+  if (e >= (long long)r0 * 2 * r1) return;
+  const int a = (int)(e % r0);
+  const long long t = e / r0;
+  const int i = (int)(t % 2), b = (int)(t / 2);
+  (void)c1;
+  const float2 v = Gp[a + (size_t)c0 * (i + 2 * b)];
+  float2 o = make_float2((float)alpha * v.x, (float)alpha * v.y);
+  if (beta != 0.0) {
+    o.x += (float)beta * G[e].x;
+    o.y += (float)beta * G[e].y;
+  }
+  G[e] = o;
+}
+
+__global__ void k_env_one(float2* e) {
+  if (threadIdx.x == 0) *e = make_float2(1.f, 0.f);
+}
+__global__ void k_env_dot_out(const float2* e, double2* out) {
+  if (threadIdx.x == 0) *out = make_double2((double)e->x, (double)e->y);
+}
+
+// The sweeps of env_sweep_kernel for environments too large for one CTA's
+// shared memory (the adjoint's ranks in the large-rank rounding mode): the
+// same contractions as strided batched complex GEMMs (compensated chunk
+// sums) over f and w zero-padded to their host rank capacities, the left
+// environments stored per cut in global memory.
+//   left:   X = E_{k-1} W_k;  E_k = F_k^H X  (F_k, X as (2 r0f) x r1 matrices)
+//   right:  X = E_{k-1} W_k;  grad_k = alpha X R_k + beta grad_k;
+//           Y_i = W_k[:, i, :] R_k;  R_{k-1}^T = conj(F_k) Y^T over (i, b)
+static qtt_status env_sweep_big(const qtt_tensor* f, const qtt_tensor* w, double alpha, double beta,
+                                void* const* grad, double2* dot_out, cudaStream_t s) {
+  const int d = f->desc.d;
+  const std::vector<int>& cf = f->rcap;
+  const std::vector<int>& cw = w->rcap;
+  size_t nf = 0, nw = 0, ne = 0, xmax = 1, rmax = 1, ymax = 1, gmax = 1;
+  std::vector<size_t> fo(d), wo(d), eo(d + 1);
+  for (int k = 1; k <= d; ++k) {
+    fo[k - 1] = nf; nf += (size_t)cf[k - 1] * 2 * cf[k];
+    wo[k - 1] = nw; nw += (size_t)cw[k - 1] * 2 * cw[k];
+    xmax = std::max(xmax, (size_t)cf[k - 1] * 2 * cw[k]);
+    rmax = std::max(rmax, (size_t)cw[k] * cf[k]);
+    ymax = std::max(ymax, (size_t)cw[k - 1] * 2 * cf[k]);
+    gmax = std::max(gmax, (size_t)cf[k - 1] * 2 * cf[k]);
+  }
+  for (int k = 0; k <= d; ++k) { eo[k] = ne; ne += (size_t)cf[k] * cw[k]; }
+  const size_t tot = nf + nw + ne + 2 * xmax + 2 * rmax + ymax + gmax;
+  float2* buf = (float2*)scratch_alloc(sizeof(float2) * tot, s);
+  if (!buf) { set_error("environment sweep (large ranks): scratch"); return QTT_ENOMEM; }
+  float2* Fp = buf;
+  float2* Wp = Fp + nf;
+  float2* Est = Wp + nw;
+  float2* X = Est + ne;
+  float2* R0 = X + 2 * xmax;
+  float2* R1 = R0 + rmax;
+  float2* Y = R1 + rmax;
+  float2* Gp = Y + ymax;
+  qtt_status st = QTT_OK;
+  for (int k = 1; k <= d; ++k) {
+    const long long n1 = (long long)cf[k - 1] * 2 * cf[k], n2 = (long long)cw[k - 1] * 2 * cw[k];
+    QTT_PROF("env_pad", s);
+    k_env_pad<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>((const float2*)f->cores + f->off[k - 1],
+                                                          f->ranks, k, cf[k - 1], cf[k], Fp + fo[k - 1]);
+    k_env_pad<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>((const float2*)w->cores + w->off[k - 1],
+                                                          w->ranks, k, cw[k - 1], cw[k], Wp + wo[k - 1]);
+  }
+  k_env_one<<<1, 32, 0, s>>>(Est + eo[0]);
+  // X (c0f x 2 c1w) = E (c0f x c0w) W_k (c0w x 2 c1w)
+  auto times_core = [&](int k, const float2* E) {
+    CGemmArgs<float2> g;
+    g.A = E; g.sAi = 1; g.sAk = cf[k - 1];
+    g.B = Wp + wo[k - 1]; g.sBk = 1; g.sBj = cw[k - 1];
+    g.C = X; g.sCi = 1; g.sCj = cf[k - 1];
+    g.M = cf[k - 1]; g.N = 2 * cw[k]; g.K = cw[k - 1];
+    return cgemm<float2>(g, 1, s, "env_gemm");
+  };
+  for (int k = 1; k <= d && st == QTT_OK; ++k) {
+    st = times_core(k, Est + eo[k - 1]);
+    if (st != QTT_OK) break;
+    CGemmArgs<float2> g;   // E_k (c1f x c1w) = F_k^H X, K = (a, i) over 2 c0f
+    g.A = Fp + fo[k - 1]; g.sAi = 2LL * cf[k - 1]; g.sAk = 1; g.conjA = 1;
+    g.B = X; g.sBk = 1; g.sBj = 2LL * cf[k - 1];
+    g.C = Est + eo[k]; g.sCi = 1; g.sCj = cf[k];
+    g.M = cf[k]; g.N = cw[k]; g.K = 2 * cf[k - 1];
+    st = cgemm<float2>(g, 1, s, "env_gemm");
+  }
+  if (st == QTT_OK && dot_out) k_env_dot_out<<<1, 32, 0, s>>>(Est + eo[d], dot_out);
+  if (st == QTT_OK && grad) {
+    float2* Rm = R0;
+    float2* Rn = R1;
+    k_env_one<<<1, 32, 0, s>>>(Rm);
+    for (int k = d; k >= 1 && st == QTT_OK; --k) {
+      st = times_core(k, Est + eo[k - 1]);
+      if (st != QTT_OK) break;
+      {
+        CGemmArgs<float2> g;   // Gp (2 c0f x c1f) = X (2 c0f x c1w) R_k (c1w x c1f)
+        g.A = X; g.sAi = 1; g.sAk = 2LL * cf[k - 1];
+        g.B = Rm; g.sBk = 1; g.sBj = cw[k];
+        g.C = Gp; g.sCi = 1; g.sCj = 2LL * cf[k - 1];
+        g.M = 2 * cf[k - 1]; g.N = cf[k]; g.K = cw[k];
+        st = cgemm<float2>(g, 1, s, "env_gemm");
+      }
+      if (st != QTT_OK) break;
+      {
+        const long long ng = (long long)cf[k - 1] * 2 * cf[k];
+        QTT_PROF("env_grad_out", s);
+        k_env_grad_out<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(Gp, f->ranks, k, cf[k - 1], cf[k],
+                                                                   alpha, beta, (float2*)grad[k - 1]);
+      }
+      if (k == 1) break;
+      {
+        CGemmArgs<float2> g;   // Y[a' + c0w (i + 2 b)] = sum_b' W[a' + c0w (i + 2 b')] R[b' + c1w b]
+        g.A = Wp + wo[k - 1]; g.sAi = 1; g.sAk = 2LL * cw[k - 1]; g.bA1 = cw[k - 1];
+        g.B = Rm; g.sBk = 1; g.sBj = cw[k];
+        g.C = Y; g.sCi = 1; g.sCj = 2LL * cw[k - 1]; g.bC1 = cw[k - 1];
+        g.M = cw[k - 1]; g.N = cf[k]; g.K = cw[k]; g.nb1 = 2;
+        st = cgemm<float2>(g, 2, s, "env_gemm");
+      }
+      if (st != QTT_OK) break;
+      {
+        CGemmArgs<float2> g;   // R_{k-1}[a' + c0w a] = sum_{i, b} Y[a', i, b] conj(F[a, i, b])
+        g.A = Fp + fo[k - 1]; g.sAi = 1; g.sAk = cf[k - 1]; g.conjA = 1;
+        g.B = Y; g.sBk = cw[k - 1]; g.sBj = 1;
+        g.C = Rn; g.sCi = cw[k - 1]; g.sCj = 1;
+        g.M = cf[k - 1]; g.N = cw[k - 1]; g.K = 2 * cf[k];
+        st = cgemm<float2>(g, 1, s, "env_gemm");
+      }
+      std::swap(Rm, Rn);
+    }
+  }
+  scratch_free(buf, s);
+  if (st != QTT_OK) return st;
+  return cuda_check(cudaGetLastError(), "environment sweep (large ranks)");
+}
+
 }  // namespace
+
+// diagnostics: 1 sends every complex64 sweep through the GEMM path
+static int g_env_big = 0;
+void set_env_big(int on) { g_env_big = (on != 0); }
 
 size_t env_smem_bytes(const qtt_tensor* f, const qtt_tensor* w) {
   int fm = 1, wm = 1;
@@ -220,7 +376,9 @@ static qtt_status env_sweep_t(const qtt_tensor* f, const qtt_tensor* w, double a
   A.dot_out = dot_out;
   A.want_grads = grad ? 1 : 0;
   const size_t smem = 4 * (size_t)A.ecap * sizeof(T);
-  if (smem > 227 * 1024) {
+  if (smem > 227 * 1024 || (g_env_big && std::is_same<T, float2>::value)) {
+    if constexpr (std::is_same<T, float2>::value)
+      return env_sweep_big(f, w, alpha, beta, grad, dot_out, s);
     set_error("environment sweep: rank capacities %d x %d need %zu bytes of shared memory", fm, wm, smem);
     return QTT_EUNSUPPORTED;
   }
@@ -317,3 +475,5 @@ qtt_status op_transpose(const qtt_op* op, cudaStream_t s, qtt_op** out) {
 }
 
 }  // namespace qtt
+
+extern "C" void qtt_debug_set_env_big(int on) { qtt::set_env_big(on); }

@@ -21,10 +21,17 @@ Memory policy: the forward residual r is kept for the backward pass when its
 cores fit in ``store_budget_bytes``; otherwise it is freed and recomputed from
 F in the backward pass (the same seeds give the same rounding, so the
 gradient is identical either way).
+
+Large ranks (a sketch rank above QTT_RANK_CAP, the rounding's large-rank
+mode): the residual is never rounded as a sum, whose rank would be that of
+T F plus that of g.  The loss is ||y||^2 - 2 Re <g, y> + ||g||^2 with
+y = round(T F), and the gradient is linear in the residual:
+2 C(F, round(T^H y)) - 2 C(F, round(T^H g)), with round(T^H g) formed once
+per target.
 """
 import torch
 
-from . import (QTT_RANK_CAP, qtt_add, qtt_conv_adjoint, qtt_conv_sinc, qtt_dot,
+from . import (QTT_RANK_CAP, qtt_add, qtt_conv_adjoint, qtt_conv_sinc, qtt_core_grads, qtt_dot,
                qtt_from_device_cores, qtt_round, empty_cores)
 
 __all__ = ["SincDeconvProblem", "deconvolve", "lipschitz_estimate", "default_step"]
@@ -54,6 +61,35 @@ class SincDeconvProblem:
         self.shape_log2 = g.log2_shape
         self.interleave = g.interleave
         self.recomputed = 0
+        self.split = sketch > QTT_RANK_CAP     # large-rank mode: no rounded residual
+        self._gadj = None                      # (g, round(T^H g), <g, g>) of the split form
+
+    def split_terms(self):
+        """round(T^H g) and <g, g> for the current target (formed once)."""
+        if self._gadj is None or self._gadj[0] is not self.g:
+            if self._gadj is not None:
+                self._gadj[1].free(torch.cuda.current_stream())
+            adj = qtt_conv_adjoint(None, self.g, self.B, self.normalize, self.eps_op,
+                                   self.eps_round, self.rround, True, self.sketch, self.seed + 4)
+            self._gadj = (self.g, adj, qtt_dot(self.g, self.g)[0].clone())
+        return self._gadj[1], self._gadj[2]
+
+    def forward_split(self, f):
+        """y = round(T f) and the loss ||y||^2 - 2 Re <g, y> + ||g||^2."""
+        y = qtt_conv_sinc(f, self.B, self.normalize, self.eps_op, self.eps_round, self.rround,
+                          True, self.sketch, self.seed)
+        _, gg = self.split_terms()
+        val = qtt_dot(y, y)[0] - 2.0 * qtt_dot(self.g, y)[0] + gg
+        return y, val
+
+    def grads_split(self, f, y, grads):
+        """2 C(f, round(T^H y)) - 2 C(f, round(T^H g)) into grads."""
+        wy = qtt_conv_adjoint(None, y, self.B, self.normalize, self.eps_op, self.eps_round,
+                              self.rround, True, self.sketch, self.seed + 2)
+        wg, _ = self.split_terms()
+        qtt_core_grads(f, wy, grads, alpha=2.0, beta=0.0)
+        qtt_core_grads(f, wg, grads, alpha=-2.0, beta=1.0)
+        wy.free(torch.cuda.current_stream())
 
     # ------------------------------------------------------------ pieces
     def handle(self, cores):
@@ -81,9 +117,17 @@ class _SincDeconvLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, problem, *cores):
         f = problem.handle(cores)
+        ranks = [1] + [int(c.shape[2]) for c in cores]
+        if problem.split:
+            y, val = problem.forward_split(f)
+            ctx.problem = problem
+            ctx.f = f
+            ctx.r = y
+            ctx.ranks = ranks
+            ctx.dtype = cores[0].dtype
+            return val.clone()
         r = problem.residual(f)
         val = qtt_dot(r, r)
-        ranks = [1] + [int(c.shape[2]) for c in cores]
         # upper bound of the residual's core storage (ranks <= QTT_RANK_CAP)
         rbytes = cores[0].element_size() * len(cores) * 2 * QTT_RANK_CAP * QTT_RANK_CAP
         if rbytes > problem.store_budget_bytes:
@@ -100,11 +144,14 @@ class _SincDeconvLoss(torch.autograd.Function):
     def backward(ctx, gout):
         problem = ctx.problem
         r = ctx.r
-        if r is None:
-            r = problem.residual(ctx.f)
-            problem.recomputed += 1
         grads = empty_cores(ctx.ranks, ctx.dtype)
-        problem.grads_into(ctx.f, r, grads)
+        if problem.split:
+            problem.grads_split(ctx.f, r, grads)
+        else:
+            if r is None:
+                r = problem.residual(ctx.f)
+                problem.recomputed += 1
+            problem.grads_into(ctx.f, r, grads)
         stream = torch.cuda.current_stream()
         r.free(stream)
         ctx.f.free(stream)

@@ -1,0 +1,80 @@
+"""Core gradients when the adjoint's ranks exceed what one CTA's shared
+memory holds (the large-rank rounding mode of 2D images, sketch ranks up to
+384): the environment sweeps then run as strided batched GEMMs.
+
+* the GEMM form against the one-CTA form on the same small problem (forced
+  by the diagnostic switch): the same loss and gradients up to FP32 sums;
+* a 256 x 256 image whose adjoint reaches ranks above 64: loss and core
+  gradients against the oracle's dense gradient 2 T^H (T f - g) contracted
+  with F's partial products, at the bound of the FP32 path
+  3 u (1 + kappa), u = 2e-6, kappa = (||T f|| + ||g||) / ||T f - g||.
+"""
+import numpy as np
+import pytest
+
+from oracle import qtt as Q, pipeline as P
+from synth import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(q, n, B, rank_g, rank_f, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    scene = S.deconv_scene_2d(rng, n, n, nscat=12)
+    gd = P.conv_dense(scene, B)
+    gd = gd + 0.01 * np.linalg.norm(gd) / np.sqrt(gd.size) * (
+        rng.standard_normal(gd.shape) + 1j * rng.standard_normal(gd.shape)) / np.sqrt(2)
+    gt = torch.from_numpy(np.ascontiguousarray(gd)).to(device="cuda", dtype=torch.complex64)
+    g = q.qtt_decompose(gt, eps=0.0, rmax=rank_g, refine=True)
+    f0 = q.qtt_decompose(gt, eps=0.0, rmax=rank_f, refine=True)
+    return g, f0
+
+
+def _loss_and_grads(q, prob, f0):
+    import torch
+    cores = [c.requires_grad_(True) for c in q.core_tensors(f0)]
+    L = prob.loss(cores)
+    grads = torch.autograd.grad(L, cores)
+    return cores, L.item(), [gk.cpu().numpy() for gk in grads]
+
+
+def test_gemm_sweep_matches_one_cta_sweep(qlib):
+    from paper_2301_13339_gb300.deconv import SincDeconvProblem
+    q = qlib
+    g, f0 = _problem(q, 32, 24.0, rank_g=16, rank_f=6, seed=5)
+    prob = SincDeconvProblem(g, 24.0, eps_op=1e-7, eps_round=1e-7)
+    _, L0, G0 = _loss_and_grads(q, prob, f0)
+    q.lib().qtt_debug_set_env_big(1)
+    try:
+        _, L1, G1 = _loss_and_grads(q, prob, f0)
+    finally:
+        q.lib().qtt_debug_set_env_big(0)
+    assert abs(L1 - L0) <= 1e-5 * abs(L0)
+    num = np.sqrt(sum(np.linalg.norm(a - b) ** 2 for a, b in zip(G0, G1)))
+    den = np.sqrt(sum(np.linalg.norm(a) ** 2 for a in G0))
+    assert num <= 1e-5 * den
+
+
+def test_core_grads_large_rank_match_oracle(qlib):
+    from paper_2301_13339_gb300.deconv import SincDeconvProblem
+    q = qlib
+    n, B = 256, 48.0
+    g, f0 = _problem(q, n, B, rank_g=64, rank_f=32, seed=8)
+    prob = SincDeconvProblem(g, B, eps_op=1e-7, eps_round=1e-7, sketch=384)
+    cores, L, grads = _loss_and_grads(q, prob, f0)
+    # the adjoint of the residual needs ranks above the one-CTA sweep's 64
+    r = prob.residual(prob.handle(cores))
+    assert max(r.ranks()) > 64
+    cf = [c.detach().cpu().numpy().astype(np.complex128) for c in cores]
+    gdense = P.to_array([c.astype(np.complex128) for c in g.cores()], (n, n))
+    w = P.deconv_dense_grad(cf, (n, n), B, gdense)
+    ref = P.core_grads(cf, Q.image_to_qtt_vector(w))
+    Lref = P.deconv_loss(cf, (n, n), B, gdense)
+    Tf = P.conv_dense(P.to_array(cf, (n, n)), B)
+    kappa = (np.linalg.norm(Tf) + np.linalg.norm(gdense)) / np.sqrt(Lref)
+    bound = 3.0 * 2e-6 * (1.0 + kappa)
+    assert abs(L - Lref) <= bound * Lref + 1e-6 * np.linalg.norm(gdense) ** 2
+    num = np.sqrt(sum(np.linalg.norm(gk - rk) ** 2 for gk, rk in zip(grads, ref)))
+    den = np.sqrt(sum(np.linalg.norm(rk) ** 2 for rk in ref))
+    assert num <= bound * den, f"gradient error {num / den:.2e} > {bound:.2e} (kappa {kappa:.1f})"

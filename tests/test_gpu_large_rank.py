@@ -88,7 +88,7 @@ def test_large_rank_arguments(qlib):
         qlib.qtt_conv_sinc(real, 8.0, sketch=128)          # float64: not in this mode
     cplx = qlib.qtt_from_cores([c.astype(np.complex64) for c in _rand_cores(rng, 8, 8)], [4, 4])
     with pytest.raises(qlib.QTTError):
-        qlib.qtt_conv_sinc(cplx, 8.0, sketch=385)          # above QTT_SKETCH_CAP_BIG
+        qlib.qtt_conv_sinc(cplx, 8.0, sketch=qlib.QTT_SKETCH_CAP_BIG + 1)   # above the cap
 
 
 def test_large_rank_tensor_core_products(qlib):
