@@ -1035,12 +1035,19 @@ def main():
                     help="TT-SVD arithmetic: tf32 = the TF32-refined mode (first Gram pass on the "
                          "tensor cores with 3xTF32 products, FP32 second pass and rank decisions), "
                          "fp32 = every pass on the CUDA cores")
+    ap.add_argument("--tc-gemm", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="products of the large-rank rounding: 1 tensor cores (3xTF32, chunk sums "
+                         "compensated), 2 tensor cores for k <= 64 only, 0 CUDA cores, -1 the "
+                         "library's default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="file for the nvidia-smi samples of the timed region (default: a temp file)")
     args = ap.parse_args()
     Clocks.csv_path = args.clocks_csv
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "ours" and args.tc_gemm >= 0:
+        import paper_2301_13339_gb300 as q
+        q.qtt_debug_set_tc_gemm(args.tc_gemm)
     wl = dict(WORKLOADS[args.workload])
     if args.sketch > 0:
         wl["sketch"] = args.sketch
@@ -1152,7 +1159,7 @@ def main():
                           "two_pass_frac": 24.0 * N * args.steps / (res["total_ms"] * 1e-3) / 1e9
                           / peaks["hbm_gbs"]},
             "clocks": res["clocks"], "refine": args.refine, "prec": args.prec,
-            "cuda_graph": bool(args.graph), "graph_output_equals_eager": res.get("graph_bitexact"),
+            "tc_gemm": args.tc_gemm, "cuda_graph": bool(args.graph), "graph_output_equals_eager": res.get("graph_bitexact"),
             "plan_ms": res["plan_ms"]}
     if not args.no_cpu_baseline:
         oranks = []

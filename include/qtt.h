@@ -511,9 +511,10 @@ qtt_status qtt_debug_tc_selftest(const float* A, const float* B, float* C, int N
  * conjA != 0.  The complex product runs as one real product over the
  * stacking [[Re A, -Im A], [Im A, Re A]] [Re B; Im B] on tcgen05 MMAs
  * (kind::tf32) with each operand split into a TF32 head and its FP32
- * remainder (three products: FP32-level accuracy) and FP32 accumulators in
- * tensor memory; runs of k above 256 are split and the partials added with
- * compensation.  *status_dev (a device int, QTT_OK on entry) receives
+ * remainder (three products: FP32-level accuracy).  Each chunk of 8 k is
+ * summed in a fresh FP32 accumulator in tensor memory and the chunk sums
+ * are added in registers with compensation; runs of k above 1024 are split
+ * and the partials added with compensation.  *status_dev (a device int, QTT_OK on entry) receives
  * QTT_ETIMEOUT if a wait on the MMA completion ran out.  Negative sizes, a
  * NULL status_dev or a NULL array of nonzero size: QTT_EINVAL; K = 0 gives
  * C = 0.  Asynchronous. */
@@ -571,10 +572,11 @@ int qtt_debug_tc_gram(const void* X, int m, long long n, int split, void* gram_p
 
 /* Diagnostics: 1 routes the large-rank rounding's products (sketch ranks
  * above 64) to the tensor-core GEMM, 2 only those with k <= 64, 0 (default)
- * all to the CUDA-core GEMM with compensated chunk sums.  The tensor cores' FP32 accumulator rounds
- * one-signed, and along the range finder's chain of products that bias
- * reaches the result (E2 ~3e-5 where the compensated GEMM stays below
- * 1e-5), so the default keeps the compensated sums. */
+ * all to the CUDA-core GEMM with compensated chunk sums.  The 3xTF32
+ * operands keep ~2^-22 of each value (FP32: 2^-24), and along the range
+ * finder's chain of products that reaches the result (exact-regime E2
+ * ~9e-6 against ~2e-6 on the CUDA cores), so the default stays on the CUDA
+ * cores. */
 void qtt_debug_set_tc_gemm(int on);
 
 /* Release the library's cached workspace and operator plans. */

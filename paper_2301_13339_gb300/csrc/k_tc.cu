@@ -198,23 +198,27 @@ extern "C" qtt_status qtt_debug_tc_selftest(const float* A, const float* B, floa
 namespace qtt {
 
 // ---------------------------------------------------------------------------
-// Complex GEMM on the tensor cores, FP32-accurate (3xTF32): C = op(A) B with
-// the strides and batching of CGemmArgs (A complex or real).
+// Complex GEMM on the tensor cores, FP32-accurate: C = op(A) B with the
+// strides and batching of CGemmArgs (A complex or real).
 //
 // The complex product is one real product over the stacking
-//   A' = [[Re A, -Im A], [Im A, Re A]]   (2M x 2K; real k 2k = Re, 2k+1 = Im)
-//   B' = [Re B; Im B]                    (2K x N)
-// whose rows 0..M-1 are Re C and rows M..2M-1 Im C.  A CTA owns 64 complex
-// rows (one M = 128 MMA) and TN_TC complex columns.  Each operand is split
-// x ~ hi + lo with hi = x and lo = x - hi both rounded to nearest TF32, and
-// C' += hi hi + hi lo + lo hi in one tensor-memory accumulator (the products
-// of 11-bit values are exact in FP32; the dropped lo lo term and the
-// rounding of lo are near 2^-22 relative, without a sign bias).  k advances 8 complex values (16 real: two MMA k-steps) per
-// chunk: the global loads of chunk c + 1 are in flight in registers while
-// the MMAs of chunk c run, and the two shared-memory buffers are released by
-// an mbarrier that the MMAs' commit arrives on.  With split-K the partial of
-// the tile goes to part (element (i, j) at i + M j) for a compensated sum.
-constexpr int TN_TC = 256;             // complex columns per CTA (MMA N)
+//   A' rows 2i = [Re a_i, -Im a_i], 2i+1 = [Im a_i, Re a_i]   (real k 2k, 2k+1)
+//   B' = [Re B; Im B] (in K-major rows: the interleaved complex storage)
+// so that row 2i of C' = A' B' is Re C[i] and row 2i+1 Im C[i].  A CTA owns
+// 64 complex rows (one M = 128 MMA) and TN_TC complex columns.  Each operand
+// is split x ~ hi + lo, hi = x and lo = x - hi both rounded to nearest TF32,
+// and hi hi + hi lo + lo hi are accumulated: products of 11-bit values are
+// exact in FP32; the dropped lo lo term and the rounding of lo are near
+// 2^-22 relative, without a sign bias.
+//
+// The tensor core's FP32 accumulator rounds one-signed, so it only sums one
+// chunk of 8 complex k (two k-steps, 6 MMAs): every chunk accumulates into a
+// fresh tensor-memory buffer, and the threads add the chunk sums into
+// registers with Kahan compensation.  Two buffers alternate (shared memory
+// and tensor memory): the MMAs of chunk c run while the threads read back
+// chunk c - 1 and load chunk c + 1.  With split-K the partial of the tile
+// goes to part (element (i, j) at i + M j) for a compensated sum.
+constexpr int TN_TC = 64;              // complex columns per CTA (MMA N)
 constexpr int TC_KC = 8;               // complex k per chunk
 constexpr int TC_THREADS = 256;
 constexpr int TC_A_TILE = 128 * 8 * 4;         // bytes of one A k-step tile (128 x 8 TF32)
@@ -222,10 +226,12 @@ constexpr int TC_B_TILE = TN_TC * 8 * 4;       // bytes of one B k-step tile
 constexpr int TC_BUF = 4 * TC_A_TILE + 4 * TC_B_TILE;   // {hi, lo} x two k-steps
 constexpr size_t TC_SMEM = 2 * (size_t)TC_BUF + 1024;
 constexpr int TC_AE = 64 * TC_KC / TC_THREADS;      // A elements per thread and chunk (2)
-constexpr int TC_BE = TN_TC * TC_KC / TC_THREADS;   // B elements per thread and chunk (8)
-// longest k run summed in one FP32 tensor accumulator (single-batch products
-// split k beyond it and add the partials with compensation)
-constexpr int TC_KMAX = 256;
+constexpr int TC_BE = TN_TC * TC_KC / TC_THREADS;   // B elements per thread and chunk (2)
+constexpr int TC_TCOLS = 2 * TN_TC;                  // tensor-memory columns (two buffers)
+// longest k run of one CTA (single-batch products split k beyond it and add
+// the partials with compensation; within a run the chunk sums are added
+// with compensation too)
+constexpr int TC_KMAX = 1024;
 
 // x rounded to the nearest TF32 value (ties away from zero): the result
 // has 11 significant bits, so the tensor core consumes it exactly
@@ -252,7 +258,7 @@ __device__ __forceinline__ void tc_put(unsigned char* tiles, int tile_bytes, int
 }
 
 template <typename TA>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
 k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, long long ldpart,
            int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char tc_dyn[];
@@ -271,7 +277,7 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      tc_smem_u32(&tmem_slot)),
-                 "r"((uint32_t)TN_TC)
+                 "r"((uint32_t)TC_TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -285,6 +291,9 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = tc_idesc_tf32(128, TN_TC);
+  // tensor-memory lanes of this warp, and its half of the columns
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const int half = warp >> 2;
 
   // this thread's elements of a chunk: A (ii, kk) and B (kk, jj)
   int a_ii[TC_AE], a_kk[TC_AE], b_kk[TC_BE], b_jj[TC_BE];
@@ -318,30 +327,42 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
                                     : make_float2(0.f, 0.f);
     }
   };
+  // compensated running sums of this thread's 32 outputs
+  float sum[32], cmp[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) { sum[q] = 0.f; cmp[q] = 0.f; }
+  auto flush = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[16];
+      tc_ld16(tmem + lane_addr + (uint32_t)(TN_TC * buf + 32 * half + 16 * h), v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float y = v[q] - cmp[16 * h + q];
+        const float t = sum[16 * h + q] + y;
+        cmp[16 * h + q] = (t - sum[16 * h + q]) - y;
+        sum[16 * h + q] = t;
+      }
+    }
+  };
 
   uint32_t phase[2] = {0u, 0u};
-  int used[2] = {0, 0};
   bool ok = true;
   if (nch > 0) load_chunk(0);
   for (int c = 0; c < nch; ++c) {
     const int buf = c & 1;
     unsigned char* sa = base + (size_t)buf * TC_BUF;
     unsigned char* sb = sa + 4 * TC_A_TILE;
-    if (used[buf]) {   // the MMAs of chunk c - 2 have read this buffer
-      ok = __syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[buf]), phase[buf])) != 0;
-      if (!ok) break;  // block-uniform; the buffer stays marked for the drain below
-      phase[buf] ^= 1u;
-      used[buf] = 0;
-    }
-    // row ii (Re C) takes [Re a, -Im a], row 64 + ii (Im C) takes [Im a, Re a]
+    // buffer buf was last used by chunk c - 2, whose MMAs completed (and
+    // whose sums were read) in the previous iteration
 #pragma unroll
     for (int t = 0; t < TC_AE; ++t) {
       const float2 a = ra[t];
       const int ii = a_ii[t], kr = 2 * a_kk[t];
-      tc_put(sa, TC_A_TILE, ii, kr, a.x);
-      tc_put(sa, TC_A_TILE, ii, kr + 1, -a.y);
-      tc_put(sa, TC_A_TILE, 64 + ii, kr, a.y);
-      tc_put(sa, TC_A_TILE, 64 + ii, kr + 1, a.x);
+      tc_put(sa, TC_A_TILE, 2 * ii, kr, a.x);
+      tc_put(sa, TC_A_TILE, 2 * ii, kr + 1, -a.y);
+      tc_put(sa, TC_A_TILE, 2 * ii + 1, kr, a.y);
+      tc_put(sa, TC_A_TILE, 2 * ii + 1, kr + 1, a.x);
     }
 #pragma unroll
     for (int t = 0; t < TC_BE; ++t) {
@@ -349,44 +370,51 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
       tc_put(sb, TC_B_TILE, b_jj[t], 2 * b_kk[t] + 1, rb[t].y);
     }
     tc_fence_proxy_async();
+    tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(TN_TC * buf);
 #pragma unroll
       for (int step = 0; step < 2; ++step) {
         const uint64_t dah = tc_sdesc(tc_smem_u32(sa + (size_t)step * TC_A_TILE), TC_LBO, TC_SBO);
         const uint64_t dal = tc_sdesc(tc_smem_u32(sa + (size_t)(2 + step) * TC_A_TILE), TC_LBO, TC_SBO);
         const uint64_t dbh = tc_sdesc(tc_smem_u32(sb + (size_t)step * TC_B_TILE), TC_LBO, TC_SBO);
         const uint64_t dbl = tc_sdesc(tc_smem_u32(sb + (size_t)(2 + step) * TC_B_TILE), TC_LBO, TC_SBO);
-        tc_mma_tf32(tmem, dah, dbh, idesc, (c > 0 || step > 0) ? 1u : 0u);
-        tc_mma_tf32(tmem, dah, dbl, idesc, 1u);
-        tc_mma_tf32(tmem, dal, dbh, idesc, 1u);
+        tc_mma_tf32(dacc, dah, dbh, idesc, step > 0 ? 1u : 0u);   // a fresh sum per chunk
+        tc_mma_tf32(dacc, dah, dbl, idesc, 1u);
+        tc_mma_tf32(dacc, dal, dbh, idesc, 1u);
       }
       tc_commit(tc_smem_u32(&mbar[buf]));
     }
-    used[buf] = 1;
     if (c + 1 < nch) load_chunk(c + 1);
-  }
-  // the last commit of each buffer (after a failed wait, still drain the
-  // other buffer's MMAs before the tensor memory is released)
-#pragma unroll
-  for (int b = 0; b < 2; ++b)
-    if (used[b]) {   // block-uniform
-      if (!__syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[b]), phase[b]))) ok = false;
-      phase[b] ^= 1u;
+    if (c >= 1) {   // chunk c - 1: wait for its MMAs, add its sums
+      const int pb = buf ^ 1;
+      ok = __syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[pb]), phase[pb])) != 0;
+      if (!ok) break;   // block-uniform; the drain below waits again with a limit
+      phase[pb] ^= 1u;
+      tc_fence_after();
+      flush(pb);
     }
-  tc_fence_after();
-  __syncthreads();
+  }
+  if (ok && nch > 0) {
+    const int lb = (nch - 1) & 1;
+    ok = __syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[lb]), phase[lb])) != 0;
+    if (ok) {
+      tc_fence_after();
+      flush(lb);
+    }
+  }
   if (!ok) {
+    // drain: every committed chunk completes before the tensor memory goes
+    for (int b = 0; b < 2; ++b) (void)__syncthreads_and(tc_mbar_wait(tc_smem_u32(&mbar[b]), phase[b]));
     if (tid == 0) atomicCAS(status, 0, (int)QTT_ETIMEOUT);
   } else {
-    // warp w reads TMEM lanes 32 (w % 4) ..: lane r < 64 holds Re of row
-    // i0 + r, lane r >= 64 Im of row i0 + r - 64; warps 0-3 take columns
-    // 0..127, warps 4-7 columns 128..255
-    const int lane_r = 32 * (warp & 3) + (tid & 31);
-    const int cbase = (warp >> 2) * (TN_TC / 2);
-    const long long i = i0 + (lane_r & 63);
-    const int comp = lane_r >> 6;
+    // lane r = 32 (warp % 4) + lane: element (i0 + r / 2), component r % 2;
+    // adjacent lanes write the two floats of one complex value
+    const int r = 32 * (warp & 3) + (tid & 31);
+    const long long i = i0 + (r >> 1);
+    const int comp = r & 1;
     float* Cf;
     long long sCi, sCj;
     if (part) {
@@ -398,21 +426,11 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
       sCi = g.sCi;
       sCj = g.sCj;
     }
-    for (int c0 = 0; c0 < TN_TC / 2; c0 += 16) {
-      if (j0 + cbase + c0 >= g.N) break;   // warp-uniform
-      float v[16];
-      if (nch > 0) {
-        tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + c0), v);
-      } else {
+    if (i < g.M) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.f;
-      }
-      if (i < g.M) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const long long j = j0 + cbase + c0 + q;
-          if (j < g.N) Cf[2 * (i * sCi + j * sCj) + comp] = v[q];
-        }
+      for (int q = 0; q < 32; ++q) {
+        const long long j = j0 + 32 * half + q;
+        if (j < g.N) Cf[2 * (i * sCi + j * sCj) + comp] = sum[q] - cmp[q];
       }
     }
   }
@@ -420,7 +438,7 @@ k_tc_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, l
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)TN_TC)
+                 "r"((uint32_t)TC_TCOLS)
                  : "memory");
 }
 
@@ -440,8 +458,8 @@ qtt_status tc_cgemm(const CGemmArgs<TA>& g, int nbatch, int* status, cudaStream_
   const int sms = device_sm_count();
   int splits = 1;
   if (nbatch == 1) {
-    // split k beyond TC_KMAX terms per accumulator, and further while the
-    // tiles alone cannot fill the GPU (chunks of at least 4 k-steps)
+    // split k beyond TC_KMAX terms per CTA, and further while the tiles
+    // alone cannot fill the GPU (runs of at least 4 chunks)
     splits = (g.K + TC_KMAX - 1) / TC_KMAX;
     if (tiles * splits < 2LL * sms)
       splits = (int)std::max<long long>(

@@ -61,28 +61,29 @@ def test_tc_cgemm_complex_3xtf32(qlib, M, N, K, conj):
     got = C.cpu().numpy().astype(np.complex128)
     Ar = A.astype(np.complex128)
     ref = (Ar.conj() if conj else Ar) @ B.astype(np.complex128)
-    # FP32 accumulation (no compensation inside a run of <= 256 k) over k
-    # terms of size |a||b|: error ~ u sqrt(k) |a||b| per element, u = 2^-24,
-    # relative to |c| ~ sqrt(k) |a||b| about u sqrt(k) (measured 2.2e-6 at
-    # k = 2000, where sqrt(2k) u = 3.8e-6)
+    # each chunk of 8 k is summed in the FP32 accumulator (error ~ u |chunk|,
+    # u = 2^-24, |chunk| ~ 4 |a||b|) and the chunks are added with
+    # compensation: for random signs the chunk errors add up like a random
+    # walk, ~ u sqrt(k) |a||b| per element, i.e. ~u relative to |c|
     scale = np.sqrt(K) * np.abs(Ar).max() * np.abs(B).max()
     assert np.abs(got - ref).max() <= 4e-6 * scale
     u = 2.0 ** -24
     assert np.linalg.norm(got - ref) <= (1e-6 + 2 * u * np.sqrt(2 * K)) * np.linalg.norm(ref)
 
 
-def test_tc_cgemm_same_sign_short_k(qlib):
-    """Positive operands with full 24-bit mantissas and a short k (16 terms).
-    The round-to-nearest hi/lo split keeps every entry within 5e-7 of the
-    FP64 product (a truncating split loses up to 2^-20 of every operand).
-    The tensor core's FP32 accumulator itself rounds one-signed: the mean
-    error of the real parts is negative and a few u of |C| (measured -1.4e-7
-    relative at k = 16), which is why a long k run biases a same-sign sum
-    and the rounding's long products stay on the compensated CUDA-core GEMM
-    by default."""
+@pytest.mark.parametrize("K", [16, 4096])
+def test_tc_cgemm_same_sign(qlib, K):
+    """Positive operands with full 24-bit mantissas.  The round-to-nearest
+    hi/lo split keeps every entry within 5e-7 of the FP64 product (a
+    truncating split loses up to 2^-20 of every operand).  The tensor core's
+    FP32 accumulator rounds one-signed, so a long uncompensated run would
+    drift by ~k u of |C|; each 8-k chunk starts from zero in tensor memory
+    and the chunk sums are added in FP32 registers with compensation, so the
+    mean error stays a fraction of u |C| at any k (measured ~ -1e-7 relative
+    at k = 16)."""
     import torch
-    rng = np.random.default_rng(17)
-    M, N, K = 64, 256, 16
+    rng = np.random.default_rng(17 + K)
+    M, N = 64, 256
     A = (rng.uniform(0.5, 1.0, (M, K)) + 1j * rng.uniform(0.5, 1.0, (M, K))).astype(np.complex64)
     B = (rng.uniform(0.5, 1.0, (K, N)) + 1j * rng.uniform(-0.1, 0.1, (K, N))).astype(np.complex64)
     C, st = qlib.tc_cgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda())
