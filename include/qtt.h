@@ -579,6 +579,18 @@ int qtt_debug_tc_gram(const void* X, int m, long long n, int split, void* gram_p
  * cores. */
 void qtt_debug_set_tc_gemm(int on);
 
+/* Diagnostics: the blocked Householder QR of the large-rank rounding on its
+ * own (the orthonormal basis of the randomised range finder, Sec. 5's
+ * TT-rounding with a sketch).  A: m x n column-major DEVICE array of dtype
+ * QTT_C64 (interleaved re, im floats) or QTT_F64, read only (the
+ * factorisation runs on a copy).  Q: m x nq column-major DEVICE array of the
+ * same dtype, caller-owned, receives the first nq columns of
+ * Q = H_1 ... H_min(m,n) (H_k = I - tau_k v_k v_k^H), so that A = Q R with R
+ * upper triangular and Q^H Q = I also where A is rank deficient.  Accepts
+ * 1 <= m <= 1024, n >= 1, 1 <= nq <= m; anything else, a NULL array or
+ * another dtype: QTT_EINVAL.  Asynchronous on `stream`. */
+qtt_status qtt_debug_big_qr(const void* A, int m, int n, int nq, int dtype, void* Q, void* stream);
+
 /* Release the library's cached workspace and operator plans. */
 void qtt_release_workspace(void);
 

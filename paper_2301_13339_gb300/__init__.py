@@ -20,7 +20,7 @@ __all__ = [
     "QTTError", "QTTTensor", "QTTOperator", "lib", "load", "qtt_decompose", "qtt_conv_sinc",
     "qtt_round", "qtt_to_full", "qtt_to_full_noalloc", "qtt_conv_adjoint", "qtt_matvec",
     "qtt_op_create",
-    "qtt_from_cores", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "QTT_SKETCH_CAP_BIG", "EXPORTED_SYMBOLS",
+    "qtt_from_cores", "big_qr", "QTT_F64", "QTT_C64", "QTT_RANK_CAP", "QTT_SKETCH_CAP_BIG", "EXPORTED_SYMBOLS",
     "QTTBatch", "qtt_batch_conv_sinc", "autotune_batch", "qtt_dot", "qtt_add", "qtt_core_grads",
     "qtt_from_device_cores", "empty_cores", "core_tensors", "qtt_decompose_rsvd", "qtt_fft",
     "qtt_hadamard", "qtt_conv_fft", "qtt_sinc_padded", "QTT_PREC_AUTO", "QTT_PREC_FP64",
@@ -44,7 +44,7 @@ EXPORTED_SYMBOLS = [
     "qtt_profile_work", "qtt_get_margins", "qtt_debug_tc_selftest", "qtt_debug_tc_cgemm",
     "qtt_debug_set_tc_gemm", "qtt_debug_tc_gram", "qtt_debug_set_orth_fix", "qtt_debug_set_tc_gram",
     "qtt_debug_set_proj_acc", "qtt_debug_fill_pool", "qtt_debug_set_heev_repair",
-    "qtt_debug_set_env_big",
+    "qtt_debug_set_env_big", "qtt_debug_big_qr",
     "qtt_core_grads", "qtt_dot", "qtt_add", "qtt_from_device_cores",
     "qtt_batch_create", "qtt_batch_run", "qtt_batch_capture", "qtt_batch_launch", "qtt_batch_info",
     "qtt_batch_free", "qtt_batch_conv_sinc", "qtt_decompose_rsvd", "qtt_fft", "qtt_hadamard",
@@ -121,6 +121,7 @@ def load(path=None):
         "qtt_debug_set_heev_cluster": (None, [d, i]),
         "qtt_decompose_rsvd": (i, [vp, i, i, i, i, vp, ctypes.c_ulonglong, vp, pp]),
         "qtt_debug_set_refine_sweeps": (None, [i]),
+        "qtt_debug_big_qr": (i, [vp, i, i, i, i, vp, vp]),
         "qtt_last_error": (ctypes.c_char_p, []),
         "qtt_version": (ctypes.c_char_p, []),
     }
@@ -608,6 +609,25 @@ def tc_gram(X, split=1, max_parts=8, stream=None):
         _check(npart)
     # element (a, b) of a partial is at a + m b: the transpose of the row-major view
     return gp[:npart].transpose(1, 2), int(st.item())
+
+
+def big_qr(A, nq=None, stream=None):
+    """First nq columns of Q in the blocked Householder QR A = Q R (A: m x n
+    complex64 or float64 CUDA tensor, m <= 1024)."""
+    import torch
+    load()
+    if A.dim() != 2 or A.device.type != "cuda":
+        raise QTTError("big_qr: A must be a 2-D CUDA tensor")
+    m, n = A.shape
+    nq = m if nq is None else int(nq)
+    code = {torch.complex64: QTT_C64, torch.float64: QTT_F64}.get(A.dtype)
+    if code is None:
+        raise QTTError("big_qr: complex64 or float64 only")
+    Ac = A.t().contiguous()          # column-major
+    Q = torch.empty((nq, m), dtype=A.dtype, device=A.device)
+    _check(_lib.qtt_debug_big_qr(ctypes.c_void_p(Ac.data_ptr()), m, n, nq, code,
+                                 ctypes.c_void_p(Q.data_ptr()), _stream(stream)))
+    return Q.t()
 
 
 def qtt_debug_set_tc_gemm(on):

@@ -39,15 +39,20 @@ constexpr int BQ_MAXM = 1024;    // rows (panel in shared memory: 1024 x 16 x 8 
 // diagonal and zeros above it written out) to Vt, and T (BQ_NB x BQ_NB,
 // column-major) to Tm.
 //
-// One warp per trailing column (BQP_THREADS = 32 warps >= kb) and one
-// barrier per reflector: every thread derives reflector k (tau, the scale
-// 1/(alpha - beta) of v, beta) itself from the column's largest entry and
-// scaled sum of squares, which the warp that updated column k in the
-// previous step measured right after its update (look-ahead); the trailing
-// update takes v_i = col_i * scal on the fly (v^H x = x_k + conj(scal)
-// sum_{i>k} conj(col_i) x_i), so column k is scaled into v only in the next
-// step, by the warp that no trailing column needs (kb <= 32 leaves one).
+// Two warps per trailing column (BQP_THREADS = 32 warps >= 2 (kb - 1) + 1),
+// each over every other 32-row stripe, and one barrier per reflector:
+// every thread derives reflector k (tau, the scale 1/(alpha - beta) of v,
+// beta) itself from the column's largest entry and scaled sum of squares,
+// which the two warps that updated column k in the previous step measured
+// right after their update (look-ahead); the trailing update takes
+// v_i = col_i * scal on the fly (v^H x = x_k + conj(scal) sum_{i>k}
+// conj(col_i) x_i, the two warps' partial sums added in a fixed order after
+// a 64-thread barrier of the pair), so column k is scaled into v only in
+// the next step, by the last warp, which no trailing column needs.
 constexpr int BQP_THREADS = 1024;
+// the pairs of the trailing columns use warps 0 .. 2 (BQ_NB - 1) - 1 and
+// named barriers 1 .. BQ_NB - 1; the last warp scales the finished column
+static_assert(2 * (BQ_NB - 1) < BQP_THREADS / 32 - 1 && BQ_NB - 1 <= 15, "panel warp layout");
 
 // largest |re|, |im| of x over rows i >= i0, and sum over i > i0 of
 // |x_i / amax|^2 (all lanes of the warp get both)
@@ -68,28 +73,130 @@ __device__ __forceinline__ void bq_col_norm(const T* x, int i0, int mp, int lane
   ssq = q;
 }
 
+__device__ __forceinline__ void bq_pair_sync(int pair) {
+  asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BQP_THREADS)
-k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __restrict__ Vt) {
+k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __restrict__ Vt,
+           const T* __restrict__ Vprev, const T* __restrict__ Tprev, int kbp) {
   using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char bq_smem[];
-  T* P = reinterpret_cast<T*>(bq_smem);
+  // with Vprev the panel's columns first receive the block reflector of the
+  // previous panel (rows p - kbp .. m - 1, V^T = Vprev, T = Tprev): the
+  // buffer holds those rows, P is its part from row p on
+  const int off = Vprev ? kbp : 0;
+  T* Xb = reinterpret_cast<T*>(bq_smem);
+  T* P = Xb + off;
   __shared__ T s_tau[BQ_NB], s_scal[BQ_NB], s_beta[BQ_NB];
   __shared__ R s_amax[BQ_NB], s_ssq[BQ_NB];
+  __shared__ R s_lam[BQ_NB][2], s_lsq[BQ_NB][2];   // look-ahead partials of each half
+  __shared__ T s_pd[BQ_NB][2];                      // partial dots of each pair
   __shared__ T s_Y[BQ_NB * BQ_NB];
   __shared__ T s_T[BQ_NB * BQ_NB];
+  __shared__ R s_wmax[BQP_THREADS / 32];
   const int mp = m - p;
-  const int ld = mp | 1;
+  const int mpp = mp + off;
+  const int ld = mpp | 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
-    const int i = e % mp, j = e / mp;
-    P[i + (size_t)ld * j] = A[(size_t)(p + i) + (size_t)m * (p + j)];
+  const int pair = warp >> 1, half = warp & 1;
+  for (int e = tid; e < mpp * kb; e += BQP_THREADS) {
+    const int i = e % mpp, j = e / mpp;
+    Xb[i + (size_t)ld * j] = A[(size_t)(p - off + i) + (size_t)m * (p + j)];
   }
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) {
     s_T[e] = szero<T>();
     s_Y[e] = szero<T>();
   }
   __syncthreads();
+  if (off > 0) {
+    // X <- (I - V T^H V^H) X with the arithmetic of bq_apply_cols (per
+    // column the same sums in the same order): W = V^H X, one warp per
+    // (reflector, 8 columns), lanes over the rows; W2 = T^H W; then each
+    // thread updates its rows of all columns.  s_Y and s_T serve as W and
+    // W2 (they are zeroed again before the factorisation uses them).
+    T* sW = s_Y;    // W[a][j] at a + BQ_NB j
+    T* sW2 = s_T;
+    {
+      const int a = warp % BQ_NB, cb = (warp / BQ_NB) * 8;
+      if (a < kbp && cb < kb) {
+        T acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = szero<T>();
+        for (int i = lane; i < mpp; i += 32) {
+          const T v = Vprev[i + (size_t)mpp * a];
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (cb + c < kb) macc(acc[c], v, Xb[i + (size_t)ld * (cb + c)]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const T w = warp_sum(acc[c]);
+          if (lane == 0 && cb + c < kb) sW[a + BQ_NB * (cb + c)] = w;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < BQ_NB * BQ_NB) {
+      const int a = tid % BQ_NB, c = tid / BQ_NB;
+      T w2 = szero<T>();
+      if (a < kbp && c < kb)
+        for (int b = 0; b <= a; ++b) macc(w2, Tprev[b + BQ_NB * a], sW[b + BQ_NB * c]);
+      sW2[a + BQ_NB * c] = w2;
+    }
+    __syncthreads();
+    for (int i = tid; i < mpp; i += BQP_THREADS) {
+      T v[BQ_NB];
+#pragma unroll
+      for (int a = 0; a < BQ_NB; ++a) v[a] = (a < kbp) ? Vprev[i + (size_t)mpp * a] : szero<T>();
+      for (int j = 0; j < kb; ++j) {
+        T sacc = szero<T>();
+#pragma unroll
+        for (int a = 0; a < BQ_NB; ++a)
+          if (a < kbp) mac(sacc, v[a], sW2[a + BQ_NB * j]);
+        Xb[i + (size_t)ld * j] = ssub(Xb[i + (size_t)ld * j], sacc);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) {
+      s_T[e] = szero<T>();
+      s_Y[e] = szero<T>();
+    }
+  }
+  {
+    R lmax = (R)0;
+    for (int e = tid; e < mp * kb; e += BQP_THREADS) {
+      const T v = P[e % mp + (size_t)ld * (e / mp)];
+      lmax = rmax(lmax, rmax(rabs(sreal(v)), rabs(simag(v))));
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = rmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (lane == 0) s_wmax[warp] = lmax;
+  }
+  __syncthreads();
+  // A panel whose largest entry lies outside [2^-E, 2^E] (E = 30 in FP32,
+  // 200 in FP64) is factored scaled by a power of two near its inverse:
+  // the dot products of the trailing updates multiply two entries and would
+  // under- or overflow.  Householder QR is homogeneous (v, tau and T do
+  // not depend on the scale, R scales with it), so only R is scaled back
+  // when the panel is written out; panels inside the range are untouched.
+  int pexp = 0;
+  {
+    R pm = (R)0;
+    for (int w = 0; w < BQP_THREADS / 32; ++w) pm = rmax(pm, s_wmax[w]);
+    const int E = sizeof(R) == 4 ? 30 : 200;
+    if (pm > (R)0 && pm < (R)INFINITY) {
+      const int e = ilogb(pm);
+      if (e < -E || e > E) pexp = e;
+    }
+  }
+  if (pexp != 0) {   // block-uniform
+    for (int e = tid; e < mp * kb; e += BQP_THREADS) {
+      T& v = P[e % mp + (size_t)ld * (e / mp)];
+      v = make_scalar<T>(scalbn(sreal(v), -pexp), scalbn(simag(v), -pexp));
+    }
+    __syncthreads();
+  }
   const int kmax = min(mp, kb);
   if (warp == 0) {
     R a, q;
@@ -97,15 +204,35 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
     if (lane == 0) { s_amax[0] = a; s_ssq[0] = q; }
   }
   __syncthreads();
+  // the unscaled look-ahead sum is exact enough wherever amax^2 neither
+  // overflows nor underflows; outside that range the column is measured
+  // again with the scaled two-pass sum
+  const R lo = sizeof(R) == 4 ? (R)1e-15 : (R)1e-140, hi = sizeof(R) == 4 ? (R)1e15 : (R)1e140;
   for (int k = 0; k < kmax; ++k) {
     const T* col = P + (size_t)ld * k;
+    R amax = s_amax[0], part = s_ssq[0];
+    if (k > 0) {
+      // column k as its two warps measured it in step k - 1; every thread
+      // combines the halves in the same order (the branch is block-uniform)
+      amax = rmax(s_lam[k][0], s_lam[k][1]);
+      if (amax == (R)0 || (amax > lo && amax < hi)) {
+        part = (amax > (R)0) ? (s_lsq[k][0] + s_lsq[k][1]) / (amax * amax) : (R)0;
+      } else {
+        if (warp == 0) {
+          R a, q;
+          bq_col_norm(col, k, mp, lane, a, q);
+          if (lane == 0) { s_amax[k] = a; s_ssq[k] = q; }
+        }
+        __syncthreads();
+        amax = s_amax[k];
+        part = s_ssq[k];
+      }
+    }
     // reflector k, scaled by the column's largest entry (no overflow or
     // underflow of |alpha - beta|^2 at any data scale)
-    const R amax = s_amax[k];
     T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
     if (amax > (R)0) {
       const R inv = (R)1 / amax;
-      const R part = s_ssq[k];
       const T al = rscale(col[k], inv);
       const R ax = sreal(al), ay = simag(al);
       if (part > (R)0 || ay != (R)0) {
@@ -118,49 +245,53 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
         beta_s = make_scalar<T>(beta * amax, (R)0);
       }
     }
-    const int nt = kb - 1 - k;   // trailing columns of the panel (<= 31)
-    if (warp < nt) {
-      // x <- (I - conj(tau) v v^H) x for trailing column j; four rows per
-      // lane in flight in the dot and in the update
-      const int j = k + 1 + warp;
+    const int nt = kb - 1 - k;   // trailing columns of the panel (<= 15)
+    if (pair < nt) {
+      // x <- (I - conj(tau) v v^H) x for trailing column j over the rows
+      // k + 1 + 32 half + 64 t + lane; four stripes per lane in flight
+      const int j = k + 1 + pair;
       T* x = P + (size_t)ld * j;
       T a0 = szero<T>(), a1 = szero<T>(), a2 = szero<T>(), a3 = szero<T>();
-      int i = k + 1 + lane;
-      for (; i + 96 < mp; i += 128) {
-        const T c0 = col[i], c1 = col[i + 32], c2 = col[i + 64], c3 = col[i + 96];
-        const T x0 = x[i], x1 = x[i + 32], x2 = x[i + 64], x3 = x[i + 96];
+      const int r0 = k + 1 + 32 * half + lane;
+      int i = r0;
+      for (; i + 192 < mp; i += 256) {
+        const T c0 = col[i], c1 = col[i + 64], c2 = col[i + 128], c3 = col[i + 192];
+        const T x0 = x[i], x1 = x[i + 64], x2 = x[i + 128], x3 = x[i + 192];
         macc(a0, c0, x0);
         macc(a1, c1, x1);
         macc(a2, c2, x2);
         macc(a3, c3, x3);
       }
-      for (; i < mp; i += 32) macc(a0, col[i], x[i]);
-      const T sdot = warp_sum(sadd(sadd(a0, a1), sadd(a2, a3)));
-      const T wdot = sadd(x[k], smul(conjg(scal), sdot));
+      for (; i < mp; i += 64) macc(a0, col[i], x[i]);
+      const T pdot = warp_sum(sadd(sadd(a0, a1), sadd(a2, a3)));
+      if (lane == 0) s_pd[pair][half] = pdot;
+      const T xk = x[k];
+      bq_pair_sync(pair);            // both partials written, both halves have read x[k]
+      const T sdot = sadd(s_pd[pair][0], s_pd[pair][1]);
+      const T wdot = sadd(xk, smul(conjg(scal), sdot));
       const T f = smul(conjg(tau), wdot);
       const T fs = smul(scal, f);
-      __syncwarp();                  // every lane has read x[k]
-      if (lane == 0) x[k] = ssub(x[k], f);
+      if (half == 0 && lane == 0) x[k] = ssub(xk, f);
       // column k + 1 (the next reflector's) also measures itself while it is
       // updated: largest |re|, |im| over rows >= k + 1 and the plain sum of
-      // squares below row k + 1
+      // squares below row k + 1, per half
       const bool look = (j == k + 1 && j < kmax);
       R am = (R)0, sq = (R)0;
-      int r = k + 1 + lane;
-      for (; r + 96 < mp; r += 128) {
+      int r = r0;
+      for (; r + 192 < mp; r += 256) {
         T y[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) y[u] = ssub(x[r + 32 * u], smul(col[r + 32 * u], fs));
+        for (int u = 0; u < 4; ++u) y[u] = ssub(x[r + 64 * u], smul(col[r + 64 * u], fs));
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          x[r + 32 * u] = y[u];
+          x[r + 64 * u] = y[u];
           if (look) {
             am = rmax(am, rmax(rabs(sreal(y[u])), rabs(simag(y[u]))));
-            if (r + 32 * u > j) sq += sabs2(y[u]);
+            if (r + 64 * u > j) sq += sabs2(y[u]);
           }
         }
       }
-      for (; r < mp; r += 32) {
+      for (; r < mp; r += 64) {
         const T y = ssub(x[r], smul(col[r], fs));
         x[r] = y;
         if (look) {
@@ -173,18 +304,7 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
           am = rmax(am, __shfl_xor_sync(0xffffffffu, am, off));
           sq += __shfl_xor_sync(0xffffffffu, sq, off);
         }
-        // the unscaled sum is exact enough wherever amax^2 neither overflows
-        // nor underflows; outside that range the column is measured again
-        // with the scaled two-pass sum
-        const R lo = sizeof(R) == 4 ? (R)1e-15 : (R)1e-140, hi = sizeof(R) == 4 ? (R)1e15 : (R)1e140;
-        if (am == (R)0 || (am > lo && am < hi)) {
-          if (lane == 0) { s_amax[j] = am; s_ssq[j] = (am > (R)0) ? sq / (am * am) : (R)0; }
-        } else {
-          __syncwarp();
-          R a, q;
-          bq_col_norm(x, j, mp, lane, a, q);
-          if (lane == 0) { s_amax[j] = a; s_ssq[j] = q; }
-        }
+        if (lane == 0) { s_lam[j][half] = am; s_lsq[j][half] = sq; }
       }
     } else if (warp == BQP_THREADS / 32 - 1 && k > 0) {
       // column k - 1 is final: v_{k-1} = col * scal below the diagonal, beta on it
@@ -232,9 +352,13 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
     }
   }
   __syncthreads();
-  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
-    const int i = e % mp, j = e / mp;
-    A[(size_t)(p + i) + (size_t)m * (p + j)] = P[i + (size_t)ld * j];
+  // rows p - off .. p - 1 (final after the previous panel's update), then
+  // the panel: R on and above the diagonal, the v_k below
+  for (int e = tid; e < mpp * kb; e += BQP_THREADS) {
+    const int i = e % mpp - off, j = e / mpp;
+    T v = P[i + (size_t)ld * j];
+    if (pexp != 0 && i >= 0 && i <= j) v = make_scalar<T>(scalbn(sreal(v), pexp), scalbn(simag(v), pexp));
+    A[(size_t)(p + i) + (size_t)m * (p + j)] = v;
   }
   // V^T rows with the implicit unit diagonal and the zeros above it
   for (int e = tid; e < mp * kb; e += BQP_THREADS) {
@@ -378,7 +502,7 @@ static std::atomic<unsigned long long> g_bq_cfg[2];
 
 template <typename T>
 static void bq_configure() {
-  if (first_on_device(&g_bq_cfg[sizeof(T) == sizeof(double) ? 1 : 0]))
+  if (first_on_device(&g_bq_cfg[Sc<T>::cplx ? 0 : 1]))
     cudaFuncSetAttribute(k_bq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
 }
@@ -420,18 +544,20 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
   const int kmax = std::min(m, n);
   const int np = (kmax + BQ_NB - 1) / BQ_NB;
   T* Vall = Tm + (size_t)((n + BQ_NB - 1) / BQ_NB) * BQ_NB * BQ_NB;   // V^T of panel pi at pi NB MAXM
-  // look-ahead: after panel p, its reflectors update the next panel's
-  // columns on s, the next panel is factored on s, and the rest of the
-  // trailing columns are updated concurrently on a side stream.  Every
-  // column receives the same updates in the same order as without the
-  // split.  The side stream forks from s and joins it by events, so the
-  // sequence is also valid inside a stream capture.
+  // look-ahead: the kernel of panel p + NB first applies panel p's
+  // reflectors to its own columns, so after panel p only the columns beyond
+  // the next panel remain; they are updated on a side stream while the next
+  // panel is factored.  Every column receives the same updates in the same
+  // order (and the same arithmetic) as without the split.  The side stream
+  // forks from s and joins it by events, so the sequence is also valid
+  // inside a stream capture.
   SideStream* ss = side_stream();
   const bool ahead = ss && np > 2;
   if (ahead) {
     cudaEventRecord(ss->fork, s);
     cudaStreamWaitEvent(ss->s, ss->fork, 0);
   }
+  bool join_pending = false;
   for (int p = 0; p < kmax; p += BQ_NB) {
     const int kb = std::min(BQ_NB, kmax - p);
     T* Tp = Tm + (size_t)(p / BQ_NB) * BQ_NB * BQ_NB;
@@ -441,29 +567,34 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
     // and a block-reflector application to nc columns, 16 M kb nc
     const double M = (double)(m - p);
     const double cplx = Sc<T>::cplx ? 1.0 : 0.25;
+    const bool fuse = ahead && p > 0;
     {
       QTT_PROF("bigqr_panel", s);
       prof_add_work("bigqr_panel", cplx * 8.0 * kb * kb * (M - kb / 3.0), 2.0 * M * kb * sizeof(T));
-      k_bq_panel<T><<<1, BQP_THREADS, sizeof(T) * (size_t)((m - p) | 1) * kb, s>>>(A, m, p, kb, Tp, Vp);
+      if (fuse)
+        prof_add_work("bigqr_panel", cplx * 16.0 * (M + BQ_NB) * BQ_NB * kb, 0.0);
+      const T* Vprev = fuse ? Vp - (size_t)BQ_NB * BQ_MAXM : nullptr;
+      const T* Tprev = fuse ? Tp - (size_t)BQ_NB * BQ_NB : nullptr;
+      const int rows = (m - p) + (fuse ? BQ_NB : 0);
+      k_bq_panel<T><<<1, BQP_THREADS, sizeof(T) * (size_t)(rows | 1) * kb, s>>>(A, m, p, kb, Tp, Vp,
+                                                                               Vprev, Tprev, BQ_NB);
     }
     const int c0 = p + kb, nc = kmax - c0;
-    if (nc > 0 && ahead) {
-      // the next panel's columns (they also need the side stream's update
-      // from the panel before: wait for it), then the rest on the side
-      const int nn = std::min(BQ_NB, nc);
-      if (p > 0) cudaStreamWaitEvent(s, ss->join, 0);
-      {
-        QTT_PROF("bigqr_update", s);
-        prof_add_work("bigqr_update", cplx * 16.0 * M * kb * nn, 2.0 * M * nn * sizeof(T));
-        k_bq_apply<T><<<(nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nn, Vp, p, kb, Tp, 1);
+    if (ahead) {
+      // the next panel needs the side stream's update from the panel before
+      if (join_pending) {
+        cudaStreamWaitEvent(s, ss->join, 0);
+        join_pending = false;
       }
+      const int nn = std::min(BQ_NB, std::max(nc, 0));
       if (nc > nn) {
-        cudaEventRecord(ss->fork, s);                 // panel p (and the update above) done
+        cudaEventRecord(ss->fork, s);                 // panel p done
         cudaStreamWaitEvent(ss->s, ss->fork, 0);
         prof_add_work("bigqr_update", cplx * 16.0 * M * kb * (nc - nn), 2.0 * M * (nc - nn) * sizeof(T));
         k_bq_apply<T><<<(nc - nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, ss->s>>>(A, m, c0 + nn, nc - nn,
                                                                            Vp, p, kb, Tp, 1);
         cudaEventRecord(ss->join, ss->s);
+        join_pending = true;
       }
     } else if (nc > 0) {
       QTT_PROF("bigqr_update", s);
@@ -494,6 +625,23 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
 }
 template qtt_status big_qr_q<float2>(float2*, int, int, int, float2*, float2*, cudaStream_t);
 template qtt_status big_qr_q<double>(double*, int, int, int, double*, double*, cudaStream_t);
+
+template <typename T>
+static qtt_status debug_big_qr(const void* A, int m, int n, int nq, void* Q, cudaStream_t s) {
+  T* Aw = (T*)scratch_alloc(sizeof(T) * (size_t)m * n, s);
+  T* Tm = (T*)scratch_alloc(sizeof(T) * big_qr_tm_elems(n), s);
+  qtt_status st = QTT_ENOMEM;
+  if (Aw && Tm) {
+    st = cuda_check(cudaMemcpyAsync(Aw, A, sizeof(T) * (size_t)m * n, cudaMemcpyDeviceToDevice, s),
+                    "big_qr copy");
+    if (st == QTT_OK) st = big_qr_q<T>(Aw, m, n, nq, (T*)Q, Tm, s);
+  } else {
+    set_error("qtt_debug_big_qr: scratch allocation failed");
+  }
+  if (Aw) scratch_free(Aw, s);
+  if (Tm) scratch_free(Tm, s);
+  return st;
+}
 
 template <typename T>
 void launch_conj_transpose(const T* S, int ls, int n, int m, T* A, cudaStream_t s) {
@@ -707,3 +855,17 @@ template qtt_status cgemm<float>(const CGemmArgs<float>&, int, cudaStream_t, con
 template qtt_status cgemm<float2>(const CGemmArgs<float2>&, int, cudaStream_t, const char*);
 
 }  // namespace qtt
+
+extern "C" qtt_status qtt_debug_big_qr(const void* A, int m, int n, int nq, int dtype, void* Q,
+                                      void* stream) {
+  qtt::clear_error();
+  if (!A || !Q || m < 1 || n < 1 || nq < 1 || nq > m || m > 1024 ||
+      (dtype != QTT_C64 && dtype != QTT_F64)) {
+    qtt::set_error("qtt_debug_big_qr: NULL array, shape %d x %d (nq %d) or dtype %d not accepted",
+                   m, n, nq, dtype);
+    return QTT_EINVAL;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  return dtype == QTT_C64 ? qtt::debug_big_qr<float2>(A, m, n, nq, Q, s)
+                          : qtt::debug_big_qr<double>(A, m, n, nq, Q, s);
+}

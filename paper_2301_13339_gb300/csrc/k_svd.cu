@@ -460,6 +460,14 @@ __device__ void eig_post(const EigArgs<T>& a, T* A, T* V, int n, int mg, int ldv
   if (a.phase_clk && tid == 0) a.phase_clk[3] = clock64();
 }
 
+// the even exponent e of the Jacobi solvers' scaling 2^-e of a Gram with
+// trace t: 0 inside [2^-60, 2^60], else the one that brings t near 2^56
+__device__ __forceinline__ int gram_scale_exp(double t) {
+  if (!(t > 0.0) || !isfinite(t)) return 0;
+  const int e = ilogb(t);
+  return (e > 60 || e < -60) ? ((e - 56) & ~1) : 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   if (a.only_if && *a.only_if == 0) return;   // a repair solve that is not needed
@@ -482,16 +490,39 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   T* A = reinterpret_cast<T*>(smem_raw);  // packed, n(n+1)/2
   T* V = A + (n * (n + 1)) / 2;           // n x n, column-major, ld n + 1
 
-  // load + identity.  V has leading dimension n + 1: the column-pair
-  // products of the orthonormalisation below then read 32 different banks.
+  // trace (FP64, norm^2 at the first level).  A Gram whose trace lies
+  // outside [2^-60, 2^60] is scaled by an even power of two 2^-e that brings
+  // the trace near 2^56: the sweeps square entries (|a_pq|^2), which
+  // overflow FP32 from a trace near 2^64 on and lose the small entries to
+  // underflow at small traces.  Every step of a sweep is homogeneous in the
+  // matrix and sqrt(2^-e) is exact, so the rotations are those of the
+  // unscaled matrix wherever that one neither over- nor underflows; the
+  // eigenvalues are scaled back before the rank decision.  V has leading
+  // dimension n + 1: the column-pair products of the orthonormalisation
+  // below then read 32 different banks.
   const int ldv = n + 1;
+  __shared__ int s_exp;
   double tr_local = 0.0;
+  for (int j = tid >> 5; j < mg; j += EIG_THREADS / 32)
+    if ((j & 31) == (tid & 31)) tr_local += a.G[j + (size_t)a.ldp * j].x;
+  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
+  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
+    if (a.write_norm2) *a.norm2 = t;
+    s_exp = gram_scale_exp(t);
+  }
+  __syncthreads();
+  const int gexp = s_exp;
   for (int j = tid >> 5; j < n; j += EIG_THREADS / 32) {
     for (int i = tid & 31; i <= j; i += 32) {
       T v = szero<T>();
       if (i < mg && j < mg) {
         double2 g = a.G[i + (size_t)a.ldp * j];
-        if (i == j) { g.y = 0.0; tr_local += g.x; }
+        g.x = scalbn(g.x, -gexp);
+        g.y = (i == j) ? 0.0 : scalbn(g.y, -gexp);
         from_d2(g, v);
       }
       A[pk_idx(i, j)] = v;
@@ -513,15 +544,7 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
       s_blk[b][1] = (unsigned short)Q;
     }
   }
-  // trace reduction (norm^2 at the first level)
-  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
-  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
   __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
-    if (a.write_norm2) *a.norm2 = t;
-  }
 
   if (a.phase_clk && tid == 0) a.phase_clk[1] = clock64();
   const double tol = 4.0 * Sc<T>::eps;
@@ -636,6 +659,10 @@ __global__ void __launch_bounds__(EIG_THREADS) gram_eig_kernel(EigArgs<T> a) {
   }
   if (!converged && a.max_sweeps == 0 && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
   if (a.phase_clk && tid == 0) { a.phase_clk[2] = clock64(); a.phase_clk[4] = nsweep; }
+  // eigenvalues back to the data's scale (exact: a power of two)
+  for (int i = tid; i < mg; i += EIG_THREADS)
+    A[pk_idx(i, i)] = rscale(sone(T()), scalbn(sreal(A[pk_idx(i, i)]), gexp));
+  __syncthreads();
 
   eig_post<T>(a, A, V, n, mg, ldv);
 }
@@ -693,8 +720,27 @@ __global__ void __launch_bounds__(EIG_THREADS)
   float2* Acur = reinterpret_cast<float2*>(smem_raw);
   float2* Anext = Acur + ((npkp + 1) & ~1);
 
+  __shared__ int s_exp;
   for (int x = tid; x < n; x += EIG_THREADS) s_pi[x] = dm_pi(x, n);
+  // trace (FP64), then the scaling of gram_eig_kernel (traces outside
+  // [2^-60, 2^60] brought near 2^56 by an even power of two)
   double tr_local = 0.0;
+  for (int y = tid >> 5; y < n; y += EIG_THREADS / 32) {
+    if ((y & 31) != (tid & 31)) continue;
+    const int py = dm_pl0(y, n);
+    if (py < mg) tr_local += a.G[py + (size_t)a.ldp * py].x;
+  }
+  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
+  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
+    if (a.write_norm2) *a.norm2 = t;
+    s_exp = gram_scale_exp(t);
+  }
+  __syncthreads();
+  const int gexp = s_exp;
   for (int y = tid >> 5; y < n; y += EIG_THREADS / 32) {
     const int py = dm_pl0(y, n);
     for (int x = tid & 31; x <= y; x += 32) {
@@ -702,14 +748,11 @@ __global__ void __launch_bounds__(EIG_THREADS)
       float2 v = make_float2(0.f, 0.f);
       if (px < mg && py < mg) {
         const double2 g = a.G[px + (size_t)a.ldp * py];
-        v = make_float2((float)g.x, x == y ? 0.f : (float)g.y);
-        if (x == y) tr_local += g.x;
+        v = make_float2((float)scalbn(g.x, -gexp), x == y ? 0.f : (float)scalbn(g.y, -gexp));
       }
       Acur[pkp(x, y)] = v;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) tr_local += __shfl_down_sync(0xffffffffu, tr_local, off);
-  if ((tid & 31) == 0) s_red[tid >> 5] = tr_local;
   // this thread's off-diagonal blocks (P < Q): source and destination
   // addresses for the whole solve; bit 31 of a destination = store conj
   const int nbo = np * (np - 1) / 2;
@@ -739,11 +782,6 @@ __global__ void __launch_bounds__(EIG_THREADS)
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < EIG_THREADS / 32; ++w) t += s_red[w];
-    if (a.write_norm2) *a.norm2 = t;
-  }
   if (a.phase_clk && tid == 0) a.phase_clk[1] = clock64();
 
   const float tol = 4.0f * Sc<float2>::eps;
@@ -837,7 +875,8 @@ __global__ void __launch_bounds__(EIG_THREADS)
   if (!converged && a.max_sweeps == 0 && tid == 0 && a.status) atomicOr(a.status, DEV_ST_JACOBI_LIMIT);
   if (a.phase_clk && tid == 0) { a.phase_clk[2] = clock64(); a.phase_clk[4] = nsweep; }
   // every player is back at its first position
-  for (int x = tid; x < n; x += EIG_THREADS) dbuf[dm_pl0(x, n)] = Acur[pkp(x, x)].x;
+  // (eigenvalues back to the data's scale: exact, a power of two)
+  for (int x = tid; x < n; x += EIG_THREADS) dbuf[dm_pl0(x, n)] = scalbnf(Acur[pkp(x, x)].x, gexp);
   if (tid == 0) hdr[0] = nsweep * (n - 1);
 }
 

@@ -67,3 +67,41 @@ def test_small_eigh_f64(qlib, n):
     assert np.abs(lam - ref).max() <= 1e-13
     assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-12
     assert np.linalg.norm(G @ U - U * lam, axis=0).max() <= 1e-13
+
+
+@pytest.mark.parametrize("solver", [0, 1, 2])
+@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("scale", [1e-30, 1e25])
+def test_small_eigh_c64_extreme_scales(qlib, solver, n, scale):
+    """Gram matrices whose squared entries leave the FP32 range (traces far
+    outside [2^-60, 2^60]): every solver works on a copy scaled by a power
+    of two, so eigenvalues and eigenvectors keep the accuracy of the
+    unscaled case."""
+    rng = np.random.default_rng(n + 7)
+    G = _herm(rng, n, SPECTRA["graded"](n, rng)) * scale
+    qlib.qtt_debug_set_eig_solver(solver)
+    try:
+        lam, U = qlib.qtt_small_eigh(G, qlib.QTT_C64)
+    finally:
+        qlib.qtt_debug_set_eig_solver(0)
+    U = U.astype(np.complex128)
+    ref = np.sort(np.linalg.eigvalsh(G))[::-1]
+    gn = np.abs(ref).max()
+    assert np.all(np.isfinite(lam)) and np.all(np.isfinite(U))
+    assert np.abs(lam - ref).max() <= 2e-5 * gn
+    assert np.abs(U.conj().T @ U - np.eye(n)).max() <= 5e-6
+    assert np.linalg.norm(G @ U - U * lam, axis=0).max() <= 2e-5 * gn
+
+
+@pytest.mark.parametrize("scale", [1e-170, 1e170])
+def test_small_eigh_f64_extreme_scales(qlib, scale):
+    """FP64 Jacobi on a Gram whose squared entries leave the FP64 range."""
+    rng = np.random.default_rng(9)
+    n = 40
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    G = (Q * np.logspace(0, -10, n)) @ Q.T * scale
+    lam, U = qlib.qtt_small_eigh(G, qlib.QTT_F64)
+    ref = np.sort(np.linalg.eigvalsh(G))[::-1]
+    assert np.abs(lam - ref).max() <= 1e-13 * scale
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-12
+    assert np.linalg.norm(G @ U - U * lam, axis=0).max() <= 1e-13 * scale
