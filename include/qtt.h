@@ -533,11 +533,13 @@ void qtt_debug_set_orth_fix(int on);
  * no kernel reads scratch it did not write).  Synchronises the stream. */
 qtt_status qtt_debug_fill_pool(size_t bytes, int value, void* stream);
 
-/* Diagnostics: in the QTT-FFT route's calls (qtt_fft, qtt_hadamard) the FP32
- * tridiagonal solver (n <= 32) checks its eigenvectors' orthonormality and a
- * Jacobi solve of the same Gram is queued behind it, run only when the
- * check fails (spectra degenerate at FP32 resolution occur in the roundings
- * of Hadamard products); 1 (default) allows that, 0 turns it off. */
+/* Diagnostics: the FP32 eigen-solves with n <= 32 in the QTT-FFT route's
+ * calls (qtt_fft, qtt_hadamard), whose roundings meet spectra degenerate at
+ * FP32 resolution.  1 (default): the tridiagonal solver, which checks its
+ * eigenvectors' orthonormality, with a Jacobi solve of the same Gram queued
+ * behind it and run only when the check fails; 2: the cyclic Jacobi solver
+ * for all of them; 0: the tridiagonal solver alone.  Other calls are not
+ * affected. */
 void qtt_debug_set_heev_repair(int on);
 
 /* Diagnostics: 1 runs every complex64 environment sweep (qtt_dot, core

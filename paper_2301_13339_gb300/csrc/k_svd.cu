@@ -1043,7 +1043,10 @@ static void launch_eig_jacobi(const EigArgs<T>& a, int mg_cap, cudaStream_t s);
 
 template <typename T>
 static void launch_eig(const EigArgs<T>& a, int mg_cap, cudaStream_t s) {
-  if (Sc<T>::cplx && g_eig_solver == 0 && !a.relative) {
+  // mode 2: inside the QTT-FFT route's calls the n <= 32 solves go to the
+  // Jacobi solver directly
+  const bool jac_small = mg_cap <= 32 && g_heev_repair == 2 && t_heev_repair;
+  if (Sc<T>::cplx && g_eig_solver == 0 && !a.relative && !jac_small) {
     EigArgs<T> b = a;
     if (g_small_eigh_clk && !a.phase_clk) b.phase_clk = g_small_eigh_clk;
     // n <= 32: the solve checks its eigenvectors' orthonormality and a
@@ -1733,7 +1736,7 @@ template void launch_gram_eig<float2>(const float2*, int, int, const int*, int, 
 // 2 = qtt_small_eigh through the relative-accuracy refinement Jacobi).
 extern "C" void qtt_debug_set_eig_solver(int which) { qtt::g_eig_solver = which; }
 extern "C" void qtt_debug_set_orth_fix(int on) { qtt::g_orth_fix = (on != 0); }
-extern "C" void qtt_debug_set_heev_repair(int on) { qtt::g_heev_repair = (on != 0); }
+extern "C" void qtt_debug_set_heev_repair(int on) { qtt::g_heev_repair = (on == 1 || on == 2) ? on : 0; }
 extern "C" void qtt_debug_set_proj_acc(int which) { qtt::g_proj_acc = (which == 1 || which == 2) ? which : 0; }
 extern "C" void qtt_debug_set_tc_gram(int split, int pass2) {
   qtt::g_tc_gram_split = (split == 1) ? 1 : 3;
