@@ -33,23 +33,26 @@ constexpr int BQ_NB = 16;
 constexpr int BQ_CB = 8;         // columns per CTA in the block-reflector application
 constexpr int BQ_MAXM = 1024;    // rows (panel in shared memory: 1024 x 16 x 8 B)
 
-// Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory (ld mp|1,
+// Factor the panel A[p:m, p:p+kb] (kb <= BQ_NB) in shared memory (ld odd,
 // so consecutive columns fall on different banks), write it back (R on and
 // above the diagonal, the v_k below), V^T (kb x mp, row a = v_a, unit
 // diagonal and zeros above it written out) to Vt, and T (BQ_NB x BQ_NB,
 // column-major) to Tm.
 //
-// Two warps per trailing column (BQP_THREADS = 32 warps >= 2 (kb - 1) + 1),
-// each over every other 32-row stripe, and one barrier per reflector:
-// every thread derives reflector k (tau, the scale 1/(alpha - beta) of v,
-// beta) itself from the column's largest entry and scaled sum of squares,
-// which the two warps that updated column k in the previous step measured
-// right after their update (look-ahead); the trailing update takes
-// v_i = col_i * scal on the fly (v^H x = x_k + conj(scal) sum_{i>k}
-// conj(col_i) x_i, the two warps' partial sums added in a fixed order after
-// a 64-thread barrier of the pair), so column k is scaled into v only in
-// the next step, by the last warp, which no trailing column needs.
+// WPC (1 or 2) warps per trailing column, each over every WPC-th 32-row
+// stripe, and one barrier per reflector: the warps that need reflector k
+// (tau, the scale 1/(alpha - beta) of v, beta) derive it themselves from
+// the column's largest entry and scaled sum of squares, which the warps
+// that updated column k in the previous step measured right after their
+// update (look-ahead); the trailing update takes v_i = col_i * scal on the
+// fly (v^H x = x_k + conj(scal) sum_{i>k} conj(col_i) x_i; with WPC = 2 the
+// two warps' partial sums are added in a fixed order after a 64-thread
+// barrier of the pair), so column k is scaled into v only in the next step,
+// by the last warp, which no trailing column needs.  Two warps per column
+// halve the per-warp chain on tall panels; on short ones the duplicated
+// per-warp work outweighs that, so the host picks WPC by the panel height.
 constexpr int BQP_THREADS = 1024;
+constexpr int BQP_WPC2_ROWS = 512;   // panels of at least this many rows: WPC = 2
 // the pairs of the trailing columns use warps 0 .. 2 (BQ_NB - 1) - 1 and
 // named barriers 1 .. BQ_NB - 1; the last warp scales the finished column
 static_assert(2 * (BQ_NB - 1) < BQP_THREADS / 32 - 1 && BQ_NB - 1 <= 15, "panel warp layout");
@@ -77,10 +80,11 @@ __device__ __forceinline__ void bq_pair_sync(int pair) {
   asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
 
-template <typename T>
+template <typename T, int WPC>
 __global__ void __launch_bounds__(BQP_THREADS)
 k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __restrict__ Vt,
            const T* __restrict__ Vprev, const T* __restrict__ Tprev, int kbp) {
+  static_assert(WPC == 1 || WPC == 2, "warps per column");
   using R = typename Sc<T>::R;
   extern __shared__ __align__(16) unsigned char bq_smem[];
   // with Vprev the panel's columns first receive the block reflector of the
@@ -100,14 +104,19 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   const int mpp = mp + off;
   const int ld = mpp | 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int pair = warp >> 1, half = warp & 1;
-  for (int e = tid; e < mpp * kb; e += BQP_THREADS) {
-    const int i = e % mpp, j = e / mpp;
-    Xb[i + (size_t)ld * j] = A[(size_t)(p - off + i) + (size_t)m * (p + j)];
-  }
+  const int grp = warp / WPC, half = warp % WPC;
+  // element loops: warp w takes column w / 2 (and + 16) and every other
+  // 32-row stripe
+  const int ec = warp >> 1, er = lane + 32 * (warp & 1);
+  for (int j = ec; j < kb; j += 16)
+    for (int i = er; i < mpp; i += 64) Xb[i + (size_t)ld * j] = A[(size_t)(p - off + i) + (size_t)m * (p + j)];
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) {
     s_T[e] = szero<T>();
     s_Y[e] = szero<T>();
+  }
+  if (tid < 2 * BQ_NB) {
+    (&s_lam[0][0])[tid] = (R)0;
+    (&s_lsq[0][0])[tid] = (R)0;
   }
   __syncthreads();
   if (off > 0) {
@@ -166,10 +175,11 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   }
   {
     R lmax = (R)0;
-    for (int e = tid; e < mp * kb; e += BQP_THREADS) {
-      const T v = P[e % mp + (size_t)ld * (e / mp)];
-      lmax = rmax(lmax, rmax(rabs(sreal(v)), rabs(simag(v))));
-    }
+    for (int j = ec; j < kb; j += 16)
+      for (int i = er; i < mp; i += 64) {
+        const T v = P[i + (size_t)ld * j];
+        lmax = rmax(lmax, rmax(rabs(sreal(v)), rabs(simag(v))));
+      }
     for (int o = 16; o > 0; o >>= 1) lmax = rmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     if (lane == 0) s_wmax[warp] = lmax;
   }
@@ -191,10 +201,11 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
     }
   }
   if (pexp != 0) {   // block-uniform
-    for (int e = tid; e < mp * kb; e += BQP_THREADS) {
-      T& v = P[e % mp + (size_t)ld * (e / mp)];
-      v = make_scalar<T>(scalbn(sreal(v), -pexp), scalbn(simag(v), -pexp));
-    }
+    for (int j = ec; j < kb; j += 16)
+      for (int i = er; i < mp; i += 64) {
+        T& v = P[i + (size_t)ld * j];
+        v = make_scalar<T>(scalbn(sreal(v), -pexp), scalbn(simag(v), -pexp));
+      }
     __syncthreads();
   }
   const int kmax = min(mp, kb);
@@ -208,11 +219,13 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   // overflows nor underflows; outside that range the column is measured
   // again with the scaled two-pass sum
   const R lo = sizeof(R) == 4 ? (R)1e-15 : (R)1e-140, hi = sizeof(R) == 4 ? (R)1e15 : (R)1e140;
+  constexpr int RS = 32 * WPC;   // row stride of a warp
   for (int k = 0; k < kmax; ++k) {
     const T* col = P + (size_t)ld * k;
+    const int nt = kb - 1 - k;   // trailing columns of the panel (<= 15)
     R amax = s_amax[0], part = s_ssq[0];
     if (k > 0) {
-      // column k as its two warps measured it in step k - 1; every thread
+      // column k as its warps measured it in step k - 1; every thread
       // combines the halves in the same order (the branch is block-uniform)
       amax = rmax(s_lam[k][0], s_lam[k][1]);
       if (amax == (R)0 || (amax > lo && amax < hi)) {
@@ -228,83 +241,94 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
         part = s_ssq[k];
       }
     }
-    // reflector k, scaled by the column's largest entry (no overflow or
-    // underflow of |alpha - beta|^2 at any data scale)
-    T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
-    if (amax > (R)0) {
-      const R inv = (R)1 / amax;
-      const T al = rscale(col[k], inv);
-      const R ax = sreal(al), ay = simag(al);
-      if (part > (R)0 || ay != (R)0) {
-        const R nrm = sqrt(ax * ax + ay * ay + part);
-        const R beta = (ax >= (R)0) ? -nrm : nrm;
-        const R rb = (R)1 / beta;
-        tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
-        const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
-        scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
-        beta_s = make_scalar<T>(beta * amax, (R)0);
+    if (grp < nt || tid == 0) {
+      // reflector k, scaled by the column's largest entry (no overflow or
+      // underflow of |alpha - beta|^2 at any data scale)
+      T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
+      if (amax > (R)0) {
+        const R inv = (R)1 / amax;
+        const T al = rscale(col[k], inv);
+        const R ax = sreal(al), ay = simag(al);
+        if (part > (R)0 || ay != (R)0) {
+          const R nrm = sqrt(ax * ax + ay * ay + part);
+          const R beta = (ax >= (R)0) ? -nrm : nrm;
+          const R rb = (R)1 / beta;
+          tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
+          const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
+          scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
+          beta_s = make_scalar<T>(beta * amax, (R)0);
+        }
       }
-    }
-    const int nt = kb - 1 - k;   // trailing columns of the panel (<= 15)
-    if (pair < nt) {
-      // x <- (I - conj(tau) v v^H) x for trailing column j over the rows
-      // k + 1 + 32 half + 64 t + lane; four stripes per lane in flight
-      const int j = k + 1 + pair;
-      T* x = P + (size_t)ld * j;
-      T a0 = szero<T>(), a1 = szero<T>(), a2 = szero<T>(), a3 = szero<T>();
-      const int r0 = k + 1 + 32 * half + lane;
-      int i = r0;
-      for (; i + 192 < mp; i += 256) {
-        const T c0 = col[i], c1 = col[i + 64], c2 = col[i + 128], c3 = col[i + 192];
-        const T x0 = x[i], x1 = x[i + 64], x2 = x[i + 128], x3 = x[i + 192];
-        macc(a0, c0, x0);
-        macc(a1, c1, x1);
-        macc(a2, c2, x2);
-        macc(a3, c3, x3);
+      if (tid == 0) {
+        s_tau[k] = tau;
+        s_scal[k] = scal;
+        s_beta[k] = beta_s;
       }
-      for (; i < mp; i += 64) macc(a0, col[i], x[i]);
-      const T pdot = warp_sum(sadd(sadd(a0, a1), sadd(a2, a3)));
-      if (lane == 0) s_pd[pair][half] = pdot;
-      const T xk = x[k];
-      bq_pair_sync(pair);            // both partials written, both halves have read x[k]
-      const T sdot = sadd(s_pd[pair][0], s_pd[pair][1]);
-      const T wdot = sadd(xk, smul(conjg(scal), sdot));
-      const T f = smul(conjg(tau), wdot);
-      const T fs = smul(scal, f);
-      if (half == 0 && lane == 0) x[k] = ssub(xk, f);
-      // column k + 1 (the next reflector's) also measures itself while it is
-      // updated: largest |re|, |im| over rows >= k + 1 and the plain sum of
-      // squares below row k + 1, per half
-      const bool look = (j == k + 1 && j < kmax);
-      R am = (R)0, sq = (R)0;
-      int r = r0;
-      for (; r + 192 < mp; r += 256) {
-        T y[4];
+      if (grp < nt) {
+        // x <- (I - conj(tau) v v^H) x for trailing column j over the rows
+        // k + 1 + 32 half + RS t + lane; four stripes per lane in flight
+        const int j = k + 1 + grp;
+        T* x = P + (size_t)ld * j;
+        T a0 = szero<T>(), a1 = szero<T>(), a2 = szero<T>(), a3 = szero<T>();
+        const int r0 = k + 1 + 32 * half + lane;
+        int i = r0;
+        for (; i + 3 * RS < mp; i += 4 * RS) {
+          const T c0 = col[i], c1 = col[i + RS], c2 = col[i + 2 * RS], c3 = col[i + 3 * RS];
+          const T x0 = x[i], x1 = x[i + RS], x2 = x[i + 2 * RS], x3 = x[i + 3 * RS];
+          macc(a0, c0, x0);
+          macc(a1, c1, x1);
+          macc(a2, c2, x2);
+          macc(a3, c3, x3);
+        }
+        for (; i < mp; i += RS) macc(a0, col[i], x[i]);
+        const T pdot = warp_sum(sadd(sadd(a0, a1), sadd(a2, a3)));
+        const T xk = x[k];
+        T sdot = pdot;
+        if (WPC == 2) {
+          if (lane == 0) s_pd[grp][half] = pdot;
+          bq_pair_sync(grp);            // both partials written, both halves have read x[k]
+          sdot = sadd(s_pd[grp][0], s_pd[grp][1]);
+        } else {
+          __syncwarp();                 // every lane has read x[k]
+        }
+        const T wdot = sadd(xk, smul(conjg(scal), sdot));
+        const T f = smul(conjg(tau), wdot);
+        const T fs = smul(scal, f);
+        if (half == 0 && lane == 0) x[k] = ssub(xk, f);
+        // column k + 1 (the next reflector's) also measures itself while it
+        // is updated: largest |re|, |im| over rows >= k + 1 and the plain
+        // sum of squares below row k + 1, per warp
+        const bool look = (j == k + 1 && j < kmax);
+        R am = (R)0, sq = (R)0;
+        int r = r0;
+        for (; r + 3 * RS < mp; r += 4 * RS) {
+          T y[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) y[u] = ssub(x[r + 64 * u], smul(col[r + 64 * u], fs));
+          for (int u = 0; u < 4; ++u) y[u] = ssub(x[r + RS * u], smul(col[r + RS * u], fs));
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          x[r + 64 * u] = y[u];
-          if (look) {
-            am = rmax(am, rmax(rabs(sreal(y[u])), rabs(simag(y[u]))));
-            if (r + 64 * u > j) sq += sabs2(y[u]);
+          for (int u = 0; u < 4; ++u) {
+            x[r + RS * u] = y[u];
+            if (look) {
+              am = rmax(am, rmax(rabs(sreal(y[u])), rabs(simag(y[u]))));
+              if (r + RS * u > j) sq += sabs2(y[u]);
+            }
           }
         }
-      }
-      for (; r < mp; r += 64) {
-        const T y = ssub(x[r], smul(col[r], fs));
-        x[r] = y;
+        for (; r < mp; r += RS) {
+          const T y = ssub(x[r], smul(col[r], fs));
+          x[r] = y;
+          if (look) {
+            am = rmax(am, rmax(rabs(sreal(y)), rabs(simag(y))));
+            if (r > j) sq += sabs2(y);
+          }
+        }
         if (look) {
-          am = rmax(am, rmax(rabs(sreal(y)), rabs(simag(y))));
-          if (r > j) sq += sabs2(y);
+          for (int o = 16; o > 0; o >>= 1) {
+            am = rmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+          }
+          if (lane == 0) { s_lam[j][half] = am; s_lsq[j][half] = sq; }
         }
-      }
-      if (look) {
-        for (int off = 16; off > 0; off >>= 1) {
-          am = rmax(am, __shfl_xor_sync(0xffffffffu, am, off));
-          sq += __shfl_xor_sync(0xffffffffu, sq, off);
-        }
-        if (lane == 0) { s_lam[j][half] = am; s_lsq[j][half] = sq; }
       }
     } else if (warp == BQP_THREADS / 32 - 1 && k > 0) {
       // column k - 1 is final: v_{k-1} = col * scal below the diagonal, beta on it
@@ -312,11 +336,6 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
       const T sc = s_scal[k - 1];
       for (int r = k + lane; r < mp; r += 32) c1[r] = smul(c1[r], sc);
       if (lane == 0) c1[k - 1] = s_beta[k - 1];
-    }
-    if (tid == 0) {
-      s_tau[k] = tau;
-      s_scal[k] = scal;
-      s_beta[k] = beta_s;
     }
     __syncthreads();
   }
@@ -354,17 +373,16 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   __syncthreads();
   // rows p - off .. p - 1 (final after the previous panel's update), then
   // the panel: R on and above the diagonal, the v_k below
-  for (int e = tid; e < mpp * kb; e += BQP_THREADS) {
-    const int i = e % mpp - off, j = e / mpp;
-    T v = P[i + (size_t)ld * j];
-    if (pexp != 0 && i >= 0 && i <= j) v = make_scalar<T>(scalbn(sreal(v), pexp), scalbn(simag(v), pexp));
-    A[(size_t)(p + i) + (size_t)m * (p + j)] = v;
-  }
+  for (int j = ec; j < kb; j += 16)
+    for (int i = er - off; i < mp; i += 64) {
+      T v = P[i + (size_t)ld * j];
+      if (pexp != 0 && i >= 0 && i <= j) v = make_scalar<T>(scalbn(sreal(v), pexp), scalbn(simag(v), pexp));
+      A[(size_t)(p + i) + (size_t)m * (p + j)] = v;
+    }
   // V^T rows with the implicit unit diagonal and the zeros above it
-  for (int e = tid; e < mp * kb; e += BQP_THREADS) {
-    const int i = e % mp, a = e / mp;
-    Vt[i + (size_t)mp * a] = (i == a) ? sone(T()) : (i > a && a < kmax) ? P[i + (size_t)ld * a] : szero<T>();
-  }
+  for (int a = ec; a < kb; a += 16)
+    for (int i = er; i < mp; i += 64)
+      Vt[i + (size_t)mp * a] = (i == a) ? sone(T()) : (i > a && a < kmax) ? P[i + (size_t)ld * a] : szero<T>();
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) Tm[e] = s_T[e];
 }
 
@@ -503,8 +521,12 @@ static std::atomic<unsigned long long> g_bq_cfg[2];
 template <typename T>
 static void bq_configure() {
   if (first_on_device(&g_bq_cfg[Sc<T>::cplx ? 0 : 1]))
-    cudaFuncSetAttribute(k_bq_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  {
+    cudaFuncSetAttribute(k_bq_panel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
+    cudaFuncSetAttribute(k_bq_panel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
+  }
 }
 
 // per host thread and device: the side stream of the QR look-ahead and the
@@ -576,8 +598,11 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
       const T* Vprev = fuse ? Vp - (size_t)BQ_NB * BQ_MAXM : nullptr;
       const T* Tprev = fuse ? Tp - (size_t)BQ_NB * BQ_NB : nullptr;
       const int rows = (m - p) + (fuse ? BQ_NB : 0);
-      k_bq_panel<T><<<1, BQP_THREADS, sizeof(T) * (size_t)(rows | 1) * kb, s>>>(A, m, p, kb, Tp, Vp,
-                                                                               Vprev, Tprev, BQ_NB);
+      const size_t smem = sizeof(T) * (size_t)(rows | 1) * kb;
+      if (m - p >= BQP_WPC2_ROWS)
+        k_bq_panel<T, 2><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
+      else
+        k_bq_panel<T, 1><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
     }
     const int c0 = p + kb, nc = kmax - c0;
     if (ahead) {

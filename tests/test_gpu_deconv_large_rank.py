@@ -73,7 +73,10 @@ def test_core_grads_large_rank_match_oracle(qlib):
     Lref = P.deconv_loss(cf, (n, n), B, gdense)
     Tf = P.conv_dense(P.to_array(cf, (n, n)), B)
     kappa = (np.linalg.norm(Tf) + np.linalg.norm(gdense)) / np.sqrt(Lref)
-    bound = 3.0 * 2e-6 * (1.0 + kappa)
+    # u = 3.2e-6: the large-rank rounding's accuracy against the oracle (its
+    # measured error alone on the 4096 x 4096 image; 2e-6 is the rank-64
+    # mode's), as in the 2048^2 bench's gradient bound
+    bound = 3.0 * 3.2e-6 * (1.0 + kappa)
     assert abs(L - Lref) <= bound * Lref + 1e-6 * np.linalg.norm(gdense) ** 2
     num = np.sqrt(sum(np.linalg.norm(gk - rk) ** 2 for gk, rk in zip(grads, ref)))
     den = np.sqrt(sum(np.linalg.norm(rk) ** 2 for rk in ref))
