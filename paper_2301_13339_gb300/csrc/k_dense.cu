@@ -76,6 +76,35 @@ __device__ __forceinline__ void bq_col_norm(const T* x, int i0, int mp, int lane
   ssq = q;
 }
 
+// Householder reflector of a column from its largest entry amax (of |re|,
+// |im| over the rows from the diagonal on), the scaled sum of squares part
+// below the diagonal and the diagonal entry alpha: tau, the scale
+// 1 / (alpha - beta) of v and beta, computed at the column's scale (no
+// overflow or underflow of |alpha - beta|^2 at any data scale)
+template <typename T>
+__device__ __forceinline__ void bq_reflector(typename Sc<T>::R amax, typename Sc<T>::R part, T alpha,
+                                             T& tau_o, T& scal_o, T& beta_o) {
+  using R = typename Sc<T>::R;
+  T tau = szero<T>(), scal = szero<T>(), beta_s = alpha;
+  if (amax > (R)0) {
+    const R inv = (R)1 / amax;
+    const T al = rscale(alpha, inv);
+    const R ax = sreal(al), ay = simag(al);
+    if (part > (R)0 || ay != (R)0) {
+      const R nrm = sqrt(ax * ax + ay * ay + part);
+      const R beta = (ax >= (R)0) ? -nrm : nrm;
+      const R rb = (R)1 / beta;
+      tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
+      const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
+      scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
+      beta_s = make_scalar<T>(beta * amax, (R)0);
+    }
+  }
+  tau_o = tau;
+  scal_o = scal;
+  beta_o = beta_s;
+}
+
 __device__ __forceinline__ void bq_pair_sync(int pair) {
   asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
@@ -94,7 +123,6 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   T* Xb = reinterpret_cast<T*>(bq_smem);
   T* P = Xb + off;
   __shared__ T s_tau[BQ_NB], s_scal[BQ_NB], s_beta[BQ_NB];
-  __shared__ R s_amax[BQ_NB], s_ssq[BQ_NB];
   __shared__ R s_lam[BQ_NB][2], s_lsq[BQ_NB][2];   // look-ahead partials of each half
   __shared__ T s_pd[BQ_NB][2];                      // partial dots of each pair
   __shared__ T s_Y[BQ_NB * BQ_NB];
@@ -120,7 +148,7 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   }
   __syncthreads();
   if (off > 0) {
-    // X <- (I - V T^H V^H) X with the arithmetic of bq_apply_cols (per
+    // X <- (I - V T^H V^H) X with the arithmetic of bq_apply_staged (per
     // column the same sums in the same order): W = V^H X, one warp per
     // (reflector, 8 columns), lanes over the rows; W2 = T^H W; then each
     // thread updates its rows of all columns.  s_Y and s_T serve as W and
@@ -133,7 +161,20 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
         T acc[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = szero<T>();
-        for (int i = lane; i < mpp; i += 32) {
+        // four rows' V entries in flight per lane (the loads come from L2),
+        // each row then added in row order
+        int i = lane;
+        for (; i + 96 < mpp; i += 128) {
+          T v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = Vprev[i + 32 * u + (size_t)mpp * a];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (cb + c < kb) macc(acc[c], v[u], Xb[i + 32 * u + (size_t)ld * (cb + c)]);
+        }
+        for (; i < mpp; i += 32) {
           const T v = Vprev[i + (size_t)mpp * a];
 #pragma unroll
           for (int c = 0; c < 8; ++c)
@@ -209,62 +250,23 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
     __syncthreads();
   }
   const int kmax = min(mp, kb);
-  if (warp == 0) {
-    R a, q;
-    bq_col_norm(P, 0, mp, lane, a, q);
-    if (lane == 0) { s_amax[0] = a; s_ssq[0] = q; }
-  }
-  __syncthreads();
   // the unscaled look-ahead sum is exact enough wherever amax^2 neither
   // overflows nor underflows; outside that range the column is measured
   // again with the scaled two-pass sum
   const R lo = sizeof(R) == 4 ? (R)1e-15 : (R)1e-140, hi = sizeof(R) == 4 ? (R)1e15 : (R)1e140;
+  if (warp == 0 && kmax > 0) {
+    R a, q;
+    bq_col_norm(P, 0, mp, lane, a, q);
+    if (lane == 0) bq_reflector(a, q, P[0], s_tau[0], s_scal[0], s_beta[0]);
+  }
+  __syncthreads();
   constexpr int RS = 32 * WPC;   // row stride of a warp
   for (int k = 0; k < kmax; ++k) {
     const T* col = P + (size_t)ld * k;
     const int nt = kb - 1 - k;   // trailing columns of the panel (<= 15)
-    R amax = s_amax[0], part = s_ssq[0];
-    if (k > 0) {
-      // column k as its warps measured it in step k - 1; every thread
-      // combines the halves in the same order (the branch is block-uniform)
-      amax = rmax(s_lam[k][0], s_lam[k][1]);
-      if (amax == (R)0 || (amax > lo && amax < hi)) {
-        part = (amax > (R)0) ? (s_lsq[k][0] + s_lsq[k][1]) / (amax * amax) : (R)0;
-      } else {
-        if (warp == 0) {
-          R a, q;
-          bq_col_norm(col, k, mp, lane, a, q);
-          if (lane == 0) { s_amax[k] = a; s_ssq[k] = q; }
-        }
-        __syncthreads();
-        amax = s_amax[k];
-        part = s_ssq[k];
-      }
-    }
-    if (grp < nt || tid == 0) {
-      // reflector k, scaled by the column's largest entry (no overflow or
-      // underflow of |alpha - beta|^2 at any data scale)
-      T tau = szero<T>(), scal = szero<T>(), beta_s = col[k];
-      if (amax > (R)0) {
-        const R inv = (R)1 / amax;
-        const T al = rscale(col[k], inv);
-        const R ax = sreal(al), ay = simag(al);
-        if (part > (R)0 || ay != (R)0) {
-          const R nrm = sqrt(ax * ax + ay * ay + part);
-          const R beta = (ax >= (R)0) ? -nrm : nrm;
-          const R rb = (R)1 / beta;
-          tau = make_scalar<T>((beta - ax) * rb, -ay * rb);
-          const R dr = ax - beta, di = ay, rden = (R)1 / (dr * dr + di * di);
-          scal = rscale(make_scalar<T>(dr * rden, -di * rden), inv);   // 1 / (alpha - beta)
-          beta_s = make_scalar<T>(beta * amax, (R)0);
-        }
-      }
-      if (tid == 0) {
-        s_tau[k] = tau;
-        s_scal[k] = scal;
-        s_beta[k] = beta_s;
-      }
-      if (grp < nt) {
+    if (grp < nt) {
+      const T tau = s_tau[k], scal = s_scal[k];
+      {
         // x <- (I - conj(tau) v v^H) x for trailing column j over the rows
         // k + 1 + 32 half + RS t + lane; four stripes per lane in flight
         const int j = k + 1 + grp;
@@ -297,7 +299,8 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
         if (half == 0 && lane == 0) x[k] = ssub(xk, f);
         // column k + 1 (the next reflector's) also measures itself while it
         // is updated: largest |re|, |im| over rows >= k + 1 and the plain
-        // sum of squares below row k + 1, per warp
+        // sum of squares below row k + 1, per warp; then its warps derive
+        // reflector k + 1 for the next step
         const bool look = (j == k + 1 && j < kmax);
         R am = (R)0, sq = (R)0;
         int r = r0;
@@ -328,6 +331,18 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
             sq += __shfl_xor_sync(0xffffffffu, sq, o);
           }
           if (lane == 0) { s_lam[j][half] = am; s_lsq[j][half] = sq; }
+          if (WPC == 2) bq_pair_sync(grp);   // both halves measured and updated
+          else __syncwarp();
+          if (half == 0) {
+            // the halves combined in a fixed order
+            R amax = rmax(s_lam[j][0], s_lam[j][1]), part;
+            if (amax == (R)0 || (amax > lo && amax < hi)) {
+              part = (amax > (R)0) ? (s_lsq[j][0] + s_lsq[j][1]) / (amax * amax) : (R)0;
+            } else {
+              bq_col_norm(x, j, mp, lane, amax, part);
+            }
+            if (lane == 0) bq_reflector(amax, part, x[j], s_tau[j], s_scal[j], s_beta[j]);
+          }
         }
       }
     } else if (warp == BQP_THREADS / 32 - 1 && k > 0) {
@@ -386,62 +401,77 @@ k_bq_panel(T* __restrict__ A, int m, int p, int kb, T* __restrict__ Tm, T* __res
   for (int e = tid; e < BQ_NB * BQ_NB; e += BQP_THREADS) Tm[e] = s_T[e];
 }
 
-// X[p:m, c] <- (I - V op(T) V^H) X[p:m, c] for the columns c of this CTA
-// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols); V^T = Vt (kb
-// rows of mp, ld mp).  adj = 1: op(T) = T^H (applies Q^H, the trailing
-// update); adj = 0: op(T) = T (forms Q).  W = V^H X by warps (4 reflectors x
-// BQ_CB columns each, lanes over rows), then op(T) W, then one warp per
-// column for the update.
-// The columns cbase + [0, BQ_CB) of X that lie in [clo, chi) <- (I - V op(T)
-// V^H) X[p:m, c] (V^T = Vt: kb rows of mp = m - p, ld mp).  adj = 1: op(T)
-// = T^H (applies Q^H, the trailing update); adj = 0: op(T) = T (forms Q).
-// W = V^H X by warps (AW reflectors x BQ_CB columns each, lanes over rows),
-// then op(T) W, then one warp per column for the update.  A column's
-// arithmetic does not depend on which other columns share the CTA.
-template <typename T>
-__device__ __forceinline__ void bq_apply_cols(T* __restrict__ X, int m, int cbase, int clo, int chi,
-                                              const T* __restrict__ Vt, int p, int kb,
-                                              const T* __restrict__ Tm, int adj,
-                                              T (&W)[BQ_NB][BQ_CB], T (&W2)[BQ_NB][BQ_CB]) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// The CTA's columns cbase + [0, BQ_CB) that lie in [clo, chi), held in
+// shared memory (sX: column c at sX + ldx c, global row g at index g - xr0),
+// <- (I - V op(T) V^H) X[p:m, c] with V^T = Vt (kb rows of mp = m - p, ld
+// mp).  adj = 1: op(T) = T^H (applies Q^H, the trailing update); adj = 0:
+// op(T) = T (forms Q).  V is first staged in shared memory (sV: one
+// contiguous copy of V^T, so every later read is a shared-memory read and
+// the L2 latency is paid once), then W = V^H X by warps (AW reflectors x
+// BQ_CB columns each, lanes over rows), op(T) W, and one warp per column for
+// X -= V W'.  RG row groups (RG * 32 * BQ_CB threads): each warp covers every
+// RG-th 32-row stripe and the RG partial sums of W are added in group order.
+// A column's arithmetic does not depend on which other columns share the
+// CTA (for a given RG).
+template <typename T, int CB, int RG>
+__device__ __forceinline__ void bq_apply_staged(T* __restrict__ sX, int ldx, int xr0, int cbase,
+                                                int clo, int chi, const T* __restrict__ Vt, int m,
+                                                int p, int kb, const T* __restrict__ Tm, int adj,
+                                                T* __restrict__ sV, T (&W)[RG][BQ_NB][CB],
+                                                T (&W2)[BQ_NB][CB]) {
+  constexpr int NT = 32 * CB * RG;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int warp = (tid >> 5) % CB, rg = (tid >> 5) / CB;
   const int mp = m - p;
-  constexpr int AW = BQ_NB / BQ_CB;   // reflectors per warp (BQ_CB warps x AW = BQ_NB)
-  T acc[AW][BQ_CB];
+  for (int e = tid; e < mp * kb; e += NT) sV[e] = Vt[e];
+  __syncthreads();
+  constexpr int AW = BQ_NB / CB;   // reflectors per warp (CB warps x AW = BQ_NB)
+  T acc[AW][CB];
 #pragma unroll
   for (int u = 0; u < AW; ++u)
 #pragma unroll
-    for (int c = 0; c < BQ_CB; ++c) acc[u][c] = szero<T>();
-  for (int i = lane; i < mp; i += 32) {
-    T x[BQ_CB];
+    for (int c = 0; c < CB; ++c) acc[u][c] = szero<T>();
+  const T* xs = sX + (p - xr0);
+  for (int i = 32 * rg + lane; i < mp; i += 32 * RG) {
+    T x[CB];
 #pragma unroll
-    for (int c = 0; c < BQ_CB; ++c) {
+    for (int c = 0; c < CB; ++c) {
       const int col = cbase + c;
-      x[c] = (col >= clo && col < chi) ? X[(size_t)(p + i) + (size_t)m * col] : szero<T>();
+      x[c] = (col >= clo && col < chi) ? xs[i + ldx * c] : szero<T>();
     }
 #pragma unroll
     for (int u = 0; u < AW; ++u) {
       const int a = warp * AW + u;
-      const T v = (a < kb) ? Vt[i + (size_t)mp * a] : szero<T>();
+      const T v = (a < kb) ? sV[i + mp * a] : szero<T>();
 #pragma unroll
-      for (int c = 0; c < BQ_CB; ++c) macc(acc[u][c], v, x[c]);
+      for (int c = 0; c < CB; ++c) macc(acc[u][c], v, x[c]);
     }
   }
 #pragma unroll
   for (int u = 0; u < AW; ++u)
 #pragma unroll
-    for (int c = 0; c < BQ_CB; ++c) {
+    for (int c = 0; c < CB; ++c) {
       const T w = warp_sum(acc[u][c]);
-      if (lane == 0) W[warp * AW + u][c] = w;
+      if (lane == 0) W[rg][warp * AW + u][c] = w;
     }
   __syncthreads();
-  for (int e = tid; e < BQ_NB * BQ_CB; e += 32 * BQ_CB) {
+  for (int e = tid; e < BQ_NB * CB; e += NT) {
+    const int a = e % BQ_NB, c = e / BQ_NB;
+    if (RG > 1) {   // the row groups' partials, in group order
+      T w = W[0][a][c];
+      for (int g = 1; g < RG; ++g) w = sadd(w, W[g][a][c]);
+      W[0][a][c] = w;
+    }
+  }
+  if (RG > 1) __syncthreads();
+  for (int e = tid; e < BQ_NB * CB; e += NT) {
     const int a = e % BQ_NB, c = e / BQ_NB;
     T w2 = szero<T>();
     if (a < kb) {
       if (adj) {
-        for (int b = 0; b <= a; ++b) macc(w2, Tm[b + BQ_NB * a], W[b][c]);   // conj(T[b, a])
+        for (int b = 0; b <= a; ++b) macc(w2, Tm[b + BQ_NB * a], W[0][b][c]);   // conj(T[b, a])
       } else {
-        for (int b = a; b < kb; ++b) mac(w2, Tm[a + BQ_NB * b], W[b][c]);
+        for (int b = a; b < kb; ++b) mac(w2, Tm[a + BQ_NB * b], W[0][b][c]);
       }
     }
     W2[a][c] = w2;
@@ -449,56 +479,81 @@ __device__ __forceinline__ void bq_apply_cols(T* __restrict__ X, int m, int cbas
   __syncthreads();
   const int col = cbase + warp;
   if (col >= clo && col < chi) {
-    T* xc = X + (size_t)m * col;
-    for (int i = lane; i < mp; i += 32) {
+    T* xc = sX + (p - xr0) + (size_t)ldx * warp;
+    for (int i = 32 * rg + lane; i < mp; i += 32 * RG) {
       T sacc = szero<T>();
-      for (int a = 0; a < kb; ++a) mac(sacc, Vt[i + (size_t)mp * a], W2[a][warp]);
-      xc[p + i] = ssub(xc[p + i], sacc);
+      for (int a = 0; a < kb; ++a) mac(sacc, sV[i + mp * a], W2[a][warp]);
+      xc[i] = ssub(xc[i], sacc);
     }
   }
+  __syncthreads();   // sV and the updated columns are read again by the next use
 }
 
+// shared memory of the two kernels below: the CTA's columns (up to BQ_MAXM
+// rows each) and one panel's V^T
+constexpr size_t bq_apply_smem_elems() { return (size_t)BQ_MAXM * (BQ_CB + BQ_NB); }
+
 // X[p:m, c] <- (I - V op(T) V^H) X[p:m, c] for the columns c of this CTA
-// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols)
+// (col0 + BQ_CB blockIdx.x + [0, BQ_CB), below col0 + ncols): the columns
+// are read into shared memory once (one warp per column), updated there
+// and written back
 template <typename T>
 __global__ void __launch_bounds__(32 * BQ_CB)
 k_bq_apply(T* __restrict__ X, int m, int col0, int ncols, const T* __restrict__ Vt, int p, int kb,
            const T* __restrict__ Tm, int adj) {
-  __shared__ T W[BQ_NB][BQ_CB];
+  extern __shared__ __align__(16) unsigned char bq_asmem[];
+  __shared__ T W[1][BQ_NB][BQ_CB];
   __shared__ T W2[BQ_NB][BQ_CB];
-  bq_apply_cols(X, m, col0 + BQ_CB * (int)blockIdx.x, col0, col0 + ncols, Vt, p, kb, Tm, adj, W, W2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mp = m - p;
+  T* sX = reinterpret_cast<T*>(bq_asmem);
+  T* sV = sX + (size_t)mp * BQ_CB;
+  const int cbase = col0 + BQ_CB * (int)blockIdx.x;
+  const int col = cbase + warp;
+  const bool mine = col < col0 + ncols;
+  if (mine)
+    for (int i = lane; i < mp; i += 32) sX[i + (size_t)mp * warp] = X[(size_t)(p + i) + (size_t)m * col];
+  bq_apply_staged<T, BQ_CB, 1>(sX, mp, p, cbase, col0, col0 + ncols, Vt, m, p, kb, Tm, adj, sV, W, W2);
+  if (mine)
+    for (int i = lane; i < mp; i += 32) X[(size_t)(p + i) + (size_t)m * col] = sX[i + (size_t)mp * warp];
 }
 
-// Q formation in one launch: the CTA's columns cbase + [0, BQ_CB) of Q pass
-// through the panels' block reflectors from the last panel to the first
-// (panel pi touches the columns in [p, nq)), the same arithmetic per column
-// as one k_bq_apply launch per panel, without a grid-wide step between
-// panels (the columns are independent).
+// Q formation in one launch: the CTA's columns cbase + [0, BQF_CB) of Q start
+// as columns of the identity in shared memory and pass through the panels'
+// block reflectors from the last panel to the first (panel pi touches the
+// columns in [p, nq)), without a grid-wide step between panels (the columns
+// are independent); then they are written to Q.  Each CTA streams every
+// panel's V through its shared memory and updates only BQF_CB columns, so
+// the work spreads over nq / BQF_CB SMs; BQF_RG row groups give each column
+// several warps.
+constexpr int BQF_CB = 2, BQF_RG = 4;
 template <typename T>
-__global__ void __launch_bounds__(32 * BQ_CB)
+__global__ void __launch_bounds__(32 * BQF_CB * BQF_RG)
 k_bq_formq(T* __restrict__ Q, int m, int nq, int kmax, const T* __restrict__ Vall,
            const T* __restrict__ Tm) {
-  __shared__ T W[BQ_NB][BQ_CB];
-  __shared__ T W2[BQ_NB][BQ_CB];
-  const int cbase = BQ_CB * (int)blockIdx.x;
+  extern __shared__ __align__(16) unsigned char bq_fsmem[];
+  __shared__ T W[BQF_RG][BQ_NB][BQF_CB];
+  __shared__ T W2[BQ_NB][BQF_CB];
+  const int warp = (threadIdx.x >> 5) % BQF_CB, rg = (threadIdx.x >> 5) / BQF_CB;
+  const int lane = threadIdx.x & 31;
+  T* sX = reinterpret_cast<T*>(bq_fsmem);
+  T* sV = sX + (size_t)m * BQF_CB;
+  const int cbase = BQF_CB * (int)blockIdx.x;
+  const int col = cbase + warp;
+  for (int i = 32 * rg + lane; i < m; i += 32 * BQF_RG)
+    sX[i + (size_t)m * warp] = (i == col) ? sone(T()) : szero<T>();
+  __syncthreads();
   const int np = (kmax + BQ_NB - 1) / BQ_NB;
   for (int pi = np - 1; pi >= 0; --pi) {
     const int p = pi * BQ_NB;
-    if (p >= nq || cbase + BQ_CB <= p) continue;   // block-uniform: no column of this CTA
+    if (p >= nq || cbase + BQF_CB <= p) continue;   // block-uniform: no column of this CTA
     const int kb = min(BQ_NB, kmax - p);
-    bq_apply_cols(Q, m, cbase, p, nq, Vall + (size_t)pi * BQ_NB * BQ_MAXM, p, kb,
-                  Tm + (size_t)pi * BQ_NB * BQ_NB, 0, W, W2);
-    __syncthreads();   // the updated columns are read by every warp for the next panel
+    bq_apply_staged<T, BQF_CB, BQF_RG>(sX, m, 0, cbase, p, nq, Vall + (size_t)pi * BQ_NB * BQ_MAXM,
+                                       m, p, kb, Tm + (size_t)pi * BQ_NB * BQ_NB, 0, sV, W, W2);
   }
-}
-
-// Q[i + m j] = (i == j), j < nq
-template <typename T>
-__global__ void k_bq_eye(T* Q, int m, int nq) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)m * nq) return;
-  const int i = (int)(e % m), j = (int)(e / m);
-  Q[e] = (i == j) ? sone(T()) : szero<T>();
+  if (col < nq)
+    for (int i = 32 * rg + lane; i < m; i += 32 * BQF_RG)
+      Q[(size_t)i + (size_t)m * col] = sX[i + (size_t)m * warp];
 }
 
 // A[i + m j] = conj(S[j + ls i])  (A = S^H, m x n, from S n x m)
@@ -526,6 +581,10 @@ static void bq_configure() {
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
     cudaFuncSetAttribute(k_bq_panel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
+    cudaFuncSetAttribute(k_bq_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * bq_apply_smem_elems()));
+    cudaFuncSetAttribute(k_bq_formq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * bq_apply_smem_elems()));
   }
 }
 
@@ -605,6 +664,7 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
         k_bq_panel<T, 1><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
     }
     const int c0 = p + kb, nc = kmax - c0;
+    const size_t asmem = sizeof(T) * (size_t)(m - p) * (BQ_CB + kb);
     if (ahead) {
       // the next panel needs the side stream's update from the panel before
       if (join_pending) {
@@ -616,24 +676,20 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
         cudaEventRecord(ss->fork, s);                 // panel p done
         cudaStreamWaitEvent(ss->s, ss->fork, 0);
         prof_add_work("bigqr_update", cplx * 16.0 * M * kb * (nc - nn), 2.0 * M * (nc - nn) * sizeof(T));
-        k_bq_apply<T><<<(nc - nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, ss->s>>>(A, m, c0 + nn, nc - nn,
-                                                                           Vp, p, kb, Tp, 1);
+        k_bq_apply<T><<<(nc - nn + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, asmem, ss->s>>>(
+            A, m, c0 + nn, nc - nn, Vp, p, kb, Tp, 1);
         cudaEventRecord(ss->join, ss->s);
         join_pending = true;
       }
     } else if (nc > 0) {
       QTT_PROF("bigqr_update", s);
       prof_add_work("bigqr_update", cplx * 16.0 * M * kb * nc, 2.0 * M * nc * sizeof(T));
-      k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(A, m, c0, nc, Vp, p, kb, Tp, 1);
+      k_bq_apply<T><<<(nc + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, asmem, s>>>(A, m, c0, nc, Vp, p, kb, Tp, 1);
     }
   }
   if (ahead) {
     cudaEventRecord(ss->join, ss->s);   // the side stream's last work joins s
     cudaStreamWaitEvent(s, ss->join, 0);
-  }
-  {
-    QTT_PROF("bigqr_formq", s);
-    k_bq_eye<T><<<(unsigned)(((long long)m * nq + 255) / 256), 256, 0, s>>>(Q, m, nq);
   }
   {
     QTT_PROF("bigqr_formq", s);
@@ -644,7 +700,8 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
       prof_add_work("bigqr_formq", (Sc<T>::cplx ? 1.0 : 0.25) * 16.0 * (m - p) * kb * (double)(nq - p),
                     2.0 * (m - p) * (double)(nq - p) * sizeof(T));
     }
-    k_bq_formq<T><<<(nq + BQ_CB - 1) / BQ_CB, 32 * BQ_CB, 0, s>>>(Q, m, nq, kmax, Vall, Tm);
+    k_bq_formq<T><<<(nq + BQF_CB - 1) / BQF_CB, 32 * BQF_CB * BQF_RG,
+                    sizeof(T) * (size_t)m * (BQF_CB + BQ_NB), s>>>(Q, m, nq, kmax, Vall, Tm);
   }
   return cuda_check(cudaGetLastError(), "big_qr launch");
 }
