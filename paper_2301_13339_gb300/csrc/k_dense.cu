@@ -766,7 +766,7 @@ __device__ __forceinline__ void cg_kadd(float2& s, float2& c, float2 v) {
 // (two buffers, one barrier per chunk).  With splits > 1 the tile's partial
 // sum goes to part + split * ldpart (ld M), summed by k_cgemm_reduce.
 template <typename TA>
-__global__ void __launch_bounds__(CG_THREADS, 2)
+__global__ void __launch_bounds__(CG_THREADS, 1)
 k_cgemm(CGemmArgs<TA> g, int nbatch, int kchunk, float2* __restrict__ part, long long ldpart) {
   __shared__ TA As[2][CG_BK][CG_BM + 1];
   __shared__ float2 Bs[2][CG_BK][CG_BN + 1];
