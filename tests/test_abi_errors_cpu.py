@@ -148,3 +148,19 @@ def test_from_cores_and_operator_arguments(lib, buf):
     _expect(lib, g(10, 0.0, 1, 1e-7, QTT_C64, None, ctypes.byref(out)), ["B > 0"])
     _expect(lib, g(10, 64.0, 1, 0.0, QTT_C64, None, ctypes.byref(out)), ["eps_op"])
     assert not out.value
+
+
+def test_big_qr_arguments(lib, buf):
+    """qtt_debug_big_qr checks its shape, its dtype and its arrays before
+    touching the device."""
+    f = lib.qtt_debug_big_qr
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    _expect(lib, f(None, 8, 4, 4, QTT_C64, p, None), ["qtt_debug_big_qr"])        # NULL A
+    _expect(lib, f(p, 8, 4, 4, QTT_C64, None, None), ["qtt_debug_big_qr"])        # NULL Q
+    _expect(lib, f(p, 1025, 4, 4, QTT_C64, p, None), ["1025"])                    # above 1024 rows
+    _expect(lib, f(p, 8, 4, 9, QTT_C64, p, None), ["nq 9"])                       # nq > m
+    _expect(lib, f(p, 8, 0, 4, QTT_C64, p, None), ["qtt_debug_big_qr"])           # no columns
+    _expect(lib, f(p, 8, 4, 4, QTT_F32, p, None), ["dtype 1"])                    # not built
