@@ -5,19 +5,22 @@
 //    Panels of BQ_NB columns are factored by one CTA in shared memory
 //    (LAPACK's H_k = I - tau_k v_k v_k^H, v_k = [1; A[k+1:, k]]), their
 //    compact-WY factor T (H_1 ... H_nb = I - V T V^H, upper triangular) is
-//    formed in the same CTA, and the trailing columns are updated with
-//    Q^H = I - V T^H V^H by many CTAs (8 columns each).  Q = H_1 ... H_k
-//    [I; 0] is then accumulated panel by panel from the last one.  Householder
-//    QR keeps Q orthonormal to working precision also when A is rank
-//    deficient, which the randomised range finder of the rounding needs.
+//    formed in the same CTA; the next panel's columns receive it inside the
+//    next panel's kernel and the other trailing columns from many CTAs on a
+//    side stream (Q^H = I - V T^H V^H, 8 columns per CTA, V staged in shared
+//    memory).  Q = H_1 ... H_k [I; 0] is then accumulated in one launch,
+//    each CTA carrying two columns through every panel from the last one.
+//    Householder QR keeps Q orthonormal to working precision also when A is
+//    rank deficient, which the randomised range finder of the rounding needs.
 //
 //  * cgemm      -- C = op(A) B for complex64 B and C and a complex64 or real
 //    A, any strides (unit stride along the rows of A or along k; along k for
 //    B; along the rows of C), batched over a two-level batch index.  64 x 64
 //    output tiles, 16-deep k chunks staged in shared memory, 4 x 4 outputs
-//    per thread; each chunk is summed with plain FMAs and added to the
-//    running sum with compensation (Kahan), so long contractions keep
-//    about one rounding error per chunk instead of one per term.
+//    per thread, one CTA per SM; each chunk is summed with plain FMAs and
+//    added to the running sum with compensation (Kahan), so long
+//    contractions keep about one rounding error per chunk instead of one
+//    per term.
 #include "qtt_internal.cuh"
 #include "house_qr.cuh"
 #include <algorithm>
