@@ -51,11 +51,11 @@ constexpr int BQ_MAXM = 1024;    // rows (panel in shared memory: 1024 x 16 x 8 
 // fly (v^H x = x_k + conj(scal) sum_{i>k} conj(col_i) x_i; with WPC = 2 the
 // two warps' partial sums are added in a fixed order after a 64-thread
 // barrier of the pair), so column k is scaled into v only in the next step,
-// by the last warp, which no trailing column needs.  Two warps per column
-// halve the per-warp chain on tall panels; on short ones the duplicated
-// per-warp work outweighs that, so the host picks WPC by the panel height.
+// by the last warp, which no trailing column needs.  The library launches
+// WPC = 1: two warps per column halve each warp's chain but duplicate its
+// fixed work, and measured slower on every panel height of the rounding
+// (up to 1024 rows).
 constexpr int BQP_THREADS = 1024;
-constexpr int BQP_WPC2_ROWS = 512;   // panels of at least this many rows: WPC = 2
 // the pairs of the trailing columns use warps 0 .. 2 (BQ_NB - 1) - 1 and
 // named barriers 1 .. BQ_NB - 1; the last warp scales the finished column
 static_assert(2 * (BQ_NB - 1) < BQP_THREADS / 32 - 1 && BQ_NB - 1 <= 15, "panel warp layout");
@@ -582,8 +582,6 @@ static void bq_configure() {
   {
     cudaFuncSetAttribute(k_bq_panel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
-    cudaFuncSetAttribute(k_bq_panel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (BQ_MAXM + 1) * BQ_NB));
     cudaFuncSetAttribute(k_bq_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * bq_apply_smem_elems()));
     cudaFuncSetAttribute(k_bq_formq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -661,10 +659,7 @@ qtt_status big_qr_q(T* A, int m, int n, int nq, T* Q, T* Tm, cudaStream_t s) {
       const T* Tprev = fuse ? Tp - (size_t)BQ_NB * BQ_NB : nullptr;
       const int rows = (m - p) + (fuse ? BQ_NB : 0);
       const size_t smem = sizeof(T) * (size_t)(rows | 1) * kb;
-      if (m - p >= BQP_WPC2_ROWS)
-        k_bq_panel<T, 2><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
-      else
-        k_bq_panel<T, 1><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
+      k_bq_panel<T, 1><<<1, BQP_THREADS, smem, s>>>(A, m, p, kb, Tp, Vp, Vprev, Tprev, BQ_NB);
     }
     const int c0 = p + kb, nc = kmax - c0;
     const size_t asmem = sizeof(T) * (size_t)(m - p) * (BQ_CB + kb);
