@@ -43,15 +43,15 @@ constexpr int BQ_MAXM = 1024;    // rows (panel in shared memory: 1024 x 16 x 8 
 // column-major) to Tm.
 //
 // WPC (1 or 2) warps per trailing column, each over every WPC-th 32-row
-// stripe, and one barrier per reflector: the warps that need reflector k
-// (tau, the scale 1/(alpha - beta) of v, beta) derive it themselves from
-// the column's largest entry and scaled sum of squares, which the warps
-// that updated column k in the previous step measured right after their
-// update (look-ahead); the trailing update takes v_i = col_i * scal on the
-// fly (v^H x = x_k + conj(scal) sum_{i>k} conj(col_i) x_i; with WPC = 2 the
-// two warps' partial sums are added in a fixed order after a 64-thread
-// barrier of the pair), so column k is scaled into v only in the next step,
-// by the last warp, which no trailing column needs.  The library launches
+// stripe, and one barrier per reflector: the warps that update column k + 1
+// in step k also measure its largest entry and scaled sum of squares and,
+// before the step's barrier, derive reflector k + 1 from them (tau, the
+// scale 1/(alpha - beta) of v, beta), which every warp reads in step k + 1
+// (look-ahead); the trailing update takes v_i = col_i * scal on the fly
+// (v^H x = x_k + conj(scal) sum_{i>k} conj(col_i) x_i; with WPC = 2 the two
+// warps' partial sums are added in a fixed order after a 64-thread barrier
+// of the pair), so column k is scaled into v only in the next step, by the
+// last warp, which no trailing column needs.  The library launches
 // WPC = 1: two warps per column halve each warp's chain but duplicate its
 // fixed work, and measured slower on every panel height of the rounding
 // (up to 1024 rows).
