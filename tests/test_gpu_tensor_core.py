@@ -79,8 +79,7 @@ def test_tc_cgemm_same_sign(qlib, K):
     FP32 accumulator rounds one-signed, so a long uncompensated run would
     drift by ~k u of |C|; each 8-k chunk starts from zero in tensor memory
     and the chunk sums are added in FP32 registers with compensation, so the
-    mean error stays a fraction of u |C| at any k (measured ~ -1e-7 relative
-    at k = 16)."""
+    mean error stays a fraction of u |C| at any k."""
     import torch
     rng = np.random.default_rng(17 + K)
     M, N = 64, 256
